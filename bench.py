@@ -1,0 +1,357 @@
+"""Benchmark of the occlusion-point reuse hot path on GB300.
+
+Workload (one step = one frame): 1920x1080 ambient occlusion, 1 cosine ray per pixel,
+radius 0.5, over the seeded ~1M-triangle terrain scene (512^2 heightfield + 300
+icospheres + 8000 boxes, seed 2), then biased occluder reuse with K = 8 (the receiver
+plus 7 shared random offsets in a 15-pixel disk).  Metric: neighbour-samples/s =
+pixels * K / frame time (trace + reuse); ms_per_step is the frame time.
+
+  python bench.py [--gpus N --steps K --warmup W]    this library (CUDA, sm_103a)
+  python bench.py --impl reference ...               the FP64 CPU oracle on host cores
+
+N > 1 runs one independent replica per GPU (the path needs no exchange between GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W, H, K, RADIUS, SEED_SCENE, SEED_OFF, DISK_R = 1920, 1080, 8, 0.5, 2, 3, 15.0
+METRIC = "reuse neighbour-samples/s (1080p AO frame: trace + biased K=8 reuse)"
+UNIT = "neighbour-samples/s"
+WORKLOAD = ("1920x1080 AO, 1 spp, R=0.5, ~1M-tri terrain (seed 2); biased occluder reuse, "
+            "K=8 (receiver + 7 shared offsets in a 15-px disk), FP32 records")
+FLOPS_PER_PAIR_AO = 21     # d (3), r^2 (5), n_x.d (5), n_z.d (5), product, r^4, divide
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def scene_inputs():
+    import synth
+    scene = synth.scene_terrain(grid=512, n_spheres=300, n_boxes=8000, seed=SEED_SCENE)
+    offs = synth.disk_offsets(K, DISK_R, seed=SEED_OFF)
+    return scene, synth.camera_c2(), offs
+
+
+# ----------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------
+# our implementation
+# ----------------------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured", d
+    return 6800.0, "fallback", {}
+
+
+def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
+    """The FP64 oracle, as it stands, on this host: trace + reuse of square pixel blocks
+    (plus the halo their neighbour sets reach) until ~budget_s of work is done."""
+    import oracle
+    osc = oracle.OracleScene(scene.tris)
+    pos, nrm, _ = oracle.gbuffer(osc, cam.as_array(), W, H, scene.eps)
+    rec = np.zeros((H, W, 8))
+    rec[..., 7] = -1.0
+    mg = np.full((H, W), np.inf)
+    out = np.zeros((H, W))
+    omg = np.zeros((H, W))
+    pat = (2, 0, 0, offs)
+    hx0, hx1 = max(0, -offs[:, 0].min()), max(0, offs[:, 0].max())
+    hy0, hy1 = max(0, -offs[:, 1].min()), max(0, offs[:, 1].max())
+    rng = np.random.default_rng(11)
+    B = 48
+    receivers, t_total, blocks = 0, 0.0, 0
+    while t_total < budget_s and blocks < 64:
+        x0 = int(rng.integers(hx0, W - B - hx1))
+        y0 = int(rng.integers(hy0, H - B - hy1))
+        t0 = time.perf_counter()
+        oracle.trace(osc, 0, pos, nrm, radius=RADIUS, seed=1, sample=0,
+                     region=(x0 - hx0, y0 - hy0, B + hx0 + hx1, B + hy0 + hy1), out=(rec, mg))
+        oracle.reuse(None, 0, pos, nrm, rec, pat, oracle.EST_BIASED, radius=RADIUS,
+                     region=(x0, y0, B, B), out=(out, omg))
+        t_total += time.perf_counter() - t0
+        receivers += B * B
+        blocks += 1
+    return {"value": receivers * K / t_total, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": (f"{blocks} random {B}x{B} receiver blocks of the 1080p frame: trace of "
+                       f"each block plus its {hx0}/{hx1}/{hy0}/{hy1}-px halo, then biased "
+                       f"K=8 reuse of the block ({t_total:.1f} s)")}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2607_23122_gb300 import occ
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = occ.Context(local)
+    scene, cam, offs = scene_inputs()
+    bvh = occ.BVH(ctx, scene.tris)
+    gb = occ.occ_gbuffer_pinhole(ctx, bvh, cam.as_array(), scene.eps, W, H)
+    ctx.sync()
+    pat = occ.Pattern.offsets_of(offs)
+    rec = occ.Occluders.empty(H, W, dev)
+    out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        occ.occ_trace_ao(ctx, gb, bvh, RADIUS, 1, 0, out=rec, stream=stream)
+        occ.occ_reuse_ao(ctx, gb, rec, pat, K, occ.OCC_EST_BIASED, out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    ctx.sync()
+    P = W * H
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                        # L2 flush outside the step's events
+        ev[i][0].record(stream)
+        occ.occ_trace_ao(ctx, gb, bvh, RADIUS, 1, i, out=rec, stream=stream)
+        ev[i][1].record(stream)
+        occ.occ_reuse_ao(ctx, gb, rec, pat, K, occ.OCC_EST_BIASED, out=out, stream=stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    ctx.sync()
+    t_trace = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]) * 1e-3
+    t_reuse = np.array([ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]) * 1e-3
+    t_step = float((t_trace + t_reuse).sum())
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = world * P * K * args.steps / t_step
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the region
+    pos_h = gb.pos4.cpu().pin_memory()
+    nrm_h = gb.nrm4.cpu().pin_memory()
+    out_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    for i in range(2):
+        occ.occ_frame_host(ctx, bvh, occ.OCC_EFFECT_AO, pos_h, nrm_h, RADIUS, None, 1, i, pat, K,
+                           occ.OCC_EST_BIASED, out_h, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        occ.occ_frame_host(ctx, bvh, occ.OCC_EFFECT_AO, pos_h, nrm_h, RADIUS, None, 1, i, pat, K,
+                           occ.OCC_EST_BIASED, out_h, stream=stream)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+
+    if rank == 0:
+        hbm, peak_kind, peaks = measured_peaks()
+        st = bvh.stats
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        tr, ru = float(t_trace.mean()), float(t_reuse.mean())
+        # trace: compulsory bytes = G-buffer read + record write + the BVH read once
+        trace_bytes = P * (32 + 32) + st["bytes"]
+        # reuse (offset window, K^2 pair densities): FP32 ALU bound
+        pairs = P * K * K
+        alu_peak = sms * 128 * 2 * (clk["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        trace_roof = {"kernel": "k_trace<AO>", "bound": "hbm",
+                      "achieved": trace_bytes / tr / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": trace_bytes / tr / 1e9 / hbm, "traffic": None,
+                      "peak_source": peak_kind,
+                      "algorithmic_bytes": trace_bytes}
+        reuse_roof = {"kernel": "k_reuse_generic<AO,biased,9>", "bound": "alu",
+                      "achieved": pairs * FLOPS_PER_PAIR_AO / ru / 1e12,
+                      "peak": alu_peak / 1e12, "unit": "TFLOP/s",
+                      "frac": pairs * FLOPS_PER_PAIR_AO / ru / alu_peak, "traffic": None,
+                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x max SM clock"}
+        dominant = trace_roof if tr >= ru else reuse_roof
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_step / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "W": W, "H": H, "K": K, "radius": RADIUS,
+                       "tris": scene.num_tris, "pattern": "offsets", "estimator": "biased",
+                       "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MB write) before every step",
+                       "parallelism": f"replicas x{world}"},
+            "reuse_pass": {"neighbour_samples_per_s": P * K / ru, "ms": ru * 1e3},
+            "trace_pass": {"rays_per_s": P / tr, "ms": tr * 1e3},
+            "roofline": dominant, "roofline_other": reuse_roof if dominant is trace_roof else trace_roof,
+            "e2e": {"value": world * P * K * e2e_steps / t_e2e, "unit": UNIT,
+                    "h2d_bytes_per_step": 2 * 16 * P, "d2h_bytes_per_step": 4 * P,
+                    "ms_per_step": t_e2e / e2e_steps * 1e3},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk, "wall_s": wall,
+            "bvh": {"nodes": st["num_nodes"], "depth": st["depth"], "bytes": st["bytes"],
+                    "build_s": st["build_seconds"]},
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(scene, cam, offs)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle
+# ----------------------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    scene, cam, offs = scene_inputs()
+    osc = oracle.OracleScene(scene.tris)
+    pos, nrm, _ = oracle.gbuffer(osc, cam.as_array(), W, H, scene.eps)
+    rec = np.zeros((H, W, 8))
+    rec[..., 7] = -1.0
+    mg = np.full((H, W), np.inf)
+    out = np.zeros((H, W))
+    omg = np.zeros((H, W))
+    pat = (2, 0, 0, offs)
+    hx0, hx1 = max(0, -offs[:, 0].min()), max(0, offs[:, 0].max())
+    hy0, hy1 = max(0, -offs[:, 1].min()), max(0, offs[:, 1].max())
+    B = 32
+    rng = np.random.default_rng(5)
+
+    def step(i):
+        x0 = int(rng.integers(hx0, W - B - hx1))
+        y0 = int(rng.integers(hy0, H - B - hy1))
+        oracle.trace(osc, 0, pos, nrm, radius=RADIUS, seed=1, sample=i,
+                     region=(x0 - hx0, y0 - hy0, B + hx0 + hx1, B + hy0 + hy1), out=(rec, mg))
+        oracle.reuse(None, 0, pos, nrm, rec, pat, oracle.EST_BIASED, radius=RADIUS,
+                     region=(x0, y0, B, B), out=(out, omg))
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    t = time.perf_counter() - t0
+    value = B * B * K * args.steps / t
+    sample = (f"each step: one random {B}x{B} receiver block of the 1080p frame, traced with "
+              f"its {hx0}/{hx1}/{hy0}/{hy1}-px halo, then biased K=8 reuse")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "W": W, "H": H, "K": K, "radius": RADIUS,
+                   "tris": scene.num_tris, "pattern": "offsets", "estimator": "biased"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

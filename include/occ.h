@@ -1,0 +1,214 @@
+/*
+ * occ.h -- C ABI of the GB300 occlusion-point reuse library (liboccreuse.so).
+ *
+ * The library computes the data-parallel hot path of "Occlusion-Point Reuse
+ * for Ray-Traced Ambient Occlusion and Shadow" on one GPU:
+ *
+ *   1. trace  (Alg. 1 and Alg. 2, step 1): one cosine-weighted AO ray (Eq. 2)
+ *      or one uniform area-light shadow ray (Eq. 5) per receiver, traced to
+ *      its closest hit; the hit point and its normal, turned toward the
+ *      receiver, form the receiver's occluder record;
+ *   2. reuse  (Alg. 1 and Alg. 2, steps 2-3): every receiver combines the
+ *      occluder records of its neighbour set N_i (Eq. 8) with balance-
+ *      heuristic MIS weights (Eqs. 10-12), giving the unbiased estimators of
+ *      Eq. 17 (AO) and Eq. 23 (shadow) with first-hit validation (Eq. 7), or
+ *      the biased estimators of Eq. 18 and Eq. 24 without it.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named *_host are host memory; every other buffer pointer is
+ *    device memory on the context's device.  The caller owns all G-buffer,
+ *    occluder and output buffers; the library owns BVHs and its workspace.
+ *  - Device buffers holding float4 data must be 16-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Compute calls are asynchronous on that stream.
+ *  - Argument errors are detected before anything is launched and return
+ *    OCC_ERR_INVALID_ARG (or OCC_ERR_UNSUPPORTED); the message is available
+ *    from occ_last_error().  A launch failure returns OCC_ERR_CUDA.  Faults a
+ *    kernel detects itself (a traversal stack overflow, a bounded wait that
+ *    ran out) are recorded in a device status word and returned as
+ *    OCC_ERR_DEVICE_CHECK by the next occ_sync().  No entry point aborts,
+ *    traps or throws across the ABI.
+ *  - A context may be used by one host thread at a time.
+ *
+ * Images are row-major, pixel (x, y) at linear index y * W + x.
+ */
+#ifndef OCC_H
+#define OCC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OCC_OK = 0,
+    OCC_ERR_INVALID_ARG = 1,
+    OCC_ERR_CUDA = 2,
+    OCC_ERR_OOM = 3,
+    OCC_ERR_TIMEOUT = 4,
+    OCC_ERR_UNSUPPORTED = 5,
+    OCC_ERR_DEVICE_CHECK = 6
+} occ_status;
+
+enum { OCC_EFFECT_AO = 0, OCC_EFFECT_SHADOW = 1 };
+
+/* Estimators (Sec. 4.3-4.4): NOREUSE is Eq. 3 / Eq. 6 with one sample; BIASED
+ * is Eq. 18 / Eq. 24 (shadow adds the all-blocked guard); UNBIASED is Eq. 17 /
+ * Eq. 23 with first-hit validation rays; BOXMEAN averages the binary
+ * visibility of N_i (final-value filtering / light-sample averaging). */
+enum { OCC_EST_NOREUSE = 0, OCC_EST_BIASED = 1, OCC_EST_UNBIASED = 2, OCC_EST_BOXMEAN = 3 };
+
+/* Neighbour patterns N_i (Eq. 8, Sec. 5 "Reuse Implementation", App. I):
+ *  GROUP:   the screen is partitioned into gw x gh blocks; N_i is i's block.
+ *  BOX:     the gw x gh window centred on i (dx in [-(gw-1)/2, gw/2]).
+ *  OFFSETS: i plus i + (dx, dy) for each of n_offsets shared offsets.
+ * Members outside the image or with an invalid G-buffer entry are dropped. */
+enum { OCC_PAT_GROUP = 0, OCC_PAT_BOX = 1, OCC_PAT_OFFSETS = 2 };
+
+enum { OCC_REC_FP32 = 0 };
+
+typedef struct occ_ctx occ_ctx;   /* opaque: device, status word, workspace */
+typedef struct occ_bvh occ_bvh;   /* opaque: device-resident wide BVH */
+
+/* G-buffer of receivers.  pos4[p] = (x.xyz, valid): x is the receiver point
+ * (the visible surface point already offset along its normal), valid is 1
+ * for a receiver and 0 for background.  nrm4[p] = (n.xyz, unused): the unit
+ * geometric normal facing the viewer.  Both W*H float4, row-major. */
+typedef struct {
+    int32_t W, H;
+    const float* pos4;
+    const float* nrm4;
+} occ_gbuffer;
+
+/* Rectangle light c + a eu + b ev, a, b in [-1/2, 1/2], eu orthogonal to ev.
+ * It emits along n_L = normalize(eu x ev); every receiver and occluder must lie
+ * on that side of its plane (Eqs. 4-5, 19-21). */
+typedef struct { float c[3], eu[3], ev[3]; } occ_rect_light;
+
+/* Occluder records (Alg. 1/2 step 1: "store hit position and oriented hit
+ * normal").  `data` is caller-owned device memory of 32 * W * H bytes holding
+ * two float4 planes: plane 0 [p] = (z.xyz, triangle id as int bits, -1 = no
+ * occluder), plane 1 [W*H + p] = (n_z.xyz facing the source receiver, t).
+ * The trace calls fill the remaining fields; the reuse calls read them. */
+typedef struct {
+    int32_t W, H;
+    int32_t format;            /* OCC_REC_FP32 */
+    void* data;
+    int32_t effect;            /* written by trace */
+    float radius;              /* AO radius R (AO) */
+    occ_rect_light light;      /* light (shadow) */
+    uint64_t seed;
+    uint32_t sample;
+} occ_occluders;
+
+typedef struct {
+    int32_t kind;              /* OCC_PAT_* */
+    int32_t gw, gh;            /* GROUP / BOX extent */
+    int32_t n_offsets;         /* OFFSETS: number of (dx, dy) pairs, K - 1 */
+    const int32_t* offsets_host;   /* OFFSETS: 2 * n_offsets ints, copied at call time */
+} occ_pattern;
+
+typedef struct {
+    int64_t num_tris, num_nodes, num_leaves;
+    int32_t depth, max_leaf_tris;
+    int64_t bytes;             /* device bytes of nodes + triangles */
+    double build_seconds;
+} occ_bvh_stats;
+
+/* ---- context ------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device` (made current on the calling
+ * thread).  OCC_ERR_UNSUPPORTED if the device is not sm_103. */
+occ_status occ_create(int device, occ_ctx** out);
+occ_status occ_destroy(occ_ctx* ctx);
+/* Message of the last non-OK status of this context ("" if none). */
+const char* occ_last_error(const occ_ctx* ctx);
+/* Waits for `stream`, then reports launch errors and device-side check flags
+ * (and clears the flags). */
+occ_status occ_sync(occ_ctx* ctx, void* stream);
+const char* occ_version(void);
+
+/* ---- scene ---------------------------------------------------------------- */
+
+/* Builds a 4-wide BVH (binned SAH, collapsed from a binary tree) over
+ * tris_host: T triangles of 3 float xyz vertices (row-major [T][3][3]); the
+ * array is copied.  Triangle ids are the input order.  Synchronous. */
+occ_status occ_bvh_build(occ_ctx* ctx, const float* tris_host, int64_t T, occ_bvh** out);
+occ_status occ_bvh_free(occ_ctx* ctx, occ_bvh* bvh);
+occ_status occ_bvh_info(const occ_bvh* bvh, occ_bvh_stats* out);
+
+/* Input stage (not part of the paper's method, which takes a raster
+ * G-buffer): pinhole primary rays.  cam_host = eye[3], target[3], up[3],
+ * vfov_deg.  Writes pos4/nrm4 (W*H float4 each); pos4 is the hit point moved
+ * `eps` along the geometric normal turned toward the camera. */
+occ_status occ_gbuffer_pinhole(occ_ctx* ctx, const occ_bvh* bvh, const float* cam_host,
+                               float eps, int32_t W, int32_t H, float* pos4, float* nrm4,
+                               void* stream);
+
+/* ---- hot path ------------------------------------------------------------- */
+
+/* Alg. 1 step 1 (Eq. 2): per receiver, the cosine-weighted direction from
+ * Philox4x32-10(counter = (pixel, sample, 0, 0), key = seed) and its closest
+ * hit on (0, radius].  out->W/H/data must be set; the call fills the rest. */
+occ_status occ_trace_ao(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh, float radius,
+                        uint64_t seed, uint32_t sample, occ_occluders* out, void* stream);
+
+/* Alg. 2 step 1 (Eq. 5): per receiver, y uniform on the light (counter =
+ * (pixel, sample, 1, 0)) and the closest hit on the segment toward y. */
+occ_status occ_trace_shadow(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh,
+                            const occ_rect_light* light, uint64_t seed, uint32_t sample,
+                            occ_occluders* out, void* stream);
+
+/* Alg. 1 steps 2-3: AO estimate per receiver into out (device float[H][W]).
+ * K must equal the pattern's size (gw*gh, or n_offsets + 1), 1 <= K <= 64.
+ * bvh_or_null is required for OCC_EST_UNBIASED and must be NULL otherwise.
+ * Invalid receivers get 1.  Estimates are not clamped. */
+occ_status occ_reuse_ao(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occluders* occ,
+                        const occ_pattern* pattern, int32_t K, int32_t estimator,
+                        const occ_bvh* bvh_or_null, float* out, void* stream);
+
+/* Alg. 2 steps 2-3: shadow visibility per receiver (Eq. 23 / Eq. 24 with the
+ * all-blocked guard of Sec. 4.4).  Same arguments as occ_reuse_ao; the light
+ * comes from the occluder records. */
+occ_status occ_reuse_shadow(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occluders* occ,
+                            const occ_pattern* pattern, int32_t K, int32_t estimator,
+                            const occ_bvh* bvh_or_null, float* out, void* stream);
+
+/* One whole frame from host memory: copies pos4_host/nrm4_host (pinned host
+ * memory recommended) to library-owned device buffers, traces (effect AO with
+ * `radius`, or SHADOW with `light`), reuses, and copies the estimate to
+ * out_host (float[H][W]), all on `stream`; returns after the stream finished. */
+occ_status occ_frame_host(occ_ctx* ctx, const occ_bvh* bvh, int32_t effect,
+                          const float* pos4_host, const float* nrm4_host, int32_t W, int32_t H,
+                          float radius, const occ_rect_light* light, uint64_t seed,
+                          uint32_t sample, const occ_pattern* pattern, int32_t K,
+                          int32_t estimator, float* out_host, void* stream);
+
+/* ---- test and debugging aids ---------------------------------------------- */
+
+/* Philox4x32-10 of n (counter[4], key[2]) items: in_dev holds 6 uint32 per
+ * item, out_dev receives 4 uint32 per item. */
+occ_status occ_debug_philox(occ_ctx* ctx, const uint32_t* in_dev, int64_t n, uint32_t* out_dev,
+                            void* stream);
+
+/* The step-1 ray of every receiver: out_dev[p] = (direction.xyz, tmax). */
+occ_status occ_debug_rays(occ_ctx* ctx, const occ_gbuffer* gb, int32_t effect, float radius,
+                          const occ_rect_light* light, uint64_t seed, uint32_t sample,
+                          float* out_dev, void* stream);
+
+/* Balance-heuristic weights seen by n receivers pix_host[i] (linear index):
+ * w_host[i*64*64 + a*64 + b] = p(z_a | x_b) / sum_e p(z_a | x_e) over the
+ * receiver's members in order, members_host[i*64 + a] = member pixel (or -1).
+ * Synchronous. */
+occ_status occ_debug_mis(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occluders* occ,
+                         const occ_pattern* pattern, int32_t K, int32_t estimator,
+                         const occ_bvh* bvh_or_null, const int32_t* pix_host, int32_t n,
+                         int32_t* members_host, float* w_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCC_H */

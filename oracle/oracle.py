@@ -169,17 +169,21 @@ def ray(effect: int, pos4, nrm4, pix: int, radius: float, light, seed: int, samp
 
 
 def trace(scene: OracleScene, effect: int, pos4: np.ndarray, nrm4: np.ndarray, radius: float = 0.0,
-          light=None, seed: int = 0, sample: int = 0, region=None):
+          light=None, seed: int = 0, sample: int = 0, region=None, out=None):
     """Step 1 of Alg. 1/2 for every pixel of ``region`` (x0, y0, w, h; default: all).
 
     Returns records float64 [H, W, 8] (z.xyz, n_z.xyz, t, tri; tri = -1 for none) and
     per-pixel margins [H, W]; pixels outside the region hold tri = -1 and margin inf.
+    ``out`` = (rec, margin) reuses caller buffers (pixels outside the region untouched).
     """
     H, W = pos4.shape[:2]
     x0, y0, w, h = region if region is not None else (0, 0, W, H)
-    rec = np.zeros((H, W, 8), dtype=np.float64)
-    rec[..., 7] = -1.0
-    mg = np.full((H, W), np.inf)
+    if out is not None:
+        rec, mg = out
+    else:
+        rec = np.zeros((H, W, 8), dtype=np.float64)
+        rec[..., 7] = -1.0
+        mg = np.full((H, W), np.inf)
     lib().orc_trace(scene.handle, effect, W, H, np.ascontiguousarray(pos4, dtype=np.float32),
                     np.ascontiguousarray(nrm4, dtype=np.float32), radius, _light(light), seed,
                     sample, x0, y0, w, h, rec, mg)
@@ -193,18 +197,22 @@ def _pattern(pattern):
 
 
 def reuse(scene, effect: int, pos4, nrm4, rec, pattern, estimator: int, radius: float = 0.0,
-          light=None, region=None):
+          light=None, region=None, out=None):
     """Estimator of Eqs. 17/18/23/24 (or a baseline) for every pixel of ``region``.
 
     ``pattern`` = (kind, gw, gh, offsets): kind 0 group blocks, 1 centred box,
     2 receiver plus shared offsets [n, 2].  ``scene`` is needed only for the
-    unbiased estimator.  Returns (out float64 [H, W], margin [H, W]).
+    unbiased estimator.  Returns (out float64 [H, W], margin [H, W]); ``out`` = (values,
+    margins) reuses caller buffers.
     """
     H, W = pos4.shape[:2]
     x0, y0, w, h = region if region is not None else (0, 0, W, H)
     kind, gw, gh, off, n_off = _pattern(pattern)
-    out = np.full((H, W), np.nan)
-    mg = np.full((H, W), np.inf)
+    if out is not None:
+        out, mg = out
+    else:
+        out = np.full((H, W), np.nan)
+        mg = np.full((H, W), np.inf)
     lib().orc_reuse(scene.handle if scene is not None else None, effect, W, H,
                     np.ascontiguousarray(pos4, dtype=np.float32),
                     np.ascontiguousarray(nrm4, dtype=np.float32),

@@ -1,0 +1,112 @@
+"""ctypes declarations of include/occ.h and the loader of liboccreuse.so.
+
+The library must exist (``build()`` makes it); there is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from .build import LIB as _LIB, build as _do_build, up_to_date as _up_to_date
+
+c_int32, c_int64, c_uint32, c_uint64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
+c_float, c_double, c_void_p, c_char_p = C.c_float, C.c_double, C.c_void_p, C.c_char_p
+
+OCC_OK = 0
+STATUS_NAMES = {0: "OCC_OK", 1: "OCC_ERR_INVALID_ARG", 2: "OCC_ERR_CUDA", 3: "OCC_ERR_OOM",
+                4: "OCC_ERR_TIMEOUT", 5: "OCC_ERR_UNSUPPORTED", 6: "OCC_ERR_DEVICE_CHECK"}
+
+OCC_EFFECT_AO, OCC_EFFECT_SHADOW = 0, 1
+OCC_EST_NOREUSE, OCC_EST_BIASED, OCC_EST_UNBIASED, OCC_EST_BOXMEAN = 0, 1, 2, 3
+OCC_PAT_GROUP, OCC_PAT_BOX, OCC_PAT_OFFSETS = 0, 1, 2
+OCC_REC_FP32 = 0
+MAX_MEMBERS = 64
+
+
+class occ_gbuffer(C.Structure):
+    _fields_ = [("W", c_int32), ("H", c_int32), ("pos4", c_void_p), ("nrm4", c_void_p)]
+
+
+class occ_rect_light(C.Structure):
+    _fields_ = [("c", c_float * 3), ("eu", c_float * 3), ("ev", c_float * 3)]
+
+
+class occ_occluders(C.Structure):
+    _fields_ = [("W", c_int32), ("H", c_int32), ("format", c_int32), ("data", c_void_p),
+                ("effect", c_int32), ("radius", c_float), ("light", occ_rect_light),
+                ("seed", c_uint64), ("sample", c_uint32)]
+
+
+class occ_pattern(C.Structure):
+    _fields_ = [("kind", c_int32), ("gw", c_int32), ("gh", c_int32), ("n_offsets", c_int32),
+                ("offsets_host", C.POINTER(c_int32))]
+
+
+class occ_bvh_stats(C.Structure):
+    _fields_ = [("num_tris", c_int64), ("num_nodes", c_int64), ("num_leaves", c_int64),
+                ("depth", c_int32), ("max_leaf_tris", c_int32), ("bytes", c_int64),
+                ("build_seconds", c_double)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/occ.h
+SIGNATURES = {
+    "occ_create": (c_int32, [C.c_int, C.POINTER(c_void_p)]),
+    "occ_destroy": (c_int32, [c_void_p]),
+    "occ_last_error": (c_char_p, [c_void_p]),
+    "occ_sync": (c_int32, [c_void_p, c_void_p]),
+    "occ_version": (c_char_p, []),
+    "occ_bvh_build": (c_int32, [c_void_p, c_void_p, c_int64, C.POINTER(c_void_p)]),
+    "occ_bvh_free": (c_int32, [c_void_p, c_void_p]),
+    "occ_bvh_info": (c_int32, [c_void_p, C.POINTER(occ_bvh_stats)]),
+    "occ_gbuffer_pinhole": (c_int32, [c_void_p, c_void_p, c_void_p, c_float, c_int32, c_int32,
+                                      c_void_p, c_void_p, c_void_p]),
+    "occ_trace_ao": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p, c_float, c_uint64,
+                               c_uint32, C.POINTER(occ_occluders), c_void_p]),
+    "occ_trace_shadow": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p,
+                                   C.POINTER(occ_rect_light), c_uint64, c_uint32,
+                                   C.POINTER(occ_occluders), c_void_p]),
+    "occ_reuse_ao": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), C.POINTER(occ_occluders),
+                               C.POINTER(occ_pattern), c_int32, c_int32, c_void_p, c_void_p,
+                               c_void_p]),
+    "occ_reuse_shadow": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), C.POINTER(occ_occluders),
+                                   C.POINTER(occ_pattern), c_int32, c_int32, c_void_p, c_void_p,
+                                   c_void_p]),
+    "occ_frame_host": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
+                                 c_int32, c_float, C.POINTER(occ_rect_light), c_uint64, c_uint32,
+                                 C.POINTER(occ_pattern), c_int32, c_int32, c_void_p, c_void_p]),
+    "occ_debug_philox": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+    "occ_debug_rays": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_int32, c_float,
+                                 C.POINTER(occ_rect_light), c_uint64, c_uint32, c_void_p,
+                                 c_void_p]),
+    "occ_debug_mis": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), C.POINTER(occ_occluders),
+                                C.POINTER(occ_pattern), c_int32, c_int32, c_void_p, c_void_p,
+                                c_int32, c_void_p, c_void_p]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Loads liboccreuse.so (building it first if allowed); raises if it is unavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _LIB
+        if not os.path.exists(path) or not _up_to_date():
+            if not build_if_missing:
+                raise RuntimeError(f"liboccreuse.so is not built ({path}); run build()")
+            _do_build()
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib

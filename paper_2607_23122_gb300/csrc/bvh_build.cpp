@@ -1,0 +1,325 @@
+// bvh_build.cpp -- host construction of the 4-wide BVH used by the traversal kernels.
+//
+// A binary BVH is built top-down with binned SAH (16 bins per axis over the
+// centroid bounds; the top levels run in parallel threads), then collapsed into
+// 4-wide nodes by repeatedly opening the child with the largest surface area.
+// Leaves keep their triangles contiguous, so the triangle array is stored in leaf
+// order as three float4 per triangle with the input id in v0.w.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <future>
+#include <limits>
+#include <thread>
+#include <vector>
+
+#include <vector_functions.h>
+#include <vector_types.h>
+
+#include "occ_bvh_host.h"
+#include "occ_layout.h"
+
+namespace occ {
+namespace {
+
+struct AABB {
+    float lo[3], hi[3];
+    AABB() {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::numeric_limits<float>::infinity();
+            hi[a] = -std::numeric_limits<float>::infinity();
+        }
+    }
+    void grow(const AABB& b) {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], b.lo[a]);
+            hi[a] = std::max(hi[a], b.hi[a]);
+        }
+    }
+    void grow(const float* p) {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], p[a]);
+            hi[a] = std::max(hi[a], p[a]);
+        }
+    }
+    bool empty() const { return lo[0] > hi[0]; }
+    float area() const {
+        if (empty()) return 0.0f;
+        const float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        return 2.0f * (dx * dy + dy * dz + dz * dx);
+    }
+};
+
+struct BNode {
+    AABB box;
+    int32_t left = -1, right = -1;   // children (internal)
+    uint32_t first = 0, count = 0;   // leaf range in the permutation
+};
+
+constexpr int kBins = 16;
+constexpr float kTraverseCost = 1.2f;
+constexpr float kIntersectCost = 1.0f;
+constexpr uint32_t kLeafMax = 8;         // never keep a leaf bigger than this
+constexpr uint32_t kParallelMin = 1u << 15;
+
+struct Builder {
+    const std::vector<AABB>& tb;           // triangle bounds
+    const std::vector<std::array<float, 3>>& tc;   // centroids
+    std::vector<uint32_t>& perm;
+
+    // Builds the subtree of perm[begin, end) into `out` (root at out[base]) and returns the
+    // index of its root.
+    int32_t build(std::vector<BNode>& out, uint32_t begin, uint32_t end, int spawn_depth) {
+        const int32_t me = (int32_t)out.size();
+        out.emplace_back();
+        AABB box, cbox;
+        for (uint32_t i = begin; i < end; ++i) {
+            box.grow(tb[perm[i]]);
+            cbox.grow(tc[perm[i]].data());
+        }
+        out[me].box = box;
+        const uint32_t n = end - begin;
+        auto make_leaf = [&]() {
+            out[me].first = begin;
+            out[me].count = n;
+            return me;
+        };
+        if (n <= 1) return make_leaf();
+
+        int best_axis = -1, best_bin = -1;
+        float best_cost = std::numeric_limits<float>::infinity();
+        for (int a = 0; a < 3; ++a) {
+            const float ext = cbox.hi[a] - cbox.lo[a];
+            if (!(ext > 0.0f)) continue;
+            AABB bb[kBins];
+            uint32_t bc[kBins] = {0};
+            const float k = kBins * (1.0f - 1e-6f) / ext;
+            for (uint32_t i = begin; i < end; ++i) {
+                int b = (int)((tc[perm[i]][a] - cbox.lo[a]) * k);
+                b = std::min(std::max(b, 0), kBins - 1);
+                bb[b].grow(tb[perm[i]]);
+                ++bc[b];
+            }
+            AABB racc;
+            float rarea[kBins];
+            uint32_t rcnt[kBins];
+            uint32_t acc = 0;
+            for (int b = kBins - 1; b > 0; --b) {
+                racc.grow(bb[b]);
+                acc += bc[b];
+                rarea[b] = racc.area();
+                rcnt[b] = acc;
+            }
+            AABB lacc;
+            uint32_t lcnt = 0;
+            for (int b = 0; b < kBins - 1; ++b) {
+                lacc.grow(bb[b]);
+                lcnt += bc[b];
+                if (lcnt == 0 || rcnt[b + 1] == 0) continue;
+                const float c = lacc.area() * lcnt + rarea[b + 1] * rcnt[b + 1];
+                if (c < best_cost) {
+                    best_cost = c;
+                    best_axis = a;
+                    best_bin = b;
+                }
+            }
+        }
+        const float parea = box.area();
+        const float split_cost =
+            kTraverseCost + kIntersectCost * best_cost / (parea > 0.0f ? parea : 1.0f);
+        const float leaf_cost = kIntersectCost * n;
+        // small ranges become leaves when SAH does not favour a split; larger ones always split
+        if (n <= kLeafMax && (best_axis < 0 || split_cost >= leaf_cost)) return make_leaf();
+        uint32_t mid;
+        if (best_axis < 0) {
+            mid = begin + n / 2;   // all centroids coincide: split the range
+        } else {
+            const float ext = cbox.hi[best_axis] - cbox.lo[best_axis];
+            const float k = kBins * (1.0f - 1e-6f) / ext;
+            auto it = std::partition(perm.begin() + begin, perm.begin() + end, [&](uint32_t t) {
+                int b = (int)((tc[t][best_axis] - cbox.lo[best_axis]) * k);
+                b = std::min(std::max(b, 0), kBins - 1);
+                return b <= best_bin;
+            });
+            mid = (uint32_t)(it - perm.begin());
+            if (mid == begin || mid == end) mid = begin + n / 2;
+        }
+        if (spawn_depth > 0 && n >= kParallelMin) {
+            std::vector<BNode> lv, rv;
+            auto fut = std::async(std::launch::async, [&]() { build(lv, begin, mid, spawn_depth - 1); });
+            build(rv, mid, end, spawn_depth - 1);
+            fut.get();
+            const int32_t lbase = (int32_t)out.size();
+            append(out, lv, lbase);
+            const int32_t rbase = (int32_t)out.size();
+            append(out, rv, rbase);
+            out[me].left = lbase;
+            out[me].right = rbase;
+        } else {
+            const int32_t l = build(out, begin, mid, 0);
+            const int32_t r = build(out, mid, end, 0);
+            out[me].left = l;
+            out[me].right = r;
+        }
+        return me;
+    }
+
+    static void append(std::vector<BNode>& out, const std::vector<BNode>& sub, int32_t base) {
+        for (const BNode& b : sub) {
+            BNode c = b;
+            if (c.left >= 0) {
+                c.left += base;
+                c.right += base;
+            }
+            out.push_back(c);
+        }
+    }
+};
+
+struct Collapser {
+    const std::vector<BNode>& bn;
+    std::vector<Node4>& nodes;
+    int max_depth = 0;
+    int64_t leaves = 0;
+    uint32_t max_leaf = 0;
+
+    static uint32_t leaf_ref(const BNode& b) {
+        return kLeafBit | ((b.count - 1u) << kLeafCountShift) | b.first;
+    }
+
+    // Emits the 4-wide node standing for binary node `b` (internal) and returns its index.
+    uint32_t emit(int32_t b, int depth) {
+        max_depth = std::max(max_depth, depth);
+        std::vector<int32_t> kids = {bn[b].left, bn[b].right};
+        while (kids.size() < 4) {
+            int pick = -1;
+            float best = -1.0f;
+            for (int i = 0; i < (int)kids.size(); ++i) {
+                const BNode& c = bn[kids[i]];
+                if (c.left < 0) continue;
+                const float a = c.box.area();
+                if (a > best) {
+                    best = a;
+                    pick = i;
+                }
+            }
+            if (pick < 0) break;
+            const int32_t open = kids[pick];
+            kids[pick] = bn[open].left;
+            kids.push_back(bn[open].right);
+        }
+        const uint32_t me = (uint32_t)nodes.size();
+        nodes.emplace_back();
+        float lo[3][4], hi[3][4];
+        uint32_t ref[4];
+        for (int c = 0; c < 4; ++c) {
+            ref[c] = kEmptyRef;
+            for (int a = 0; a < 3; ++a) {
+                lo[a][c] = std::numeric_limits<float>::infinity();
+                hi[a][c] = -std::numeric_limits<float>::infinity();
+            }
+        }
+        for (int c = 0; c < (int)kids.size(); ++c) {
+            const BNode& k = bn[kids[c]];
+            for (int a = 0; a < 3; ++a) {
+                lo[a][c] = k.box.lo[a];
+                hi[a][c] = k.box.hi[a];
+            }
+            if (k.left < 0) {
+                ref[c] = leaf_ref(k);
+                ++leaves;
+                max_leaf = std::max(max_leaf, k.count);
+            } else {
+                ref[c] = emit(kids[c], depth + 1);
+            }
+        }
+        Node4& n = nodes[me];
+        n.lox = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
+        n.hix = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
+        n.loy = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
+        n.hiy = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
+        n.loz = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
+        n.hiz = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
+        n.child = make_uint4(ref[0], ref[1], ref[2], ref[3]);
+        n.pad = make_uint4(0, 0, 0, 0);
+        return me;
+    }
+};
+
+}  // namespace
+
+bool build_bvh4(const float* tris, int64_t T, HostBVH* out, std::string* err) {
+    if (T <= 0 || T > (int64_t)kLeafFirstMask) {
+        *err = "triangle count must be in [1, 2^26)";
+        return false;
+    }
+    std::vector<AABB> tb((size_t)T);
+    std::vector<std::array<float, 3>> tc((size_t)T);
+    for (int64_t t = 0; t < T; ++t) {
+        const float* v = tris + 9 * t;
+        for (int q = 0; q < 3; ++q) {
+            for (int a = 0; a < 3; ++a) {
+                if (!std::isfinite(v[3 * q + a])) {
+                    *err = "triangle coordinates must be finite";
+                    return false;
+                }
+            }
+            tb[t].grow(v + 3 * q);
+        }
+        for (int a = 0; a < 3; ++a) tc[t][a] = 0.5f * (tb[t].lo[a] + tb[t].hi[a]);
+    }
+    std::vector<uint32_t> perm((size_t)T);
+    for (int64_t t = 0; t < T; ++t) perm[t] = (uint32_t)t;
+    std::vector<BNode> bn;
+    bn.reserve((size_t)(2 * T));
+    Builder b{tb, tc, perm};
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    int spawn = 0;
+    while ((1u << spawn) < hw && spawn < 6) ++spawn;
+    b.build(bn, 0, (uint32_t)T, spawn);
+
+    out->nodes.clear();
+    Collapser col{bn, out->nodes};
+    if (bn[0].left < 0) {
+        // the whole scene is one leaf: a root node with that single child
+        Node4 n;
+        std::memset(&n, 0, sizeof(n));
+        const float inf = std::numeric_limits<float>::infinity();
+        n.lox = make_float4(bn[0].box.lo[0], inf, inf, inf);
+        n.hix = make_float4(bn[0].box.hi[0], -inf, -inf, -inf);
+        n.loy = make_float4(bn[0].box.lo[1], inf, inf, inf);
+        n.hiy = make_float4(bn[0].box.hi[1], -inf, -inf, -inf);
+        n.loz = make_float4(bn[0].box.lo[2], inf, inf, inf);
+        n.hiz = make_float4(bn[0].box.hi[2], -inf, -inf, -inf);
+        n.child = make_uint4(Collapser::leaf_ref(bn[0]), kEmptyRef, kEmptyRef, kEmptyRef);
+        out->nodes.push_back(n);
+        col.leaves = 1;
+        col.max_leaf = bn[0].count;
+        col.max_depth = 0;
+    } else {
+        col.emit(0, 0);
+    }
+    if (3 * (col.max_depth + 1) > kStackSize) {
+        *err = "BVH too deep for the traversal stack";
+        return false;
+    }
+    out->tris.resize((size_t)(3 * T));
+    for (int64_t i = 0; i < T; ++i) {
+        const uint32_t id = perm[i];
+        const float* v = tris + 9 * (int64_t)id;
+        float idf;
+        std::memcpy(&idf, &id, sizeof(idf));
+        out->tris[3 * i + 0] = make_float4(v[0], v[1], v[2], idf);
+        out->tris[3 * i + 1] = make_float4(v[3], v[4], v[5], 0.0f);
+        out->tris[3 * i + 2] = make_float4(v[6], v[7], v[8], 0.0f);
+    }
+    out->num_leaves = col.leaves;
+    out->depth = col.max_depth + 1;
+    out->max_leaf_tris = (int)col.max_leaf;
+    return true;
+}
+
+}  // namespace occ

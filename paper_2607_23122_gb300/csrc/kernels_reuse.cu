@@ -1,0 +1,436 @@
+// kernels_reuse.cu -- steps 2-3 of Algorithms 1 and 2: occluder-domain reuse with
+// balance-heuristic MIS (Eqs. 10-12) for AO (Eqs. 15, 17, 18) and area-light shadows
+// (Eqs. 20, 21, 23, 24), plus the no-reuse and box-mean baselines.
+//
+// Densities are evaluated in FP32 without the constant factors 1/pi and 1/Area,
+// which cancel in every ratio p(z_j|x_i) / sum_k p(z_j|x_k).
+//
+//  k_reuse_group    GROUP patterns with power-of-two blocks (the paper's shared
+//                   groups mapped onto warp lanes).  Lane j owns candidate z_j and
+//                   evaluates its column p(z_j|x_k) for all K receivers (receiver data
+//                   exchanged through shared memory), normalises by P_j, and a
+//                   recursive-halving shuffle reduce-scatter (K-1 shuffles) hands lane
+//                   i its B_i = sum_j p(z_j|x_i)/P_j.
+//  k_reuse_generic  any pattern: one thread per receiver, members' receiver data held
+//                   in registers, K^2 pair densities.
+//  k_reuse_simple   NOREUSE / BOXMEAN.
+#include <cuda_runtime.h>
+
+#include "occ_device.cuh"
+#include "occ_kernels.h"
+
+namespace occ {
+namespace {
+
+constexpr float kSupportSlack = 1.0f + 1.0f / 65536.0f;
+constexpr float kValidateTmax = 1.0f + 1.0f / 1024.0f;
+
+struct ReuseArgs {
+    GBufView gb;
+    RecView rec;
+    PatternParams pat;
+    float R2s;          // AO: R^2 (1 + 2^-16)
+    LightParams lp;
+    DevBVH bvh;         // unbiased only
+    float* out;
+    unsigned* status;
+};
+
+__device__ __forceinline__ RectLight make_light_dev(const LightParams& p) {
+    RectLight L;
+    L.c = make_float3(p.c[0], p.c[1], p.c[2]);
+    L.eu = make_float3(p.eu[0], p.eu[1], p.eu[2]);
+    L.ev = make_float3(p.ev[0], p.ev[1], p.ev[2]);
+    L.n = normalize3(cross3(L.eu, L.ev));
+    L.inv_eu2 = 1.0f / dot3(L.eu, L.eu);
+    L.inv_ev2 = 1.0f / dot3(L.ev, L.ev);
+    L.lim = 0.5f * kSupportSlack;
+    return L;
+}
+
+// Receiver data needed by the density of each effect.
+struct Recv {
+    float3 x;
+    float3 n;       // AO: normal.  Shadow: (n_L.(c - x), (x - c).eu, (x - c).ev)
+    bool valid;
+};
+
+template <int EFFECT>
+__device__ __forceinline__ Recv make_recv(float4 P, float4 N, const RectLight& L) {
+    Recv r;
+    r.x = f3(P);
+    r.valid = P.w != 0.0f;
+    if (EFFECT == kAO) {
+        r.n = f3(N);
+    } else {
+        const float3 xc = sub3(r.x, L.c);
+        r.n = make_float3(-dot3(L.n, xc), dot3(xc, L.eu), dot3(xc, L.ev));
+    }
+    return r;
+}
+
+// Eq. 15 without Occ and 1/pi: max(0, n_x.d) max(0, -n_z.d) / r^4 inside the radius.
+__device__ __forceinline__ float dens_ao(float3 z, float3 nz, const Recv& r, float R2s) {
+    const float3 d = sub3(z, r.x);
+    const float r2 = dot3(d, d);
+    const float a = dot3(r.n, d);
+    const float b = -dot3(nz, d);
+    const bool ok = (a > 0.0f) & (b > 0.0f) & (r2 > 0.0f) & (r2 <= R2s);
+    return ok ? __fdividef(a * b, r2 * r2) : 0.0f;
+}
+
+// Eqs. 20-21 without Occ and 1/Area: the ray x + s d meets the light plane at
+// s_L = n_L.(c - x) / n_L.d (> 1, hitting the emitting side); y' = x + s_L d must lie
+// in the rectangle; J = s_L^2 (-n_z.d) / (-n_L.d).
+__device__ __forceinline__ float dens_sh(float3 z, float3 nz, const Recv& r, const RectLight& L) {
+    const float3 d = sub3(z, r.x);
+    const float nd = dot3(L.n, d);
+    const float cz = -dot3(nz, d);
+    if (!(nd < 0.0f) || !(cz > 0.0f)) return 0.0f;
+    const float inv = 1.0f / nd;
+    const float sL = r.n.x * inv;
+    if (!(sL > 1.0f)) return 0.0f;
+    const float a = fmaf(sL, dot3(d, L.eu), r.n.y) * L.inv_eu2;
+    const float b = fmaf(sL, dot3(d, L.ev), r.n.z) * L.inv_ev2;
+    if (fabsf(a) > L.lim || fabsf(b) > L.lim) return 0.0f;
+    return sL * sL * cz * (-inv);
+}
+
+template <int EFFECT>
+__device__ __forceinline__ float density(float3 z, float3 nz, const Recv& r, float R2s,
+                                         const RectLight& L) {
+    if (EFFECT == kAO) return dens_ao(z, nz, r, R2s);
+    return dens_sh(z, nz, r, L);
+}
+
+// Eq. 7 for a reused candidate: the closest hit from x toward z (t in (0, 1 + 2^-10]
+// in units of z - x) is z's own triangle.
+__device__ __forceinline__ bool first_hit(const DevBVH& bvh, float3 x, float3 z, uint32_t tri,
+                                          unsigned* status) {
+    const Hit h = closest_hit(bvh, x, sub3(z, x), kValidateTmax, status);
+    return h.id == tri;
+}
+
+__device__ __forceinline__ void tile_pixel(int* x, int* y) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    *x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+    *y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+}
+
+// Members of N_i in a fixed order (the receiver's own slot returned in *self).
+// GROUP: row-major over the block; BOX: row-major over the window; OFFSETS: the
+// receiver, then each offset.  Out-of-image and invalid pixels are dropped.
+template <int MAXK>
+__device__ __forceinline__ int gather_members(const PatternParams& pat, const GBufView& gb, int x,
+                                              int y, int* mem, int* self) {
+    int n = 0;
+    *self = 0;
+    for (int a = 0; a < pat.K; ++a) {
+        int px, py;
+        if (pat.kind == 0) {
+            px = (x / pat.gw) * pat.gw + a % pat.gw;
+            py = (y / pat.gh) * pat.gh + a / pat.gw;
+        } else if (pat.kind == 1) {
+            px = x - (pat.gw - 1) / 2 + a % pat.gw;
+            py = y - (pat.gh - 1) / 2 + a / pat.gw;
+        } else {
+            px = x + (a == 0 ? 0 : pat.off[a - 1].x);
+            py = y + (a == 0 ? 0 : pat.off[a - 1].y);
+        }
+        if (px < 0 || py < 0 || px >= gb.W || py >= gb.H) continue;
+        const int q = py * gb.W + px;
+        if (__ldg(&gb.pos[q].w) == 0.0f) continue;
+        if (px == x && py == y) *self = n;
+        if (n < MAXK) mem[n++] = q;
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------------------
+// Generic per-receiver kernel (any pattern).
+// ---------------------------------------------------------------------------------------
+template <int EFFECT, int EST, int MAXK>
+__global__ void __launch_bounds__(128) k_reuse_generic(ReuseArgs a) {
+    int x, y;
+    tile_pixel(&x, &y);
+    if (x >= a.gb.W || y >= a.gb.H) return;
+    const int i = y * a.gb.W + x;
+    if (__ldg(&a.gb.pos[i].w) == 0.0f) {
+        a.out[i] = 1.0f;
+        return;
+    }
+    RectLight L;
+    if (EFFECT == kShadow) L = make_light_dev(a.lp);
+    int mem[MAXK];
+    int self;
+    const int n = gather_members<MAXK>(a.pat, a.gb, x, y, mem, &self);
+    Recv rk[MAXK];
+#pragma unroll
+    for (int b = 0; b < MAXK; ++b)
+        if (b < n) rk[b] = make_recv<EFFECT>(__ldg(a.gb.pos + mem[b]), __ldg(a.gb.nrm + mem[b]), L);
+    float B = 0.0f;
+    int blocked = 0;
+#pragma unroll 1
+    for (int c = 0; c < n; ++c) {
+        const int j = mem[c];
+        const float4 r0 = __ldg(a.rec.r0 + j);
+        const int tri = __float_as_int(r0.w);
+        if (tri < 0) continue;
+        ++blocked;
+        const float3 z = f3(r0), nz = f3(__ldg(a.rec.r1 + j));
+        float Psum = 0.0f, pi = 0.0f;
+#pragma unroll
+        for (int b = 0; b < MAXK; ++b) {
+            if (b < n) {
+                float q = density<EFFECT>(z, nz, rk[b], a.R2s, L);
+                if (EST == kUnbiased && q > 0.0f && b != c)
+                    if (!first_hit(a.bvh, rk[b].x, z, (uint32_t)tri, a.status)) q = 0.0f;
+                Psum += q;
+                if (b == self) pi = q;
+            }
+        }
+        if (pi > 0.0f) B += pi / Psum;
+    }
+    float res = 1.0f - B;
+    if (EFFECT == kShadow && EST == kBiased && blocked == n) res = 0.0f;
+    a.out[i] = res;
+}
+
+// ---------------------------------------------------------------------------------------
+// NOREUSE (Eq. 3 / Eq. 6 with one sample) and BOXMEAN (mean visibility over N_i).
+// ---------------------------------------------------------------------------------------
+template <int EST>
+__global__ void __launch_bounds__(128) k_reuse_simple(ReuseArgs a) {
+    int x, y;
+    tile_pixel(&x, &y);
+    if (x >= a.gb.W || y >= a.gb.H) return;
+    const int i = y * a.gb.W + x;
+    if (__ldg(&a.gb.pos[i].w) == 0.0f) {
+        a.out[i] = 1.0f;
+        return;
+    }
+    if (EST == kNoReuse) {
+        a.out[i] = __float_as_int(__ldg(&a.rec.r0[i].w)) < 0 ? 1.0f : 0.0f;
+        return;
+    }
+    int mem[kMaxMembers];
+    int self;
+    const int n = gather_members<kMaxMembers>(a.pat, a.gb, x, y, mem, &self);
+    int vis = 0;
+    for (int c = 0; c < n; ++c) vis += __float_as_int(__ldg(&a.rec.r0[mem[c]].w)) < 0 ? 1 : 0;
+    a.out[i] = (float)vis / (float)n;
+}
+
+// ---------------------------------------------------------------------------------------
+// Warp-cooperative GROUP kernel.  K = GW * GH lanes per group, 32 / K groups per warp
+// laid side by side (warp block = (32/K * GW) x GH pixels), 8 warps stacked per CTA.
+// ---------------------------------------------------------------------------------------
+template <int EFFECT, int EST, int GW, int GH>
+__global__ void __launch_bounds__(256) k_reuse_group(ReuseArgs a) {
+    constexpr int K = GW * GH;
+    constexpr int GPW = 32 / K;
+    constexpr int BW = GPW * GW;
+    __shared__ float4 s_x[8][32];
+    __shared__ float4 s_n[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / K, m = lane % K;
+    const int x = blockIdx.x * BW + g * GW + m % GW;
+    const int y = (blockIdx.y * 8 + warp) * GH + m / GW;
+    const bool inside = x < a.gb.W && y < a.gb.H;
+    const int i = inside ? y * a.gb.W + x : 0;
+    RectLight L;
+    if (EFFECT == kShadow) L = make_light_dev(a.lp);
+
+    float4 P = make_float4(0.0f, 0.0f, 0.0f, 0.0f), N = P;
+    float4 R0 = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1)), R1 = P;
+    if (inside) {
+        P = __ldg(a.gb.pos + i);
+        N = __ldg(a.gb.nrm + i);
+        R0 = __ldg(a.rec.r0 + i);
+        R1 = __ldg(a.rec.r1 + i);
+    }
+    const bool valid = inside && P.w != 0.0f;
+    const bool hit = valid && __float_as_int(R0.w) >= 0;
+    // receiver data for the density: AO (x, n); shadow (x, precomputed plane terms)
+    const Recv me = make_recv<EFFECT>(P, N, L);
+    s_x[warp][lane] = make_float4(me.x.x, me.x.y, me.x.z, valid ? 1.0f : 0.0f);
+    s_n[warp][lane] = make_float4(me.n.x, me.n.y, me.n.z, 0.0f);
+    __syncwarp();
+
+    const unsigned gmask = (K == 32 ? 0xFFFFFFFFu : ((1u << K) - 1u)) << (g * K);
+    const unsigned vmask = __ballot_sync(0xFFFFFFFFu, valid) & gmask;
+    const unsigned hmask = __ballot_sync(0xFFFFFFFFu, hit) & gmask;
+
+    // column of candidate z_m: densities at every receiver of the group
+    float r[K];
+    const float3 z = f3(R0), nz = f3(R1);
+    float Psum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 sx = s_x[warp][g * K + k];
+        const float4 sn = s_n[warp][g * K + k];
+        Recv rk;
+        rk.x = f3(sx);
+        rk.n = f3(sn);
+        float q = 0.0f;
+        if (hit && sx.w != 0.0f) q = density<EFFECT>(z, nz, rk, a.R2s, L);
+        if (EST == kUnbiased && q > 0.0f && k != m)
+            if (!first_hit(a.bvh, rk.x, z, (uint32_t)__float_as_int(R0.w), a.status)) q = 0.0f;
+        r[k] = q;
+        Psum += q;
+    }
+    const float inv = Psum > 0.0f ? 1.0f / Psum : 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r[k] *= inv;
+
+    // reduce-scatter over the group's lanes: lane m ends with sum_j r_j[m]
+#pragma unroll
+    for (int h = K / 2; h >= 1; h >>= 1) {
+        const bool upper = (m & h) != 0;
+#pragma unroll
+        for (int e = 0; e < h; ++e) {
+            const float keep = upper ? r[e + h] : r[e];
+            const float send = upper ? r[e] : r[e + h];
+            r[e] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, h);
+        }
+    }
+    if (!inside) return;
+    float res;
+    if (!valid) {
+        res = 1.0f;
+    } else {
+        res = 1.0f - r[0];
+        if (EFFECT == kShadow && EST == kBiased && vmask == hmask) res = 0.0f;
+    }
+    a.out[i] = res;
+}
+
+// ---------------------------------------------------------------------------------------
+// MIS weights of selected receivers (debug / tests): w[a][b] = p(z_a|x_b) / P_a.
+// ---------------------------------------------------------------------------------------
+template <int EFFECT, int EST>
+__global__ void k_debug_mis(ReuseArgs a, const int32_t* pix, int32_t npix, int32_t* members,
+                            float* w) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npix) return;
+    const int i = pix[t];
+    const int x = i % a.gb.W, y = i / a.gb.W;
+    RectLight L;
+    if (EFFECT == kShadow) L = make_light_dev(a.lp);
+    int mem[kMaxMembers];
+    int self;
+    int n = 0;
+    if (a.gb.pos[i].w != 0.0f) n = gather_members<kMaxMembers>(a.pat, a.gb, x, y, mem, &self);
+    for (int c = 0; c < kMaxMembers; ++c) members[t * kMaxMembers + c] = c < n ? mem[c] : -1;
+    float* wt = w + (size_t)t * kMaxMembers * kMaxMembers;
+    for (int c = 0; c < n; ++c) {
+        const float4 r0 = a.rec.r0[mem[c]];
+        const int tri = __float_as_int(r0.w);
+        const float3 z = f3(r0), nz = f3(a.rec.r1[mem[c]]);
+        float Psum = 0.0f;
+        for (int b = 0; b < n; ++b) {
+            float q = 0.0f;
+            if (tri >= 0) {
+                const Recv rk = make_recv<EFFECT>(a.gb.pos[mem[b]], a.gb.nrm[mem[b]], L);
+                q = density<EFFECT>(z, nz, rk, a.R2s, L);
+                if (EST == kUnbiased && q > 0.0f && b != c)
+                    if (!first_hit(a.bvh, rk.x, z, (uint32_t)tri, a.status)) q = 0.0f;
+            }
+            wt[c * kMaxMembers + b] = q;
+            Psum += q;
+        }
+        for (int b = 0; b < n; ++b)
+            wt[c * kMaxMembers + b] = Psum > 0.0f ? wt[c * kMaxMembers + b] / Psum : 0.0f;
+    }
+}
+
+template <int EFFECT, int EST, int GW, int GH>
+void launch_group_t(const ReuseArgs& a, cudaStream_t s) {
+    constexpr int K = GW * GH;
+    constexpr int BW = (32 / K) * GW;
+    const dim3 grid((unsigned)((a.gb.W + BW - 1) / BW), (unsigned)((a.gb.H + 8 * GH - 1) / (8 * GH)));
+    k_reuse_group<EFFECT, EST, GW, GH><<<grid, 256, 0, s>>>(a);
+}
+
+template <int EFFECT, int EST>
+bool launch_group(const ReuseArgs& a, cudaStream_t s) {
+    const int gw = a.pat.gw, gh = a.pat.gh;
+    if (gw == 2 && gh == 1) { launch_group_t<EFFECT, EST, 2, 1>(a, s); return true; }
+    if (gw == 2 && gh == 2) { launch_group_t<EFFECT, EST, 2, 2>(a, s); return true; }
+    if (gw == 4 && gh == 2) { launch_group_t<EFFECT, EST, 4, 2>(a, s); return true; }
+    if (gw == 4 && gh == 4) { launch_group_t<EFFECT, EST, 4, 4>(a, s); return true; }
+    return false;
+}
+
+template <int EFFECT, int EST>
+void launch_generic(const ReuseArgs& a, cudaStream_t s) {
+    const dim3 grid((unsigned)((a.gb.W + 15) / 16), (unsigned)((a.gb.H + 7) / 8));
+    if (a.pat.K <= 9)
+        k_reuse_generic<EFFECT, EST, 9><<<grid, 128, 0, s>>>(a);
+    else if (a.pat.K <= 16)
+        k_reuse_generic<EFFECT, EST, 16><<<grid, 128, 0, s>>>(a);
+    else
+        k_reuse_generic<EFFECT, EST, kMaxMembers><<<grid, 128, 0, s>>>(a);
+}
+
+template <int EFFECT>
+void launch_effect(int est, const ReuseArgs& a, cudaStream_t s) {
+    const dim3 grid((unsigned)((a.gb.W + 15) / 16), (unsigned)((a.gb.H + 7) / 8));
+    if (est == kNoReuse) {
+        k_reuse_simple<kNoReuse><<<grid, 128, 0, s>>>(a);
+    } else if (est == kBoxMean) {
+        k_reuse_simple<kBoxMean><<<grid, 128, 0, s>>>(a);
+    } else if (est == kBiased) {
+        if (a.pat.kind != 0 || !launch_group<EFFECT, kBiased>(a, s)) launch_generic<EFFECT, kBiased>(a, s);
+    } else {
+        if (a.pat.kind != 0 || !launch_group<EFFECT, kUnbiased>(a, s)) launch_generic<EFFECT, kUnbiased>(a, s);
+    }
+}
+
+ReuseArgs make_args(const GBufView& gb, const RecView& rec, const PatternParams& pat, float radius,
+                    const LightParams& light, const DevBVH* bvh, float* out, unsigned* status) {
+    ReuseArgs a;
+    a.gb = gb;
+    a.rec = rec;
+    a.pat = pat;
+    a.R2s = (float)((double)radius * (double)radius * (1.0 + 1.0 / 65536.0));
+    a.lp = light;
+    a.bvh = bvh ? *bvh : DevBVH{nullptr, nullptr};
+    a.out = out;
+    a.status = status;
+    return a;
+}
+
+}  // namespace
+
+cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const RecView& rec,
+                         const PatternParams& pat, float radius, const LightParams& light,
+                         const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s) {
+    if (gb.W <= 0 || gb.H <= 0) return cudaSuccess;
+    const ReuseArgs a = make_args(gb, rec, pat, radius, light, bvh, out, status);
+    if (effect == kAO)
+        launch_effect<kAO>(estimator, a, s);
+    else
+        launch_effect<kShadow>(estimator, a, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_mis(int effect, int estimator, const GBufView& gb, const RecView& rec,
+                             const PatternParams& pat, float radius, const LightParams& light,
+                             const DevBVH* bvh, const int32_t* pix, int32_t n, int32_t* members,
+                             float* w, unsigned* status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const ReuseArgs a = make_args(gb, rec, pat, radius, light, bvh, nullptr, status);
+    const unsigned blocks = (unsigned)((n + 63) / 64);
+    const bool unb = estimator == kUnbiased;
+    if (effect == kAO) {
+        if (unb) k_debug_mis<kAO, kUnbiased><<<blocks, 64, 0, s>>>(a, pix, n, members, w);
+        else k_debug_mis<kAO, kBiased><<<blocks, 64, 0, s>>>(a, pix, n, members, w);
+    } else {
+        if (unb) k_debug_mis<kShadow, kUnbiased><<<blocks, 64, 0, s>>>(a, pix, n, members, w);
+        else k_debug_mis<kShadow, kBiased><<<blocks, 64, 0, s>>>(a, pix, n, members, w);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace occ

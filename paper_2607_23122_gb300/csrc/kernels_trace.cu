@@ -1,0 +1,190 @@
+// kernels_trace.cu -- step 1 of Algorithms 1 and 2 (occluder generation) and the
+// pinhole G-buffer input stage.
+//
+// One thread per receiver.  A CTA of 128 threads covers a 16 x 8 pixel tile and
+// each warp an 8 x 4 sub-tile, so neighbouring rays start from neighbouring
+// receivers and touch the same BVH nodes (short AO rays stay local).
+#include <cuda_runtime.h>
+
+#include "occ_device.cuh"
+#include "occ_kernels.h"
+
+namespace occ {
+namespace {
+
+constexpr int kTileW = 16, kTileH = 8;
+
+__device__ __forceinline__ void tile_pixel(int* x, int* y) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    *x = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
+    *y = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
+}
+
+__device__ __forceinline__ RectLight make_light(const LightParams& p) {
+    RectLight L;
+    L.c = make_float3(p.c[0], p.c[1], p.c[2]);
+    L.eu = make_float3(p.eu[0], p.eu[1], p.eu[2]);
+    L.ev = make_float3(p.ev[0], p.ev[1], p.ev[2]);
+    L.n = normalize3(cross3(L.eu, L.ev));
+    L.inv_eu2 = 1.0f / dot3(L.eu, L.eu);
+    L.inv_ev2 = 1.0f / dot3(L.ev, L.ev);
+    L.lim = 0.5f * (1.0f + 1.0f / 65536.0f);
+    return L;
+}
+
+// Step-1 ray of receiver p: origin x, direction, tmax.
+template <int EFFECT>
+__device__ __forceinline__ float3 step1_ray(float3 x, float3 n, uint32_t p, float radius,
+                                            const RectLight& L, uint64_t seed, uint32_t sample,
+                                            float* tmax) {
+    if (EFFECT == kAO) {
+        *tmax = radius;
+        return cosine_direction(n, uniform_pair(seed, p, sample, kStreamAO));
+    } else {
+        return light_direction(L, x, uniform_pair(seed, p, sample, kStreamShadow), tmax);
+    }
+}
+
+template <int EFFECT>
+__global__ void __launch_bounds__(128) k_trace(GBufView gb, DevBVH bvh, float radius,
+                                               LightParams lp, uint64_t seed, uint32_t sample,
+                                               RecView rec, unsigned* status) {
+    int x, y;
+    tile_pixel(&x, &y);
+    if (x >= gb.W || y >= gb.H) return;
+    const uint32_t p = (uint32_t)y * (uint32_t)gb.W + (uint32_t)x;
+    const float4 P = __ldg(gb.pos + p);
+    if (P.w == 0.0f) {
+        rec.r0[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
+        rec.r1[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        return;
+    }
+    const float3 xo = f3(P), n = f3(__ldg(gb.nrm + p));
+    RectLight L;
+    if (EFFECT == kShadow) L = make_light(lp);
+    float tmax;
+    const float3 d = step1_ray<EFFECT>(xo, n, p, radius, L, seed, sample, &tmax);
+    const Hit h = closest_hit(bvh, xo, d, tmax, status);
+    if (h.id == kNoHit) {
+        rec.r0[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
+        rec.r1[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        return;
+    }
+    const float3 nz = hit_normal(bvh, h.slot, d);
+    rec.r0[p] = make_float4(fmaf(h.t, d.x, xo.x), fmaf(h.t, d.y, xo.y), fmaf(h.t, d.z, xo.z),
+                            __uint_as_float(h.id));
+    rec.r1[p] = make_float4(nz.x, nz.y, nz.z, h.t);
+}
+
+__global__ void __launch_bounds__(128) k_gbuffer(DevBVH bvh, float3 eye, float3 f, float3 rt,
+                                                 float3 up, float th, float aspect, float eps,
+                                                 int W, int H, float4* pos, float4* nrm,
+                                                 unsigned* status) {
+    int x, y;
+    tile_pixel(&x, &y);
+    if (x >= W || y >= H) return;
+    const uint32_t p = (uint32_t)y * (uint32_t)W + (uint32_t)x;
+    const float sx = (2.0f * ((float)x + 0.5f) / (float)W - 1.0f) * th * aspect;
+    const float sy = (1.0f - 2.0f * ((float)y + 0.5f) / (float)H) * th;
+    const float3 d = normalize3(make_float3(f.x + sx * rt.x + sy * up.x, f.y + sx * rt.y + sy * up.y,
+                                            f.z + sx * rt.z + sy * up.z));
+    const Hit h = closest_hit(bvh, eye, d, 3.0e38f, status);
+    if (h.id == kNoHit) {
+        pos[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        nrm[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        return;
+    }
+    const float3 n = hit_normal(bvh, h.slot, d);
+    pos[p] = make_float4(fmaf(h.t, d.x, eye.x) + eps * n.x, fmaf(h.t, d.y, eye.y) + eps * n.y,
+                         fmaf(h.t, d.z, eye.z) + eps * n.z, 1.0f);
+    nrm[p] = make_float4(n.x, n.y, n.z, 0.0f);
+}
+
+__global__ void k_debug_philox(const uint32_t* in, int64_t n, uint32_t* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t* q = in + 6 * i;
+    const uint4 w = philox4x32_10(make_uint4(q[0], q[1], q[2], q[3]), make_uint2(q[4], q[5]));
+    out[4 * i + 0] = w.x;
+    out[4 * i + 1] = w.y;
+    out[4 * i + 2] = w.z;
+    out[4 * i + 3] = w.w;
+}
+
+template <int EFFECT>
+__global__ void k_debug_rays(GBufView gb, float radius, LightParams lp, uint64_t seed,
+                             uint32_t sample, float4* out) {
+    int x, y;
+    tile_pixel(&x, &y);
+    if (x >= gb.W || y >= gb.H) return;
+    const uint32_t p = (uint32_t)y * (uint32_t)gb.W + (uint32_t)x;
+    const float4 P = gb.pos[p];
+    if (P.w == 0.0f) {
+        out[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        return;
+    }
+    RectLight L;
+    if (EFFECT == kShadow) L = make_light(lp);
+    float tmax;
+    const float3 d = step1_ray<EFFECT>(f3(P), f3(gb.nrm[p]), p, radius, L, seed, sample, &tmax);
+    out[p] = make_float4(d.x, d.y, d.z, tmax);
+}
+
+dim3 tile_grid(int W, int H) {
+    return dim3((unsigned)((W + kTileW - 1) / kTileW), (unsigned)((H + kTileH - 1) / kTileH));
+}
+
+}  // namespace
+
+cudaError_t launch_trace(int effect, const GBufView& gb, const DevBVH& bvh, float radius,
+                         const LightParams& light, uint64_t seed, uint32_t sample, RecView rec,
+                         unsigned* status, cudaStream_t s) {
+    if (gb.W <= 0 || gb.H <= 0) return cudaSuccess;
+    const dim3 grid = tile_grid(gb.W, gb.H);
+    if (effect == kAO)
+        k_trace<kAO><<<grid, 128, 0, s>>>(gb, bvh, radius, light, seed, sample, rec, status);
+    else
+        k_trace<kShadow><<<grid, 128, 0, s>>>(gb, bvh, radius, light, seed, sample, rec, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gbuffer(const DevBVH& bvh, const float* cam, float eps, int W, int H,
+                           float4* pos, float4* nrm, unsigned* status, cudaStream_t s) {
+    if (W <= 0 || H <= 0) return cudaSuccess;
+    // camera basis in FP32: forward, right = forward x up, up' = right x forward
+    auto norm = [](float3 a) {
+        const float l = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+        return make_float3(a.x / l, a.y / l, a.z / l);
+    };
+    auto cr = [](float3 a, float3 b) {
+        return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+    };
+    const float3 eye = make_float3(cam[0], cam[1], cam[2]);
+    const float3 f = norm(make_float3(cam[3] - cam[0], cam[4] - cam[1], cam[5] - cam[2]));
+    const float3 rt = norm(cr(f, make_float3(cam[6], cam[7], cam[8])));
+    const float3 up = cr(rt, f);
+    const float th = tanf(0.5f * cam[9] * 3.14159265358979f / 180.0f);
+    k_gbuffer<<<tile_grid(W, H), 128, 0, s>>>(bvh, eye, f, rt, up, th, (float)W / (float)H, eps,
+                                              W, H, pos, nrm, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_philox(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_debug_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
+                              const LightParams& light, uint64_t seed, uint32_t sample,
+                              float4* out, cudaStream_t s) {
+    if (gb.W <= 0 || gb.H <= 0) return cudaSuccess;
+    const dim3 grid = tile_grid(gb.W, gb.H);
+    if (effect == kAO)
+        k_debug_rays<kAO><<<grid, 128, 0, s>>>(gb, radius, light, seed, sample, out);
+    else
+        k_debug_rays<kShadow><<<grid, 128, 0, s>>>(gb, radius, light, seed, sample, out);
+    return cudaGetLastError();
+}
+
+}  // namespace occ

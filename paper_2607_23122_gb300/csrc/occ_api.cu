@@ -1,0 +1,502 @@
+// occ_api.cu -- the C ABI declared in include/occ.h: argument checks, ownership,
+// launches on the caller's stream, and error / device-status reporting.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "occ.h"
+#include "occ_bvh_host.h"
+#include "occ_kernels.h"
+
+#define OCC_EXPORT extern "C" __attribute__((visibility("default")))
+
+struct occ_ctx {
+    int device = 0;
+    unsigned* status = nullptr;          // device status word (kStatus* bits)
+    std::string last_error;
+    // workspace of occ_frame_host: pos4, nrm4, records, output
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+struct occ_bvh {
+    int device = 0;
+    occ::Node4* nodes = nullptr;
+    float4* tris = nullptr;
+    occ_bvh_stats stats{};
+};
+
+namespace {
+
+occ_status fail(occ_ctx* ctx, occ_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->last_error = buf;
+    }
+    return st;
+}
+
+occ_status cuda_fail(occ_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? OCC_ERR_OOM : OCC_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+occ_status check_ctx(occ_ctx* ctx) {
+    if (!ctx) return OCC_ERR_INVALID_ARG;
+    const cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return OCC_OK;
+}
+
+occ_status check_gbuffer(occ_ctx* ctx, const occ_gbuffer* gb) {
+    if (!gb) return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer is NULL");
+    if (gb->W <= 0 || gb->H <= 0 || (int64_t)gb->W * gb->H > (int64_t)1 << 31)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer size %dx%d out of range", gb->W, gb->H);
+    if (!gb->pos4 || !gb->nrm4) return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pointers are NULL");
+    if (!aligned16(gb->pos4) || !aligned16(gb->nrm4))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pointers must be 16-byte aligned");
+    return OCC_OK;
+}
+
+occ_status check_occluders(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occluders* o) {
+    if (!o) return fail(ctx, OCC_ERR_INVALID_ARG, "occluders is NULL");
+    if (o->W != gb->W || o->H != gb->H)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "occluder size %dx%d != gbuffer size %dx%d", o->W,
+                    o->H, gb->W, gb->H);
+    if (o->format != OCC_REC_FP32)
+        return fail(ctx, OCC_ERR_UNSUPPORTED, "occluder format %d not supported", o->format);
+    if (!o->data || !aligned16(o->data))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "occluder data must be a 16-byte aligned pointer");
+    return OCC_OK;
+}
+
+occ_status check_light(occ_ctx* ctx, const occ_rect_light* l) {
+    if (!l) return fail(ctx, OCC_ERR_INVALID_ARG, "light is NULL");
+    double eu2 = 0, ev2 = 0, uv = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(l->c[a]) || !std::isfinite(l->eu[a]) || !std::isfinite(l->ev[a]))
+            return fail(ctx, OCC_ERR_INVALID_ARG, "light has non-finite values");
+        eu2 += (double)l->eu[a] * l->eu[a];
+        ev2 += (double)l->ev[a] * l->ev[a];
+        uv += (double)l->eu[a] * l->ev[a];
+    }
+    if (!(eu2 > 0) || !(ev2 > 0)) return fail(ctx, OCC_ERR_INVALID_ARG, "light edges are zero");
+    if (std::fabs(uv) > 1e-6 * std::sqrt(eu2 * ev2))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "light edges eu and ev must be orthogonal");
+    return OCC_OK;
+}
+
+occ::LightParams to_params(const occ_rect_light* l) {
+    occ::LightParams p{};
+    if (l) {
+        std::memcpy(p.c, l->c, sizeof(p.c));
+        std::memcpy(p.eu, l->eu, sizeof(p.eu));
+        std::memcpy(p.ev, l->ev, sizeof(p.ev));
+    }
+    return p;
+}
+
+occ_status make_pattern(occ_ctx* ctx, const occ_pattern* pat, int32_t K, occ::PatternParams* out) {
+    if (!pat) return fail(ctx, OCC_ERR_INVALID_ARG, "pattern is NULL");
+    std::memset(out, 0, sizeof(*out));
+    out->kind = pat->kind;
+    out->K = K;
+    if (K < 1 || K > occ::kMaxMembers)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "K = %d must be in [1, %d]", K, occ::kMaxMembers);
+    if (pat->kind == OCC_PAT_GROUP || pat->kind == OCC_PAT_BOX) {
+        if (pat->gw < 1 || pat->gh < 1 || pat->gw > 64 || pat->gh > 64)
+            return fail(ctx, OCC_ERR_INVALID_ARG, "pattern extent %dx%d invalid", pat->gw, pat->gh);
+        if (pat->gw * pat->gh != K)
+            return fail(ctx, OCC_ERR_INVALID_ARG, "K = %d != gw*gh = %d", K, pat->gw * pat->gh);
+        out->gw = pat->gw;
+        out->gh = pat->gh;
+        const int hx0 = (pat->gw - 1) / 2, hy0 = (pat->gh - 1) / 2;
+        out->halo[0] = hx0;
+        out->halo[1] = pat->gw / 2;
+        out->halo[2] = hy0;
+        out->halo[3] = pat->gh / 2;
+    } else if (pat->kind == OCC_PAT_OFFSETS) {
+        if (pat->n_offsets != K - 1)
+            return fail(ctx, OCC_ERR_INVALID_ARG, "K = %d != n_offsets + 1 = %d", K, pat->n_offsets + 1);
+        if (pat->n_offsets > 0 && !pat->offsets_host)
+            return fail(ctx, OCC_ERR_INVALID_ARG, "offsets_host is NULL");
+        out->gw = out->gh = 1;
+        out->n_off = pat->n_offsets;
+        for (int a = 0; a < pat->n_offsets; ++a) {
+            const int dx = pat->offsets_host[2 * a], dy = pat->offsets_host[2 * a + 1];
+            if (dx == 0 && dy == 0)
+                return fail(ctx, OCC_ERR_INVALID_ARG, "offset %d is (0, 0)", a);
+            if (dx < -256 || dx > 256 || dy < -256 || dy > 256)
+                return fail(ctx, OCC_ERR_INVALID_ARG, "offset %d out of [-256, 256]", a);
+            for (int b = 0; b < a; ++b)
+                if (pat->offsets_host[2 * b] == dx && pat->offsets_host[2 * b + 1] == dy)
+                    return fail(ctx, OCC_ERR_INVALID_ARG, "offset %d repeats offset %d", a, b);
+            out->off[a] = make_int2(dx, dy);
+            out->halo[0] = std::max(out->halo[0], -dx);
+            out->halo[1] = std::max(out->halo[1], dx);
+            out->halo[2] = std::max(out->halo[2], -dy);
+            out->halo[3] = std::max(out->halo[3], dy);
+        }
+    } else {
+        return fail(ctx, OCC_ERR_INVALID_ARG, "pattern kind %d invalid", pat->kind);
+    }
+    return OCC_OK;
+}
+
+occ::GBufView view(const occ_gbuffer* gb) {
+    return occ::GBufView{gb->W, gb->H, reinterpret_cast<const float4*>(gb->pos4),
+                         reinterpret_cast<const float4*>(gb->nrm4)};
+}
+
+occ::RecView rec_view(const occ_occluders* o) {
+    float4* base = reinterpret_cast<float4*>(o->data);
+    return occ::RecView{base, base + (size_t)o->W * o->H};
+}
+
+occ::DevBVH dev_bvh(const occ_bvh* b) { return occ::DevBVH{b->nodes, b->tris}; }
+
+occ_status launched(occ_ctx* ctx, cudaError_t e, const char* what) {
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    return OCC_OK;
+}
+
+occ_status reuse_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const occ_occluders* occ,
+                        const occ_pattern* pattern, int32_t K, int32_t estimator,
+                        const occ_bvh* bvh, float* out, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if ((st = check_gbuffer(ctx, gb)) != OCC_OK) return st;
+    if ((st = check_occluders(ctx, gb, occ)) != OCC_OK) return st;
+    if (occ->effect != effect)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "occluder records were traced for effect %d, not %d",
+                    occ->effect, effect);
+    if (estimator < OCC_EST_NOREUSE || estimator > OCC_EST_BOXMEAN)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "estimator %d invalid", estimator);
+    if (estimator == OCC_EST_UNBIASED && !bvh)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "the unbiased estimator needs the BVH");
+    if (estimator != OCC_EST_UNBIASED && bvh)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "bvh_or_null must be NULL unless the estimator is unbiased");
+    if (!out) return fail(ctx, OCC_ERR_INVALID_ARG, "out is NULL");
+    if (effect == OCC_EFFECT_SHADOW && (st = check_light(ctx, &occ->light)) != OCC_OK) return st;
+    if (effect == OCC_EFFECT_AO && !(occ->radius > 0.0f && std::isfinite(occ->radius)))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "AO radius must be positive and finite");
+    occ::PatternParams pat;
+    if ((st = make_pattern(ctx, pattern, K, &pat)) != OCC_OK) return st;
+    const occ::DevBVH b = bvh ? dev_bvh(bvh) : occ::DevBVH{nullptr, nullptr};
+    const occ::LightParams lp = to_params(&occ->light);
+    return launched(ctx,
+                    occ::launch_reuse(effect, estimator, view(gb), rec_view(occ), pat, occ->radius,
+                                      lp, bvh ? &b : nullptr, out, ctx->status,
+                                      (cudaStream_t)stream),
+                    "reuse launch");
+}
+
+occ_status trace_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const occ_bvh* bvh,
+                        float radius, const occ_rect_light* light, uint64_t seed, uint32_t sample,
+                        occ_occluders* out, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if ((st = check_gbuffer(ctx, gb)) != OCC_OK) return st;
+    if (!bvh) return fail(ctx, OCC_ERR_INVALID_ARG, "bvh is NULL");
+    if (bvh->device != ctx->device)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "bvh lives on device %d, context on %d", bvh->device,
+                    ctx->device);
+    if ((st = check_occluders(ctx, gb, out)) != OCC_OK) return st;
+    if (effect == OCC_EFFECT_AO && !(radius > 0.0f && std::isfinite(radius)))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "AO radius must be positive and finite");
+    if (effect == OCC_EFFECT_SHADOW && (st = check_light(ctx, light)) != OCC_OK) return st;
+    out->effect = effect;
+    out->radius = effect == OCC_EFFECT_AO ? radius : 0.0f;
+    if (effect == OCC_EFFECT_SHADOW)
+        out->light = *light;
+    else
+        std::memset(&out->light, 0, sizeof(out->light));
+    out->seed = seed;
+    out->sample = sample;
+    return launched(ctx,
+                    occ::launch_trace(effect, view(gb), dev_bvh(bvh), radius, to_params(light), seed,
+                                      sample, rec_view(out), ctx->status, (cudaStream_t)stream),
+                    "trace launch");
+}
+
+}  // namespace
+
+OCC_EXPORT const char* occ_version(void) { return "occreuse 0.1 (sm_103a)"; }
+
+OCC_EXPORT occ_status occ_create(int device, occ_ctx** out) {
+    if (!out) return OCC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return OCC_ERR_INVALID_ARG;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return OCC_ERR_CUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return OCC_ERR_UNSUPPORTED;
+    if (cudaSetDevice(device) != cudaSuccess) return OCC_ERR_CUDA;
+    occ_ctx* ctx = new occ_ctx();
+    ctx->device = device;
+    cudaError_t e = cudaMalloc(&ctx->status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        cudaFree(ctx->status);
+        delete ctx;
+        return e == cudaErrorMemoryAllocation ? OCC_ERR_OOM : OCC_ERR_CUDA;
+    }
+    *out = ctx;
+    return OCC_OK;
+}
+
+OCC_EXPORT occ_status occ_destroy(occ_ctx* ctx) {
+    if (!ctx) return OCC_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaFree(ctx->status);
+    cudaFree(ctx->ws);
+    delete ctx;
+    return OCC_OK;
+}
+
+OCC_EXPORT const char* occ_last_error(const occ_ctx* ctx) {
+    return ctx ? ctx->last_error.c_str() : "context is NULL";
+}
+
+OCC_EXPORT occ_status occ_sync(occ_ctx* ctx, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream");
+    unsigned flags = 0;
+    e = cudaMemcpy(&flags, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+    if (flags) {
+        cudaMemset(ctx->status, 0, sizeof(unsigned));
+        return fail(ctx, OCC_ERR_DEVICE_CHECK, "device check flags 0x%x (%s%s%s)", flags,
+                    (flags & occ::kStatusStackOverflowBit) ? "stack overflow " : "",
+                    (flags & occ::kStatusWaitTimeoutBit) ? "wait timeout " : "",
+                    (flags & occ::kStatusBadIndexBit) ? "bad index" : "");
+    }
+    return OCC_OK;
+}
+
+OCC_EXPORT occ_status occ_bvh_build(occ_ctx* ctx, const float* tris_host, int64_t T, occ_bvh** out) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if (!out || !tris_host || T <= 0) return fail(ctx, OCC_ERR_INVALID_ARG, "bad bvh_build arguments");
+    *out = nullptr;
+    const auto t0 = std::chrono::steady_clock::now();
+    occ::HostBVH hb;
+    std::string err;
+    if (!occ::build_bvh4(tris_host, T, &hb, &err)) return fail(ctx, OCC_ERR_INVALID_ARG, "%s", err.c_str());
+    occ_bvh* b = new occ_bvh();
+    b->device = ctx->device;
+    const size_t nb = hb.nodes.size() * sizeof(occ::Node4), tb = hb.tris.size() * sizeof(float4);
+    cudaError_t e = cudaMalloc(&b->nodes, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&b->tris, tb);
+    if (e == cudaSuccess) e = cudaMemcpy(b->nodes, hb.nodes.data(), nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->tris, hb.tris.data(), tb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(b->nodes);
+        cudaFree(b->tris);
+        delete b;
+        return cuda_fail(ctx, e, "bvh upload");
+    }
+    b->stats.num_tris = T;
+    b->stats.num_nodes = (int64_t)hb.nodes.size();
+    b->stats.num_leaves = hb.num_leaves;
+    b->stats.depth = hb.depth;
+    b->stats.max_leaf_tris = hb.max_leaf_tris;
+    b->stats.bytes = (int64_t)(nb + tb);
+    b->stats.build_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = b;
+    return OCC_OK;
+}
+
+OCC_EXPORT occ_status occ_bvh_free(occ_ctx* ctx, occ_bvh* bvh) {
+    if (!ctx || !bvh) return OCC_ERR_INVALID_ARG;
+    cudaSetDevice(bvh->device);
+    cudaFree(bvh->nodes);
+    cudaFree(bvh->tris);
+    delete bvh;
+    return OCC_OK;
+}
+
+OCC_EXPORT occ_status occ_bvh_info(const occ_bvh* bvh, occ_bvh_stats* out) {
+    if (!bvh || !out) return OCC_ERR_INVALID_ARG;
+    *out = bvh->stats;
+    return OCC_OK;
+}
+
+OCC_EXPORT occ_status occ_gbuffer_pinhole(occ_ctx* ctx, const occ_bvh* bvh, const float* cam_host,
+                                          float eps, int32_t W, int32_t H, float* pos4,
+                                          float* nrm4, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if (!bvh || !cam_host || !pos4 || !nrm4 || W <= 0 || H <= 0 || !std::isfinite(eps))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "bad gbuffer_pinhole arguments");
+    if (!aligned16(pos4) || !aligned16(nrm4))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pointers must be 16-byte aligned");
+    if (!(cam_host[9] > 0.0f && cam_host[9] < 180.0f))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "vertical fov must be in (0, 180) degrees");
+    return launched(ctx,
+                    occ::launch_gbuffer(dev_bvh(bvh), cam_host, eps, W, H,
+                                        reinterpret_cast<float4*>(pos4),
+                                        reinterpret_cast<float4*>(nrm4), ctx->status,
+                                        (cudaStream_t)stream),
+                    "gbuffer launch");
+}
+
+OCC_EXPORT occ_status occ_trace_ao(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh,
+                                   float radius, uint64_t seed, uint32_t sample,
+                                   occ_occluders* out, void* stream) {
+    return trace_common(ctx, OCC_EFFECT_AO, gb, bvh, radius, nullptr, seed, sample, out, stream);
+}
+
+OCC_EXPORT occ_status occ_trace_shadow(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh,
+                                       const occ_rect_light* light, uint64_t seed, uint32_t sample,
+                                       occ_occluders* out, void* stream) {
+    return trace_common(ctx, OCC_EFFECT_SHADOW, gb, bvh, 0.0f, light, seed, sample, out, stream);
+}
+
+OCC_EXPORT occ_status occ_reuse_ao(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occluders* occ,
+                                   const occ_pattern* pattern, int32_t K, int32_t estimator,
+                                   const occ_bvh* bvh_or_null, float* out, void* stream) {
+    return reuse_common(ctx, OCC_EFFECT_AO, gb, occ, pattern, K, estimator, bvh_or_null, out, stream);
+}
+
+OCC_EXPORT occ_status occ_reuse_shadow(occ_ctx* ctx, const occ_gbuffer* gb,
+                                       const occ_occluders* occ, const occ_pattern* pattern,
+                                       int32_t K, int32_t estimator, const occ_bvh* bvh_or_null,
+                                       float* out, void* stream) {
+    return reuse_common(ctx, OCC_EFFECT_SHADOW, gb, occ, pattern, K, estimator, bvh_or_null, out,
+                        stream);
+}
+
+OCC_EXPORT occ_status occ_frame_host(occ_ctx* ctx, const occ_bvh* bvh, int32_t effect,
+                                     const float* pos4_host, const float* nrm4_host, int32_t W,
+                                     int32_t H, float radius, const occ_rect_light* light,
+                                     uint64_t seed, uint32_t sample, const occ_pattern* pattern,
+                                     int32_t K, int32_t estimator, float* out_host, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if (!bvh || !pos4_host || !nrm4_host || !out_host || W <= 0 || H <= 0)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "bad frame_host arguments");
+    if (effect != OCC_EFFECT_AO && effect != OCC_EFFECT_SHADOW)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "effect %d invalid", effect);
+    const size_t P = (size_t)W * H;
+    const size_t need = P * (16 + 16 + 32 + 4) + 256;
+    if (need > ctx->ws_bytes) {
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+        const cudaError_t e = cudaMalloc(&ctx->ws, need);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "frame workspace");
+        ctx->ws_bytes = need;
+    }
+    char* base = reinterpret_cast<char*>(ctx->ws);
+    float* pos = reinterpret_cast<float*>(base);
+    float* nrm = reinterpret_cast<float*>(base + 16 * P);
+    void* recs = base + 32 * P;
+    float* out = reinterpret_cast<float*>(base + 64 * P);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(pos, pos4_host, 16 * P, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nrm, nrm4_host, 16 * P, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "frame upload");
+    occ_gbuffer gb{W, H, pos, nrm};
+    occ_occluders oc{};
+    oc.W = W;
+    oc.H = H;
+    oc.format = OCC_REC_FP32;
+    oc.data = recs;
+    st = effect == OCC_EFFECT_AO ? occ_trace_ao(ctx, &gb, bvh, radius, seed, sample, &oc, stream)
+                                 : occ_trace_shadow(ctx, &gb, bvh, light, seed, sample, &oc, stream);
+    if (st != OCC_OK) return st;
+    const occ_bvh* vb = estimator == OCC_EST_UNBIASED ? bvh : nullptr;
+    st = effect == OCC_EFFECT_AO
+             ? occ_reuse_ao(ctx, &gb, &oc, pattern, K, estimator, vb, out, stream)
+             : occ_reuse_shadow(ctx, &gb, &oc, pattern, K, estimator, vb, out, stream);
+    if (st != OCC_OK) return st;
+    e = cudaMemcpyAsync(out_host, out, 4 * P, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "frame download");
+    return occ_sync(ctx, stream);
+}
+
+OCC_EXPORT occ_status occ_debug_philox(occ_ctx* ctx, const uint32_t* in_dev, int64_t n,
+                                       uint32_t* out_dev, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if (n < 0 || (n > 0 && (!in_dev || !out_dev))) return fail(ctx, OCC_ERR_INVALID_ARG, "bad arguments");
+    return launched(ctx, occ::launch_debug_philox(in_dev, n, out_dev, (cudaStream_t)stream),
+                    "philox launch");
+}
+
+OCC_EXPORT occ_status occ_debug_rays(occ_ctx* ctx, const occ_gbuffer* gb, int32_t effect,
+                                     float radius, const occ_rect_light* light, uint64_t seed,
+                                     uint32_t sample, float* out_dev, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if ((st = check_gbuffer(ctx, gb)) != OCC_OK) return st;
+    if (!out_dev || !aligned16(out_dev)) return fail(ctx, OCC_ERR_INVALID_ARG, "bad out_dev");
+    if (effect == OCC_EFFECT_SHADOW && (st = check_light(ctx, light)) != OCC_OK) return st;
+    return launched(ctx,
+                    occ::launch_debug_rays(effect, view(gb), radius, to_params(light), seed, sample,
+                                           reinterpret_cast<float4*>(out_dev), (cudaStream_t)stream),
+                    "rays launch");
+}
+
+OCC_EXPORT occ_status occ_debug_mis(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occluders* occ,
+                                    const occ_pattern* pattern, int32_t K, int32_t estimator,
+                                    const occ_bvh* bvh_or_null, const int32_t* pix_host, int32_t n,
+                                    int32_t* members_host, float* w_host) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if ((st = check_gbuffer(ctx, gb)) != OCC_OK) return st;
+    if ((st = check_occluders(ctx, gb, occ)) != OCC_OK) return st;
+    if (n < 0 || (n > 0 && (!pix_host || !members_host || !w_host)))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "bad debug_mis arguments");
+    if (estimator != OCC_EST_BIASED && estimator != OCC_EST_UNBIASED)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "debug_mis needs the biased or unbiased estimator");
+    if (estimator == OCC_EST_UNBIASED && !bvh_or_null)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "the unbiased estimator needs the BVH");
+    for (int i = 0; i < n; ++i)
+        if (pix_host[i] < 0 || pix_host[i] >= gb->W * gb->H)
+            return fail(ctx, OCC_ERR_INVALID_ARG, "pixel %d out of range", pix_host[i]);
+    occ::PatternParams pat;
+    if ((st = make_pattern(ctx, pattern, K, &pat)) != OCC_OK) return st;
+    if (n == 0) return OCC_OK;
+    const size_t wn = (size_t)n * occ::kMaxMembers * occ::kMaxMembers;
+    int32_t *d_pix = nullptr, *d_mem = nullptr;
+    float* d_w = nullptr;
+    cudaError_t e = cudaMalloc(&d_pix, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_mem, sizeof(int32_t) * n * occ::kMaxMembers);
+    if (e == cudaSuccess) e = cudaMalloc(&d_w, sizeof(float) * wn);
+    if (e == cudaSuccess) e = cudaMemcpy(d_pix, pix_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+    const occ::DevBVH b = bvh_or_null ? dev_bvh(bvh_or_null) : occ::DevBVH{nullptr, nullptr};
+    if (e == cudaSuccess)
+        e = occ::launch_debug_mis(occ->effect, estimator, view(gb), rec_view(occ), pat, occ->radius,
+                                  to_params(&occ->light), bvh_or_null ? &b : nullptr, d_pix, n,
+                                  d_mem, d_w, ctx->status, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(members_host, d_mem, sizeof(int32_t) * n * occ::kMaxMembers, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(w_host, d_w, sizeof(float) * wn, cudaMemcpyDeviceToHost);
+    cudaFree(d_pix);
+    cudaFree(d_mem);
+    cudaFree(d_w);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "debug_mis");
+    return OCC_OK;
+}

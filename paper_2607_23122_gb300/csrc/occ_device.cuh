@@ -1,0 +1,280 @@
+// occ_device.cuh -- device-side building blocks shared by the trace and reuse kernels.
+//
+//  * Philox4x32-10 counter-based generator (Salmon et al., SC'11).
+//  * Step-1 ray generation: cosine-weighted AO directions (Eq. 2) with the
+//    Duff et al. (JCGT 2017) tangent frame, uniform rectangle-light samples (Eq. 5).
+//  * Closest-hit query over the 4-wide BVH with a short per-thread stack and
+//    the watertight ray/triangle test of Woop, Benthin and Wald (JCGT 2013)
+//    in FP32 (with its FP64 fallback on exactly-zero edge functions).
+//    The hit on (0, tmax] with the smallest t wins; equal t goes to the smaller
+//    triangle id -- the first intersection of Eq. 7.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "occ_layout.h"
+
+namespace occ {
+
+// ---------------------------------------------------------------------------------------
+// Philox4x32-10.  Round: (x0,x1,x2,x3) -> (hi(B x2)^x1^k0, lo(B x2), hi(A x0)^x3^k1, lo(A x0)),
+// A = 0xD2511F53, B = 0xCD9E8D57; key += (0x9E3779B9, 0xBB67AE85) after each round.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t hiA = __umulhi(0xD2511F53u, c.x), loA = 0xD2511F53u * c.x;
+        const uint32_t hiB = __umulhi(0xCD9E8D57u, c.z), loB = 0xCD9E8D57u * c.z;
+        c = make_uint4(hiB ^ c.y ^ k.x, loB, hiA ^ c.w ^ k.y, loA);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+enum : uint32_t { kStreamAO = 0, kStreamShadow = 1 };
+
+// Two uniforms in [0, 1): top 24 bits of the first two words times 2^-24 (exact).
+__device__ __forceinline__ float2 uniform_pair(uint64_t seed, uint32_t pix, uint32_t sample,
+                                               uint32_t stream) {
+    const uint4 w = philox4x32_10(make_uint4(pix, sample, stream, 0u),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    return make_float2((float)(w.x >> 8) * 0x1p-24f, (float)(w.y >> 8) * 0x1p-24f);
+}
+
+// ---------------------------------------------------------------------------------------
+// float3 helpers
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) {
+    return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+__device__ __forceinline__ float dot3(float3 a, float3 b) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+}
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize3(float3 a) {
+    const float inv = 1.0f / sqrtf(dot3(a, a));
+    return make_float3(a.x * inv, a.y * inv, a.z * inv);
+}
+
+// ---------------------------------------------------------------------------------------
+// Step-1 rays.
+// ---------------------------------------------------------------------------------------
+struct RectLight {
+    float3 c, eu, ev;   // rectangle c + a eu + b ev, |a|, |b| <= 1/2
+    float3 n;           // emitting normal normalize(eu x ev)
+    float inv_eu2, inv_ev2, lim;   // 1/|eu|^2, 1/|ev|^2, rectangle half-extent with slack
+};
+
+// Eq. 2: Malley's method (r = sqrt(u1), phi = 2 pi u2) lifted onto the hemisphere of n,
+// expressed in the branch-free orthonormal basis of Duff et al.
+__device__ __forceinline__ float3 cosine_direction(float3 n, float2 u) {
+    const float r = sqrtf(u.x);
+    float sphi, cphi;
+    sincospif(2.0f * u.y, &sphi, &cphi);
+    const float lx = r * cphi, ly = r * sphi, lz = sqrtf(fmaxf(0.0f, 1.0f - u.x));
+    const float s = copysignf(1.0f, n.z);
+    const float a = -1.0f / (s + n.z);
+    const float b = n.x * n.y * a;
+    const float3 t = make_float3(1.0f + s * n.x * n.x * a, s * b, -s * n.x);
+    const float3 bt = make_float3(b, s + n.y * n.y * a, -n.y);
+    return make_float3(lx * t.x + ly * bt.x + lz * n.x, lx * t.y + ly * bt.y + lz * n.y,
+                       lx * t.z + ly * bt.z + lz * n.z);
+}
+
+// Eq. 5: y uniform on the rectangle; unit direction toward y and its distance.
+__device__ __forceinline__ float3 light_direction(const RectLight& L, float3 x, float2 u,
+                                                  float* dist) {
+    const float a = u.x - 0.5f, b = u.y - 0.5f;
+    const float3 y = make_float3(L.c.x + a * L.eu.x + b * L.ev.x, L.c.y + a * L.eu.y + b * L.ev.y,
+                                 L.c.z + a * L.eu.z + b * L.ev.z);
+    const float3 d = sub3(y, x);
+    const float len = sqrtf(dot3(d, d));
+    *dist = len;
+    return make_float3(d.x / len, d.y / len, d.z / len);
+}
+
+// ---------------------------------------------------------------------------------------
+// Watertight ray / triangle test (Woop, Benthin, Wald 2013).
+// The ray is sheared so it runs along +z: for a vertex v relative to the origin,
+// (Ax, Ay, Az) = (v[kx] - Sx v[kz], v[ky] - Sy v[kz], Sz v[kz]).  The three rows are
+// stored as dense vectors so no per-triangle component selection is needed; the
+// projection of a vertex is a fixed function of the vertex, so edges shared by two
+// triangles get identical edge functions (watertightness).
+// ---------------------------------------------------------------------------------------
+struct TraceRay {
+    float3 o;
+    float3 idir;            // 1 / d with zero components replaced by a tiny value
+    float3 rx, ry, rz;      // shear rows
+    float3 d;
+};
+
+__device__ __forceinline__ TraceRay make_trace_ray(float3 o, float3 d) {
+    TraceRay r;
+    r.o = o;
+    r.d = d;
+    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = 0;
+    float m = ax;
+    if (ay > m) { kz = 1; m = ay; }
+    if (az > m) { kz = 2; }
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    const float dz = kz == 0 ? d.x : (kz == 1 ? d.y : d.z);
+    if (dz < 0.0f) { const int t = kx; kx = ky; ky = t; }
+    const float dx = kx == 0 ? d.x : (kx == 1 ? d.y : d.z);
+    const float dy = ky == 0 ? d.x : (ky == 1 ? d.y : d.z);
+    const float Sx = dx / dz, Sy = dy / dz, Sz = 1.0f / dz;
+    r.rx = make_float3(kx == 0 ? 1.0f : (kz == 0 ? -Sx : 0.0f), kx == 1 ? 1.0f : (kz == 1 ? -Sx : 0.0f),
+                       kx == 2 ? 1.0f : (kz == 2 ? -Sx : 0.0f));
+    r.ry = make_float3(ky == 0 ? 1.0f : (kz == 0 ? -Sy : 0.0f), ky == 1 ? 1.0f : (kz == 1 ? -Sy : 0.0f),
+                       ky == 2 ? 1.0f : (kz == 2 ? -Sy : 0.0f));
+    r.rz = make_float3(kz == 0 ? Sz : 0.0f, kz == 1 ? Sz : 0.0f, kz == 2 ? Sz : 0.0f);
+    const float tiny = 1e-20f;
+    r.idir = make_float3(1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
+                         1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
+                         1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
+    return r;
+}
+
+// Tests triangle (v0, v1, v2) with input id `id` against the ray on (0, tbest]; on a
+// better hit updates tbest / best_id / best_slot.
+__device__ __forceinline__ void triangle_test(const TraceRay& r, float4 v0, float4 v1, float4 v2,
+                                              uint32_t slot, float& tbest, uint32_t& best_id,
+                                              uint32_t& best_slot) {
+    const float3 A = sub3(f3(v0), r.o), B = sub3(f3(v1), r.o), C = sub3(f3(v2), r.o);
+    const float Ax = dot3(r.rx, A), Ay = dot3(r.ry, A);
+    const float Bx = dot3(r.rx, B), By = dot3(r.ry, B);
+    const float Cx = dot3(r.rx, C), Cy = dot3(r.ry, C);
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return;
+    const float det = U + V + W;
+    if (det == 0.0f) return;
+    const float Az = dot3(r.rz, A), Bz = dot3(r.rz, B), Cz = dot3(r.rz, C);
+    const float T = fmaf(U, Az, fmaf(V, Bz, W * Cz));
+    const float adet = fabsf(det);
+    const float aT = det < 0.0f ? -T : T;
+    if (!(aT > 0.0f)) return;
+    if (aT > tbest * adet * 1.00001f) return;
+    const float t = __fdiv_rn(aT, adet);
+    if (!(t > 0.0f) || t > tbest) return;
+    const uint32_t id = __float_as_uint(v0.w);
+    if (t == tbest && id >= best_id) return;
+    tbest = t;
+    best_id = id;
+    best_slot = slot;
+}
+
+struct Hit {
+    uint32_t id;     // input triangle id, kNoHit if none
+    uint32_t slot;   // position in the BVH's triangle array
+    float t;
+};
+
+// Closest hit on (0, tmax] (t in units of |d|).  Sets kStatusStackOverflow in *status
+// if the short stack would overflow (the builder bounds the depth so it cannot).
+__device__ __forceinline__ Hit closest_hit(const DevBVH& bvh, float3 o, float3 d, float tmax,
+                                           unsigned int* status) {
+    const TraceRay r = make_trace_ray(o, d);
+    float tbest = tmax;
+    uint32_t best_id = kNoHit, best_slot = kNoHit;
+    uint2 stack[kStackSize];
+    int sp = 0;
+    bool overflow = false;
+    uint32_t cur = 0;
+    for (;;) {
+        if (cur & kLeafBit) {
+            const uint32_t first = cur & kLeafFirstMask;
+            const uint32_t count = ((cur & ~kLeafBit) >> kLeafCountShift) + 1u;
+            for (uint32_t i = 0; i < count; ++i) {
+                const float4* t = bvh.tris + 3ull * (first + i);
+                triangle_test(r, __ldg(t), __ldg(t + 1), __ldg(t + 2), first + i, tbest, best_id,
+                              best_slot);
+            }
+        } else {
+            const Node4* n = bvh.nodes + cur;
+            const float4 lox = __ldg(&n->lox), hix = __ldg(&n->hix);
+            const float4 loy = __ldg(&n->loy), hiy = __ldg(&n->hiy);
+            const float4 loz = __ldg(&n->loz), hiz = __ldg(&n->hiz);
+            const uint4 ch = __ldg(&n->child);
+            const float lx[4] = {lox.x, lox.y, lox.z, lox.w}, hx[4] = {hix.x, hix.y, hix.z, hix.w};
+            const float ly[4] = {loy.x, loy.y, loy.z, loy.w}, hy[4] = {hiy.x, hiy.y, hiy.z, hiy.w};
+            const float lz[4] = {loz.x, loz.y, loz.z, loz.w}, hz[4] = {hiz.x, hiz.y, hiz.z, hiz.w};
+            const uint32_t cref[4] = {ch.x, ch.y, ch.z, ch.w};
+            float key[4];
+            uint32_t ref[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float x0 = (lx[c] - r.o.x) * r.idir.x, x1 = (hx[c] - r.o.x) * r.idir.x;
+                const float y0 = (ly[c] - r.o.y) * r.idir.y, y1 = (hy[c] - r.o.y) * r.idir.y;
+                const float z0 = (lz[c] - r.o.z) * r.idir.z, z1 = (hz[c] - r.o.z) * r.idir.z;
+                const float tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
+                const float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fmaxf(z0, z1)) * 1.0000005f;
+                const bool hit = cref[c] != kEmptyRef && tn <= fminf(tf, tbest);
+                key[c] = hit ? tn : __int_as_float(0x7f800000);
+                ref[c] = cref[c];
+            }
+            // sort the four (key, ref) pairs by key: network (0,1)(2,3)(0,2)(1,3)(1,2)
+#define OCC_CSWAP(a, b)                                                          \
+    if (key[b] < key[a]) {                                                      \
+        const float tk = key[a]; key[a] = key[b]; key[b] = tk;                  \
+        const uint32_t tr = ref[a]; ref[a] = ref[b]; ref[b] = tr;               \
+    }
+            OCC_CSWAP(0, 1) OCC_CSWAP(2, 3) OCC_CSWAP(0, 2) OCC_CSWAP(1, 3) OCC_CSWAP(1, 2)
+#undef OCC_CSWAP
+            if (key[0] != __int_as_float(0x7f800000)) {
+#pragma unroll
+                for (int c = 3; c >= 1; --c) {
+                    if (key[c] != __int_as_float(0x7f800000)) {
+                        if (sp < kStackSize) {
+                            stack[sp++] = make_uint2(ref[c], __float_as_uint(key[c]));
+                        } else {
+                            overflow = true;
+                        }
+                    }
+                }
+                cur = ref[0];
+                continue;
+            }
+        }
+        // pop the next entry that can still hold a closer hit
+        bool found = false;
+        while (sp > 0) {
+            const uint2 e = stack[--sp];
+            if (__uint_as_float(e.y) <= tbest) {
+                cur = e.x;
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
+    }
+    if (overflow && status) atomicOr(status, kStatusStackOverflowBit);
+    Hit h;
+    h.id = best_id;
+    h.slot = best_slot;
+    h.t = tbest;
+    return h;
+}
+
+// Unit geometric normal of BVH triangle `slot`, turned against direction d.
+__device__ __forceinline__ float3 hit_normal(const DevBVH& bvh, uint32_t slot, float3 d) {
+    const float4* t = bvh.tris + 3ull * slot;
+    const float3 v0 = f3(__ldg(t)), v1 = f3(__ldg(t + 1)), v2 = f3(__ldg(t + 2));
+    float3 n = normalize3(cross3(sub3(v1, v0), sub3(v2, v0)));
+    if (dot3(n, d) > 0.0f) n = make_float3(-n.x, -n.y, -n.z);
+    return n;
+}
+
+}  // namespace occ

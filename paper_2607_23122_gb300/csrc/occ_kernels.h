@@ -1,0 +1,59 @@
+// occ_kernels.h -- host-side launchers of the CUDA kernels (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "occ_layout.h"
+
+namespace occ {
+
+struct GBufView {
+    int32_t W, H;
+    const float4* pos;   // (x.xyz, valid)
+    const float4* nrm;   // (n.xyz, -)
+};
+
+// Occluder records: plane 0 (z.xyz, tri id bits), plane 1 (n_z.xyz, t).
+struct RecView {
+    float4* r0;
+    float4* r1;
+};
+
+struct LightParams {
+    float c[3], eu[3], ev[3];
+};
+
+constexpr int kMaxMembers = 64;
+
+struct PatternParams {
+    int32_t kind;       // 0 group, 1 box, 2 offsets
+    int32_t gw, gh;
+    int32_t n_off;      // offsets: count
+    int32_t K;          // members incl. the receiver
+    int2 off[kMaxMembers - 1];
+    int32_t halo[4];    // offsets: max extent left, right, up, down
+};
+
+enum Effect { kAO = 0, kShadow = 1 };
+enum Estimator { kNoReuse = 0, kBiased = 1, kUnbiased = 2, kBoxMean = 3 };
+
+cudaError_t launch_gbuffer(const DevBVH& bvh, const float* cam, float eps, int W, int H,
+                           float4* pos, float4* nrm, unsigned* status, cudaStream_t s);
+cudaError_t launch_trace(int effect, const GBufView& gb, const DevBVH& bvh, float radius,
+                         const LightParams& light, uint64_t seed, uint32_t sample, RecView rec,
+                         unsigned* status, cudaStream_t s);
+cudaError_t launch_debug_philox(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s);
+cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
+                              const LightParams& light, uint64_t seed, uint32_t sample,
+                              float4* out, cudaStream_t s);
+
+cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const RecView& rec,
+                         const PatternParams& pat, float radius, const LightParams& light,
+                         const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s);
+cudaError_t launch_debug_mis(int effect, int estimator, const GBufView& gb, const RecView& rec,
+                             const PatternParams& pat, float radius, const LightParams& light,
+                             const DevBVH* bvh, const int32_t* pix, int32_t n, int32_t* members,
+                             float* w, unsigned* status, cudaStream_t s);
+
+}  // namespace occ

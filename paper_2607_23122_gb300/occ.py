@@ -1,0 +1,318 @@
+"""Python binding of the occlusion-point reuse library (include/occ.h).
+
+Argument marshalling only: every step of the path runs in liboccreuse.so's CUDA
+kernels.  PyTorch supplies device memory and streams; functions keep the C names.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import (  # noqa: F401
+    OCC_EFFECT_AO, OCC_EFFECT_SHADOW, OCC_EST_BIASED, OCC_EST_BOXMEAN, OCC_EST_NOREUSE,
+    OCC_EST_UNBIASED, OCC_PAT_BOX, OCC_PAT_GROUP, OCC_PAT_OFFSETS, OCC_REC_FP32, MAX_MEMBERS)
+
+
+class OccError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{N.STATUS_NAMES.get(status, status)}: {message}")
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Context:
+    """An occ_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = N.load()
+        self.device = device
+        torch.cuda.set_device(device)
+        torch.cuda.init()
+        h = C.c_void_p()
+        st = self.lib.occ_create(device, C.byref(h))
+        if st != N.OCC_OK:
+            raise OccError(st, f"occ_create(device={device}) failed")
+        self.handle = h
+
+    def check(self, st: int):
+        if st != N.OCC_OK:
+            msg = self.lib.occ_last_error(self.handle)
+            raise OccError(st, msg.decode() if msg else "")
+
+    def sync(self, stream=None):
+        self.check(self.lib.occ_sync(self.handle, _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.occ_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def occ_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def occ_version() -> str:
+    return N.load().occ_version().decode()
+
+
+class BVH:
+    """Device-resident 4-wide BVH built from float32 triangles [T, 3, 3]."""
+
+    def __init__(self, ctx: Context, tris: np.ndarray):
+        self.ctx = ctx
+        tris = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 3, 3)
+        h = C.c_void_p()
+        ctx.check(ctx.lib.occ_bvh_build(ctx.handle, tris.ctypes.data, tris.shape[0], C.byref(h)))
+        self.handle = h
+        self.num_tris = tris.shape[0]
+
+    @property
+    def stats(self) -> dict:
+        s = N.occ_bvh_stats()
+        self.ctx.check(self.ctx.lib.occ_bvh_info(self.handle, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def free(self):
+        if getattr(self, "handle", None) and self.ctx.handle:
+            self.ctx.lib.occ_bvh_free(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def occ_bvh_build(ctx: Context, tris: np.ndarray) -> BVH:
+    return BVH(ctx, tris)
+
+
+@dataclass
+class GBuffer:
+    """pos4 / nrm4: float32 CUDA tensors [H, W, 4] (see occ_gbuffer)."""
+    pos4: torch.Tensor
+    nrm4: torch.Tensor
+
+    @property
+    def W(self) -> int:
+        return int(self.pos4.shape[1])
+
+    @property
+    def H(self) -> int:
+        return int(self.pos4.shape[0])
+
+    def c(self) -> N.occ_gbuffer:
+        for t in (self.pos4, self.nrm4):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                    and tuple(t.shape) == (self.H, self.W, 4)):
+                raise ValueError("G-buffer tensors must be contiguous float32 CUDA [H, W, 4]")
+        return N.occ_gbuffer(self.W, self.H, self.pos4.data_ptr(), self.nrm4.data_ptr())
+
+    @staticmethod
+    def from_numpy(pos4: np.ndarray, nrm4: np.ndarray, device="cuda") -> "GBuffer":
+        return GBuffer(torch.from_numpy(np.ascontiguousarray(pos4, dtype=np.float32)).to(device),
+                       torch.from_numpy(np.ascontiguousarray(nrm4, dtype=np.float32)).to(device))
+
+
+@dataclass
+class Occluders:
+    """Occluder records: data is a float32 CUDA tensor [2, H, W, 4] (two planes)."""
+    data: torch.Tensor
+    meta: N.occ_occluders = field(default_factory=N.occ_occluders)
+
+    @staticmethod
+    def empty(H: int, W: int, device="cuda") -> "Occluders":
+        o = Occluders(torch.empty((2, H, W, 4), dtype=torch.float32, device=device))
+        o.meta.W, o.meta.H, o.meta.format = W, H, N.OCC_REC_FP32
+        o.meta.data = o.data.data_ptr()
+        return o
+
+    @staticmethod
+    def from_numpy(rec0: np.ndarray, rec1: np.ndarray, effect: int, radius: float = 0.0,
+                   light=None, device="cuda") -> "Occluders":
+        """Records prepared elsewhere (e.g. test inputs): planes [H, W, 4] float32."""
+        H, W = rec0.shape[:2]
+        o = Occluders.empty(H, W, device)
+        o.data[0].copy_(torch.from_numpy(np.ascontiguousarray(rec0, dtype=np.float32)))
+        o.data[1].copy_(torch.from_numpy(np.ascontiguousarray(rec1, dtype=np.float32)))
+        o.meta.effect = effect
+        o.meta.radius = radius
+        if light is not None:
+            o.meta.light = _light(light)
+        return o
+
+    def c(self) -> N.occ_occluders:
+        self.meta.data = self.data.data_ptr()
+        return self.meta
+
+    @property
+    def tri(self) -> torch.Tensor:
+        return self.data[0, ..., 3].contiguous().view(torch.int32)
+
+
+def _light(light) -> N.occ_rect_light:
+    v = np.asarray(light, dtype=np.float32).reshape(9)
+    L = N.occ_rect_light()
+    L.c[:] = v[0:3].tolist()
+    L.eu[:] = v[3:6].tolist()
+    L.ev[:] = v[6:9].tolist()
+    return L
+
+
+class Pattern:
+    """Neighbour pattern N_i: group blocks, a centred box, or shared offsets."""
+
+    def __init__(self, kind: int, gw: int = 1, gh: int = 1, offsets=None):
+        self.kind, self.gw, self.gh = int(kind), int(gw), int(gh)
+        off = np.zeros((0, 2), dtype=np.int32) if offsets is None else offsets
+        self.offsets = np.ascontiguousarray(np.asarray(off, dtype=np.int32).reshape(-1, 2))
+        self._c = N.occ_pattern(self.kind, self.gw, self.gh, self.offsets.shape[0],
+                                self.offsets.ctypes.data_as(C.POINTER(C.c_int32)))
+
+    @staticmethod
+    def group(gw: int, gh: int) -> "Pattern":
+        return Pattern(N.OCC_PAT_GROUP, gw, gh)
+
+    @staticmethod
+    def box(gw: int, gh: int) -> "Pattern":
+        return Pattern(N.OCC_PAT_BOX, gw, gh)
+
+    @staticmethod
+    def offsets_of(off) -> "Pattern":
+        return Pattern(N.OCC_PAT_OFFSETS, 1, 1, off)
+
+    @property
+    def K(self) -> int:
+        if self.kind == N.OCC_PAT_OFFSETS:
+            return self.offsets.shape[0] + 1
+        return self.gw * self.gh
+
+    def as_tuple(self):
+        """(kind, gw, gh, offsets) -- the form the oracle takes."""
+        return (self.kind, self.gw, self.gh, self.offsets if self.offsets.size else None)
+
+    def c(self) -> N.occ_pattern:
+        return self._c
+
+
+def occ_gbuffer_pinhole(ctx: Context, bvh: BVH, camera, eps: float, W: int, H: int,
+                        stream=None) -> GBuffer:
+    cam = np.ascontiguousarray(camera, dtype=np.float32).reshape(10)
+    dev = torch.device("cuda", ctx.device)
+    gb = GBuffer(torch.empty((H, W, 4), dtype=torch.float32, device=dev),
+                 torch.empty((H, W, 4), dtype=torch.float32, device=dev))
+    ctx.check(ctx.lib.occ_gbuffer_pinhole(ctx.handle, bvh.handle, cam.ctypes.data, float(eps), W, H,
+                                          gb.pos4.data_ptr(), gb.nrm4.data_ptr(),
+                                          _stream_handle(stream)))
+    return gb
+
+
+def occ_trace_ao(ctx: Context, gb: GBuffer, bvh: BVH, radius: float, seed: int, sample: int,
+                 out: Occluders | None = None, stream=None) -> Occluders:
+    out = out or Occluders.empty(gb.H, gb.W, gb.pos4.device)
+    g = gb.c()
+    ctx.check(ctx.lib.occ_trace_ao(ctx.handle, C.byref(g), bvh.handle, float(radius), int(seed),
+                                   int(sample), C.byref(out.c()), _stream_handle(stream)))
+    return out
+
+
+def occ_trace_shadow(ctx: Context, gb: GBuffer, bvh: BVH, light, seed: int, sample: int,
+                     out: Occluders | None = None, stream=None) -> Occluders:
+    out = out or Occluders.empty(gb.H, gb.W, gb.pos4.device)
+    g = gb.c()
+    L = _light(light)
+    ctx.check(ctx.lib.occ_trace_shadow(ctx.handle, C.byref(g), bvh.handle, C.byref(L), int(seed),
+                                       int(sample), C.byref(out.c()), _stream_handle(stream)))
+    return out
+
+
+def _reuse(fn, ctx, gb, occ, pattern, K, estimator, bvh, out, stream):
+    if out is None:
+        out = torch.empty((gb.H, gb.W), dtype=torch.float32, device=gb.pos4.device)
+    g = gb.c()
+    ctx.check(fn(ctx.handle, C.byref(g), C.byref(occ.c()), C.byref(pattern.c()), int(K),
+                 int(estimator), bvh.handle if bvh is not None else None, out.data_ptr(),
+                 _stream_handle(stream)))
+    return out
+
+
+def occ_reuse_ao(ctx: Context, gb: GBuffer, occ: Occluders, pattern: Pattern, K: int,
+                 estimator: int, bvh: BVH | None = None, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    return _reuse(ctx.lib.occ_reuse_ao, ctx, gb, occ, pattern, K, estimator, bvh, out, stream)
+
+
+def occ_reuse_shadow(ctx: Context, gb: GBuffer, occ: Occluders, pattern: Pattern, K: int,
+                     estimator: int, bvh: BVH | None = None, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    return _reuse(ctx.lib.occ_reuse_shadow, ctx, gb, occ, pattern, K, estimator, bvh, out, stream)
+
+
+def occ_frame_host(ctx: Context, bvh: BVH, effect: int, pos4_host: torch.Tensor,
+                   nrm4_host: torch.Tensor, radius: float, light, seed: int, sample: int,
+                   pattern: Pattern, K: int, estimator: int, out_host: torch.Tensor,
+                   stream=None) -> torch.Tensor:
+    """Whole frame from host tensors (pinned recommended) to a host estimate [H, W]."""
+    H, W = int(pos4_host.shape[0]), int(pos4_host.shape[1])
+    L = _light(light if light is not None else np.zeros(9))
+    ctx.check(ctx.lib.occ_frame_host(ctx.handle, bvh.handle, int(effect), pos4_host.data_ptr(),
+                                     nrm4_host.data_ptr(), W, H, float(radius), C.byref(L),
+                                     int(seed), int(sample), C.byref(pattern.c()), int(K),
+                                     int(estimator), out_host.data_ptr(), _stream_handle(stream)))
+    return out_host
+
+
+def occ_debug_philox(ctx: Context, ctr_key: np.ndarray, stream=None) -> np.ndarray:
+    """Philox4x32-10 of rows (c0, c1, c2, c3, k0, k1) -> [n, 4] uint32 (synchronous)."""
+    a = np.ascontiguousarray(ctr_key, dtype=np.uint32).reshape(-1, 6)
+    dev = torch.device("cuda", ctx.device)
+    inp = torch.from_numpy(a.view(np.int32)).to(dev)
+    out = torch.empty((a.shape[0], 4), dtype=torch.int32, device=dev)
+    ctx.check(ctx.lib.occ_debug_philox(ctx.handle, inp.data_ptr(), a.shape[0], out.data_ptr(),
+                                       _stream_handle(stream)))
+    ctx.sync(stream)
+    return out.cpu().numpy().view(np.uint32)
+
+
+def occ_debug_rays(ctx: Context, gb: GBuffer, effect: int, radius: float, light, seed: int,
+                   sample: int, stream=None) -> torch.Tensor:
+    out = torch.empty((gb.H, gb.W, 4), dtype=torch.float32, device=gb.pos4.device)
+    g = gb.c()
+    L = _light(light if light is not None else np.zeros(9))
+    ctx.check(ctx.lib.occ_debug_rays(ctx.handle, C.byref(g), int(effect), float(radius), C.byref(L),
+                                     int(seed), int(sample), out.data_ptr(),
+                                     _stream_handle(stream)))
+    return out
+
+
+def occ_debug_mis(ctx: Context, gb: GBuffer, occ: Occluders, pattern: Pattern, K: int,
+                  estimator: int, pix, bvh: BVH | None = None):
+    """(members [n, 64] int32, weights [n, 64, 64] float32) for receivers `pix`."""
+    pix = np.ascontiguousarray(pix, dtype=np.int32).reshape(-1)
+    n = pix.shape[0]
+    mem = np.zeros((n, N.MAX_MEMBERS), dtype=np.int32)
+    w = np.zeros((n, N.MAX_MEMBERS, N.MAX_MEMBERS), dtype=np.float32)
+    g = gb.c()
+    ctx.check(ctx.lib.occ_debug_mis(ctx.handle, C.byref(g), C.byref(occ.c()), C.byref(pattern.c()),
+                                    int(K), int(estimator), bvh.handle if bvh is not None else None,
+                                    pix.ctypes.data, n, mem.ctypes.data, w.ctypes.data))
+    return mem, w

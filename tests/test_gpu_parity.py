@@ -1,0 +1,323 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical
+seeded inputs.  The G-buffer fed to both sides is the oracle's; record-conditioned
+reuse tests feed both sides the oracle's records rounded to FP32.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+AO, SH = 0, 1
+NOREUSE, BIASED, UNBIASED, BOXMEAN = 0, 1, 2, 3
+R_C1 = 1.0
+LIGHT_C1 = np.array([0.0, 0.5, 3.0, 3.0, 0, 0, 0, -3.0, 0], dtype=np.float32)
+
+
+@pytest.fixture(scope="module")
+def occ():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_23122_gb300 import occ as occmod
+    return occmod
+
+
+@pytest.fixture(scope="module")
+def ctx(occ):
+    return occ.Context(0)
+
+
+@pytest.fixture(scope="module")
+def c1(orc, occ, ctx):
+    scene = synth.scene_c1()
+    osc = orc.OracleScene(scene.tris)
+    pos, nrm, otri = orc.gbuffer(osc, synth.camera_c1().as_array(), 64, 64, scene.eps)
+    return {"scene": scene, "osc": osc, "bvh": occ.BVH(ctx, scene.tris), "pos": pos, "nrm": nrm,
+            "otri": otri, "gb": occ.GBuffer.from_numpy(pos, nrm)}
+
+
+@pytest.fixture(scope="module")
+def terrain_small(orc, occ, ctx):
+    scene = synth.scene_terrain(grid=96, n_spheres=20, n_boxes=300, seed=5, sphere_subdiv=2,
+                                extent=6.0)
+    osc = orc.OracleScene(scene.tris)
+    cam = synth.Camera(eye=(0.0, -6.0, 3.0), target=(0.0, 0.0, 0.0), vfov_deg=55.0)
+    pos, nrm, otri = orc.gbuffer(osc, cam.as_array(), 96, 72, scene.eps)
+    return {"scene": scene, "osc": osc, "bvh": occ.BVH(ctx, scene.tris), "pos": pos, "nrm": nrm,
+            "otri": otri, "cam": cam, "gb": occ.GBuffer.from_numpy(pos, nrm)}
+
+
+def _patterns(occ):
+    return {
+        "group2x1": occ.Pattern.group(2, 1), "group2x2": occ.Pattern.group(2, 2),
+        "group4x2": occ.Pattern.group(4, 2), "group4x4": occ.Pattern.group(4, 4),
+        "group3x2": occ.Pattern.group(3, 2), "box3x3": occ.Pattern.box(3, 3),
+        "disk8": occ.Pattern.offsets_of(synth.disk_offsets(8, 15.0, seed=3)),
+        "disk16": occ.Pattern.offsets_of(synth.disk_offsets(16, 6.0, seed=4)),
+    }
+
+
+# --------------------------------------------------------------------------------------
+# RNG and step-1 rays
+# --------------------------------------------------------------------------------------
+
+def test_philox_bitexact(orc, occ, ctx):
+    rng = np.random.default_rng(1)
+    n = 1 << 14
+    ck = rng.integers(0, 2**32, size=(n, 6), dtype=np.uint64).astype(np.uint32)
+    ck[:256, :4] = np.arange(256)[:, None]   # counters that differ in one word
+    got = occ.occ_debug_philox(ctx, ck)
+    want = np.array([orc.philox4x32_10(r[:4], r[4:]) for r in ck], dtype=np.uint32)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("effect", [AO, SH])
+def test_step1_rays_match_oracle(orc, occ, ctx, c1, effect):
+    g = occ.occ_debug_rays(ctx, c1["gb"], effect, R_C1, LIGHT_C1, seed=77, sample=3).cpu().numpy()
+    pos, nrm = c1["pos"], c1["nrm"]
+    H, W = pos.shape[:2]
+    worst_d, worst_t = 0.0, 0.0
+    for p in range(0, H * W, 7):
+        y, x = divmod(p, W)
+        if pos[y, x, 3] == 0:
+            assert np.all(g[y, x] == 0)
+            continue
+        d, tmax = orc.ray(effect, pos[y, x], nrm[y, x], p, R_C1, LIGHT_C1, 77, 3)
+        worst_d = max(worst_d, np.abs(g[y, x, :3] - d).max())
+        worst_t = max(worst_t, abs(g[y, x, 3] - tmax) / tmax)
+    assert worst_d <= 2e-6, worst_d
+    assert worst_t <= 1e-6, worst_t
+
+
+# --------------------------------------------------------------------------------------
+# G-buffer input stage and closest hit
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["c1", "terrain_small"])
+def test_gbuffer_matches_oracle(orc, occ, ctx, which, request):
+    s = request.getfixturevalue(which)
+    cam = synth.camera_c1() if which == "c1" else s["cam"]
+    H, W = s["pos"].shape[:2]
+    gb = occ.occ_gbuffer_pinhole(ctx, s["bvh"], cam.as_array(), s["scene"].eps, W, H)
+    ctx.sync()
+    gp, gn = gb.pos4.cpu().numpy(), gb.nrm4.cpu().numpy()
+    ov = s["pos"][..., 3] > 0
+    gv = gp[..., 3] > 0
+    # primary-ray ids are not returned; validity and geometry are compared instead
+    diff = ov != gv
+    assert diff.sum() <= P.budget(H * W), diff.sum()
+    both = ov & gv
+    same_plane = np.abs((gn[both, :3] * s["nrm"][both, :3]).sum(-1) - 1) < 1e-6
+    assert same_plane.mean() > 0.995
+    pe = np.abs(gp[both, :3] - s["pos"][both, :3]).max(-1)[same_plane]
+    assert pe.max() <= 1e-4, pe.max()
+
+
+@pytest.mark.parametrize("effect", [AO, SH])
+@pytest.mark.parametrize("which", ["c1", "terrain_small"])
+def test_trace_matches_oracle(orc, occ, ctx, which, effect, request):
+    s = request.getfixturevalue(which)
+    light = LIGHT_C1 if which == "c1" else synth.light_c3().as_array()
+    R = R_C1 if which == "c1" else 0.5
+    valid = s["pos"][..., 3] > 0
+    for sample in range(3):
+        o = (occ.occ_trace_ao(ctx, s["gb"], s["bvh"], R, 1234, sample) if effect == AO else
+             occ.occ_trace_shadow(ctx, s["gb"], s["bvh"], light, 1234, sample))
+        ctx.sync()
+        orec, omg = orc.trace(s["osc"], effect, s["pos"], s["nrm"], radius=R, light=light,
+                              seed=1234, sample=sample)
+        res = P.compare_trace(o, orec, omg, valid, f"{which} effect {effect} sample {sample}")
+        assert res["hits"] > 0.03 * valid.sum()
+
+
+# --------------------------------------------------------------------------------------
+# Reuse on identical (oracle) records: FP32 kernels vs FP64 oracle, <= 1e-5
+# --------------------------------------------------------------------------------------
+
+PATTERN_NAMES = ["group2x1", "group2x2", "group4x2", "group4x4", "group3x2", "box3x3", "disk8",
+                 "disk16"]
+
+
+@pytest.mark.parametrize("est", [NOREUSE, BIASED, UNBIASED, BOXMEAN])
+@pytest.mark.parametrize("pname", PATTERN_NAMES)
+@pytest.mark.parametrize("effect", [AO, SH])
+def test_reuse_record_conditioned(orc, occ, ctx, c1, effect, pname, est):
+    pat = _patterns(occ)[pname]
+    light = LIGHT_C1
+    valid = c1["pos"][..., 3] > 0
+    for sample in range(2):
+        orec, _ = orc.trace(c1["osc"], effect, c1["pos"], c1["nrm"], radius=R_C1, light=light,
+                            seed=99, sample=sample)
+        r0, r1 = P.to_f32_records(orec)
+        rec32 = P.widen_records(r0, r1)
+        o = occ.Occluders.from_numpy(r0, r1, effect, radius=R_C1, light=light)
+        bvh = c1["bvh"] if est == UNBIASED else None
+        fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
+        g = fn(ctx, c1["gb"], o, pat, pat.K, est, bvh=bvh)
+        ctx.sync()
+        ref, mg = orc.reuse(c1["osc"], effect, c1["pos"], c1["nrm"], rec32, pat.as_tuple(), est,
+                            radius=R_C1, light=light)
+        P.compare_out(g.cpu().numpy(), ref, mg, valid, f"{pname} est {est} effect {effect}")
+
+
+@pytest.mark.parametrize("effect", [AO, SH])
+@pytest.mark.parametrize("pname", ["group4x2", "box3x3", "disk8"])
+def test_reuse_end_to_end(orc, occ, ctx, terrain_small, effect, pname):
+    """Both sides trace their own records from the same G-buffer, then reuse them."""
+    s = terrain_small
+    pat = _patterns(occ)[pname]
+    light = synth.light_c3().as_array()
+    valid = s["pos"][..., 3] > 0
+    errs = []
+    for est in (BIASED, UNBIASED):
+        o = (occ.occ_trace_ao(ctx, s["gb"], s["bvh"], 0.5, 5, 0) if effect == AO else
+             occ.occ_trace_shadow(ctx, s["gb"], s["bvh"], light, 5, 0))
+        fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
+        g = fn(ctx, s["gb"], o, pat, pat.K, est, bvh=s["bvh"] if est == UNBIASED else None)
+        ctx.sync()
+        orec, omg = orc.trace(s["osc"], effect, s["pos"], s["nrm"], radius=0.5, light=light,
+                              seed=5, sample=0)
+        tr = P.compare_trace(o, orec, omg, valid, "end-to-end trace")
+        ref, mg = orc.reuse(s["osc"], effect, s["pos"], s["nrm"], orec, pat.as_tuple(), est,
+                            radius=0.5, light=light)
+        err = np.abs(g.cpu().numpy() - ref)[valid]
+        errs.append(err)
+        # pixels whose neighbour set holds a listed trace disagreement are excluded
+        if tr["mismatch"] == 0:
+            frac_over = (err > P.OUT_ATOL).mean()
+            assert frac_over <= 2e-3, (est, frac_over, np.sort(err)[-5:])
+            assert np.quantile(err, 0.999) <= 1e-4
+    print("end-to-end max err", [float(e.max()) for e in errs])
+
+
+def test_mis_weights_sum_to_one(orc, occ, ctx, c1):
+    orec, _ = orc.trace(c1["osc"], AO, c1["pos"], c1["nrm"], radius=R_C1, seed=3, sample=0)
+    r0, r1 = P.to_f32_records(orec)
+    o = occ.Occluders.from_numpy(r0, r1, AO, radius=R_C1)
+    rng = np.random.default_rng(0)
+    valid_idx = np.flatnonzero(c1["pos"][..., 3].reshape(-1) > 0)
+    pix = rng.choice(valid_idx, size=200, replace=False)
+    rows = 0
+    for pname in ("group4x2", "box3x3", "disk8"):
+        pat = _patterns(occ)[pname]
+        for est, bvh in ((BIASED, None), (UNBIASED, c1["bvh"])):
+            mem, w = occ.occ_debug_mis(ctx, c1["gb"], o, pat, pat.K, est, pix, bvh=bvh)
+            s = w.sum(axis=2)
+            nz = s > 0
+            assert np.allclose(s[nz], 1.0, atol=2e-6)
+            rows += int(nz.sum())
+            # the same weights from the oracle
+            for t in range(0, 200, 25):
+                py, px = divmod(int(pix[t]), 64)
+                omem, ow = orc.mis_weights(c1["osc"], AO, c1["pos"], c1["nrm"],
+                                           P.widen_records(r0, r1), pat.as_tuple(), est, px, py,
+                                           radius=R_C1)
+                n = len(omem)
+                assert np.array_equal(mem[t, :n], omem) and np.all(mem[t, n:] == -1)
+                assert np.allclose(w[t, :n, :n], ow, atol=2e-6)
+    assert rows > 300
+
+
+# --------------------------------------------------------------------------------------
+# Closed-form scenes and edge cases
+# --------------------------------------------------------------------------------------
+
+def test_unoccluded_and_blocked_scenes_exact(orc, occ, ctx):
+    pos, nrm = synth.receiver_grid(40, 24, 0.05, z=synth.scene_plane_only().eps)
+    gb = occ.GBuffer.from_numpy(pos, nrm)
+    light = synth.light_c3().as_array()
+    pats = _patterns(occ)
+    lit = occ.BVH(ctx, synth.scene_plane_only().tris)
+    blk = occ.BVH(ctx, synth.scene_fully_blocked(2.0).tris)
+    for pname in ("group4x2", "box3x3", "disk8"):
+        pat = pats[pname]
+        for est in (NOREUSE, BIASED, UNBIASED, BOXMEAN):
+            bv = lit if est == UNBIASED else None
+            o = occ.occ_trace_ao(ctx, gb, lit, 1.0, 1, 0)
+            assert np.all(occ.occ_reuse_ao(ctx, gb, o, pat, pat.K, est, bvh=bv).cpu().numpy() == 1.0)
+            o = occ.occ_trace_shadow(ctx, gb, lit, light, 1, 0)
+            assert np.all(occ.occ_reuse_shadow(ctx, gb, o, pat, pat.K, est, bvh=bv).cpu().numpy() == 1.0)
+            if est != UNBIASED:
+                o = occ.occ_trace_shadow(ctx, gb, blk, light, 1, 0)
+                out = occ.occ_reuse_shadow(ctx, gb, o, pat, pat.K, est).cpu().numpy()
+                assert np.all(out == 0.0), (pname, est)
+    ctx.sync()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (7, 3), (33, 17), (16, 8)])
+def test_ragged_and_tiny_images(orc, occ, ctx, c1, shape):
+    W, H = shape
+    pos = np.ascontiguousarray(c1["pos"][20:20 + H, 10:10 + W])
+    nrm = np.ascontiguousarray(c1["nrm"][20:20 + H, 10:10 + W])
+    gb = occ.GBuffer.from_numpy(pos, nrm)
+    valid = pos[..., 3] > 0
+    for pname in ("group4x2", "box3x3", "disk8", "group3x2"):
+        pat = _patterns(occ)[pname]
+        o = occ.occ_trace_ao(ctx, gb, c1["bvh"], R_C1, 8, 1)
+        r0, r1, _ = P.gpu_records(o)
+        for est in (NOREUSE, BIASED, UNBIASED, BOXMEAN):
+            g = occ.occ_reuse_ao(ctx, gb, o, pat, pat.K, est,
+                                 bvh=c1["bvh"] if est == UNBIASED else None)
+            ctx.sync()
+            ref, mg = orc.reuse(c1["osc"], AO, pos, nrm, P.widen_records(r0, r1), pat.as_tuple(),
+                                est, radius=R_C1)
+            P.compare_out(g.cpu().numpy(), ref, mg, valid, f"{shape} {pname} {est}")
+
+
+def test_all_invalid_gbuffer_and_max_k(orc, occ, ctx, c1):
+    pos = np.zeros((20, 30, 4), dtype=np.float32)
+    gb = occ.GBuffer.from_numpy(pos, pos)
+    o = occ.occ_trace_ao(ctx, gb, c1["bvh"], 1.0, 1, 0)
+    _, _, tri = P.gpu_records(o)
+    assert np.all(tri == -1)
+    for pat in (occ.Pattern.box(8, 8), occ.Pattern.group(4, 2)):
+        out = occ.occ_reuse_ao(ctx, gb, o, pat, pat.K, BIASED).cpu().numpy()
+        assert np.all(out == 1.0)
+    # K = 64 (8 x 8 box) on real records
+    pat = occ.Pattern.box(8, 8)
+    orec, _ = orc.trace(c1["osc"], AO, c1["pos"], c1["nrm"], radius=R_C1, seed=4, sample=0)
+    r0, r1 = P.to_f32_records(orec)
+    o = occ.Occluders.from_numpy(r0, r1, AO, radius=R_C1)
+    g = occ.occ_reuse_ao(ctx, c1["gb"], o, pat, 64, BIASED)
+    ctx.sync()
+    ref, mg = orc.reuse(c1["osc"], AO, c1["pos"], c1["nrm"], P.widen_records(r0, r1),
+                        pat.as_tuple(), BIASED, radius=R_C1)
+    P.compare_out(g.cpu().numpy(), ref, mg, c1["pos"][..., 3] > 0, "box8x8")
+
+
+def test_invalid_arguments_rejected(occ, ctx, c1):
+    o = occ.occ_trace_ao(ctx, c1["gb"], c1["bvh"], 1.0, 1, 0)
+    pat = occ.Pattern.group(4, 2)
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_reuse_ao(ctx, c1["gb"], o, pat, 7, BIASED)            # K != gw*gh
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_reuse_ao(ctx, c1["gb"], o, pat, 8, UNBIASED)          # unbiased needs the BVH
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_reuse_ao(ctx, c1["gb"], o, pat, 8, BIASED, bvh=c1["bvh"])
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_reuse_shadow(ctx, c1["gb"], o, pat, 8, BIASED)        # records are AO
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_trace_ao(ctx, c1["gb"], c1["bvh"], -1.0, 1, 0)
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_trace_shadow(ctx, c1["gb"], c1["bvh"], [0, 0, 4, 1, 0, 0, 1, 1, 0], 1, 0)
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_reuse_ao(ctx, c1["gb"], o, occ.Pattern.offsets_of([[0, 0]]), 2, BIASED)
+    ctx.sync()
+
+
+def test_frame_host_matches_device_path(occ, ctx, c1):
+    import torch
+    pat = _patterns(occ)["box3x3"]
+    pos_h = torch.from_numpy(c1["pos"]).pin_memory()
+    nrm_h = torch.from_numpy(c1["nrm"]).pin_memory()
+    out_h = torch.empty((64, 64), dtype=torch.float32).pin_memory()
+    occ.occ_frame_host(ctx, c1["bvh"], AO, pos_h, nrm_h, R_C1, None, 21, 2, pat, 9, BIASED, out_h)
+    o = occ.occ_trace_ao(ctx, c1["gb"], c1["bvh"], R_C1, 21, 2)
+    d = occ.occ_reuse_ao(ctx, c1["gb"], o, pat, 9, BIASED)
+    ctx.sync()
+    assert torch.equal(out_h, d.cpu())
