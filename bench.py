@@ -39,8 +39,8 @@ L2_FLUSH_BYTES = 512 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -145,7 +145,7 @@ def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
     rng = np.random.default_rng(11)
     B = 48
     receivers, t_total, blocks = 0, 0.0, 0
-    while t_total < budget_s and blocks < 64:
+    while t_total < budget_s and blocks < 100000:
         x0 = int(rng.integers(hx0, W - B - hx1))
         y0 = int(rng.integers(hy0, H - B - hy1))
         t0 = time.perf_counter()
@@ -189,14 +189,14 @@ def run_ours(args):
         occ.occ_trace_ao(ctx, gb, bvh, RADIUS, 1, 0, out=rec, stream=stream)
         occ.occ_reuse_ao(ctx, gb, rec, pat, K, occ.OCC_EST_BIASED, out=out, stream=stream)
 
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         flush.zero_()
         step()
     ctx.sync()
     P = W * H
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    clocks.start()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
