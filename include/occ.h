@@ -186,6 +186,38 @@ occ_status occ_frame_host(occ_ctx* ctx, const occ_bvh* bvh, int32_t effect,
                           uint32_t sample, const occ_pattern* pattern, int32_t K,
                           int32_t estimator, float* out_host, void* stream);
 
+/* ---- allocation-free frame -------------------------------------------------- */
+
+/* The paper has no counterpart to this call; it serves callers that cannot allocate
+ * device memory: plugins whose host application owns every device allocation, and
+ * real-time frame loops that cannot afford the device-wide synchronisation that
+ * cudaMalloc / cudaFree may cause.  Such callers cannot create an occ_ctx (which
+ * allocates its status word) nor provide a record workspace.
+ *
+ * One frame on the current device: the step-1 trace of `effect` (AO with `radius`,
+ * or SHADOW with `light`) for every receiver of gb, then the reuse of `estimator`
+ * over `pattern` into out (device float[H][W]).  The caller passes the G-buffer,
+ * the BVH and `out`; the occluder records and the device status word live in a
+ * static device array inside the library (calls no cudaMalloc, cudaFree or other
+ * allocating routine).  Limits and behaviour:
+ *  - frames of at most 1,048,576 pixels (e.g. 1280x720, 1024x1024); larger ones
+ *    return OCC_ERR_INVALID_ARG with a message and launch nothing;
+ *  - the array (32 MiB) is held by every GPU that loads the library until exit;
+ *  - the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current: make that first call before
+ *    any stream capture;
+ *  - every call shares the array and overwrites the previous call's records; calls
+ *    that overlap on the GPU (other streams or host threads) race on it;
+ *  - the status word is cleared at the start of each call; if flags_host is not
+ *    NULL the call waits for `stream`, stores the flags there and returns
+ *    OCC_ERR_DEVICE_CHECK when any is set; with NULL the call stays asynchronous;
+ *  - err_msg (err_len bytes, may be NULL) receives the message of a failure. */
+occ_status occ_frame_noalloc(const occ_gbuffer* gb, const occ_bvh* bvh, int32_t effect,
+                             float radius, const occ_rect_light* light, uint64_t seed,
+                             uint32_t sample, const occ_pattern* pattern, int32_t K,
+                             int32_t estimator, float* out, uint32_t* flags_host, char* err_msg,
+                             int32_t err_len, void* stream);
+
 /* ---- test and debugging aids ---------------------------------------------- */
 
 /* Philox4x32-10 of n (counter[4], key[2]) items: in_dev holds 6 uint32 per

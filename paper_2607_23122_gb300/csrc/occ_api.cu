@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include <cuda_runtime.h>
@@ -498,5 +499,103 @@ OCC_EXPORT occ_status occ_debug_mis(occ_ctx* ctx, const occ_gbuffer* gb, const o
     cudaFree(d_mem);
     cudaFree(d_w);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "debug_mis");
+    return OCC_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// occ_frame_noalloc: one frame (trace + reuse) that allocates no device memory.
+//
+// Callers such as render-engine plugins that must draw all device memory from the
+// host application's own pools, or real-time frame loops that cannot afford the
+// device-wide synchronisation cudaMalloc / cudaFree may cause, cannot create an
+// occ_ctx (its status word is allocated) nor hand the library a workspace.  This
+// entry point keeps its scratch -- the occluder records of the frame and the device
+// status word -- in the file-scope array below, which every GPU that loads the
+// library holds until the process exits.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxPixels = int64_t(1) << 20;   // e.g. 1280x720 or 1024x1024
+constexpr int kNoAllocMaxDevices = 64;
+
+// [0, 2 * max) : two float4 record planes; [2 * max] : device status word (+ padding)
+static __device__ __align__(256) float4 g_noalloc_scratch[2 * kNoAllocMaxPixels + 16];
+
+std::mutex g_noalloc_mutex;
+float4* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+
+OCC_EXPORT occ_status occ_frame_noalloc(const occ_gbuffer* gb, const occ_bvh* bvh, int32_t effect,
+                                        float radius, const occ_rect_light* light, uint64_t seed,
+                                        uint32_t sample, const occ_pattern* pattern, int32_t K,
+                                        int32_t estimator, float* out, uint32_t* flags_host,
+                                        char* err_msg, int32_t err_len, void* stream) {
+    occ_ctx local;   // carries validation messages only; owns no device memory
+    auto finish = [&](occ_status st) {
+        if (st != OCC_OK && err_msg && err_len > 0)
+            snprintf(err_msg, (size_t)err_len, "%s", local.last_error.c_str());
+        return st;
+    };
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return finish(cuda_fail(&local, e, "cudaGetDevice"));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return finish(fail(&local, OCC_ERR_UNSUPPORTED, "device %d beyond the supported %d", dev,
+                           kNoAllocMaxDevices));
+    local.device = dev;
+    occ_status st = check_gbuffer(&local, gb);
+    if (st != OCC_OK) return finish(st);
+    const int64_t P = (int64_t)gb->W * gb->H;
+    if (P > kNoAllocMaxPixels)
+        return finish(fail(&local, OCC_ERR_INVALID_ARG,
+                           "frame of %lld pixels exceeds the %lld-pixel maximum of the static "
+                           "scratch of occ_frame_noalloc",
+                           (long long)P, (long long)kNoAllocMaxPixels));
+    if (!bvh) return finish(fail(&local, OCC_ERR_INVALID_ARG, "bvh is NULL"));
+    if (bvh->device != dev)
+        return finish(fail(&local, OCC_ERR_INVALID_ARG, "bvh lives on device %d, current device is %d",
+                           bvh->device, dev));
+    if (effect != OCC_EFFECT_AO && effect != OCC_EFFECT_SHADOW)
+        return finish(fail(&local, OCC_ERR_INVALID_ARG, "effect %d invalid", effect));
+    if (effect == OCC_EFFECT_AO && !(radius > 0.0f && std::isfinite(radius)))
+        return finish(fail(&local, OCC_ERR_INVALID_ARG, "AO radius must be positive and finite"));
+    if (effect == OCC_EFFECT_SHADOW && (st = check_light(&local, light)) != OCC_OK) return finish(st);
+    if (estimator < OCC_EST_NOREUSE || estimator > OCC_EST_BOXMEAN)
+        return finish(fail(&local, OCC_ERR_INVALID_ARG, "estimator %d invalid", estimator));
+    if (!out) return finish(fail(&local, OCC_ERR_INVALID_ARG, "out is NULL"));
+    occ::PatternParams pat;
+    if ((st = make_pattern(&local, pattern, K, &pat)) != OCC_OK) return finish(st);
+
+    float4* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return finish(cuda_fail(&local, e, "cudaGetSymbolAddress"));
+            g_noalloc_ptr[dev] = static_cast<float4*>(p);
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    const occ::RecView rec{base, base + P};
+    unsigned* status = reinterpret_cast<unsigned*>(base + 2 * kNoAllocMaxPixels);
+    cudaStream_t s = (cudaStream_t)stream;
+    const occ::LightParams lp = to_params(effect == OCC_EFFECT_SHADOW ? light : nullptr);
+    const occ::DevBVH b = dev_bvh(bvh);
+    e = cudaMemsetAsync(status, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess)
+        e = occ::launch_trace(effect, view(gb), b, radius, lp, seed, sample, rec, status, s);
+    if (e == cudaSuccess)
+        e = occ::launch_reuse(effect, estimator, view(gb), rec, pat, radius, lp,
+                              estimator == OCC_EST_UNBIASED ? &b : nullptr, out, status, s);
+    if (e != cudaSuccess) return finish(cuda_fail(&local, e, "occ_frame_noalloc launch"));
+    if (flags_host) {
+        e = cudaMemcpyAsync(flags_host, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return finish(cuda_fail(&local, e, "occ_frame_noalloc status"));
+        if (*flags_host)
+            return finish(fail(&local, OCC_ERR_DEVICE_CHECK, "device check flags 0x%x", *flags_host));
+    }
     return OCC_OK;
 }

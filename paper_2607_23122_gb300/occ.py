@@ -281,6 +281,33 @@ def occ_frame_host(ctx: Context, bvh: BVH, effect: int, pos4_host: torch.Tensor,
     return out_host
 
 
+NOALLOC_MAX_PIXELS = 1 << 20
+
+
+def occ_frame_noalloc(gb: GBuffer, bvh: BVH, effect: int, radius: float, light, seed: int,
+                      sample: int, pattern: Pattern, K: int, estimator: int, out: torch.Tensor,
+                      check: bool = True, stream=None) -> torch.Tensor:
+    """One frame (trace + reuse) into `out` with no device allocation (see occ.h).
+
+    For callers that cannot allocate device memory; frames up to NOALLOC_MAX_PIXELS.
+    Records live in a library-static array shared by all calls, so calls must not
+    overlap on the GPU.  With check=True the call waits for the stream and raises
+    on device-check flags.
+    """
+    lib = N.load()
+    g = gb.c()
+    L = _light(light if light is not None else np.zeros(9))
+    flags = C.c_uint32(0)
+    msg = C.create_string_buffer(512)
+    st = lib.occ_frame_noalloc(C.byref(g), bvh.handle, int(effect), float(radius), C.byref(L),
+                               int(seed), int(sample), C.byref(pattern.c()), int(K),
+                               int(estimator), out.data_ptr(), C.byref(flags) if check else None,
+                               msg, 512, _stream_handle(stream))
+    if st != N.OCC_OK:
+        raise OccError(st, msg.value.decode())
+    return out
+
+
 def occ_debug_philox(ctx: Context, ctr_key: np.ndarray, stream=None) -> np.ndarray:
     """Philox4x32-10 of rows (c0, c1, c2, c3, k0, k1) -> [n, 4] uint32 (synchronous)."""
     a = np.ascontiguousarray(ctr_key, dtype=np.uint32).reshape(-1, 6)
