@@ -47,11 +47,13 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=None) -> str:
+    """Compiles the library.  OCC_NVCC_EXTRA (environment) appends nvcc flags, e.g. a
+    tuning define such as -DOCC_TRACE_MIN_BLOCKS=10; set it with force=True."""
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
-    extra = list(extra or [])
+    extra = list(extra or []) + os.environ.get("OCC_NVCC_EXTRA", "").split()
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")

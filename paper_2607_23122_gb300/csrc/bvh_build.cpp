@@ -60,9 +60,15 @@ struct BNode {
 };
 
 constexpr int kBins = 16;
-constexpr float kTraverseCost = 1.2f;
+#ifndef OCC_SAH_TRAVERSE
+#define OCC_SAH_TRAVERSE 1.2f
+#endif
+#ifndef OCC_SAH_LEAFMAX
+#define OCC_SAH_LEAFMAX 8
+#endif
+constexpr float kTraverseCost = OCC_SAH_TRAVERSE;
 constexpr float kIntersectCost = 1.0f;
-constexpr uint32_t kLeafMax = 8;         // never keep a leaf bigger than this
+constexpr uint32_t kLeafMax = OCC_SAH_LEAFMAX;   // never keep a leaf bigger than this
 constexpr uint32_t kParallelMin = 1u << 15;
 
 struct Builder {
@@ -182,6 +188,7 @@ struct Builder {
 struct Collapser {
     const std::vector<BNode>& bn;
     std::vector<Node4>& nodes;
+    float pad;          // absolute growth of every child box (see build_bvh4)
     int max_depth = 0;
     int64_t leaves = 0;
     uint32_t max_leaf = 0;
@@ -225,8 +232,8 @@ struct Collapser {
         for (int c = 0; c < (int)kids.size(); ++c) {
             const BNode& k = bn[kids[c]];
             for (int a = 0; a < 3; ++a) {
-                lo[a][c] = k.box.lo[a];
-                hi[a][c] = k.box.hi[a];
+                lo[a][c] = k.box.lo[a] - pad;
+                hi[a][c] = k.box.hi[a] + pad;
             }
             if (k.left < 0) {
                 ref[c] = leaf_ref(k);
@@ -281,19 +288,26 @@ bool build_bvh4(const float* tris, int64_t T, HostBVH* out, std::string* err) {
     while ((1u << spawn) < hw && spawn < 6) ++spawn;
     b.build(bn, 0, (uint32_t)T, spawn);
 
+    // Child boxes grow by 2^-17 of the largest coordinate magnitude.  The traversal's
+    // slab test takes one FMA per plane (lo * idir - o * idir), whose rounding moves a
+    // plane by at most about 2^-23 of the coordinate magnitude; the growth keeps every
+    // box conservative for rays whose origins lie within a few scene radii.
+    float mag = 1.0f;
+    for (int64_t i = 0; i < 9 * T; ++i) mag = std::max(mag, std::fabs(tris[i]));
     out->nodes.clear();
-    Collapser col{bn, out->nodes};
+    Collapser col{bn, out->nodes, std::ldexp(mag, -17)};
     if (bn[0].left < 0) {
         // the whole scene is one leaf: a root node with that single child
         Node4 n;
         std::memset(&n, 0, sizeof(n));
         const float inf = std::numeric_limits<float>::infinity();
-        n.lox = make_float4(bn[0].box.lo[0], inf, inf, inf);
-        n.hix = make_float4(bn[0].box.hi[0], -inf, -inf, -inf);
-        n.loy = make_float4(bn[0].box.lo[1], inf, inf, inf);
-        n.hiy = make_float4(bn[0].box.hi[1], -inf, -inf, -inf);
-        n.loz = make_float4(bn[0].box.lo[2], inf, inf, inf);
-        n.hiz = make_float4(bn[0].box.hi[2], -inf, -inf, -inf);
+        const float p = col.pad;
+        n.lox = make_float4(bn[0].box.lo[0] - p, inf, inf, inf);
+        n.hix = make_float4(bn[0].box.hi[0] + p, -inf, -inf, -inf);
+        n.loy = make_float4(bn[0].box.lo[1] - p, inf, inf, inf);
+        n.hiy = make_float4(bn[0].box.hi[1] + p, -inf, -inf, -inf);
+        n.loz = make_float4(bn[0].box.lo[2] - p, inf, inf, inf);
+        n.hiz = make_float4(bn[0].box.hi[2] + p, -inf, -inf, -inf);
         n.child = make_uint4(Collapser::leaf_ref(bn[0]), kEmptyRef, kEmptyRef, kEmptyRef);
         out->nodes.push_back(n);
         col.leaves = 1;

@@ -14,6 +14,12 @@ namespace {
 
 constexpr int kTileW = 16, kTileH = 8;
 
+// Minimum resident CTAs per SM requested from the register allocator for the trace
+// kernel (8 -> 64 registers, 10 -> 48, 12 -> 40).
+#ifndef OCC_TRACE_MIN_BLOCKS
+#define OCC_TRACE_MIN_BLOCKS 8
+#endif
+
 __device__ __forceinline__ void tile_pixel(int* x, int* y) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     *x = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
@@ -45,26 +51,54 @@ __device__ __forceinline__ float3 step1_ray(float3 x, float3 n, uint32_t p, floa
     }
 }
 
+// Box holding every AO segment of the warp: the valid origins widened by the radius
+// (with slack for the rounding of |direction| and of the box test), reduced over lanes.
+__device__ __forceinline__ uint32_t warp_start_node(const DevBVH& bvh, bool valid, float3 x,
+                                                    float radius) {
+    const float inf = __int_as_float(0x7f800000);
+    float lo[3] = {valid ? x.x : inf, valid ? x.y : inf, valid ? x.z : inf};
+    float hi[3] = {valid ? x.x : -inf, valid ? x.y : -inf, valid ? x.z : -inf};
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xFFFFFFFFu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xFFFFFFFFu, hi[a], o));
+        }
+    }
+    if (!(lo[0] <= hi[0])) return kEmptyRef;   // no valid receiver in this warp
+    const float mag = fmaxf(fmaxf(fmaxf(fabsf(lo[0]), fabsf(hi[0])), fmaxf(fabsf(lo[1]), fabsf(hi[1]))),
+                            fmaxf(fabsf(lo[2]), fabsf(hi[2])));
+    const float pad = radius * 1.001f + 1e-5f * (1.0f + mag);
+    return start_node(bvh, make_float3(lo[0] - pad, lo[1] - pad, lo[2] - pad),
+                      make_float3(hi[0] + pad, hi[1] + pad, hi[2] + pad));
+}
+
 template <int EFFECT>
-__global__ void __launch_bounds__(128) k_trace(GBufView gb, DevBVH bvh, float radius,
+__global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS) k_trace(GBufView gb, DevBVH bvh, float radius,
                                                LightParams lp, uint64_t seed, uint32_t sample,
                                                RecView rec, unsigned* status) {
     int x, y;
     tile_pixel(&x, &y);
-    if (x >= gb.W || y >= gb.H) return;
-    const uint32_t p = (uint32_t)y * (uint32_t)gb.W + (uint32_t)x;
-    const float4 P = __ldg(gb.pos + p);
-    if (P.w == 0.0f) {
+    const bool inside = x < gb.W && y < gb.H;
+    const uint32_t p = inside ? (uint32_t)y * (uint32_t)gb.W + (uint32_t)x : 0u;
+    const float4 P = inside ? __ldg(gb.pos + p) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const bool valid = inside && P.w != 0.0f;
+    const float3 xo = f3(P);
+    // AO segments are short: start below the part of the tree they cannot leave
+    const uint32_t start = EFFECT == kAO ? warp_start_node(bvh, valid, xo, radius) : 0u;
+    if (!inside) return;
+    if (!valid) {
         rec.r0[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
         rec.r1[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         return;
     }
-    const float3 xo = f3(P), n = f3(__ldg(gb.nrm + p));
+    const float3 n = f3(__ldg(gb.nrm + p));
     RectLight L;
     if (EFFECT == kShadow) L = make_light(lp);
     float tmax;
     const float3 d = step1_ray<EFFECT>(xo, n, p, radius, L, seed, sample, &tmax);
-    const Hit h = closest_hit(bvh, xo, d, tmax, status);
+    const Hit h = closest_hit(bvh, xo, d, tmax, status, start);
     if (h.id == kNoHit) {
         rec.r0[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
         rec.r1[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);

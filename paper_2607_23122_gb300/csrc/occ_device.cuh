@@ -109,6 +109,8 @@ __device__ __forceinline__ float3 light_direction(const RectLight& L, float3 x, 
 struct TraceRay {
     float3 o;
     float3 idir;            // 1 / d with zero components replaced by a tiny value
+    float3 oidir;           // o * idir: slab distances are lo * idir - oidir (one FMA)
+    int near[3], far[3];    // float4 index in Node4 of the near / far planes per axis
     float3 rx, ry, rz;      // shear rows
     float3 d;
 };
@@ -128,16 +130,28 @@ __device__ __forceinline__ TraceRay make_trace_ray(float3 o, float3 d) {
     if (dz < 0.0f) { const int t = kx; kx = ky; ky = t; }
     const float dx = kx == 0 ? d.x : (kx == 1 ? d.y : d.z);
     const float dy = ky == 0 ? d.x : (ky == 1 ? d.y : d.z);
-    const float Sx = dx / dz, Sy = dy / dz, Sz = 1.0f / dz;
+    // One reciprocal serves every triangle of the ray, so its rounding is the same for
+    // all of them (watertightness needs consistency, not correct rounding).
+    const float Sz = __frcp_rn(dz);
+    const float Sx = dx * Sz, Sy = dy * Sz;
     r.rx = make_float3(kx == 0 ? 1.0f : (kz == 0 ? -Sx : 0.0f), kx == 1 ? 1.0f : (kz == 1 ? -Sx : 0.0f),
                        kx == 2 ? 1.0f : (kz == 2 ? -Sx : 0.0f));
     r.ry = make_float3(ky == 0 ? 1.0f : (kz == 0 ? -Sy : 0.0f), ky == 1 ? 1.0f : (kz == 1 ? -Sy : 0.0f),
                        ky == 2 ? 1.0f : (kz == 2 ? -Sy : 0.0f));
     r.rz = make_float3(kz == 0 ? Sz : 0.0f, kz == 1 ? Sz : 0.0f, kz == 2 ? Sz : 0.0f);
     const float tiny = 1e-20f;
-    r.idir = make_float3(1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
-                         1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
-                         1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
+    r.idir = make_float3(__frcp_rn(fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x)),
+                         __frcp_rn(fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
+                         __frcp_rn(fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
+    r.oidir = make_float3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
+    // Node4 holds lox, hix, loy, hiy, loz, hiz as consecutive float4: for a positive
+    // direction component the low plane is entered first.
+    r.near[0] = r.idir.x >= 0.0f ? 0 : 1;
+    r.near[1] = r.idir.y >= 0.0f ? 2 : 3;
+    r.near[2] = r.idir.z >= 0.0f ? 4 : 5;
+    r.far[0] = 1 - r.near[0];
+    r.far[1] = 5 - r.near[1];
+    r.far[2] = 9 - r.near[2];
     return r;
 }
 
@@ -182,83 +196,112 @@ struct Hit {
     float t;
 };
 
-// Closest hit on (0, tmax] (t in units of |d|).  Sets kStatusStackOverflow in *status
-// if the short stack would overflow (the builder bounds the depth so it cannot).
+// Children of node `cur` hit by the ray before tbest, nearest first: the nearest goes to
+// *next, the others are pushed far-to-near.  *next = kEmptyRef if none is hit.
+__device__ __forceinline__ void visit_node(const DevBVH& bvh, uint32_t cur, const TraceRay& r,
+                                           float tbest, uint2* stack, int& sp, bool& overflow,
+                                           uint32_t* next) {
+    // Slab test of the four children: near / far planes are picked by address (the ray's
+    // direction signs), each plane distance is one FMA; boxes are grown at build time so
+    // this is conservative.
+    const float4* nb = reinterpret_cast<const float4*>(bvh.nodes + cur);
+    const float4 nx = __ldg(nb + r.near[0]), fx = __ldg(nb + r.far[0]);
+    const float4 ny = __ldg(nb + r.near[1]), fy = __ldg(nb + r.far[1]);
+    const float4 nz = __ldg(nb + r.near[2]), fz = __ldg(nb + r.far[2]);
+    const uint4 ch = __ldg(reinterpret_cast<const uint4*>(nb + 6));
+    const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, fxs[4] = {fx.x, fx.y, fx.z, fx.w};
+    const float nys[4] = {ny.x, ny.y, ny.z, ny.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w};
+    const float nzs[4] = {nz.x, nz.y, nz.z, nz.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
+    const uint32_t cref[4] = {ch.x, ch.y, ch.z, ch.w};
+    const float inf = __int_as_float(0x7f800000);
+    float key[4];
+    uint32_t ref[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float tn = fmaxf(fmaxf(fmaf(nxs[c], r.idir.x, -r.oidir.x), fmaf(nys[c], r.idir.y, -r.oidir.y)),
+                               fmaxf(fmaf(nzs[c], r.idir.z, -r.oidir.z), 0.0f));
+        const float tf = fminf(fminf(fmaf(fxs[c], r.idir.x, -r.oidir.x), fmaf(fys[c], r.idir.y, -r.oidir.y)),
+                               fminf(fmaf(fzs[c], r.idir.z, -r.oidir.z), tbest));
+        const bool hit = cref[c] != kEmptyRef && tn <= tf;
+        key[c] = hit ? tn : inf;
+        ref[c] = cref[c];
+    }
+    // near-to-far order (sorting network (0,1)(2,3)(0,2)(1,3)(1,2)): the nearest child is
+    // visited next, the others are pushed far-to-near so closer ones pop first
+#define OCC_CSWAP(a, b)                                                          \
+    if (key[b] < key[a]) {                                                      \
+        const float tk = key[a]; key[a] = key[b]; key[b] = tk;                  \
+        const uint32_t tr = ref[a]; ref[a] = ref[b]; ref[b] = tr;               \
+    }
+    OCC_CSWAP(0, 1) OCC_CSWAP(2, 3) OCC_CSWAP(0, 2) OCC_CSWAP(1, 3) OCC_CSWAP(1, 2)
+#undef OCC_CSWAP
+#pragma unroll
+    for (int c = 3; c >= 1; --c) {
+        if (key[c] != inf) {
+            if (sp < kStackSize) stack[sp++] = make_uint2(ref[c], __float_as_uint(key[c]));
+            else overflow = true;
+        }
+    }
+    *next = key[0] != inf ? ref[0] : kEmptyRef;
+}
+
+// Pops the next entry that can still hold a hit before tbest (kEmptyRef when none).
+__device__ __forceinline__ uint32_t pop_next(const uint2* stack, int& sp, float tbest) {
+    while (sp > 0) {
+        const uint2 e = stack[--sp];
+        if (__uint_as_float(e.y) <= tbest) return e.x;
+    }
+    return kEmptyRef;
+}
+
+__device__ __forceinline__ bool is_leaf_ref(uint32_t ref) { return (ref & kLeafBit) != 0u; }
+
+// Closest hit on (0, tmax] (t in units of |d|), starting at `start`: the root (0), any
+// node or leaf reference whose subtree holds every triangle the ray can meet, or
+// kEmptyRef when none can be met.  While-while traversal: each lane walks internal
+// nodes until every active lane holds a postponed leaf, then all lanes test their
+// leaves together, which keeps the warp's lanes on the same code path.  Sets
+// kStatusStackOverflowBit in *status if the short stack would overflow (the builder
+// bounds the tree depth so that it cannot).
 __device__ __forceinline__ Hit closest_hit(const DevBVH& bvh, float3 o, float3 d, float tmax,
-                                           unsigned int* status) {
+                                           unsigned int* status, uint32_t start = 0u) {
     const TraceRay r = make_trace_ray(o, d);
     float tbest = tmax;
     uint32_t best_id = kNoHit, best_slot = kNoHit;
     uint2 stack[kStackSize];
     int sp = 0;
     bool overflow = false;
-    uint32_t cur = 0;
-    for (;;) {
-        if (cur & kLeafBit) {
-            const uint32_t first = cur & kLeafFirstMask;
-            const uint32_t count = ((cur & ~kLeafBit) >> kLeafCountShift) + 1u;
+    uint32_t cur = start, leaf = kEmptyRef;
+    if (cur != kEmptyRef && is_leaf_ref(cur)) {
+        leaf = cur;
+        cur = kEmptyRef;
+    }
+    while (cur != kEmptyRef || leaf != kEmptyRef) {
+        while (cur != kEmptyRef && !is_leaf_ref(cur)) {
+            uint32_t next;
+            visit_node(bvh, cur, r, tbest, stack, sp, overflow, &next);
+            cur = next != kEmptyRef ? next : pop_next(stack, sp, tbest);
+            if (cur != kEmptyRef && is_leaf_ref(cur) && leaf == kEmptyRef) {
+                leaf = cur;   // postpone the leaf and keep walking internal nodes
+                cur = pop_next(stack, sp, tbest);
+            }
+            if (!__any_sync(__activemask(), leaf == kEmptyRef)) break;
+        }
+        while (leaf != kEmptyRef) {
+            const uint32_t first = leaf & kLeafFirstMask;
+            const uint32_t count = ((leaf & ~kLeafBit) >> kLeafCountShift) + 1u;
             for (uint32_t i = 0; i < count; ++i) {
                 const float4* t = bvh.tris + 3ull * (first + i);
                 triangle_test(r, __ldg(t), __ldg(t + 1), __ldg(t + 2), first + i, tbest, best_id,
                               best_slot);
             }
-        } else {
-            const Node4* n = bvh.nodes + cur;
-            const float4 lox = __ldg(&n->lox), hix = __ldg(&n->hix);
-            const float4 loy = __ldg(&n->loy), hiy = __ldg(&n->hiy);
-            const float4 loz = __ldg(&n->loz), hiz = __ldg(&n->hiz);
-            const uint4 ch = __ldg(&n->child);
-            const float lx[4] = {lox.x, lox.y, lox.z, lox.w}, hx[4] = {hix.x, hix.y, hix.z, hix.w};
-            const float ly[4] = {loy.x, loy.y, loy.z, loy.w}, hy[4] = {hiy.x, hiy.y, hiy.z, hiy.w};
-            const float lz[4] = {loz.x, loz.y, loz.z, loz.w}, hz[4] = {hiz.x, hiz.y, hiz.z, hiz.w};
-            const uint32_t cref[4] = {ch.x, ch.y, ch.z, ch.w};
-            float key[4];
-            uint32_t ref[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float x0 = (lx[c] - r.o.x) * r.idir.x, x1 = (hx[c] - r.o.x) * r.idir.x;
-                const float y0 = (ly[c] - r.o.y) * r.idir.y, y1 = (hy[c] - r.o.y) * r.idir.y;
-                const float z0 = (lz[c] - r.o.z) * r.idir.z, z1 = (hz[c] - r.o.z) * r.idir.z;
-                const float tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), 0.0f));
-                const float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fmaxf(z0, z1)) * 1.0000005f;
-                const bool hit = cref[c] != kEmptyRef && tn <= fminf(tf, tbest);
-                key[c] = hit ? tn : __int_as_float(0x7f800000);
-                ref[c] = cref[c];
-            }
-            // sort the four (key, ref) pairs by key: network (0,1)(2,3)(0,2)(1,3)(1,2)
-#define OCC_CSWAP(a, b)                                                          \
-    if (key[b] < key[a]) {                                                      \
-        const float tk = key[a]; key[a] = key[b]; key[b] = tk;                  \
-        const uint32_t tr = ref[a]; ref[a] = ref[b]; ref[b] = tr;               \
-    }
-            OCC_CSWAP(0, 1) OCC_CSWAP(2, 3) OCC_CSWAP(0, 2) OCC_CSWAP(1, 3) OCC_CSWAP(1, 2)
-#undef OCC_CSWAP
-            if (key[0] != __int_as_float(0x7f800000)) {
-#pragma unroll
-                for (int c = 3; c >= 1; --c) {
-                    if (key[c] != __int_as_float(0x7f800000)) {
-                        if (sp < kStackSize) {
-                            stack[sp++] = make_uint2(ref[c], __float_as_uint(key[c]));
-                        } else {
-                            overflow = true;
-                        }
-                    }
-                }
-                cur = ref[0];
-                continue;
+            if (cur != kEmptyRef && is_leaf_ref(cur)) {
+                leaf = cur;
+                cur = pop_next(stack, sp, tbest);
+            } else {
+                leaf = kEmptyRef;
             }
         }
-        // pop the next entry that can still hold a closer hit
-        bool found = false;
-        while (sp > 0) {
-            const uint2 e = stack[--sp];
-            if (__uint_as_float(e.y) <= tbest) {
-                cur = e.x;
-                found = true;
-                break;
-            }
-        }
-        if (!found) break;
     }
     if (overflow && status) atomicOr(status, kStatusStackOverflowBit);
     Hit h;
@@ -266,6 +309,41 @@ __device__ __forceinline__ Hit closest_hit(const DevBVH& bvh, float3 o, float3 d
     h.slot = best_slot;
     h.t = tbest;
     return h;
+}
+
+// Start reference for rays whose segments all lie inside the box [qlo, qhi]: walk down
+// from the root while exactly one child box overlaps the query box.  The subtree
+// returned holds every triangle that any such ray can meet (the skipped siblings' boxes
+// do not reach the query box); kEmptyRef means no triangle can be met.  Uniform across
+// the calling threads when the query box is.
+__device__ __forceinline__ uint32_t start_node(const DevBVH& bvh, float3 qlo, float3 qhi) {
+    uint32_t cur = 0;
+    for (int level = 0; level < kStackSize; ++level) {
+        const Node4* n = bvh.nodes + cur;
+        const float4 lox = __ldg(&n->lox), hix = __ldg(&n->hix);
+        const float4 loy = __ldg(&n->loy), hiy = __ldg(&n->hiy);
+        const float4 loz = __ldg(&n->loz), hiz = __ldg(&n->hiz);
+        const uint4 ch = __ldg(&n->child);
+        const float lx[4] = {lox.x, lox.y, lox.z, lox.w}, hx[4] = {hix.x, hix.y, hix.z, hix.w};
+        const float ly[4] = {loy.x, loy.y, loy.z, loy.w}, hy[4] = {hiy.x, hiy.y, hiy.z, hiy.w};
+        const float lz[4] = {loz.x, loz.y, loz.z, loz.w}, hz[4] = {hiz.x, hiz.y, hiz.z, hiz.w};
+        const uint32_t cref[4] = {ch.x, ch.y, ch.z, ch.w};
+        int count = 0;
+        uint32_t only = kEmptyRef;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const bool ov = cref[c] != kEmptyRef && lx[c] <= qhi.x && hx[c] >= qlo.x &&
+                            ly[c] <= qhi.y && hy[c] >= qlo.y && lz[c] <= qhi.z && hz[c] >= qlo.z;
+            if (ov) {
+                ++count;
+                only = cref[c];
+            }
+        }
+        if (count == 0) return kEmptyRef;
+        if (count > 1 || is_leaf_ref(only)) return count > 1 ? cur : only;
+        cur = only;
+    }
+    return cur;
 }
 
 // Unit geometric normal of BVH triangle `slot`, turned against direction d.

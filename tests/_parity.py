@@ -5,9 +5,12 @@ Tolerances (FP32 path against the FP64 oracle on identical inputs):
     from its threshold: barycentric edge, t interval, tie) is below TRACE_MARGIN;
     such disagreements are listed and may not exceed DISAGREE_FRAC of the pixels
     (at least one pixel is allowed on small images);
-  * hit distance error <= max(T_RTOL * t, T_ATOL * scale), scale = 1 + max|coordinate|
-    (a hit near the ray origin carries the absolute rounding of the coordinates), hit
-    point error <= POS_ATOL * scale and normal error <= NRM_ATOL;
+  * hit distance error <= max(T_RTOL * t, T_ATOL * scale) + DIR_ERR * t / |cos i|, where
+    scale = 1 + max|coordinate| (a hit near the ray origin carries the absolute rounding
+    of the coordinates) and i is the incidence angle of the ray on the hit triangle (the
+    FP32 ray direction differs from the FP64 one by ~DIR_ERR, which a grazing hit turns
+    into a distance error); hit point error <= POS_ATOL * scale plus the same grazing term,
+    normal error <= NRM_ATOL;
   * per-pixel AO / visibility <= OUT_ATOL absolute, except pixels whose reuse margin
     (support tests and validation rays) is below REUSE_MARGIN, listed likewise.
 """
@@ -20,6 +23,7 @@ REUSE_MARGIN = 1e-4
 DISAGREE_FRAC = 1e-4
 T_RTOL = 1e-5
 T_ATOL = 2.0 ** -20
+DIR_ERR = 1e-6
 POS_ATOL = 1e-5
 NRM_ATOL = 2e-6
 OUT_ATOL = 1e-5
@@ -59,7 +63,15 @@ def widen_records(r0: np.ndarray, r1: np.ndarray) -> np.ndarray:
     return rec
 
 
-def compare_trace(occ, orec: np.ndarray, omargin: np.ndarray, valid: np.ndarray, what: str = ""):
+def _cos_incidence(orec: np.ndarray, pos4: np.ndarray, sel: np.ndarray) -> np.ndarray:
+    """Cosine between each hit's ray (receiver -> hit point) and the hit normal."""
+    w = orec[..., :3][sel] - pos4[..., :3].astype(np.float64)[sel]
+    w /= np.linalg.norm(w, axis=-1, keepdims=True)
+    return (w * orec[..., 3:6][sel]).sum(-1)
+
+
+def compare_trace(occ, orec: np.ndarray, omargin: np.ndarray, valid: np.ndarray, pos4: np.ndarray,
+                  what: str = ""):
     r0, r1, tri = gpu_records(occ)
     otri = orec[..., 7].astype(np.int64)
     mism = (tri != otri) & valid
@@ -74,10 +86,12 @@ def compare_trace(occ, orec: np.ndarray, omargin: np.ndarray, valid: np.ndarray,
         scale = 1.0 + np.abs(orec[..., :3][both]).max(axis=-1)
         t_ref = np.abs(orec[..., 6][both])
         t_err = np.abs(r1[..., 3][both] - orec[..., 6][both])
-        t_tol = np.maximum(T_RTOL * t_ref, T_ATOL * scale)
+        # incidence cosine from the oracle record (ray direction = (z - x) / |z - x|)
+        graze = DIR_ERR * t_ref / np.maximum(np.abs(_cos_incidence(orec, pos4, both)), 1e-4)
+        t_tol = np.maximum(T_RTOL * t_ref, T_ATOL * scale) + graze
         assert np.all(t_err <= t_tol), f"{what}: t err {t_err.max()} (worst ratio {(t_err / t_tol).max()})"
         z_err = np.abs(r0[..., :3][both] - orec[..., :3][both]).max(axis=-1)
-        assert (z_err / scale).max() <= POS_ATOL, f"{what}: z err {(z_err / scale).max()}"
+        assert np.all(z_err <= POS_ATOL * scale + graze), f"{what}: z err {z_err.max()}"
         n_err = np.abs(r1[..., :3][both] - orec[..., 3:6][both]).max()
         assert n_err <= NRM_ATOL, f"{what}: n_z err {n_err}"
     return {"mismatch": int(mism.sum()), "hits": int(both.sum()),

@@ -131,7 +131,7 @@ def test_trace_matches_oracle(orc, occ, ctx, which, effect, request):
         ctx.sync()
         orec, omg = orc.trace(s["osc"], effect, s["pos"], s["nrm"], radius=R, light=light,
                               seed=1234, sample=sample)
-        res = P.compare_trace(o, orec, omg, valid, f"{which} effect {effect} sample {sample}")
+        res = P.compare_trace(o, orec, omg, valid, s["pos"], f"{which} effect {effect} sample {sample}")
         assert res["hits"] > 0.03 * valid.sum()
 
 
@@ -182,7 +182,7 @@ def test_reuse_end_to_end(orc, occ, ctx, terrain_small, effect, pname):
         ctx.sync()
         orec, omg = orc.trace(s["osc"], effect, s["pos"], s["nrm"], radius=0.5, light=light,
                               seed=5, sample=0)
-        tr = P.compare_trace(o, orec, omg, valid, "end-to-end trace")
+        tr = P.compare_trace(o, orec, omg, valid, s["pos"], "end-to-end trace")
         ref, mg = orc.reuse(s["osc"], effect, s["pos"], s["nrm"], orec, pat.as_tuple(), est,
                             radius=0.5, light=light)
         err = np.abs(g.cpu().numpy() - ref)[valid]
