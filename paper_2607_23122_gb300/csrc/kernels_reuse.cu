@@ -11,8 +11,10 @@
 //                   exchanged through shared memory), normalises by P_j, and a
 //                   recursive-halving shuffle reduce-scatter (K-1 shuffles) hands lane
 //                   i its B_i = sum_j p(z_j|x_i)/P_j.
+//  k_reuse_tile     (kernels_reuse_tile.cu) biased box / offset windows with the tile
+//                   and its halo staged in shared memory by TMA.
 //  k_reuse_generic  any pattern: one thread per receiver, members' receiver data held
-//                   in registers, K^2 pair densities.
+//                   in registers, K^2 pair densities (unbiased windows, odd groups).
 //  k_reuse_simple   NOREUSE / BOXMEAN.
 #include <cuda_runtime.h>
 
@@ -374,17 +376,25 @@ void launch_generic(const ReuseArgs& a, cudaStream_t s) {
 }
 
 template <int EFFECT>
-void launch_effect(int est, const ReuseArgs& a, cudaStream_t s) {
+cudaError_t launch_effect(int est, const ReuseArgs& a, cudaStream_t s) {
     const dim3 grid((unsigned)((a.gb.W + 15) / 16), (unsigned)((a.gb.H + 7) / 8));
     if (est == kNoReuse) {
         k_reuse_simple<kNoReuse><<<grid, 128, 0, s>>>(a);
     } else if (est == kBoxMean) {
         k_reuse_simple<kBoxMean><<<grid, 128, 0, s>>>(a);
     } else if (est == kBiased) {
-        if (a.pat.kind != 0 || !launch_group<EFFECT, kBiased>(a, s)) launch_generic<EFFECT, kBiased>(a, s);
+        if (a.pat.kind != 0) {
+            cudaError_t e = cudaSuccess;
+            if (launch_reuse_tile(EFFECT, a.gb, a.rec, a.pat, a.R2s, a.lp, a.out, a.status, s, &e))
+                return e;
+            launch_generic<EFFECT, kBiased>(a, s);
+        } else if (!launch_group<EFFECT, kBiased>(a, s)) {
+            launch_generic<EFFECT, kBiased>(a, s);
+        }
     } else {
         if (a.pat.kind != 0 || !launch_group<EFFECT, kUnbiased>(a, s)) launch_generic<EFFECT, kUnbiased>(a, s);
     }
+    return cudaSuccess;
 }
 
 ReuseArgs make_args(const GBufView& gb, const RecView& rec, const PatternParams& pat, float radius,
@@ -408,11 +418,10 @@ cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const Re
                          const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s) {
     if (gb.W <= 0 || gb.H <= 0) return cudaSuccess;
     const ReuseArgs a = make_args(gb, rec, pat, radius, light, bvh, out, status);
-    if (effect == kAO)
-        launch_effect<kAO>(estimator, a, s);
-    else
-        launch_effect<kShadow>(estimator, a, s);
-    return cudaGetLastError();
+    const cudaError_t e = effect == kAO ? launch_effect<kAO>(estimator, a, s)
+                                        : launch_effect<kShadow>(estimator, a, s);
+    const cudaError_t l = cudaGetLastError();
+    return e != cudaSuccess ? e : l;
 }
 
 cudaError_t launch_debug_mis(int effect, int estimator, const GBufView& gb, const RecView& rec,

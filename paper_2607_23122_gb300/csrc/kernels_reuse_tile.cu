@@ -1,0 +1,368 @@
+// kernels_reuse_tile.cu -- biased occluder reuse (Eq. 18 AO / Eq. 24 shadow) for window
+// patterns (a centred box or shared offsets), with the receiver tile and the halo its
+// neighbour sets reach staged in shared memory by the Tensor Memory Accelerator.
+//
+// Persistent CTAs walk the image in TW x TH receiver tiles.  For each tile one thread
+// issues four 2D bulk-tensor copies (cp.async.bulk.tensor) of the G-buffer and record
+// planes -- (TW + halo) x (TH + halo) float4 each, zero-filled outside the image --
+// completing on an mbarrier; every thread then evaluates its receiver's K x K pair
+// densities from shared memory (K receivers held in registers, K candidate records
+// read once each), normalises by P_j = sum_k p(z_j|x_k) and writes 1 - B_i.
+// Waits on the mbarrier are bounded: on expiry the CTA records kStatusWaitTimeoutBit,
+// drains its copies (again bounded) and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "occ_device.cuh"
+#include "occ_kernels.h"
+
+namespace occ {
+namespace {
+
+constexpr float kSupportSlackT = 1.0f + 1.0f / 65536.0f;
+constexpr int kTileW = 32;
+constexpr uint32_t kWaitSpins = 1u << 24;
+
+struct TileArgs {
+    int W, H;
+    int TW, TH;            // receivers per tile
+    int hx0, hy0;          // halo left / top
+    int SW, SH;            // staged extent (pixels)
+    int tiles_x, n_tiles;
+    int stages;            // 1, or 2 to prefetch the next tile during this one
+    int kind, gw, gh, K;   // pattern (kind 1 box, 2 offsets)
+    int2 off[kMaxMembers - 1];
+    float R2s;
+    LightParams lp;
+    float* out;
+    unsigned* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+// Bounded wait for phase `parity` of the barrier.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitSpins; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ RectLight tile_light(const LightParams& p) {
+    RectLight L;
+    L.c = make_float3(p.c[0], p.c[1], p.c[2]);
+    L.eu = make_float3(p.eu[0], p.eu[1], p.eu[2]);
+    L.ev = make_float3(p.ev[0], p.ev[1], p.ev[2]);
+    L.n = normalize3(cross3(L.eu, L.ev));
+    L.inv_eu2 = 1.0f / dot3(L.eu, L.eu);
+    L.inv_ev2 = 1.0f / dot3(L.ev, L.ev);
+    L.lim = 0.5f * kSupportSlackT;
+    return L;
+}
+
+// Receiver terms: AO (x, n); shadow (x, (n_L.(c - x), (x - c).eu, (x - c).ev)).
+template <int EFFECT>
+__device__ __forceinline__ void recv_terms(float4 P, float4 N, const RectLight& L, float3* x,
+                                           float3* t) {
+    *x = f3(P);
+    if (EFFECT == kAO) {
+        *t = f3(N);
+    } else {
+        const float3 xc = sub3(*x, L.c);
+        *t = make_float3(-dot3(L.n, xc), dot3(xc, L.eu), dot3(xc, L.ev));
+    }
+}
+
+// Biased pair density without 1/pi or 1/Area (they cancel in every ratio).
+template <int EFFECT>
+__device__ __forceinline__ float pair_density(float3 z, float3 nz, float3 x, float3 t, float R2s,
+                                              const RectLight& L) {
+    const float3 d = sub3(z, x);
+    if (EFFECT == kAO) {
+        const float r2 = dot3(d, d);
+        const float a = dot3(t, d);
+        const float b = -dot3(nz, d);
+        const bool ok = (a > 0.0f) & (b > 0.0f) & (r2 > 0.0f) & (r2 <= R2s);
+        return ok ? __fdividef(a * b, r2 * r2) : 0.0f;
+    } else {
+        const float nd = dot3(L.n, d);
+        const float cz = -dot3(nz, d);
+        if (!(nd < 0.0f) || !(cz > 0.0f)) return 0.0f;
+        const float inv = 1.0f / nd;
+        const float sL = t.x * inv;
+        if (!(sL > 1.0f)) return 0.0f;
+        const float a = fmaf(sL, dot3(d, L.eu), t.y) * L.inv_eu2;
+        const float b = fmaf(sL, dot3(d, L.ev), t.z) * L.inv_ev2;
+        if (fabsf(a) > L.lim || fabsf(b) > L.lim) return 0.0f;
+        return sL * sL * cz * (-inv);
+    }
+}
+
+template <int EFFECT, int MAXK>
+__global__ void __launch_bounds__(512, 1)
+    k_reuse_tile(const __grid_constant__ CUtensorMap tm_pos, const __grid_constant__ CUtensorMap tm_nrm,
+                 const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ CUtensorMap tm_r1,
+                 const __grid_constant__ TileArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    // bulk-tensor copies need 128-byte aligned shared destinations: align the base (the
+    // launch adds 128 bytes of slack) and round every plane up to a multiple of 128 bytes
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    const int plane = ((a.SW * a.SH + 7) / 8) * 8;          // float4 per plane
+    const uint32_t bytes = 4u * (uint32_t)(a.SW * a.SH) * 16u;   // bytes the copies deliver
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+    }
+    __syncthreads();
+    RectLight L;
+    if (EFFECT == kShadow) L = tile_light(a.lp);
+    const int lx = threadIdx.x % a.TW, ly = threadIdx.x / a.TW;
+    const bool active_thread = ly < a.TH;
+    // buffer b holds the G-buffer and record planes of one staged tile
+    auto issue = [&](int tile, int b) {
+        float4* base = reinterpret_cast<float4*>(smem) + (size_t)b * 4 * plane;
+        const int x0 = (tile % a.tiles_x) * a.TW, y0 = (tile / a.tiles_x) * a.TH;
+        const int gx = 4 * (x0 - a.hx0), gy = y0 - a.hy0;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[b], bytes);
+        tma_load_2d(base, &tm_pos, gx, gy, &bar[b]);
+        tma_load_2d(base + plane, &tm_nrm, gx, gy, &bar[b]);
+        tma_load_2d(base + 2 * plane, &tm_r0, gx, gy, &bar[b]);
+        tma_load_2d(base + 3 * plane, &tm_r1, gx, gy, &bar[b]);
+    };
+    uint32_t parity[2] = {0u, 0u};
+    if (threadIdx.x == 0 && (int)blockIdx.x < a.n_tiles) issue(blockIdx.x, 0);
+    int it = 0;
+    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
+        const int b = a.stages == 2 ? (it & 1) : 0;
+        if (a.stages == 2 && threadIdx.x == 0 && tile + (int)gridDim.x < a.n_tiles)
+            issue(tile + gridDim.x, b ^ 1);   // prefetch: that buffer was released last iteration
+        if (!mbar_wait(&bar[b], parity[b])) {
+            if (threadIdx.x == 0) atomicOr(a.status, kStatusWaitTimeoutBit);
+            mbar_wait(&bar[b], parity[b]);          // let the copies drain (bounded)
+            if (a.stages == 2) mbar_wait(&bar[b ^ 1], parity[b ^ 1]);
+            return;
+        }
+        parity[b] ^= 1u;
+        const float4* s_pos = reinterpret_cast<const float4*>(smem) + (size_t)b * 4 * plane;
+        const float4* s_nrm = s_pos + plane;
+        const float4* s_r0 = s_pos + 2 * plane;
+        const float4* s_r1 = s_pos + 3 * plane;
+        const int x0 = (tile % a.tiles_x) * a.TW, y0 = (tile / a.tiles_x) * a.TH;
+        const int x = x0 + lx, y = y0 + ly;
+        if (active_thread && x < a.W && y < a.H) {
+            const int sc = (ly + a.hy0) * a.SW + (lx + a.hx0);
+            float res = 1.0f;
+            if (s_pos[sc].w != 0.0f) {
+                // member slots: fixed order, invalid or outside members masked out
+                int sidx[MAXK];
+                uint32_t vmask = 0;
+                int self = 0;
+#pragma unroll
+                for (int s = 0; s < MAXK; ++s) {
+                    sidx[s] = sc;
+                    if (s < a.K) {
+                        int dx, dy;
+                        if (a.kind == 1) {
+                            dx = s % a.gw - (a.gw - 1) / 2;
+                            dy = s / a.gw - (a.gh - 1) / 2;
+                        } else {
+                            dx = s == 0 ? 0 : a.off[s - 1].x;
+                            dy = s == 0 ? 0 : a.off[s - 1].y;
+                        }
+                        const int px = x + dx, py = y + dy;
+                        const int q = sc + dy * a.SW + dx;
+                        if (px >= 0 && py >= 0 && px < a.W && py < a.H && s_pos[q].w != 0.0f) {
+                            vmask |= 1u << s;
+                            sidx[s] = q;
+                        }
+                        if (dx == 0 && dy == 0) self = s;
+                    }
+                }
+                float3 rx[MAXK], rt[MAXK];
+#pragma unroll
+                for (int s = 0; s < MAXK; ++s)
+                    recv_terms<EFFECT>(s_pos[sidx[s]], s_nrm[sidx[s]], L, &rx[s], &rt[s]);
+                float B = 0.0f;
+                uint32_t blocked = 0;
+#pragma unroll 1
+                for (int c = 0; c < a.K; ++c) {
+                    if (!((vmask >> c) & 1u)) continue;
+                    const float4 r0 = s_r0[sidx[c]];
+                    if (__float_as_int(r0.w) < 0) continue;
+                    blocked |= 1u << c;
+                    const float3 z = f3(r0), nz = f3(s_r1[sidx[c]]);
+                    float Psum = 0.0f, pi = 0.0f;
+#pragma unroll
+                    for (int s = 0; s < MAXK; ++s) {
+                        if ((vmask >> s) & 1u) {
+                            const float q = pair_density<EFFECT>(z, nz, rx[s], rt[s], a.R2s, L);
+                            Psum += q;
+                            if (s == self) pi = q;
+                        }
+                    }
+                    if (pi > 0.0f) B += pi / Psum;
+                }
+                res = 1.0f - B;
+                if (EFFECT == kShadow && blocked == vmask) res = 0.0f;   // all-blocked guard
+            }
+            a.out[y * a.W + x] = res;
+        }
+        __syncthreads();   // buffer b is free for the copies issued next
+        if (a.stages == 1 && threadIdx.x == 0 && tile + (int)gridDim.x < a.n_tiles)
+            issue(tile + gridDim.x, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2D view of a W x H float4 plane as float32 [H][4W]; box = (4 SW, SH).
+bool make_map(CUtensorMap* m, const void* base, int W, int H, int SW, int SH) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)4 * W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)W * 16};
+    const cuuint32_t box[2] = {(cuuint32_t)(4 * SW), (cuuint32_t)SH};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int EFFECT, int MAXK>
+cudaError_t launch_t(const CUtensorMap* maps, const TileArgs& a, size_t smem, int sms,
+                     cudaStream_t s) {
+    auto k = k_reuse_tile<EFFECT, MAXK>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = a.n_tiles < sms ? a.n_tiles : sms;
+    k<<<grid, a.TW * a.TH, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
+    return cudaPeekAtLastError();
+}
+
+}  // namespace
+
+// Returns false (nothing launched) when the pattern or the staging does not fit this
+// kernel: not a box / offsets pattern, K > 16, a halo wider than the TMA box allows, or a
+// tile that does not fit in shared memory.
+bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const PatternParams& pat,
+                       float R2s, const LightParams& light, float* out, unsigned* status,
+                       cudaStream_t s, cudaError_t* err) {
+    *err = cudaSuccess;
+    if (pat.kind != 1 && pat.kind != 2) return false;
+    if (pat.K > 16) return false;
+    const int hx = pat.halo[0] + pat.halo[1], hy = pat.halo[2] + pat.halo[3];
+    const int SW = kTileW + hx;
+    if (4 * SW > 256) return false;
+    int dev = 0, sms = 0, max_smem = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    // largest tile height whose staging fits; two buffers (prefetch) when they fit
+    int TH = 16, stages = 1;
+    size_t smem = 0;
+    for (; TH >= 4; TH /= 2) {
+        if (hy + TH > 256) continue;
+        smem = (size_t)4 * (((size_t)SW * (TH + hy) + 7) / 8 * 8) * 16;   // 128-byte planes
+        if (2 * smem + 1024 <= (size_t)max_smem) {
+            stages = 2;
+            smem = 2 * smem + 128;
+            break;
+        }
+        if (smem + 1024 <= (size_t)max_smem) {
+            smem += 128;
+            break;
+        }
+    }
+    if (TH < 4) return false;
+    TileArgs a;
+    a.W = gb.W;
+    a.H = gb.H;
+    a.TW = kTileW;
+    a.TH = TH;
+    a.hx0 = pat.halo[0];
+    a.hy0 = pat.halo[2];
+    a.SW = SW;
+    a.SH = TH + hy;
+    a.tiles_x = (gb.W + kTileW - 1) / kTileW;
+    a.n_tiles = a.tiles_x * ((gb.H + TH - 1) / TH);
+    a.stages = stages;
+    a.kind = pat.kind;
+    a.gw = pat.gw;
+    a.gh = pat.gh;
+    a.K = pat.K;
+    for (int i = 0; i < kMaxMembers - 1; ++i) a.off[i] = pat.off[i];
+    a.R2s = R2s;
+    a.lp = light;
+    a.out = out;
+    a.status = status;
+    CUtensorMap maps[4];
+    if (!make_map(&maps[0], gb.pos, gb.W, gb.H, a.SW, a.SH) ||
+        !make_map(&maps[1], gb.nrm, gb.W, gb.H, a.SW, a.SH) ||
+        !make_map(&maps[2], rec.r0, gb.W, gb.H, a.SW, a.SH) ||
+        !make_map(&maps[3], rec.r1, gb.W, gb.H, a.SW, a.SH))
+        return false;
+    if (effect == kAO)
+        *err = pat.K <= 9 ? launch_t<kAO, 9>(maps, a, smem, sms, s) : launch_t<kAO, 16>(maps, a, smem, sms, s);
+    else
+        *err = pat.K <= 9 ? launch_t<kShadow, 9>(maps, a, smem, sms, s)
+                          : launch_t<kShadow, 16>(maps, a, smem, sms, s);
+    return true;
+}
+
+}  // namespace occ

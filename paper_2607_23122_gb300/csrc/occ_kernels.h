@@ -51,6 +51,12 @@ cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
 cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const RecView& rec,
                          const PatternParams& pat, float radius, const LightParams& light,
                          const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s);
+// TMA-staged biased reuse for box / offset patterns; returns false (nothing launched) when
+// the pattern or its staging does not fit that kernel.
+bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const PatternParams& pat,
+                       float R2s, const LightParams& light, float* out, unsigned* status,
+                       cudaStream_t s, cudaError_t* err);
+
 cudaError_t launch_debug_mis(int effect, int estimator, const GBufView& gb, const RecView& rec,
                              const PatternParams& pat, float radius, const LightParams& light,
                              const DevBVH* bvh, const int32_t* pix, int32_t n, int32_t* members,
