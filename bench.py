@@ -36,6 +36,22 @@ FLOPS_PER_PAIR_AO = 21     # d (3), r^2 (5), n_x.d (5), n_z.d (5), product, r^4,
 L2_FLUSH_BYTES = 512 << 20
 
 
+class L2Flush:
+    """Evicts the step's data from L2 before a timed call: writes a buffer four times the
+    L2 size, then reads it back so the lines left behind are clean (otherwise the timed
+    kernel would also pay for writing the flush buffer's dirty lines back to HBM)."""
+
+    def __init__(self, device):
+        import torch
+        self.buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+        self.sink = torch.empty((), dtype=torch.float32, device=device)
+
+    def zero_(self):
+        import torch
+        self.buf.zero_()
+        torch.sum(self.buf, dim=0, out=self.sink)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -163,6 +179,45 @@ def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
                        f"K=8 reuse of the block ({t_total:.1f} s)")}
 
 
+GROUP_BYTES_PER_PX = 52   # x 12, n 12, z 12, n_z 12, out 4
+
+
+def time_kernel(fn, flush, stream, iters: int) -> dict:
+    """Mean CUDA-event time of fn(stream) with the L2 flushed before every call."""
+    import torch
+    for _ in range(3):
+        fn(stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(iters)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        fn(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    t = np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3
+    return {"s": float(t.mean()), "ms": float(t.mean() * 1e3), "ms_min": float(t.min() * 1e3)}
+
+
+def shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream) -> dict:
+    """1080p area-light shadow frame on the same scene: trace, biased K=8 reuse, and the
+    no-reuse and light-sample box-mean (Light(8)) baselines on the same records."""
+    import synth
+    light = synth.light_c3().as_array()
+    tr = time_kernel(lambda st: occ.occ_trace_shadow(ctx, gb, bvh, light, 1, 0, out=rec, stream=st),
+                     flush, stream, 100)
+    ru = time_kernel(lambda st: occ.occ_reuse_shadow(ctx, gb, rec, pat, K, occ.OCC_EST_BIASED,
+                                                     out=out, stream=st), flush, stream, 100)
+    lb = time_kernel(lambda st: occ.occ_reuse_shadow(ctx, gb, rec, pat, K, occ.OCC_EST_BOXMEAN,
+                                                     out=out, stream=st), flush, stream, 100)
+    gr = time_kernel(lambda st: occ.occ_reuse_shadow(ctx, gb, rec, occ.Pattern.group(4, 2), 8,
+                                                     occ.OCC_EST_BIASED, out=out, stream=st),
+                     flush, stream, 100)
+    return {"trace_ms": tr["ms"], "reuse_offsets_k8_ms": ru["ms"], "light8_boxmean_ms": lb["ms"],
+            "reuse_group4x2_ms": gr["ms"], "ms_per_frame": tr["ms"] + ru["ms"],
+            "light": "1 x 0.5 rectangle at z=4 facing down"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -182,7 +237,7 @@ def run_ours(args):
     pat = occ.Pattern.offsets_of(offs)
     rec = occ.Occluders.empty(H, W, dev)
     out = torch.empty((H, W), dtype=torch.float32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -243,6 +298,14 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_e2e = float(tt.item())
 
+    # the paper's own layout: 4x2 shared groups (K = 8) on warp lanes, HBM bound
+    extra = {}
+    if rank == 0:
+        extra["reuse_group4x2"] = time_kernel(
+            lambda st: occ.occ_reuse_ao(ctx, gb, rec, occ.Pattern.group(4, 2), 8, occ.OCC_EST_BIASED,
+                                        out=out, stream=st), flush, stream, 200)
+        extra["shadow"] = shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream)
+
     if rank == 0:
         hbm, peak_kind, peaks = measured_peaks()
         st = bvh.stats
@@ -271,7 +334,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "W": W, "H": H, "K": K, "radius": RADIUS,
                        "tris": scene.num_tris, "pattern": "offsets", "estimator": "biased",
-                       "l2": f"flushed ({L2_FLUSH_BYTES >> 20} MB write) before every step",
+                       "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB written, then read back)",
                        "parallelism": f"replicas x{world}"},
             "reuse_pass": {"neighbour_samples_per_s": P * K / ru, "ms": ru * 1e3},
             "trace_pass": {"rays_per_s": P / tr, "ms": tr * 1e3},
@@ -281,6 +344,12 @@ def run_ours(args):
                     "ms_per_step": t_e2e / e2e_steps * 1e3},
             "gpu_launches": 2 * args.steps,
             "clocks": clk, "wall_s": wall,
+            "reuse_group4x2": dict(extra["reuse_group4x2"], kernel="k_reuse_group<AO,biased,4,2>",
+                                   algorithmic_bytes=P * GROUP_BYTES_PER_PX,
+                                   achieved_gbs=P * GROUP_BYTES_PER_PX / extra["reuse_group4x2"]["s"] / 1e9,
+                                   frac_hbm=P * GROUP_BYTES_PER_PX / extra["reuse_group4x2"]["s"] / 1e9 / hbm,
+                                   neighbour_samples_per_s=P * 8 / extra["reuse_group4x2"]["s"]),
+            "shadow_frame": extra["shadow"],
             "bvh": {"nodes": st["num_nodes"], "depth": st["depth"], "bytes": st["bytes"],
                     "build_s": st["build_seconds"]},
         }

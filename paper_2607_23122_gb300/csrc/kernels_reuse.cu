@@ -225,88 +225,8 @@ __global__ void __launch_bounds__(128) k_reuse_simple(ReuseArgs a) {
 
 // ---------------------------------------------------------------------------------------
 // Warp-cooperative GROUP kernel.  K = GW * GH lanes per group, 32 / K groups per warp
-// laid side by side (warp block = (32/K * GW) x GH pixels), 8 warps stacked per CTA.
+// laid side by side (warp block = (32/K * GW) x GH pixels), 8 warps side by side per CTA.
 // ---------------------------------------------------------------------------------------
-template <int EFFECT, int EST, int GW, int GH>
-__global__ void __launch_bounds__(256) k_reuse_group(ReuseArgs a) {
-    constexpr int K = GW * GH;
-    constexpr int GPW = 32 / K;
-    constexpr int BW = GPW * GW;
-    __shared__ float4 s_x[8][32];
-    __shared__ float4 s_n[8][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane / K, m = lane % K;
-    const int x = blockIdx.x * BW + g * GW + m % GW;
-    const int y = (blockIdx.y * 8 + warp) * GH + m / GW;
-    const bool inside = x < a.gb.W && y < a.gb.H;
-    const int i = inside ? y * a.gb.W + x : 0;
-    RectLight L;
-    if (EFFECT == kShadow) L = make_light_dev(a.lp);
-
-    float4 P = make_float4(0.0f, 0.0f, 0.0f, 0.0f), N = P;
-    float4 R0 = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1)), R1 = P;
-    if (inside) {
-        P = __ldg(a.gb.pos + i);
-        N = __ldg(a.gb.nrm + i);
-        R0 = __ldg(a.rec.r0 + i);
-        R1 = __ldg(a.rec.r1 + i);
-    }
-    const bool valid = inside && P.w != 0.0f;
-    const bool hit = valid && __float_as_int(R0.w) >= 0;
-    // receiver data for the density: AO (x, n); shadow (x, precomputed plane terms)
-    const Recv me = make_recv<EFFECT>(P, N, L);
-    s_x[warp][lane] = make_float4(me.x.x, me.x.y, me.x.z, valid ? 1.0f : 0.0f);
-    s_n[warp][lane] = make_float4(me.n.x, me.n.y, me.n.z, 0.0f);
-    __syncwarp();
-
-    const unsigned gmask = (K == 32 ? 0xFFFFFFFFu : ((1u << K) - 1u)) << (g * K);
-    const unsigned vmask = __ballot_sync(0xFFFFFFFFu, valid) & gmask;
-    const unsigned hmask = __ballot_sync(0xFFFFFFFFu, hit) & gmask;
-
-    // column of candidate z_m: densities at every receiver of the group
-    float r[K];
-    const float3 z = f3(R0), nz = f3(R1);
-    float Psum = 0.0f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const float4 sx = s_x[warp][g * K + k];
-        const float4 sn = s_n[warp][g * K + k];
-        Recv rk;
-        rk.x = f3(sx);
-        rk.n = f3(sn);
-        float q = 0.0f;
-        if (hit && sx.w != 0.0f) q = density<EFFECT>(z, nz, rk, a.R2s, L);
-        if (EST == kUnbiased && q > 0.0f && k != m)
-            if (!first_hit(a.bvh, rk.x, z, (uint32_t)__float_as_int(R0.w), a.status)) q = 0.0f;
-        r[k] = q;
-        Psum += q;
-    }
-    const float inv = Psum > 0.0f ? 1.0f / Psum : 0.0f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r[k] *= inv;
-
-    // reduce-scatter over the group's lanes: lane m ends with sum_j r_j[m]
-#pragma unroll
-    for (int h = K / 2; h >= 1; h >>= 1) {
-        const bool upper = (m & h) != 0;
-#pragma unroll
-        for (int e = 0; e < h; ++e) {
-            const float keep = upper ? r[e + h] : r[e];
-            const float send = upper ? r[e] : r[e + h];
-            r[e] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, h);
-        }
-    }
-    if (!inside) return;
-    float res;
-    if (!valid) {
-        res = 1.0f;
-    } else {
-        res = 1.0f - r[0];
-        if (EFFECT == kShadow && EST == kBiased && vmask == hmask) res = 0.0f;
-    }
-    a.out[i] = res;
-}
-
 // ---------------------------------------------------------------------------------------
 // MIS weights of selected receivers (debug / tests): w[a][b] = p(z_a|x_b) / P_a.
 // ---------------------------------------------------------------------------------------
@@ -346,13 +266,120 @@ __global__ void k_debug_mis(ReuseArgs a, const int32_t* pix, int32_t npix, int32
     }
 }
 
+// Loading the hit-normal plane only for rays that hit saves bytes but adds a dependent
+// round trip; OCC_GROUP_EAGER_R1=1 loads it together with the other planes (measured
+// slower for AO at 1080p: 32.2 vs 28.8 us).
+#ifndef OCC_GROUP_EAGER_R1
+#define OCC_GROUP_EAGER_R1 0
+#endif
+// warps per CTA of the group kernel (side by side) and the load flavour: every byte of
+// the G-buffer and records is read exactly once, so streaming loads (evict-first) can be
+// used instead of read-only cached loads.
+#ifndef OCC_GROUP_WARPS
+#define OCC_GROUP_WARPS 8
+#endif
+#ifndef OCC_GROUP_STREAM_LOADS
+#define OCC_GROUP_STREAM_LOADS 0
+#endif
+template <typename T>
+__device__ __forceinline__ T group_load(const T* p) {
+    if (OCC_GROUP_STREAM_LOADS) return __ldcs(p);
+    return __ldg(p);
+}
+
+template <int EFFECT, int EST, int GW, int GH>
+__global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs a) {
+    constexpr int K = GW * GH;
+    constexpr int GPW = 32 / K;
+    constexpr int BW = GPW * GW;
+    // receiver exchange buffer; group slots are K + 2 float4 apart so that the groups of a
+    // warp reading their k-th member hit different shared-memory banks
+    constexpr int GS = K + 2;
+    __shared__ float4 s_x[OCC_GROUP_WARPS][GPW * GS];
+    __shared__ float4 s_n[OCC_GROUP_WARPS][GPW * GS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / K, m = lane % K;
+    // the CTA's warps sit side by side: each row of the CTA is contiguous pixels
+    const int x = (blockIdx.x * OCC_GROUP_WARPS + warp) * BW + g * GW + m % GW;
+    const int y = blockIdx.y * GH + m / GW;
+    const bool inside = x < a.gb.W && y < a.gb.H;
+    const int i = inside ? y * a.gb.W + x : 0;
+    RectLight L;
+    if (EFFECT == kShadow) L = make_light_dev(a.lp);
+
+    float4 P = make_float4(0.0f, 0.0f, 0.0f, 0.0f), N = P;
+    float4 R0 = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1)), R1 = P;
+    if (inside) {
+        P = group_load(a.gb.pos + i);
+        N = group_load(a.gb.nrm + i);
+        R0 = group_load(a.rec.r0 + i);
+        if (OCC_GROUP_EAGER_R1) R1 = group_load(a.rec.r1 + i);
+    }
+    const bool valid = inside && P.w != 0.0f;
+    const bool hit = valid && __float_as_int(R0.w) >= 0;
+    // a ray that missed provides no candidate, so its hit normal is not needed
+    if (!OCC_GROUP_EAGER_R1 && hit) R1 = group_load(a.rec.r1 + i);
+    // receiver data for the density: AO (x, n); shadow (x, precomputed plane terms)
+    const Recv me = make_recv<EFFECT>(P, N, L);
+    s_x[warp][g * GS + m] = make_float4(me.x.x, me.x.y, me.x.z, valid ? 1.0f : 0.0f);
+    s_n[warp][g * GS + m] = make_float4(me.n.x, me.n.y, me.n.z, 0.0f);
+    __syncwarp();
+
+    const unsigned gmask = (K == 32 ? 0xFFFFFFFFu : ((1u << K) - 1u)) << (g * K);
+    const unsigned vmask = __ballot_sync(0xFFFFFFFFu, valid) & gmask;
+    const unsigned hmask = __ballot_sync(0xFFFFFFFFu, hit) & gmask;
+
+    // column of candidate z_m: densities at every receiver of the group
+    float r[K];
+    const float3 z = f3(R0), nz = f3(R1);
+    float Psum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 sx = s_x[warp][g * GS + k];
+        const float4 sn = s_n[warp][g * GS + k];
+        Recv rk;
+        rk.x = f3(sx);
+        rk.n = f3(sn);
+        float q = 0.0f;
+        if (hit && sx.w != 0.0f) q = density<EFFECT>(z, nz, rk, a.R2s, L);
+        if (EST == kUnbiased && q > 0.0f && k != m)
+            if (!first_hit(a.bvh, rk.x, z, (uint32_t)__float_as_int(R0.w), a.status)) q = 0.0f;
+        r[k] = q;
+        Psum += q;
+    }
+    const float inv = Psum > 0.0f ? 1.0f / Psum : 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r[k] *= inv;
+
+    // reduce-scatter over the group's lanes: lane m ends with sum_j r_j[m]
+#pragma unroll
+    for (int h = K / 2; h >= 1; h >>= 1) {
+        const bool upper = (m & h) != 0;
+#pragma unroll
+        for (int e = 0; e < h; ++e) {
+            const float keep = upper ? r[e + h] : r[e];
+            const float send = upper ? r[e] : r[e + h];
+            r[e] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, h);
+        }
+    }
+    if (!inside) return;
+    float res = 1.0f;
+    if (valid) {
+        res = 1.0f - r[0];
+        if (EFFECT == kShadow && EST == kBiased && vmask == hmask) res = 0.0f;
+    }
+    a.out[i] = res;
+}
+
 template <int EFFECT, int EST, int GW, int GH>
 void launch_group_t(const ReuseArgs& a, cudaStream_t s) {
     constexpr int K = GW * GH;
     constexpr int BW = (32 / K) * GW;
-    const dim3 grid((unsigned)((a.gb.W + BW - 1) / BW), (unsigned)((a.gb.H + 8 * GH - 1) / (8 * GH)));
-    k_reuse_group<EFFECT, EST, GW, GH><<<grid, 256, 0, s>>>(a);
+    constexpr int CW = OCC_GROUP_WARPS * BW;
+    const dim3 grid((unsigned)((a.gb.W + CW - 1) / CW), (unsigned)((a.gb.H + GH - 1) / GH));
+    k_reuse_group<EFFECT, EST, GW, GH><<<grid, 32 * OCC_GROUP_WARPS, 0, s>>>(a);
 }
+
 
 template <int EFFECT, int EST>
 bool launch_group(const ReuseArgs& a, cudaStream_t s) {
