@@ -67,7 +67,19 @@ enum { OCC_EST_NOREUSE = 0, OCC_EST_BIASED = 1, OCC_EST_UNBIASED = 2, OCC_EST_BO
  * Members outside the image or with an invalid G-buffer entry are dropped. */
 enum { OCC_PAT_GROUP = 0, OCC_PAT_BOX = 1, OCC_PAT_OFFSETS = 2 };
 
-enum { OCC_REC_FP32 = 0 };
+/* Storage formats.  FP32: as described at occ_gbuffer / occ_occluders.  PACKED (16 bytes
+ * per pixel each, FP32 arithmetic on the unpacked values):
+ *  - G-buffer: one float4 plane (x.xyz, normal as octahedral 2 x 16-bit snorm code in the
+ *    w bits; code 0x80008000 marks an invalid pixel);
+ *  - records: one 16-byte plane: words 0-1 hold z - x_source as three 21-bit signed
+ *    fixed-point numbers in units of offset_scale * 2^-20 (bits 0-20, 21-41, 42-62) and
+ *    bit 63 = occluder present; word 2 the octahedral n_z code; word 3 the triangle
+ *    id or -1.  offset_scale (written by the trace) bounds |z - x_source|: R for AO,
+ *    for shadows the largest distance between the scene's bounding box and the light.
+ * Octahedral normals: Cigolle et al., "A Survey of Efficient Representations for
+ * Independent Unit Vectors", JCGT 2014. */
+enum { OCC_GB_FP32 = 0, OCC_GB_PACKED = 1 };
+enum { OCC_REC_FP32 = 0, OCC_REC_PACKED = 1 };
 
 typedef struct occ_ctx occ_ctx;   /* opaque: device, status word, workspace */
 typedef struct occ_bvh occ_bvh;   /* opaque: device-resident wide BVH */
@@ -78,8 +90,9 @@ typedef struct occ_bvh occ_bvh;   /* opaque: device-resident wide BVH */
  * geometric normal facing the viewer.  Both W*H float4, row-major. */
 typedef struct {
     int32_t W, H;
-    const float* pos4;
-    const float* nrm4;
+    const float* pos4;         /* FP32: pos4 plane; PACKED: the packed plane */
+    const float* nrm4;         /* FP32: nrm4 plane; PACKED: unused (NULL) */
+    int32_t format;            /* OCC_GB_FP32 (0) or OCC_GB_PACKED */
 } occ_gbuffer;
 
 /* Rectangle light c + a eu + b ev, a, b in [-1/2, 1/2], eu orthogonal to ev.
@@ -88,19 +101,21 @@ typedef struct {
 typedef struct { float c[3], eu[3], ev[3]; } occ_rect_light;
 
 /* Occluder records (Alg. 1/2 step 1: "store hit position and oriented hit
- * normal").  `data` is caller-owned device memory of 32 * W * H bytes holding
+ * normal").  `data` is caller-owned device memory.  FP32: 32 * W * H bytes holding
  * two float4 planes: plane 0 [p] = (z.xyz, triangle id as int bits, -1 = no
  * occluder), plane 1 [W*H + p] = (n_z.xyz facing the source receiver, t).
- * The trace calls fill the remaining fields; the reuse calls read them. */
+ * PACKED: 16 * W * H bytes (see the formats above).  The trace calls write the
+ * format given in `format` and fill the remaining fields; the reuse calls read them. */
 typedef struct {
     int32_t W, H;
-    int32_t format;            /* OCC_REC_FP32 */
+    int32_t format;            /* OCC_REC_FP32 or OCC_REC_PACKED */
     void* data;
     int32_t effect;            /* written by trace */
     float radius;              /* AO radius R (AO) */
     occ_rect_light light;      /* light (shadow) */
     uint64_t seed;
     uint32_t sample;
+    float offset_scale;        /* PACKED: offset unit * 2^20 (written by trace) */
 } occ_occluders;
 
 typedef struct {
@@ -146,6 +161,11 @@ occ_status occ_bvh_info(const occ_bvh* bvh, occ_bvh_stats* out);
 occ_status occ_gbuffer_pinhole(occ_ctx* ctx, const occ_bvh* bvh, const float* cam_host,
                                float eps, int32_t W, int32_t H, float* pos4, float* nrm4,
                                void* stream);
+
+/* Packs an FP32 G-buffer into the PACKED format (16 bytes per pixel): receiver
+ * point kept in FP32, normal octahedral-encoded; invalid pixels get the invalid
+ * code.  packed_out: W*H float4, device, 16-byte aligned. */
+occ_status occ_pack_gbuffer(occ_ctx* ctx, const occ_gbuffer* gb, float* packed_out, void* stream);
 
 /* ---- hot path ------------------------------------------------------------- */
 

@@ -20,12 +20,14 @@ STATUS_NAMES = {0: "OCC_OK", 1: "OCC_ERR_INVALID_ARG", 2: "OCC_ERR_CUDA", 3: "OC
 OCC_EFFECT_AO, OCC_EFFECT_SHADOW = 0, 1
 OCC_EST_NOREUSE, OCC_EST_BIASED, OCC_EST_UNBIASED, OCC_EST_BOXMEAN = 0, 1, 2, 3
 OCC_PAT_GROUP, OCC_PAT_BOX, OCC_PAT_OFFSETS = 0, 1, 2
-OCC_REC_FP32 = 0
+OCC_REC_FP32, OCC_REC_PACKED = 0, 1
+OCC_GB_FP32, OCC_GB_PACKED = 0, 1
 MAX_MEMBERS = 64
 
 
 class occ_gbuffer(C.Structure):
-    _fields_ = [("W", c_int32), ("H", c_int32), ("pos4", c_void_p), ("nrm4", c_void_p)]
+    _fields_ = [("W", c_int32), ("H", c_int32), ("pos4", c_void_p), ("nrm4", c_void_p),
+                ("format", c_int32)]
 
 
 class occ_rect_light(C.Structure):
@@ -35,7 +37,7 @@ class occ_rect_light(C.Structure):
 class occ_occluders(C.Structure):
     _fields_ = [("W", c_int32), ("H", c_int32), ("format", c_int32), ("data", c_void_p),
                 ("effect", c_int32), ("radius", c_float), ("light", occ_rect_light),
-                ("seed", c_uint64), ("sample", c_uint32)]
+                ("seed", c_uint64), ("sample", c_uint32), ("offset_scale", c_float)]
 
 
 class occ_pattern(C.Structure):
@@ -61,6 +63,7 @@ SIGNATURES = {
     "occ_bvh_info": (c_int32, [c_void_p, C.POINTER(occ_bvh_stats)]),
     "occ_gbuffer_pinhole": (c_int32, [c_void_p, c_void_p, c_void_p, c_float, c_int32, c_int32,
                                       c_void_p, c_void_p, c_void_p]),
+    "occ_pack_gbuffer": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p, c_void_p]),
     "occ_trace_ao": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p, c_float, c_uint64,
                                c_uint32, C.POINTER(occ_occluders), c_void_p]),
     "occ_trace_shadow": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p,

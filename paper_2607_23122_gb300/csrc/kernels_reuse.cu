@@ -58,17 +58,38 @@ struct Recv {
 };
 
 template <int EFFECT>
-__device__ __forceinline__ Recv make_recv(float4 P, float4 N, const RectLight& L) {
+__device__ __forceinline__ Recv make_recv(float3 x, float3 n, bool valid, const RectLight& L) {
     Recv r;
-    r.x = f3(P);
-    r.valid = P.w != 0.0f;
+    r.x = x;
+    r.valid = valid;
     if (EFFECT == kAO) {
-        r.n = f3(N);
+        r.n = n;
     } else {
         const float3 xc = sub3(r.x, L.c);
         r.n = make_float3(-dot3(L.n, xc), dot3(xc, L.eu), dot3(xc, L.ev));
     }
     return r;
+}
+
+// Receiver data of pixel q, from either G-buffer format.
+template <int EFFECT>
+__device__ __forceinline__ Recv fetch_recv(const GBufView& gb, int q, const RectLight& L) {
+    float3 x = make_float3(0.0f, 0.0f, 0.0f), n = x;
+    const bool v = gb_fetch(gb.pos, gb.nrm, gb.packed != 0, q, &x, &n);
+    return make_recv<EFFECT>(x, n, v, L);
+}
+
+// Candidate of pixel q whose own receiver point is xsrc: occluder point and normal; returns
+// the triangle id (< 0: no occluder).  Either record format.
+__device__ __forceinline__ int fetch_cand(const RecView& rec, int q, float3 xsrc, float3* z,
+                                          float3* nz) {
+    const float4 r0 = __ldg(rec.r0 + q);
+    const int tri = __float_as_int(r0.w);
+    if (tri < 0) return tri;
+    if (rec.packed) return rec_unpack(r0, xsrc, rec.scale, z, nz);
+    *z = f3(r0);
+    *nz = f3(__ldg(rec.r1 + q));
+    return tri;
 }
 
 // Eq. 15 without Occ and 1/pi: max(0, n_x.d) max(0, -n_z.d) / r^4 inside the radius.
@@ -141,7 +162,7 @@ __device__ __forceinline__ int gather_members(const PatternParams& pat, const GB
         }
         if (px < 0 || py < 0 || px >= gb.W || py >= gb.H) continue;
         const int q = py * gb.W + px;
-        if (__ldg(&gb.pos[q].w) == 0.0f) continue;
+        if (!gb_valid(gb.pos, gb.packed != 0, q)) continue;
         if (px == x && py == y) *self = n;
         if (n < MAXK) mem[n++] = q;
     }
@@ -157,7 +178,7 @@ __global__ void __launch_bounds__(128) k_reuse_generic(ReuseArgs a) {
     tile_pixel(&x, &y);
     if (x >= a.gb.W || y >= a.gb.H) return;
     const int i = y * a.gb.W + x;
-    if (__ldg(&a.gb.pos[i].w) == 0.0f) {
+    if (!gb_valid(a.gb.pos, a.gb.packed != 0, i)) {
         a.out[i] = 1.0f;
         return;
     }
@@ -169,17 +190,15 @@ __global__ void __launch_bounds__(128) k_reuse_generic(ReuseArgs a) {
     Recv rk[MAXK];
 #pragma unroll
     for (int b = 0; b < MAXK; ++b)
-        if (b < n) rk[b] = make_recv<EFFECT>(__ldg(a.gb.pos + mem[b]), __ldg(a.gb.nrm + mem[b]), L);
+        if (b < n) rk[b] = fetch_recv<EFFECT>(a.gb, mem[b], L);
     float B = 0.0f;
     int blocked = 0;
 #pragma unroll 1
     for (int c = 0; c < n; ++c) {
-        const int j = mem[c];
-        const float4 r0 = __ldg(a.rec.r0 + j);
-        const int tri = __float_as_int(r0.w);
+        float3 z, nz;
+        const int tri = fetch_cand(a.rec, mem[c], f3(__ldg(a.gb.pos + mem[c])), &z, &nz);
         if (tri < 0) continue;
         ++blocked;
-        const float3 z = f3(r0), nz = f3(__ldg(a.rec.r1 + j));
         float Psum = 0.0f, pi = 0.0f;
 #pragma unroll
         for (int b = 0; b < MAXK; ++b) {
@@ -207,7 +226,7 @@ __global__ void __launch_bounds__(128) k_reuse_simple(ReuseArgs a) {
     tile_pixel(&x, &y);
     if (x >= a.gb.W || y >= a.gb.H) return;
     const int i = y * a.gb.W + x;
-    if (__ldg(&a.gb.pos[i].w) == 0.0f) {
+    if (!gb_valid(a.gb.pos, a.gb.packed != 0, i)) {
         a.out[i] = 1.0f;
         return;
     }
@@ -242,18 +261,18 @@ __global__ void k_debug_mis(ReuseArgs a, const int32_t* pix, int32_t npix, int32
     int mem[kMaxMembers];
     int self;
     int n = 0;
-    if (a.gb.pos[i].w != 0.0f) n = gather_members<kMaxMembers>(a.pat, a.gb, x, y, mem, &self);
+    if (gb_valid(a.gb.pos, a.gb.packed != 0, i))
+        n = gather_members<kMaxMembers>(a.pat, a.gb, x, y, mem, &self);
     for (int c = 0; c < kMaxMembers; ++c) members[t * kMaxMembers + c] = c < n ? mem[c] : -1;
     float* wt = w + (size_t)t * kMaxMembers * kMaxMembers;
     for (int c = 0; c < n; ++c) {
-        const float4 r0 = a.rec.r0[mem[c]];
-        const int tri = __float_as_int(r0.w);
-        const float3 z = f3(r0), nz = f3(a.rec.r1[mem[c]]);
+        float3 z, nz;
+        const int tri = fetch_cand(a.rec, mem[c], fetch_recv<EFFECT>(a.gb, mem[c], L).x, &z, &nz);
         float Psum = 0.0f;
         for (int b = 0; b < n; ++b) {
             float q = 0.0f;
             if (tri >= 0) {
-                const Recv rk = make_recv<EFFECT>(a.gb.pos[mem[b]], a.gb.nrm[mem[b]], L);
+                const Recv rk = fetch_recv<EFFECT>(a.gb, mem[b], L);
                 q = density<EFFECT>(z, nz, rk, a.R2s, L);
                 if (EST == kUnbiased && q > 0.0f && b != c)
                     if (!first_hit(a.bvh, rk.x, z, (uint32_t)tri, a.status)) q = 0.0f;
@@ -287,7 +306,7 @@ __device__ __forceinline__ T group_load(const T* p) {
     return __ldg(p);
 }
 
-template <int EFFECT, int EST, int GW, int GH>
+template <int EFFECT, int EST, int GW, int GH, bool PACKED>
 __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs a) {
     constexpr int K = GW * GH;
     constexpr int GPW = 32 / K;
@@ -309,18 +328,35 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
 
     float4 P = make_float4(0.0f, 0.0f, 0.0f, 0.0f), N = P;
     float4 R0 = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1)), R1 = P;
-    if (inside) {
-        P = group_load(a.gb.pos + i);
-        N = group_load(a.gb.nrm + i);
-        R0 = group_load(a.rec.r0 + i);
-        if (OCC_GROUP_EAGER_R1) R1 = group_load(a.rec.r1 + i);
+    float3 z = make_float3(0.0f, 0.0f, 0.0f), nz = z, nx = z;
+    bool valid, hit;
+    if (PACKED) {
+        // 16 + 16 bytes per pixel: (x, octahedral normal) and the packed record
+        if (inside) {
+            P = group_load(a.gb.pos + i);
+            R0 = group_load(a.rec.r0 + i);
+        }
+        valid = inside && __float_as_uint(P.w) != kOctInvalid;
+        hit = valid && __float_as_int(R0.w) >= 0;
+        if (valid) nx = oct_decode(__float_as_uint(P.w));
+        if (hit) rec_unpack(R0, f3(P), a.rec.scale, &z, &nz);
+    } else {
+        if (inside) {
+            P = group_load(a.gb.pos + i);
+            N = group_load(a.gb.nrm + i);
+            R0 = group_load(a.rec.r0 + i);
+            if (OCC_GROUP_EAGER_R1) R1 = group_load(a.rec.r1 + i);
+        }
+        valid = inside && P.w != 0.0f;
+        hit = valid && __float_as_int(R0.w) >= 0;
+        // a ray that missed provides no candidate, so its hit normal is not needed
+        if (!OCC_GROUP_EAGER_R1 && hit) R1 = group_load(a.rec.r1 + i);
+        nx = f3(N);
+        z = f3(R0);
+        nz = f3(R1);
     }
-    const bool valid = inside && P.w != 0.0f;
-    const bool hit = valid && __float_as_int(R0.w) >= 0;
-    // a ray that missed provides no candidate, so its hit normal is not needed
-    if (!OCC_GROUP_EAGER_R1 && hit) R1 = group_load(a.rec.r1 + i);
     // receiver data for the density: AO (x, n); shadow (x, precomputed plane terms)
-    const Recv me = make_recv<EFFECT>(P, N, L);
+    const Recv me = make_recv<EFFECT>(f3(P), nx, valid, L);
     s_x[warp][g * GS + m] = make_float4(me.x.x, me.x.y, me.x.z, valid ? 1.0f : 0.0f);
     s_n[warp][g * GS + m] = make_float4(me.n.x, me.n.y, me.n.z, 0.0f);
     __syncwarp();
@@ -331,7 +367,6 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
 
     // column of candidate z_m: densities at every receiver of the group
     float r[K];
-    const float3 z = f3(R0), nz = f3(R1);
     float Psum = 0.0f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -377,13 +412,17 @@ void launch_group_t(const ReuseArgs& a, cudaStream_t s) {
     constexpr int BW = (32 / K) * GW;
     constexpr int CW = OCC_GROUP_WARPS * BW;
     const dim3 grid((unsigned)((a.gb.W + CW - 1) / CW), (unsigned)((a.gb.H + GH - 1) / GH));
-    k_reuse_group<EFFECT, EST, GW, GH><<<grid, 32 * OCC_GROUP_WARPS, 0, s>>>(a);
+    if (a.gb.packed && a.rec.packed)
+        k_reuse_group<EFFECT, EST, GW, GH, true><<<grid, 32 * OCC_GROUP_WARPS, 0, s>>>(a);
+    else if (!a.gb.packed && !a.rec.packed)
+        k_reuse_group<EFFECT, EST, GW, GH, false><<<grid, 32 * OCC_GROUP_WARPS, 0, s>>>(a);
 }
 
 
 template <int EFFECT, int EST>
 bool launch_group(const ReuseArgs& a, cudaStream_t s) {
     const int gw = a.pat.gw, gh = a.pat.gh;
+    if ((a.gb.packed != 0) != (a.rec.packed != 0)) return false;
     if (gw == 2 && gh == 1) { launch_group_t<EFFECT, EST, 2, 1>(a, s); return true; }
     if (gw == 2 && gh == 2) { launch_group_t<EFFECT, EST, 2, 2>(a, s); return true; }
     if (gw == 4 && gh == 2) { launch_group_t<EFFECT, EST, 4, 2>(a, s); return true; }
@@ -412,7 +451,8 @@ cudaError_t launch_effect(int est, const ReuseArgs& a, cudaStream_t s) {
     } else if (est == kBiased) {
         if (a.pat.kind != 0) {
             cudaError_t e = cudaSuccess;
-            if (launch_reuse_tile(EFFECT, a.gb, a.rec, a.pat, a.R2s, a.lp, a.out, a.status, s, &e))
+            if (!a.gb.packed && !a.rec.packed &&
+                launch_reuse_tile(EFFECT, a.gb, a.rec, a.pat, a.R2s, a.lp, a.out, a.status, s, &e))
                 return e;
             launch_generic<EFFECT, kBiased>(a, s);
         } else if (!launch_group<EFFECT, kBiased>(a, s)) {

@@ -51,6 +51,20 @@ __device__ __forceinline__ float3 step1_ray(float3 x, float3 n, uint32_t p, floa
     }
 }
 
+// Record of receiver p (tri < 0: no occluder) in the buffer's format.
+__device__ __forceinline__ void write_record(const RecView& rec, uint32_t p, float3 xsrc, float3 z,
+                                             float3 nz, float t, int tri) {
+    if (rec.packed) {
+        rec.r0[p] = rec_pack(xsrc, z, nz, tri, rec.scale);
+    } else if (tri < 0) {
+        rec.r0[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
+        rec.r1[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    } else {
+        rec.r0[p] = make_float4(z.x, z.y, z.z, __int_as_float(tri));
+        rec.r1[p] = make_float4(nz.x, nz.y, nz.z, t);
+    }
+}
+
 // Box holding every AO segment of the warp: the valid origins widened by the radius
 // (with slack for the rounding of |direction| and of the box test), reduced over lanes.
 __device__ __forceinline__ uint32_t warp_start_node(const DevBVH& bvh, bool valid, float3 x,
@@ -82,32 +96,27 @@ __global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS) k_trace(GBufView gb
     tile_pixel(&x, &y);
     const bool inside = x < gb.W && y < gb.H;
     const uint32_t p = inside ? (uint32_t)y * (uint32_t)gb.W + (uint32_t)x : 0u;
-    const float4 P = inside ? __ldg(gb.pos + p) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    const bool valid = inside && P.w != 0.0f;
-    const float3 xo = f3(P);
+    float3 xo = make_float3(0.0f, 0.0f, 0.0f), n = xo;
+    const bool valid = inside && gb_fetch(gb.pos, gb.nrm, gb.packed != 0, (int)p, &xo, &n);
     // AO segments are short: start below the part of the tree they cannot leave
     const uint32_t start = EFFECT == kAO ? warp_start_node(bvh, valid, xo, radius) : 0u;
     if (!inside) return;
     if (!valid) {
-        rec.r0[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
-        rec.r1[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        write_record(rec, p, xo, xo, xo, 0.0f, -1);
         return;
     }
-    const float3 n = f3(__ldg(gb.nrm + p));
     RectLight L;
     if (EFFECT == kShadow) L = make_light(lp);
     float tmax;
     const float3 d = step1_ray<EFFECT>(xo, n, p, radius, L, seed, sample, &tmax);
     const Hit h = closest_hit(bvh, xo, d, tmax, status, start);
     if (h.id == kNoHit) {
-        rec.r0[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
-        rec.r1[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        write_record(rec, p, xo, xo, xo, 0.0f, -1);
         return;
     }
     const float3 nz = hit_normal(bvh, h.slot, d);
-    rec.r0[p] = make_float4(fmaf(h.t, d.x, xo.x), fmaf(h.t, d.y, xo.y), fmaf(h.t, d.z, xo.z),
-                            __uint_as_float(h.id));
-    rec.r1[p] = make_float4(nz.x, nz.y, nz.z, h.t);
+    const float3 z = make_float3(fmaf(h.t, d.x, xo.x), fmaf(h.t, d.y, xo.y), fmaf(h.t, d.z, xo.z));
+    write_record(rec, p, xo, z, nz, h.t, (int)h.id);
 }
 
 __global__ void __launch_bounds__(128) k_gbuffer(DevBVH bvh, float3 eye, float3 f, float3 rt,
@@ -152,16 +161,25 @@ __global__ void k_debug_rays(GBufView gb, float radius, LightParams lp, uint64_t
     tile_pixel(&x, &y);
     if (x >= gb.W || y >= gb.H) return;
     const uint32_t p = (uint32_t)y * (uint32_t)gb.W + (uint32_t)x;
-    const float4 P = gb.pos[p];
-    if (P.w == 0.0f) {
+    float3 xo, n;
+    if (!gb_fetch(gb.pos, gb.nrm, gb.packed != 0, (int)p, &xo, &n)) {
         out[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         return;
     }
     RectLight L;
     if (EFFECT == kShadow) L = make_light(lp);
     float tmax;
-    const float3 d = step1_ray<EFFECT>(f3(P), f3(gb.nrm[p]), p, radius, L, seed, sample, &tmax);
+    const float3 d = step1_ray<EFFECT>(xo, n, p, radius, L, seed, sample, &tmax);
     out[p] = make_float4(d.x, d.y, d.z, tmax);
+}
+
+// FP32 G-buffer -> packed G-buffer (receiver point kept, normal octahedral-encoded).
+__global__ void k_pack_gbuffer(GBufView gb, float4* out) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)gb.W * gb.H) return;
+    const float4 P = __ldg(gb.pos + p);
+    const uint32_t code = P.w != 0.0f ? oct_encode(f3(__ldg(gb.nrm + p))) : kOctInvalid;
+    out[p] = make_float4(P.x, P.y, P.z, __uint_as_float(code));
 }
 
 dim3 tile_grid(int W, int H) {
@@ -200,6 +218,13 @@ cudaError_t launch_gbuffer(const DevBVH& bvh, const float* cam, float eps, int W
     const float th = tanf(0.5f * cam[9] * 3.14159265358979f / 180.0f);
     k_gbuffer<<<tile_grid(W, H), 128, 0, s>>>(bvh, eye, f, rt, up, th, (float)W / (float)H, eps,
                                               W, H, pos, nrm, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_gbuffer(const GBufView& gb, float4* out, cudaStream_t s) {
+    const int64_t n = (int64_t)gb.W * gb.H;
+    if (n <= 0) return cudaSuccess;
+    k_pack_gbuffer<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(gb, out);
     return cudaGetLastError();
 }
 

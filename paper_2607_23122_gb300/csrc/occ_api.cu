@@ -31,6 +31,7 @@ struct occ_bvh {
     occ::Node4* nodes = nullptr;
     float4* tris = nullptr;
     occ_bvh_stats stats{};
+    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // scene bounds
 };
 
 namespace {
@@ -65,8 +66,11 @@ occ_status check_gbuffer(occ_ctx* ctx, const occ_gbuffer* gb) {
     if (!gb) return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer is NULL");
     if (gb->W <= 0 || gb->H <= 0 || (int64_t)gb->W * gb->H > (int64_t)1 << 31)
         return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer size %dx%d out of range", gb->W, gb->H);
-    if (!gb->pos4 || !gb->nrm4) return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pointers are NULL");
-    if (!aligned16(gb->pos4) || !aligned16(gb->nrm4))
+    if (gb->format != OCC_GB_FP32 && gb->format != OCC_GB_PACKED)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer format %d invalid", gb->format);
+    if (!gb->pos4 || (gb->format == OCC_GB_FP32 && !gb->nrm4))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pointers are NULL");
+    if (!aligned16(gb->pos4) || (gb->format == OCC_GB_FP32 && !aligned16(gb->nrm4)))
         return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pointers must be 16-byte aligned");
     return OCC_OK;
 }
@@ -76,7 +80,7 @@ occ_status check_occluders(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occlud
     if (o->W != gb->W || o->H != gb->H)
         return fail(ctx, OCC_ERR_INVALID_ARG, "occluder size %dx%d != gbuffer size %dx%d", o->W,
                     o->H, gb->W, gb->H);
-    if (o->format != OCC_REC_FP32)
+    if (o->format != OCC_REC_FP32 && o->format != OCC_REC_PACKED)
         return fail(ctx, OCC_ERR_UNSUPPORTED, "occluder format %d not supported", o->format);
     if (!o->data || !aligned16(o->data))
         return fail(ctx, OCC_ERR_INVALID_ARG, "occluder data must be a 16-byte aligned pointer");
@@ -158,12 +162,38 @@ occ_status make_pattern(occ_ctx* ctx, const occ_pattern* pat, int32_t K, occ::Pa
 
 occ::GBufView view(const occ_gbuffer* gb) {
     return occ::GBufView{gb->W, gb->H, reinterpret_cast<const float4*>(gb->pos4),
-                         reinterpret_cast<const float4*>(gb->nrm4)};
+                         reinterpret_cast<const float4*>(gb->nrm4), gb->format == OCC_GB_PACKED};
 }
 
 occ::RecView rec_view(const occ_occluders* o) {
     float4* base = reinterpret_cast<float4*>(o->data);
-    return occ::RecView{base, base + (size_t)o->W * o->H};
+    if (o->format == OCC_REC_PACKED) return occ::RecView{base, nullptr, 1, o->offset_scale};
+    return occ::RecView{base, base + (size_t)o->W * o->H, 0, 0.0f};
+}
+
+// Bound on |z - x_source| for packed records: R for AO; for shadows the largest distance
+// between the scene box (grown by 1% of its diagonal, covering the receiver offsets) and
+// the light rectangle -- both convex, so the maximum is found at their corners.
+float offset_scale_for(const occ_bvh* bvh, int effect, float radius, const occ_rect_light* L) {
+    if (effect == OCC_EFFECT_AO) return radius * (1.0f + 1.0f / 1024.0f);
+    double diag = 0.0;
+    for (int a = 0; a < 3; ++a) diag += (double)(bvh->hi[a] - bvh->lo[a]) * (bvh->hi[a] - bvh->lo[a]);
+    const double grow = 0.01 * std::sqrt(diag) + 1e-6;
+    double best = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        double p[3];
+        for (int a = 0; a < 3; ++a) p[a] = ((c >> a) & 1) ? bvh->hi[a] + grow : bvh->lo[a] - grow;
+        for (int l = 0; l < 4; ++l) {
+            const double su = (l & 1) ? 0.5 : -0.5, sv = (l & 2) ? 0.5 : -0.5;
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double y = L->c[a] + su * L->eu[a] + sv * L->ev[a];
+                d2 += (y - p[a]) * (y - p[a]);
+            }
+            best = std::max(best, d2);
+        }
+    }
+    return (float)(std::sqrt(best) * (1.0 + 1.0 / 1024.0));
 }
 
 occ::DevBVH dev_bvh(const occ_bvh* b) { return occ::DevBVH{b->nodes, b->tris}; }
@@ -190,6 +220,8 @@ occ_status reuse_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
     if (estimator != OCC_EST_UNBIASED && bvh)
         return fail(ctx, OCC_ERR_INVALID_ARG, "bvh_or_null must be NULL unless the estimator is unbiased");
     if (!out) return fail(ctx, OCC_ERR_INVALID_ARG, "out is NULL");
+    if (occ->format == OCC_REC_PACKED && !(occ->offset_scale > 0.0f && std::isfinite(occ->offset_scale)))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "packed records need a positive offset_scale");
     if (effect == OCC_EFFECT_SHADOW && (st = check_light(ctx, &occ->light)) != OCC_OK) return st;
     if (effect == OCC_EFFECT_AO && !(occ->radius > 0.0f && std::isfinite(occ->radius)))
         return fail(ctx, OCC_ERR_INVALID_ARG, "AO radius must be positive and finite");
@@ -226,6 +258,7 @@ occ_status trace_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
         std::memset(&out->light, 0, sizeof(out->light));
     out->seed = seed;
     out->sample = sample;
+    out->offset_scale = offset_scale_for(bvh, effect, radius, light);
     return launched(ctx,
                     occ::launch_trace(effect, view(gb), dev_bvh(bvh), radius, to_params(light), seed,
                                       sample, rec_view(out), ctx->status, (cudaStream_t)stream),
@@ -315,6 +348,15 @@ OCC_EXPORT occ_status occ_bvh_build(occ_ctx* ctx, const float* tris_host, int64_
         delete b;
         return cuda_fail(ctx, e, "bvh upload");
     }
+    for (int a = 0; a < 3; ++a) {
+        b->lo[a] = tris_host[a];
+        b->hi[a] = tris_host[a];
+    }
+    for (int64_t i = 0; i < 3 * T; ++i)
+        for (int a = 0; a < 3; ++a) {
+            b->lo[a] = std::min(b->lo[a], tris_host[3 * i + a]);
+            b->hi[a] = std::max(b->hi[a], tris_host[3 * i + a]);
+        }
     b->stats.num_tris = T;
     b->stats.num_nodes = (int64_t)hb.nodes.size();
     b->stats.num_leaves = hb.num_leaves;
@@ -359,6 +401,21 @@ OCC_EXPORT occ_status occ_gbuffer_pinhole(occ_ctx* ctx, const occ_bvh* bvh, cons
                                         reinterpret_cast<float4*>(nrm4), ctx->status,
                                         (cudaStream_t)stream),
                     "gbuffer launch");
+}
+
+OCC_EXPORT occ_status occ_pack_gbuffer(occ_ctx* ctx, const occ_gbuffer* gb, float* packed_out,
+                                       void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if ((st = check_gbuffer(ctx, gb)) != OCC_OK) return st;
+    if (gb->format != OCC_GB_FP32)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "occ_pack_gbuffer needs an FP32 G-buffer");
+    if (!packed_out || !aligned16(packed_out))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "packed_out must be a 16-byte aligned pointer");
+    return launched(ctx,
+                    occ::launch_pack_gbuffer(view(gb), reinterpret_cast<float4*>(packed_out),
+                                             (cudaStream_t)stream),
+                    "pack launch");
 }
 
 OCC_EXPORT occ_status occ_trace_ao(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh,

@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "occ_layout.h"
@@ -59,6 +60,101 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 __device__ __forceinline__ float3 normalize3(float3 a) {
     const float inv = 1.0f / sqrtf(dot3(a, a));
     return make_float3(a.x * inv, a.y * inv, a.z * inv);
+}
+
+// ---------------------------------------------------------------------------------------
+// Packed formats.  Octahedral unit-vector code (Cigolle et al., JCGT 2014): project n
+// onto the octahedron |x|+|y|+|z| = 1, fold the lower half over the diagonals, store
+// (x, y) as two 16-bit snorms.  0x80008000 (never produced: codes are clamped to
+// +-32767) marks an invalid G-buffer pixel.
+// ---------------------------------------------------------------------------------------
+constexpr uint32_t kOctInvalid = 0x80008000u;
+
+__device__ __forceinline__ float sign_nz(float v) { return v >= 0.0f ? 1.0f : -1.0f; }
+
+__device__ __forceinline__ uint32_t oct_encode(float3 n) {
+    const float inv = 1.0f / (fabsf(n.x) + fabsf(n.y) + fabsf(n.z));
+    float px = n.x * inv, py = n.y * inv;
+    if (n.z < 0.0f) {
+        const float fx = (1.0f - fabsf(py)) * sign_nz(px);
+        const float fy = (1.0f - fabsf(px)) * sign_nz(py);
+        px = fx;
+        py = fy;
+    }
+    const int qx = __float2int_rn(fminf(fmaxf(px, -1.0f), 1.0f) * 32767.0f);
+    const int qy = __float2int_rn(fminf(fmaxf(py, -1.0f), 1.0f) * 32767.0f);
+    return ((uint32_t)qx & 0xFFFFu) | ((uint32_t)qy << 16);
+}
+
+// The unfolded vector is formed in integers (units of 1/32767): its z, and whether the
+// code lies in the folded half, are then exact, so every decoder agrees on the sign of z
+// (the tangent frame built from a normal branches on that sign).
+__device__ __forceinline__ float3 oct_decode(uint32_t c) {
+    int qx = (int)(int16_t)(c & 0xFFFFu), qy = (int)(int16_t)(c >> 16);
+    const int qz = 32767 - abs(qx) - abs(qy);
+    if (qz < 0) {
+        const int tx = qx;
+        qx = (32767 - abs(qy)) * (tx >= 0 ? 1 : -1);
+        qy = (32767 - abs(tx)) * (qy >= 0 ? 1 : -1);
+    }
+    const float x = (float)qx, y = (float)qy, z = (float)qz;
+    const float inv = rsqrtf(x * x + y * y + z * z);
+    return make_float3(x * inv, y * inv, z * inv);
+}
+
+// G-buffer entry p: receiver point, normal, validity.
+__device__ __forceinline__ bool gb_fetch(const float4* pos, const float4* nrm, bool packed, int p,
+                                         float3* x, float3* n) {
+    const float4 q = __ldg(pos + p);
+    *x = make_float3(q.x, q.y, q.z);
+    if (packed) {
+        const uint32_t c = __float_as_uint(q.w);
+        if (c == kOctInvalid) return false;
+        *n = oct_decode(c);
+        return true;
+    }
+    if (q.w == 0.0f) return false;
+    const float4 m = __ldg(nrm + p);
+    *n = make_float3(m.x, m.y, m.z);
+    return true;
+}
+
+__device__ __forceinline__ bool gb_valid(const float4* pos, bool packed, int p) {
+    const float4 q = __ldg(pos + p);
+    return packed ? __float_as_uint(q.w) != kOctInvalid : q.w != 0.0f;
+}
+
+// Packed record: words 0-1 = 64 bits holding dz = z - x_source as three 21-bit signed
+// fixed-point numbers (units of scale * 2^-20; bits 0-20, 21-41, 42-62) and bit 63 set;
+// word 2 = octahedral n_z; word 3 = triangle id (-1: no occluder).
+__device__ __forceinline__ uint64_t fix21(float v, float inv_unit) {
+    const int q = max(-1048575, min(1048575, __float2int_rn(v * inv_unit)));
+    return (uint64_t)((uint32_t)q & 0x1FFFFFu);
+}
+
+__device__ __forceinline__ float unfix21(uint64_t bits, float unit) {
+    const int q = (int)((uint32_t)(bits & 0x1FFFFFu) << 11) >> 11;   // sign-extend 21 bits
+    return (float)q * unit;
+}
+
+__device__ __forceinline__ float4 rec_pack(float3 xsrc, float3 z, float3 nz, int tri, float scale) {
+    if (tri < 0) return make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
+    const float inv_unit = 1048576.0f / scale;
+    const uint64_t w = fix21(z.x - xsrc.x, inv_unit) | (fix21(z.y - xsrc.y, inv_unit) << 21) |
+                       (fix21(z.z - xsrc.z, inv_unit) << 42) | (1ull << 63);
+    return make_float4(__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)(w >> 32)),
+                       __uint_as_float(oct_encode(nz)), __int_as_float(tri));
+}
+
+// Unpacks a packed record of a source receiver at xsrc; returns its triangle id.
+__device__ __forceinline__ int rec_unpack(float4 r, float3 xsrc, float scale, float3* z,
+                                          float3* nz) {
+    const uint64_t w = (uint64_t)__float_as_uint(r.x) | ((uint64_t)__float_as_uint(r.y) << 32);
+    const float unit = scale * (1.0f / 1048576.0f);
+    *z = make_float3(xsrc.x + unfix21(w, unit), xsrc.y + unfix21(w >> 21, unit),
+                     xsrc.z + unfix21(w >> 42, unit));
+    *nz = oct_decode(__float_as_uint(r.z));
+    return __float_as_int(r.w);
 }
 
 // ---------------------------------------------------------------------------------------

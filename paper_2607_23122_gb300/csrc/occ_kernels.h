@@ -10,14 +10,18 @@ namespace occ {
 
 struct GBufView {
     int32_t W, H;
-    const float4* pos;   // (x.xyz, valid)
-    const float4* nrm;   // (n.xyz, -)
+    const float4* pos;   // FP32: (x.xyz, valid); packed: (x.xyz, octahedral normal code)
+    const float4* nrm;   // FP32: (n.xyz, -); packed: unused
+    int32_t packed;
 };
 
-// Occluder records: plane 0 (z.xyz, tri id bits), plane 1 (n_z.xyz, t).
+// Occluder records.  FP32: plane 0 (z.xyz, tri id bits), plane 1 (n_z.xyz, t).
+// Packed: plane 0 only, (half3 z - x_source, flags, octahedral n_z, tri id).
 struct RecView {
     float4* r0;
     float4* r1;
+    int32_t packed;
+    float scale;       // packed: offset unit * 2^20
 };
 
 struct LightParams {
@@ -43,6 +47,7 @@ cudaError_t launch_gbuffer(const DevBVH& bvh, const float* cam, float eps, int W
 cudaError_t launch_trace(int effect, const GBufView& gb, const DevBVH& bvh, float radius,
                          const LightParams& light, uint64_t seed, uint32_t sample, RecView rec,
                          unsigned* status, cudaStream_t s);
+cudaError_t launch_pack_gbuffer(const GBufView& gb, float4* out, cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s);
 cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
                               const LightParams& light, uint64_t seed, uint32_t sample,

@@ -14,7 +14,8 @@ import torch
 from . import _native as N
 from ._native import (  # noqa: F401
     OCC_EFFECT_AO, OCC_EFFECT_SHADOW, OCC_EST_BIASED, OCC_EST_BOXMEAN, OCC_EST_NOREUSE,
-    OCC_EST_UNBIASED, OCC_PAT_BOX, OCC_PAT_GROUP, OCC_PAT_OFFSETS, OCC_REC_FP32, MAX_MEMBERS)
+    OCC_EST_UNBIASED, OCC_GB_FP32, OCC_GB_PACKED, OCC_PAT_BOX, OCC_PAT_GROUP, OCC_PAT_OFFSETS,
+    OCC_REC_FP32, OCC_REC_PACKED, MAX_MEMBERS)
 
 
 class OccError(RuntimeError):
@@ -108,9 +109,10 @@ def occ_bvh_build(ctx: Context, tris: np.ndarray) -> BVH:
 
 @dataclass
 class GBuffer:
-    """pos4 / nrm4: float32 CUDA tensors [H, W, 4] (see occ_gbuffer)."""
+    """pos4 / nrm4: float32 CUDA tensors [H, W, 4] (see occ_gbuffer).  A packed G-buffer
+    has only pos4 (the packed plane) and nrm4 = None."""
     pos4: torch.Tensor
-    nrm4: torch.Tensor
+    nrm4: torch.Tensor | None = None
 
     @property
     def W(self) -> int:
@@ -120,12 +122,18 @@ class GBuffer:
     def H(self) -> int:
         return int(self.pos4.shape[0])
 
+    @property
+    def packed(self) -> bool:
+        return self.nrm4 is None
+
     def c(self) -> N.occ_gbuffer:
-        for t in (self.pos4, self.nrm4):
+        for t in (self.pos4,) if self.packed else (self.pos4, self.nrm4):
             if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
                     and tuple(t.shape) == (self.H, self.W, 4)):
                 raise ValueError("G-buffer tensors must be contiguous float32 CUDA [H, W, 4]")
-        return N.occ_gbuffer(self.W, self.H, self.pos4.data_ptr(), self.nrm4.data_ptr())
+        return N.occ_gbuffer(self.W, self.H, self.pos4.data_ptr(),
+                             None if self.packed else self.nrm4.data_ptr(),
+                             N.OCC_GB_PACKED if self.packed else N.OCC_GB_FP32)
 
     @staticmethod
     def from_numpy(pos4: np.ndarray, nrm4: np.ndarray, device="cuda") -> "GBuffer":
@@ -135,16 +143,38 @@ class GBuffer:
 
 @dataclass
 class Occluders:
-    """Occluder records: data is a float32 CUDA tensor [2, H, W, 4] (two planes)."""
+    """Occluder records: data is a float32 CUDA tensor [2, H, W, 4] (two FP32 planes) or
+    [1, H, W, 4] (the packed plane, 16 bytes per pixel)."""
     data: torch.Tensor
     meta: N.occ_occluders = field(default_factory=N.occ_occluders)
 
     @staticmethod
-    def empty(H: int, W: int, device="cuda") -> "Occluders":
-        o = Occluders(torch.empty((2, H, W, 4), dtype=torch.float32, device=device))
-        o.meta.W, o.meta.H, o.meta.format = W, H, N.OCC_REC_FP32
+    def empty(H: int, W: int, device="cuda", packed: bool = False) -> "Occluders":
+        o = Occluders(torch.empty((1 if packed else 2, H, W, 4), dtype=torch.float32,
+                                  device=device))
+        o.meta.W, o.meta.H = W, H
+        o.meta.format = N.OCC_REC_PACKED if packed else N.OCC_REC_FP32
         o.meta.data = o.data.data_ptr()
         return o
+
+    @staticmethod
+    def from_packed(plane: np.ndarray, effect: int, offset_scale: float, radius: float = 0.0,
+                    light=None, device="cuda") -> "Occluders":
+        """Packed records prepared elsewhere: [H, W, 4] float32 view of the 16-byte records,
+        offsets in units of offset_scale * 2^-20."""
+        H, W = plane.shape[:2]
+        o = Occluders.empty(H, W, device, packed=True)
+        o.data[0].copy_(torch.from_numpy(np.ascontiguousarray(plane, dtype=np.float32)))
+        o.meta.effect = effect
+        o.meta.radius = radius
+        o.meta.offset_scale = offset_scale
+        if light is not None:
+            o.meta.light = _light(light)
+        return o
+
+    @property
+    def packed(self) -> bool:
+        return self.meta.format == N.OCC_REC_PACKED
 
     @staticmethod
     def from_numpy(rec0: np.ndarray, rec1: np.ndarray, effect: int, radius: float = 0.0,
@@ -226,9 +256,18 @@ def occ_gbuffer_pinhole(ctx: Context, bvh: BVH, camera, eps: float, W: int, H: i
     return gb
 
 
+def occ_pack_gbuffer(ctx: Context, gb: GBuffer, stream=None) -> GBuffer:
+    """FP32 G-buffer -> packed G-buffer (16 bytes per pixel)."""
+    out = torch.empty((gb.H, gb.W, 4), dtype=torch.float32, device=gb.pos4.device)
+    g = gb.c()
+    ctx.check(ctx.lib.occ_pack_gbuffer(ctx.handle, C.byref(g), out.data_ptr(),
+                                       _stream_handle(stream)))
+    return GBuffer(out, None)
+
+
 def occ_trace_ao(ctx: Context, gb: GBuffer, bvh: BVH, radius: float, seed: int, sample: int,
-                 out: Occluders | None = None, stream=None) -> Occluders:
-    out = out or Occluders.empty(gb.H, gb.W, gb.pos4.device)
+                 out: Occluders | None = None, stream=None, packed: bool = False) -> Occluders:
+    out = out or Occluders.empty(gb.H, gb.W, gb.pos4.device, packed=packed)
     g = gb.c()
     ctx.check(ctx.lib.occ_trace_ao(ctx.handle, C.byref(g), bvh.handle, float(radius), int(seed),
                                    int(sample), C.byref(out.c()), _stream_handle(stream)))
@@ -236,8 +275,8 @@ def occ_trace_ao(ctx: Context, gb: GBuffer, bvh: BVH, radius: float, seed: int, 
 
 
 def occ_trace_shadow(ctx: Context, gb: GBuffer, bvh: BVH, light, seed: int, sample: int,
-                     out: Occluders | None = None, stream=None) -> Occluders:
-    out = out or Occluders.empty(gb.H, gb.W, gb.pos4.device)
+                     out: Occluders | None = None, stream=None, packed: bool = False) -> Occluders:
+    out = out or Occluders.empty(gb.H, gb.W, gb.pos4.device, packed=packed)
     g = gb.c()
     L = _light(light)
     ctx.check(ctx.lib.occ_trace_shadow(ctx.handle, C.byref(g), bvh.handle, C.byref(L), int(seed),

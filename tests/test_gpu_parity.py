@@ -321,3 +321,87 @@ def test_frame_host_matches_device_path(occ, ctx, c1):
     d = occ.occ_reuse_ao(ctx, c1["gb"], o, pat, 9, BIASED)
     ctx.sync()
     assert torch.equal(out_h, d.cpu())
+
+
+# --------------------------------------------------------------------------------------
+# Packed formats (octahedral normals, FP16 occluder offsets; FP32 arithmetic)
+# --------------------------------------------------------------------------------------
+
+from tests import _packing as PK  # noqa: E402
+
+
+def test_pack_gbuffer_matches_reference_codec(occ, ctx, c1):
+    packed = occ.occ_pack_gbuffer(ctx, c1["gb"])
+    ctx.sync()
+    got = packed.pos4.cpu().numpy()
+    want = PK.pack_gbuffer(c1["pos"], c1["nrm"])
+    assert np.array_equal(got[..., :3], want[..., :3])
+    gc, wc = got[..., 3].view(np.uint32), want[..., 3].view(np.uint32)
+    assert (gc == wc).mean() > 0.999
+    valid = c1["pos"][..., 3] > 0
+    dec = PK.oct_decode(gc[valid])
+    assert np.abs(dec - c1["nrm"][valid][:, :3]).max() < 2e-4      # octahedral 2x16 error
+
+
+@pytest.mark.parametrize("effect", [AO, SH])
+def test_packed_trace_matches_oracle(orc, occ, ctx, c1, effect):
+    ppos = PK.pack_gbuffer(c1["pos"], c1["nrm"])
+    upos, unrm = PK.unpack_gbuffer(ppos)           # what the packed trace sees
+    gb = occ.GBuffer(occ.torch.from_numpy(ppos).cuda(), None)
+    valid = upos[..., 3] > 0
+    for sample in range(2):
+        o = (occ.occ_trace_ao(ctx, gb, c1["bvh"], R_C1, 17, sample, packed=True) if effect == AO
+             else occ.occ_trace_shadow(ctx, gb, c1["bvh"], LIGHT_C1, 17, sample, packed=True))
+        ctx.sync()
+        grec = PK.unpack_records(o.data[0].cpu().numpy(), upos, o.meta.offset_scale)
+        orec, omg = orc.trace(c1["osc"], effect, upos, unrm, radius=R_C1, light=LIGHT_C1, seed=17,
+                              sample=sample)
+        gtri, otri = grec[..., 7], orec[..., 7]
+        mism = (gtri != otri) & valid
+        bad = np.argwhere(mism & (omg >= P.TRACE_MARGIN))
+        assert len(bad) == 0, [(int(py), int(px), int(gtri[py, px]), int(otri[py, px]),
+                                float(omg[py, px]), grec[py, px, :3].tolist(),
+                                orec[py, px, :3].tolist(), upos[py, px, :3].tolist(),
+                                unrm[py, px, :3].tolist()) for py, px in bad[:4]]
+        assert mism.sum() <= P.budget(int(valid.sum()))
+        both = valid & (gtri >= 0) & (gtri == otri)
+        unit = o.meta.offset_scale * 2.0 ** -20
+        zerr = np.abs(grec[..., :3][both] - orec[..., :3][both])
+        assert np.all(zerr <= unit + 1e-5 * (1 + np.abs(orec[..., :3][both]))), zerr.max()
+        assert np.abs(grec[..., 3:6][both] - orec[..., 3:6][both]).max() < 2e-4
+
+
+@pytest.mark.parametrize("pname", ["group4x2", "group2x2", "box3x3", "disk8"])
+@pytest.mark.parametrize("effect", [AO, SH])
+def test_packed_reuse(orc, occ, ctx, c1, effect, pname):
+    """Packed G-buffer and records: (a) the FP32 kernels against the oracle on the same
+    unpacked values (<= 1e-5); (b) the packing error against the full-precision oracle."""
+    pat = _patterns(occ)[pname]
+    ppos = PK.pack_gbuffer(c1["pos"], c1["nrm"])
+    upos, unrm = PK.unpack_gbuffer(ppos)
+    gb = occ.GBuffer(occ.torch.from_numpy(ppos).cuda(), None)
+    valid = upos[..., 3] > 0
+    errs = []
+    for sample in range(2):
+        orec, _ = orc.trace(c1["osc"], effect, c1["pos"], c1["nrm"], radius=R_C1, light=LIGHT_C1,
+                            seed=41, sample=sample)
+        scale = 1.001 * R_C1 if effect == AO else 12.0     # bounds |z - x| in this scene
+        prec = PK.pack_records(orec, c1["pos"], scale)
+        urec = PK.unpack_records(prec, upos, scale)
+        o = occ.Occluders.from_packed(prec, effect, scale, radius=R_C1, light=LIGHT_C1)
+        fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
+        for est in (BIASED, UNBIASED):
+            g = fn(ctx, gb, o, pat, pat.K, est, bvh=c1["bvh"] if est == UNBIASED else None)
+            ctx.sync()
+            g = g.cpu().numpy()
+            ref, mg = orc.reuse(c1["osc"], effect, upos, unrm, urec, pat.as_tuple(), est,
+                                radius=R_C1, light=LIGHT_C1)
+            P.compare_out(g, ref, mg, valid, f"packed {pname} {est}")
+            full, _ = orc.reuse(c1["osc"], effect, c1["pos"], c1["nrm"], orec, pat.as_tuple(), est,
+                                radius=R_C1, light=LIGHT_C1)
+            if est == BIASED:
+                errs.append(np.abs(g - full)[valid])
+    e = np.concatenate(errs)
+    print(f"packing error vs FP64 oracle ({pname}, effect {effect}): max {e.max():.2e} "
+          f"p99.9 {np.quantile(e, 0.999):.2e} mean {e.mean():.2e}")
+    assert np.quantile(e, 0.999) <= 1e-3

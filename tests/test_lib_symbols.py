@@ -46,7 +46,7 @@ def test_version_and_no_gpu_errors_are_clean():
 def test_struct_layouts_match_the_header():
     """Sizes of the ctypes mirrors equal the C structs (LP64)."""
     from paper_2607_23122_gb300 import _native as N
-    assert ctypes.sizeof(N.occ_gbuffer) == 24
+    assert ctypes.sizeof(N.occ_gbuffer) == 32
     assert ctypes.sizeof(N.occ_rect_light) == 36
     assert ctypes.sizeof(N.occ_pattern) == 24
     assert ctypes.sizeof(N.occ_bvh_stats) == 48
