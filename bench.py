@@ -218,6 +218,24 @@ def shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream) -> dict:
             "light": "1 x 0.5 rectangle at z=4 facing down"}
 
 
+PACKED_GROUP_BYTES_PER_PX = 30   # x 12, octahedral n 4, offsets 6, octahedral n_z 4, out 4
+
+
+def packed_frame(occ, ctx, gb, bvh, pat, out, flush, stream) -> dict:
+    """The same AO frame with packed G-buffer and records (16 + 16 bytes per pixel)."""
+    pgb = occ.occ_pack_gbuffer(ctx, gb)
+    prec = occ.Occluders.empty(H, W, gb.pos4.device, packed=True)
+    tr = time_kernel(lambda st: occ.occ_trace_ao(ctx, pgb, bvh, RADIUS, 1, 0, out=prec, stream=st),
+                     flush, stream, 100)
+    ru = time_kernel(lambda st: occ.occ_reuse_ao(ctx, pgb, prec, pat, K, occ.OCC_EST_BIASED,
+                                                 out=out, stream=st), flush, stream, 100)
+    gr = time_kernel(lambda st: occ.occ_reuse_ao(ctx, pgb, prec, occ.Pattern.group(4, 2), 8,
+                                                 occ.OCC_EST_BIASED, out=out, stream=st),
+                     flush, stream, 100)
+    return {"trace_ms": tr["ms"], "reuse_offsets_k8_ms": ru["ms"], "reuse_group4x2_ms": gr["ms"],
+            "ms_per_frame": tr["ms"] + ru["ms"], "bytes_per_px_stored": 16 + 16 + 4}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -305,6 +323,7 @@ def run_ours(args):
             lambda st: occ.occ_reuse_ao(ctx, gb, rec, occ.Pattern.group(4, 2), 8, occ.OCC_EST_BIASED,
                                         out=out, stream=st), flush, stream, 200)
         extra["shadow"] = shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream)
+        extra["packed"] = packed_frame(occ, ctx, gb, bvh, pat, out, flush, stream)
 
     if rank == 0:
         hbm, peak_kind, peaks = measured_peaks()
@@ -350,6 +369,9 @@ def run_ours(args):
                                    frac_hbm=P * GROUP_BYTES_PER_PX / extra["reuse_group4x2"]["s"] / 1e9 / hbm,
                                    neighbour_samples_per_s=P * 8 / extra["reuse_group4x2"]["s"]),
             "shadow_frame": extra["shadow"],
+            "packed_frame": dict(extra["packed"],
+                                 group_frac_hbm=P * PACKED_GROUP_BYTES_PER_PX
+                                 / (extra["packed"]["reuse_group4x2_ms"] * 1e-3) / 1e9 / hbm),
             "bvh": {"nodes": st["num_nodes"], "depth": st["depth"], "bytes": st["bytes"],
                     "build_s": st["build_seconds"]},
         }

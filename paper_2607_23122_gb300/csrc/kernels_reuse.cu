@@ -134,6 +134,14 @@ __device__ __forceinline__ bool first_hit(const DevBVH& bvh, float3 x, float3 z,
     return h.id == tri;
 }
 
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 1;
+    return n;
+}
+
 __device__ __forceinline__ void tile_pixel(int* x, int* y) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     *x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
