@@ -206,6 +206,52 @@ occ_status occ_frame_host(occ_ctx* ctx, const occ_bvh* bvh, int32_t effect,
                           uint32_t sample, const occ_pattern* pattern, int32_t K,
                           int32_t estimator, float* out_host, void* stream);
 
+/* ---- batched frames, captured batches and tuning ----------------------------- */
+
+/* One view of a batched frame.  gb and rec describe caller-owned buffers (either
+ * format; rec.W/H/format/data set by the caller, the rest of rec is written as by the
+ * trace calls); effect with radius (AO) or light (shadow); Philox seed and sample;
+ * neighbour pattern with K <= 16 and estimator (the unbiased one uses the batch's
+ * BVH); out: device float[H][W]. */
+typedef struct {
+    occ_gbuffer gb;
+    occ_occluders rec;
+    int32_t effect;
+    float radius;
+    occ_rect_light light;
+    uint64_t seed;
+    uint32_t sample;
+    occ_pattern pattern;
+    int32_t K, estimator;
+    float* out;
+} occ_view;
+
+/* Trace and reuse of n_views (<= 256) views of any sizes, effects, patterns and
+ * estimators as one persistent trace launch and one persistent reuse launch over the
+ * views' concatenated 16x8 tiles (uneven views share the GPU without a launch each).
+ * Results equal the per-view calls'. */
+occ_status occ_frame_batch(occ_ctx* ctx, const occ_bvh* bvh, occ_view* views, int32_t n_views,
+                           void* stream);
+
+/* A batched frame captured as a CUDA graph: the views' buffers, sizes, patterns and
+ * parameters are fixed at capture; each launch replays it with new per-view seeds and
+ * samples (uploaded before the replay on the launch stream). */
+typedef struct occ_batch occ_batch;
+occ_status occ_batch_capture(occ_ctx* ctx, const occ_bvh* bvh, occ_view* views, int32_t n_views,
+                             occ_batch** out);
+occ_status occ_batch_launch(occ_ctx* ctx, occ_batch* batch, const uint64_t* seeds_host,
+                            const uint32_t* samples_host, void* stream);
+occ_status occ_batch_free(occ_ctx* ctx, occ_batch* batch);
+
+/* Launch choices an autotuner may change (0 = built-in default everywhere). */
+typedef struct {
+    int32_t reuse_tile_rows;     /* TMA window kernel: receiver rows per tile (4, 8, 16) */
+    int32_t reuse_window_path;   /* window patterns: 1 TMA tile kernel, 2 per-receiver kernel */
+    int32_t batch_ctas_per_sm;   /* persistent batched kernels: CTAs per SM (1 .. 16) */
+} occ_tuning;
+occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t);
+occ_status occ_get_tuning(const occ_ctx* ctx, occ_tuning* t);
+
 /* ---- allocation-free frame -------------------------------------------------- */
 
 /* The paper has no counterpart to this call; it serves callers that cannot allocate

@@ -45,6 +45,18 @@ class occ_pattern(C.Structure):
                 ("offsets_host", C.POINTER(c_int32))]
 
 
+class occ_view(C.Structure):
+    _fields_ = [("gb", occ_gbuffer), ("rec", occ_occluders), ("effect", c_int32),
+                ("radius", c_float), ("light", occ_rect_light), ("seed", c_uint64),
+                ("sample", c_uint32), ("pattern", occ_pattern), ("K", c_int32),
+                ("estimator", c_int32), ("out", c_void_p)]
+
+
+class occ_tuning(C.Structure):
+    _fields_ = [("reuse_tile_rows", c_int32), ("reuse_window_path", c_int32),
+                ("batch_ctas_per_sm", c_int32)]
+
+
 class occ_bvh_stats(C.Structure):
     _fields_ = [("num_tris", c_int64), ("num_nodes", c_int64), ("num_leaves", c_int64),
                 ("depth", c_int32), ("max_leaf_tris", c_int32), ("bytes", c_int64),
@@ -82,6 +94,13 @@ SIGNATURES = {
                                     C.POINTER(occ_rect_light), c_uint64, c_uint32,
                                     C.POINTER(occ_pattern), c_int32, c_int32, c_void_p, c_void_p,
                                     c_char_p, c_int32, c_void_p]),
+    "occ_frame_batch": (c_int32, [c_void_p, c_void_p, C.POINTER(occ_view), c_int32, c_void_p]),
+    "occ_batch_capture": (c_int32, [c_void_p, c_void_p, C.POINTER(occ_view), c_int32,
+                                    C.POINTER(c_void_p)]),
+    "occ_batch_launch": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "occ_batch_free": (c_int32, [c_void_p, c_void_p]),
+    "occ_set_tuning": (c_int32, [c_void_p, C.POINTER(occ_tuning)]),
+    "occ_get_tuning": (c_int32, [c_void_p, C.POINTER(occ_tuning)]),
     "occ_debug_philox": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "occ_debug_rays": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_int32, c_float,
                                  C.POINTER(occ_rect_light), c_uint64, c_uint32, c_void_p,

@@ -1,0 +1,137 @@
+"""Autotuner for the launch choices exposed by occ_tuning.
+
+For a workload key (image size, pattern, K, formats, effect, estimator) it times each
+candidate configuration on the caller's own buffers with CUDA events, keeps the fastest,
+and stores it in a JSON cache so later runs apply it without measuring:
+
+  * reuse of window patterns (box / offsets): TMA-staged tile kernel with 4, 8 or 16
+    receiver rows per tile, or the per-receiver kernel;
+  * persistent batched kernels: CTAs per SM (1, 2, 4, 8 or all that fit).
+
+Cache: $OCC_TUNE_CACHE, else ~/.cache/occreuse/tuning.json.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+from . import occ as O
+
+_LOCK = threading.Lock()
+
+REUSE_CANDIDATES = [
+    {"reuse_tile_rows": 16, "reuse_window_path": 1},
+    {"reuse_tile_rows": 8, "reuse_window_path": 1},
+    {"reuse_tile_rows": 4, "reuse_window_path": 1},
+    {"reuse_tile_rows": 0, "reuse_window_path": 2},
+]
+BATCH_CANDIDATES = [{"batch_ctas_per_sm": n} for n in (0, 1, 2, 4, 8)]
+
+
+def cache_path() -> str:
+    return os.environ.get("OCC_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "occreuse",
+                                       "tuning.json"))
+
+
+def load_cache(path: str | None = None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str | None = None) -> None:
+    path = path or cache_path()
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def reuse_key(gb: O.GBuffer, rec: O.Occluders, pattern: O.Pattern, estimator: int,
+              effect: int) -> str:
+    return (f"reuse/{gb.W}x{gb.H}/pat{pattern.kind}:{pattern.gw}x{pattern.gh}/K{pattern.K}/"
+            f"gb{int(gb.packed)}/rec{int(rec.packed)}/eff{effect}/est{estimator}")
+
+
+def batch_key(views: list) -> str:
+    px = sum(v.gb.W * v.gb.H for v in views)
+    kinds = sorted({(v.effect, v.estimator, v.pattern.K) for v in views})
+    return f"batch/{len(views)}views/{px}px/{kinds}"
+
+
+def _time(fn, iters: int) -> float:
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(iters):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    times.sort()
+    return times[len(times) // 2]   # median, ms
+
+
+def _apply(ctx: O.Context, cfg: dict) -> None:
+    base = O.occ_get_tuning(ctx)
+    base.update(cfg)
+    O.occ_set_tuning(ctx, **base)
+
+
+def tune_reuse(ctx: O.Context, gb: O.GBuffer, rec: O.Occluders, pattern: O.Pattern,
+               estimator: int, out, bvh=None, iters: int = 15, use_cache: bool = True) -> dict:
+    """Picks the window-reuse configuration for this workload and applies it to ctx."""
+    key = reuse_key(gb, rec, pattern, estimator, rec.meta.effect)
+    with _LOCK:
+        cache = load_cache() if use_cache else {}
+    if key in cache:
+        _apply(ctx, cache[key]["best"])
+        return cache[key]
+    fn = O.occ_reuse_ao if rec.meta.effect == O.OCC_EFFECT_AO else O.occ_reuse_shadow
+    timings = []
+    cands = REUSE_CANDIDATES if pattern.kind != O.OCC_PAT_GROUP else [{}]
+    for cfg in cands:
+        _apply(ctx, cfg)
+        ms = _time(lambda: fn(ctx, gb, rec, pattern, pattern.K, estimator, bvh=bvh, out=out), iters)
+        timings.append({"config": cfg, "ms": ms})
+    best = min(timings, key=lambda t: t["ms"])
+    entry = {"best": best["config"], "timings": timings}
+    _apply(ctx, best["config"])
+    with _LOCK:
+        cache = load_cache()
+        cache[key] = entry
+        save_cache(cache)
+    return entry
+
+
+def tune_batch(ctx: O.Context, bvh: O.BVH, views: list, iters: int = 10,
+               use_cache: bool = True) -> dict:
+    """Picks the CTAs-per-SM of the persistent batched kernels for this view mix."""
+    key = batch_key(views)
+    with _LOCK:
+        cache = load_cache() if use_cache else {}
+    if key in cache:
+        _apply(ctx, cache[key]["best"])
+        return cache[key]
+    timings = []
+    for cfg in BATCH_CANDIDATES:
+        _apply(ctx, cfg)
+        ms = _time(lambda: O.occ_frame_batch(ctx, bvh, views), iters)
+        timings.append({"config": cfg, "ms": ms})
+    best = min(timings, key=lambda t: t["ms"])
+    entry = {"best": best["config"], "timings": timings}
+    _apply(ctx, best["config"])
+    with _LOCK:
+        cache = load_cache()
+        cache[key] = entry
+        save_cache(cache)
+    return entry

@@ -181,9 +181,7 @@ __device__ __forceinline__ int gather_members(const PatternParams& pat, const GB
 // Generic per-receiver kernel (any pattern).
 // ---------------------------------------------------------------------------------------
 template <int EFFECT, int EST, int MAXK>
-__global__ void __launch_bounds__(128) k_reuse_generic(ReuseArgs a) {
-    int x, y;
-    tile_pixel(&x, &y);
+__device__ __forceinline__ void reuse_pixel(const ReuseArgs& a, int x, int y) {
     if (x >= a.gb.W || y >= a.gb.H) return;
     const int i = y * a.gb.W + x;
     if (!gb_valid(a.gb.pos, a.gb.packed != 0, i)) {
@@ -225,13 +223,18 @@ __global__ void __launch_bounds__(128) k_reuse_generic(ReuseArgs a) {
     a.out[i] = res;
 }
 
+template <int EFFECT, int EST, int MAXK>
+__global__ void __launch_bounds__(128) k_reuse_generic(ReuseArgs a) {
+    int x, y;
+    tile_pixel(&x, &y);
+    reuse_pixel<EFFECT, EST, MAXK>(a, x, y);
+}
+
 // ---------------------------------------------------------------------------------------
 // NOREUSE (Eq. 3 / Eq. 6 with one sample) and BOXMEAN (mean visibility over N_i).
 // ---------------------------------------------------------------------------------------
 template <int EST>
-__global__ void __launch_bounds__(128) k_reuse_simple(ReuseArgs a) {
-    int x, y;
-    tile_pixel(&x, &y);
+__device__ __forceinline__ void reuse_simple_pixel(const ReuseArgs& a, int x, int y) {
     if (x >= a.gb.W || y >= a.gb.H) return;
     const int i = y * a.gb.W + x;
     if (!gb_valid(a.gb.pos, a.gb.packed != 0, i)) {
@@ -250,10 +253,58 @@ __global__ void __launch_bounds__(128) k_reuse_simple(ReuseArgs a) {
     a.out[i] = (float)vis / (float)n;
 }
 
+template <int EST>
+__global__ void __launch_bounds__(128) k_reuse_simple(ReuseArgs a) {
+    int x, y;
+    tile_pixel(&x, &y);
+    reuse_simple_pixel<EST>(a, x, y);
+}
+
 // ---------------------------------------------------------------------------------------
-// Warp-cooperative GROUP kernel.  K = GW * GH lanes per group, 32 / K groups per warp
-// laid side by side (warp block = (32/K * GW) x GH pixels), 8 warps side by side per CTA.
+// Batched reuse over views of different sizes, patterns, effects and estimators: the
+// persistent counterpart of k_trace_batch (same tile space and view lookup); each tile
+// runs the per-receiver evaluation of its view.
 // ---------------------------------------------------------------------------------------
+template <int MAXK>
+__global__ void __launch_bounds__(128) k_reuse_batch(const BatchView* views, int n_views,
+                                                     int n_tiles, DevBVH bvh, unsigned* status) {
+    __shared__ int s_first[kMaxBatchViews + 1];
+    for (int v = threadIdx.x; v <= n_views; v += blockDim.x)
+        s_first[v] = v < n_views ? views[v].first_tile : n_tiles;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        int lo = 0, hi = n_views - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_first[mid] <= tile) lo = mid; else hi = mid - 1;
+        }
+        const BatchView* v = views + lo;
+        const int t = tile - s_first[lo];
+        const int x = (t % v->tiles_x) * 16 + (warp & 1) * 8 + (lane & 7);
+        const int y = (t / v->tiles_x) * 8 + (warp >> 1) * 4 + (lane >> 3);
+        ReuseArgs a;
+        a.gb = v->gb;
+        a.rec = v->rec;
+        a.pat = v->pat;
+        a.R2s = v->R2s;
+        a.lp = v->light;
+        a.bvh = bvh;
+        a.out = v->out;
+        a.status = status;
+        const int est = v->estimator;
+        if (est == kNoReuse) reuse_simple_pixel<kNoReuse>(a, x, y);
+        else if (est == kBoxMean) reuse_simple_pixel<kBoxMean>(a, x, y);
+        else if (v->effect == kAO) {
+            if (est == kBiased) reuse_pixel<kAO, kBiased, MAXK>(a, x, y);
+            else reuse_pixel<kAO, kUnbiased, MAXK>(a, x, y);
+        } else {
+            if (est == kBiased) reuse_pixel<kShadow, kBiased, MAXK>(a, x, y);
+            else reuse_pixel<kShadow, kUnbiased, MAXK>(a, x, y);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // MIS weights of selected receivers (debug / tests): w[a][b] = p(z_a|x_b) / P_a.
 // ---------------------------------------------------------------------------------------
@@ -293,6 +344,10 @@ __global__ void k_debug_mis(ReuseArgs a, const int32_t* pix, int32_t npix, int32
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Warp-cooperative GROUP kernel.  K = GW * GH lanes per group, 32 / K groups per warp
+// laid side by side (warp block = (32/K * GW) x GH pixels), 8 warps side by side per CTA.
+// ---------------------------------------------------------------------------------------
 // Loading the hit-normal plane only for rays that hit saves bytes but adds a dependent
 // round trip; OCC_GROUP_EAGER_R1=1 loads it together with the other planes (measured
 // slower for AO at 1080p: 32.2 vs 28.8 us).
@@ -450,7 +505,7 @@ void launch_generic(const ReuseArgs& a, cudaStream_t s) {
 }
 
 template <int EFFECT>
-cudaError_t launch_effect(int est, const ReuseArgs& a, cudaStream_t s) {
+cudaError_t launch_effect(int est, const ReuseArgs& a, cudaStream_t s, const Tuning& tune) {
     const dim3 grid((unsigned)((a.gb.W + 15) / 16), (unsigned)((a.gb.H + 7) / 8));
     if (est == kNoReuse) {
         k_reuse_simple<kNoReuse><<<grid, 128, 0, s>>>(a);
@@ -459,8 +514,9 @@ cudaError_t launch_effect(int est, const ReuseArgs& a, cudaStream_t s) {
     } else if (est == kBiased) {
         if (a.pat.kind != 0) {
             cudaError_t e = cudaSuccess;
-            if (!a.gb.packed && !a.rec.packed &&
-                launch_reuse_tile(EFFECT, a.gb, a.rec, a.pat, a.R2s, a.lp, a.out, a.status, s, &e))
+            if (!a.gb.packed && !a.rec.packed && tune.window_path != 2 &&
+                launch_reuse_tile(EFFECT, a.gb, a.rec, a.pat, a.R2s, a.lp, a.out, a.status, s, &e,
+                                  tune.tile_rows))
                 return e;
             launch_generic<EFFECT, kBiased>(a, s);
         } else if (!launch_group<EFFECT, kBiased>(a, s)) {
@@ -490,13 +546,28 @@ ReuseArgs make_args(const GBufView& gb, const RecView& rec, const PatternParams&
 
 cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const RecView& rec,
                          const PatternParams& pat, float radius, const LightParams& light,
-                         const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s) {
+                         const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s,
+                         const Tuning& tune) {
     if (gb.W <= 0 || gb.H <= 0) return cudaSuccess;
     const ReuseArgs a = make_args(gb, rec, pat, radius, light, bvh, out, status);
-    const cudaError_t e = effect == kAO ? launch_effect<kAO>(estimator, a, s)
-                                        : launch_effect<kShadow>(estimator, a, s);
+    const cudaError_t e = effect == kAO ? launch_effect<kAO>(estimator, a, s, tune)
+                                        : launch_effect<kShadow>(estimator, a, s, tune);
     const cudaError_t l = cudaGetLastError();
     return e != cudaSuccess ? e : l;
+}
+
+cudaError_t launch_reuse_batch(const BatchView* views, int n_views, int n_tiles, int max_k,
+                               const DevBVH& bvh, int per_sm_wanted, unsigned* status,
+                               cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    auto k = max_k <= 9 ? k_reuse_batch<9> : k_reuse_batch<16>;
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    if (per_sm_wanted > 0 && per_sm_wanted < per_sm) per_sm = per_sm_wanted;
+    const int ctas = per_sm * sm_count();
+    k<<<ctas < n_tiles ? ctas : n_tiles, 128, 0, s>>>(views, n_views, n_tiles, bvh, status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_debug_mis(int effect, int estimator, const GBufView& gb, const RecView& rec,

@@ -301,7 +301,7 @@ cudaError_t launch_t(const CUtensorMap* maps, const TileArgs& a, size_t smem, in
 // tile that does not fit in shared memory.
 bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const PatternParams& pat,
                        float R2s, const LightParams& light, float* out, unsigned* status,
-                       cudaStream_t s, cudaError_t* err) {
+                       cudaStream_t s, cudaError_t* err, int tile_rows) {
     *err = cudaSuccess;
     if (pat.kind != 1 && pat.kind != 2) return false;
     if (pat.K > 16) return false;
@@ -314,7 +314,7 @@ bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const
         cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return false;
     // largest tile height whose staging fits; two buffers (prefetch) when they fit
-    int TH = 16, stages = 1;
+    int TH = (tile_rows == 4 || tile_rows == 8) ? tile_rows : 16, stages = 1;
     size_t smem = 0;
     for (; TH >= 4; TH /= 2) {
         if (hy + TH > 256) continue;

@@ -88,12 +88,12 @@ __device__ __forceinline__ uint32_t warp_start_node(const DevBVH& bvh, bool vali
                       make_float3(hi[0] + pad, hi[1] + pad, hi[2] + pad));
 }
 
+// Step 1 for pixel (x, y) of a view.  Warp-collective (the warp shares its start node):
+// every lane of the warp must call it, with pixels of the same view.
 template <int EFFECT>
-__global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS) k_trace(GBufView gb, DevBVH bvh, float radius,
-                                               LightParams lp, uint64_t seed, uint32_t sample,
-                                               RecView rec, unsigned* status) {
-    int x, y;
-    tile_pixel(&x, &y);
+__device__ __forceinline__ void trace_pixel(const GBufView& gb, const DevBVH& bvh, float radius,
+                                            const LightParams& lp, uint64_t seed, uint32_t sample,
+                                            const RecView& rec, unsigned* status, int x, int y) {
     const bool inside = x < gb.W && y < gb.H;
     const uint32_t p = inside ? (uint32_t)y * (uint32_t)gb.W + (uint32_t)x : 0u;
     float3 xo = make_float3(0.0f, 0.0f, 0.0f), n = xo;
@@ -117,6 +117,46 @@ __global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS) k_trace(GBufView gb
     const float3 nz = hit_normal(bvh, h.slot, d);
     const float3 z = make_float3(fmaf(h.t, d.x, xo.x), fmaf(h.t, d.y, xo.y), fmaf(h.t, d.z, xo.z));
     write_record(rec, p, xo, z, nz, h.t, (int)h.id);
+}
+
+template <int EFFECT>
+__global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS) k_trace(GBufView gb, DevBVH bvh, float radius,
+                                               LightParams lp, uint64_t seed, uint32_t sample,
+                                               RecView rec, unsigned* status) {
+    int x, y;
+    tile_pixel(&x, &y);
+    trace_pixel<EFFECT>(gb, bvh, radius, lp, seed, sample, rec, status, x, y);
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched step 1 over views of different sizes and effects: persistent CTAs stride over
+// the concatenated 16 x 8 tiles of all views (view of a tile found by binary search on
+// the tile offsets, staged in shared memory).
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS)
+    k_trace_batch(const BatchView* views, const BatchDyn* dyn, int n_views, int n_tiles, DevBVH bvh,
+                  unsigned* status) {
+    __shared__ int s_first[kMaxBatchViews + 1];
+    for (int v = threadIdx.x; v <= n_views; v += blockDim.x)
+        s_first[v] = v < n_views ? views[v].first_tile : n_tiles;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        int lo = 0, hi = n_views - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_first[mid] <= tile) lo = mid; else hi = mid - 1;
+        }
+        const BatchView& v = views[lo];
+        const int t = tile - s_first[lo];
+        const int x = (t % v.tiles_x) * kTileW + (warp & 1) * 8 + (lane & 7);
+        const int y = (t / v.tiles_x) * kTileH + (warp >> 1) * 4 + (lane >> 3);
+        const BatchDyn d = dyn[lo];
+        if (v.effect == kAO)
+            trace_pixel<kAO>(v.gb, bvh, v.radius, v.light, d.seed, d.sample, v.rec, status, x, y);
+        else
+            trace_pixel<kShadow>(v.gb, bvh, v.radius, v.light, d.seed, d.sample, v.rec, status, x, y);
+    }
 }
 
 __global__ void __launch_bounds__(128) k_gbuffer(DevBVH bvh, float3 eye, float3 f, float3 rt,
@@ -219,6 +259,25 @@ cudaError_t launch_gbuffer(const DevBVH& bvh, const float* cam, float eps, int W
     k_gbuffer<<<tile_grid(W, H), 128, 0, s>>>(bvh, eye, f, rt, up, th, (float)W / (float)H, eps,
                                               W, H, pos, nrm, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_trace_batch(const BatchView* views, const BatchDyn* dyn, int n_views, int n_tiles,
+                               const DevBVH& bvh, int ctas, unsigned* status, cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    k_trace_batch<<<ctas < n_tiles ? ctas : n_tiles, 128, 0, s>>>(views, dyn, n_views, n_tiles, bvh,
+                                                                  status);
+    return cudaGetLastError();
+}
+
+int trace_batch_ctas(int per_sm_wanted) {
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_batch, 128, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    if (per_sm_wanted > 0 && per_sm_wanted < per_sm) per_sm = per_sm_wanted;
+    return per_sm * sms;
 }
 
 cudaError_t launch_pack_gbuffer(const GBufView& gb, float4* out, cudaStream_t s) {

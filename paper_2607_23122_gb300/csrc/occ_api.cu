@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -24,6 +25,22 @@ struct occ_ctx {
     // workspace of occ_frame_host: pos4, nrm4, records, output
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    occ::Tuning tune;
+    // work table of occ_frame_batch: device copy, pinned staging, upload-done event
+    void* batch_dev = nullptr;
+    void* batch_host = nullptr;
+    size_t batch_bytes = 0;
+    cudaEvent_t batch_ev = nullptr;
+};
+
+struct occ_batch {
+    int device = 0;
+    occ::BatchView* views = nullptr;     // device
+    occ::BatchDyn* dyn = nullptr;        // device
+    occ::BatchDyn* dyn_host = nullptr;   // pinned
+    cudaEvent_t uploaded = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int n_views = 0;
 };
 
 struct occ_bvh {
@@ -232,7 +249,7 @@ occ_status reuse_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
     return launched(ctx,
                     occ::launch_reuse(effect, estimator, view(gb), rec_view(occ), pat, occ->radius,
                                       lp, bvh ? &b : nullptr, out, ctx->status,
-                                      (cudaStream_t)stream),
+                                      (cudaStream_t)stream, ctx->tune),
                     "reuse launch");
 }
 
@@ -299,6 +316,9 @@ OCC_EXPORT occ_status occ_destroy(occ_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaFree(ctx->status);
     cudaFree(ctx->ws);
+    cudaFree(ctx->batch_dev);
+    cudaFreeHost(ctx->batch_host);
+    if (ctx->batch_ev) cudaEventDestroy(ctx->batch_ev);
     delete ctx;
     return OCC_OK;
 }
@@ -556,6 +576,217 @@ OCC_EXPORT occ_status occ_debug_mis(occ_ctx* ctx, const occ_gbuffer* gb, const o
     cudaFree(d_mem);
     cudaFree(d_w);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "debug_mis");
+    return OCC_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched frames (occ_frame_batch), captured batches (occ_batch_*) and tuning.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kBatchTileW = 16, kBatchTileH = 8;
+
+// Validates the views and fills the device work table (host side); writes the record
+// metadata back into each view as the trace calls do.
+occ_status build_batch(occ_ctx* ctx, const occ_bvh* bvh, occ_view* views, int32_t n,
+                       std::vector<occ::BatchView>* table, std::vector<occ::BatchDyn>* dyn,
+                       int* n_tiles, int* max_k) {
+    if (!bvh) return fail(ctx, OCC_ERR_INVALID_ARG, "bvh is NULL");
+    if (!views || n < 1 || n > occ::kMaxBatchViews)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "n_views must be in [1, %d]", occ::kMaxBatchViews);
+    table->resize(n);
+    dyn->resize(n);
+    int64_t tiles = 0;
+    *max_k = 1;
+    for (int i = 0; i < n; ++i) {
+        occ_view& v = views[i];
+        occ_status st;
+        if ((st = check_gbuffer(ctx, &v.gb)) != OCC_OK) return st;
+        if ((st = check_occluders(ctx, &v.gb, &v.rec)) != OCC_OK) return st;
+        if (v.effect == OCC_EFFECT_AO && !(v.radius > 0.0f && std::isfinite(v.radius)))
+            return fail(ctx, OCC_ERR_INVALID_ARG, "view %d: AO radius must be positive", i);
+        if (v.effect == OCC_EFFECT_SHADOW && (st = check_light(ctx, &v.light)) != OCC_OK) return st;
+        if (v.effect != OCC_EFFECT_AO && v.effect != OCC_EFFECT_SHADOW)
+            return fail(ctx, OCC_ERR_INVALID_ARG, "view %d: effect %d invalid", i, v.effect);
+        if (v.estimator < OCC_EST_NOREUSE || v.estimator > OCC_EST_BOXMEAN)
+            return fail(ctx, OCC_ERR_INVALID_ARG, "view %d: estimator invalid", i);
+        if (v.K > 16) return fail(ctx, OCC_ERR_UNSUPPORTED, "view %d: batched views need K <= 16", i);
+        if (!v.out) return fail(ctx, OCC_ERR_INVALID_ARG, "view %d: out is NULL", i);
+        occ::BatchView& b = (*table)[i];
+        std::memset(&b, 0, sizeof(b));
+        if ((st = make_pattern(ctx, &v.pattern, v.K, &b.pat)) != OCC_OK) return st;
+        v.rec.effect = v.effect;
+        v.rec.radius = v.effect == OCC_EFFECT_AO ? v.radius : 0.0f;
+        if (v.effect == OCC_EFFECT_SHADOW) v.rec.light = v.light;
+        else std::memset(&v.rec.light, 0, sizeof(v.rec.light));
+        v.rec.seed = v.seed;
+        v.rec.sample = v.sample;
+        v.rec.offset_scale = offset_scale_for(bvh, v.effect, v.radius, &v.light);
+        b.gb = view(&v.gb);
+        b.rec = rec_view(&v.rec);
+        b.effect = v.effect;
+        b.estimator = v.estimator;
+        b.radius = v.rec.radius;
+        b.light = to_params(v.effect == OCC_EFFECT_SHADOW ? &v.light : nullptr);
+        b.R2s = (float)((double)v.rec.radius * (double)v.rec.radius * (1.0 + 1.0 / 65536.0));
+        b.out = v.out;
+        b.tiles_x = (v.gb.W + kBatchTileW - 1) / kBatchTileW;
+        b.first_tile = (int32_t)tiles;
+        tiles += (int64_t)b.tiles_x * ((v.gb.H + kBatchTileH - 1) / kBatchTileH);
+        (*dyn)[i].seed = v.seed;
+        (*dyn)[i].sample = v.sample;
+        (*dyn)[i].pad = 0;
+        *max_k = std::max(*max_k, v.K);
+    }
+    if (tiles > (int64_t)1 << 30) return fail(ctx, OCC_ERR_INVALID_ARG, "batch too large");
+    *n_tiles = (int)tiles;
+    return OCC_OK;
+}
+
+cudaError_t launch_batch(occ_ctx* ctx, const occ_bvh* bvh, const occ::BatchView* views,
+                         const occ::BatchDyn* dyn, int n, int n_tiles, int max_k, cudaStream_t s) {
+    const occ::DevBVH b = dev_bvh(bvh);
+    cudaError_t e = occ::launch_trace_batch(views, dyn, n, n_tiles, b,
+                                            occ::trace_batch_ctas(ctx->tune.batch_per_sm), ctx->status, s);
+    if (e == cudaSuccess)
+        e = occ::launch_reuse_batch(views, n, n_tiles, max_k, b, ctx->tune.batch_per_sm, ctx->status, s);
+    return e;
+}
+
+}  // namespace
+
+OCC_EXPORT occ_status occ_frame_batch(occ_ctx* ctx, const occ_bvh* bvh, occ_view* views,
+                                      int32_t n_views, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    std::vector<occ::BatchView> table;
+    std::vector<occ::BatchDyn> dyn;
+    int n_tiles = 0, max_k = 1;
+    if ((st = build_batch(ctx, bvh, views, n_views, &table, &dyn, &n_tiles, &max_k)) != OCC_OK) return st;
+    const size_t tb = table.size() * sizeof(occ::BatchView), db = dyn.size() * sizeof(occ::BatchDyn);
+    cudaError_t e = cudaSuccess;
+    if (!ctx->batch_ev) e = cudaEventCreateWithFlags(&ctx->batch_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess && ctx->batch_bytes < tb + db) {
+        // the previous upload must be done before its buffers go away
+        if (ctx->batch_bytes) cudaEventSynchronize(ctx->batch_ev);
+        cudaFree(ctx->batch_dev);
+        cudaFreeHost(ctx->batch_host);
+        ctx->batch_dev = ctx->batch_host = nullptr;
+        ctx->batch_bytes = 0;
+        e = cudaMalloc(&ctx->batch_dev, tb + db);
+        if (e == cudaSuccess) e = cudaMallocHost(&ctx->batch_host, tb + db);
+        if (e == cudaSuccess) ctx->batch_bytes = tb + db;
+    } else if (e == cudaSuccess) {
+        e = cudaEventSynchronize(ctx->batch_ev);   // staging is free once the last upload ran
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch table");
+    char* host = static_cast<char*>(ctx->batch_host);
+    std::memcpy(host, table.data(), tb);
+    std::memcpy(host + tb, dyn.data(), db);
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(ctx->batch_dev, host, tb + db, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->batch_ev, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
+    char* dev = static_cast<char*>(ctx->batch_dev);
+    return launched(ctx,
+                    launch_batch(ctx, bvh, reinterpret_cast<occ::BatchView*>(dev),
+                                 reinterpret_cast<occ::BatchDyn*>(dev + tb), n_views, n_tiles, max_k, s),
+                    "batch launch");
+}
+
+OCC_EXPORT occ_status occ_batch_capture(occ_ctx* ctx, const occ_bvh* bvh, occ_view* views,
+                                        int32_t n_views, occ_batch** out) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if (!out) return fail(ctx, OCC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    std::vector<occ::BatchView> table;
+    std::vector<occ::BatchDyn> dyn;
+    int n_tiles = 0, max_k = 1;
+    if ((st = build_batch(ctx, bvh, views, n_views, &table, &dyn, &n_tiles, &max_k)) != OCC_OK) return st;
+    occ_batch* b = new occ_batch();
+    b->device = ctx->device;
+    b->n_views = n_views;
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    const size_t tb = table.size() * sizeof(occ::BatchView), db = dyn.size() * sizeof(occ::BatchDyn);
+    cudaError_t e = cudaMalloc(&b->views, tb);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dyn, db);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->dyn_host, db);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemcpy(b->views, table.data(), tb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->dyn, dyn.data(), db, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t le = launch_batch(ctx, bvh, b->views, b->dyn, n_views, n_tiles, max_k, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        occ_batch_free(ctx, b);
+        return cuda_fail(ctx, e, "batch capture");
+    }
+    *out = b;
+    return OCC_OK;
+}
+
+OCC_EXPORT occ_status occ_batch_launch(occ_ctx* ctx, occ_batch* b, const uint64_t* seeds_host,
+                                       const uint32_t* samples_host, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if (!b || b->device != ctx->device) return fail(ctx, OCC_ERR_INVALID_ARG, "bad batch");
+    if (!seeds_host || !samples_host) return fail(ctx, OCC_ERR_INVALID_ARG, "seeds/samples are NULL");
+    cudaError_t e = cudaEventSynchronize(b->uploaded);   // the pinned values are free again
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch staging");
+    for (int i = 0; i < b->n_views; ++i) {
+        b->dyn_host[i].seed = seeds_host[i];
+        b->dyn_host[i].sample = samples_host[i];
+        b->dyn_host[i].pad = 0;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(b->dyn, b->dyn_host, sizeof(occ::BatchDyn) * b->n_views, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->uploaded, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+    return launched(ctx, e, "batch replay");
+}
+
+OCC_EXPORT occ_status occ_batch_free(occ_ctx* ctx, occ_batch* b) {
+    if (!ctx || !b) return OCC_ERR_INVALID_ARG;
+    cudaSetDevice(b->device);
+    if (b->uploaded) cudaEventSynchronize(b->uploaded);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->uploaded) cudaEventDestroy(b->uploaded);
+    cudaFree(b->views);
+    cudaFree(b->dyn);
+    cudaFreeHost(b->dyn_host);
+    delete b;
+    return OCC_OK;
+}
+
+OCC_EXPORT occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t) {
+    if (!ctx || !t) return OCC_ERR_INVALID_ARG;
+    if (t->reuse_tile_rows != 0 && t->reuse_tile_rows != 4 && t->reuse_tile_rows != 8 &&
+        t->reuse_tile_rows != 16)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "reuse_tile_rows must be 0, 4, 8 or 16");
+    if (t->reuse_window_path < 0 || t->reuse_window_path > 2)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "reuse_window_path must be 0, 1 or 2");
+    if (t->batch_ctas_per_sm < 0 || t->batch_ctas_per_sm > 16)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "batch_ctas_per_sm must be in [0, 16]");
+    ctx->tune.tile_rows = t->reuse_tile_rows;
+    ctx->tune.window_path = t->reuse_window_path;
+    ctx->tune.batch_per_sm = t->batch_ctas_per_sm;
+    return OCC_OK;
+}
+
+OCC_EXPORT occ_status occ_get_tuning(const occ_ctx* ctx, occ_tuning* t) {
+    if (!ctx || !t) return OCC_ERR_INVALID_ARG;
+    t->reuse_tile_rows = ctx->tune.tile_rows;
+    t->reuse_window_path = ctx->tune.window_path;
+    t->batch_ctas_per_sm = ctx->tune.batch_per_sm;
     return OCC_OK;
 }
 

@@ -40,6 +40,27 @@ struct PatternParams {
 };
 
 enum Effect { kAO = 0, kShadow = 1 };
+
+// One view of a batched frame (device-resident work table; see occ_frame_batch).
+constexpr int kMaxBatchViews = 256;
+struct BatchView {
+    GBufView gb;
+    RecView rec;
+    int32_t effect, estimator;
+    float radius;
+    LightParams light;
+    PatternParams pat;
+    float R2s;            // AO: R^2 (1 + 2^-16), rounded to float on the host
+    float* out;
+    int32_t tiles_x;      // 16 x 8 tiles per row of this view
+    int32_t first_tile;   // offset of this view in the batch's tile space
+};
+// Per-frame values of a view, kept apart so a captured batch can be replayed with new ones.
+struct BatchDyn {
+    uint64_t seed;
+    uint32_t sample;
+    uint32_t pad;
+};
 enum Estimator { kNoReuse = 0, kBiased = 1, kUnbiased = 2, kBoxMean = 3 };
 
 cudaError_t launch_gbuffer(const DevBVH& bvh, const float* cam, float eps, int W, int H,
@@ -53,14 +74,30 @@ cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
                               const LightParams& light, uint64_t seed, uint32_t sample,
                               float4* out, cudaStream_t s);
 
+// Launch choices (0 = default); see occ_tuning.
+struct Tuning {
+    int tile_rows = 0;
+    int window_path = 0;
+    int batch_per_sm = 0;
+};
+
 cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const RecView& rec,
                          const PatternParams& pat, float radius, const LightParams& light,
-                         const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s);
+                         const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s,
+                         const Tuning& tune = Tuning());
+// Batched frame over several views (persistent kernels over the concatenated tiles).
+cudaError_t launch_trace_batch(const BatchView* views, const BatchDyn* dyn, int n_views, int n_tiles,
+                               const DevBVH& bvh, int ctas, unsigned* status, cudaStream_t s);
+int trace_batch_ctas(int per_sm_wanted);
+cudaError_t launch_reuse_batch(const BatchView* views, int n_views, int n_tiles, int max_k,
+                               const DevBVH& bvh, int per_sm_wanted, unsigned* status,
+                               cudaStream_t s);
+
 // TMA-staged biased reuse for box / offset patterns; returns false (nothing launched) when
 // the pattern or its staging does not fit that kernel.
 bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const PatternParams& pat,
                        float R2s, const LightParams& light, float* out, unsigned* status,
-                       cudaStream_t s, cudaError_t* err);
+                       cudaStream_t s, cudaError_t* err, int tile_rows);
 
 cudaError_t launch_debug_mis(int effect, int estimator, const GBufView& gb, const RecView& rec,
                              const PatternParams& pat, float radius, const LightParams& light,

@@ -382,3 +382,99 @@ def occ_debug_mis(ctx: Context, gb: GBuffer, occ: Occluders, pattern: Pattern, K
                                     int(K), int(estimator), bvh.handle if bvh is not None else None,
                                     pix.ctypes.data, n, mem.ctypes.data, w.ctypes.data))
     return mem, w
+
+
+# ------------------------------------------------------------------------------------
+# Batched frames, captured batches, tuning
+# ------------------------------------------------------------------------------------
+
+@dataclass
+class View:
+    """One view of a batched frame (see occ_view)."""
+    gb: GBuffer
+    rec: Occluders
+    out: torch.Tensor
+    effect: int = OCC_EFFECT_AO
+    radius: float = 0.5
+    light: object = None
+    seed: int = 0
+    sample: int = 0
+    pattern: Pattern = None
+    estimator: int = OCC_EST_BIASED
+
+    def c(self) -> N.occ_view:
+        v = N.occ_view()
+        v.gb = self.gb.c()
+        v.rec = self.rec.c()
+        v.effect = self.effect
+        v.radius = self.radius
+        v.light = _light(self.light if self.light is not None else np.zeros(9))
+        v.seed = self.seed
+        v.sample = self.sample
+        v.pattern = self.pattern.c()
+        v.K = self.pattern.K
+        v.estimator = self.estimator
+        v.out = self.out.data_ptr()
+        return v
+
+
+def _views_array(views):
+    arr = (N.occ_view * len(views))()
+    for i, v in enumerate(views):
+        arr[i] = v.c()
+    return arr
+
+
+def _copy_back(arr, views):
+    for i, v in enumerate(views):
+        v.rec.meta = arr[i].rec
+
+
+def occ_frame_batch(ctx: Context, bvh: BVH, views: list, stream=None):
+    """Trace and reuse every view in one persistent launch pair (occ_frame_batch)."""
+    arr = _views_array(views)
+    ctx.check(ctx.lib.occ_frame_batch(ctx.handle, bvh.handle, arr, len(views),
+                                      _stream_handle(stream)))
+    _copy_back(arr, views)
+
+
+class Batch:
+    """A batched frame captured as a CUDA graph; replay() runs it with new seeds/samples."""
+
+    def __init__(self, ctx: Context, bvh: BVH, views: list):
+        self.ctx, self.views = ctx, views
+        arr = _views_array(views)
+        h = C.c_void_p()
+        ctx.check(ctx.lib.occ_batch_capture(ctx.handle, bvh.handle, arr, len(views), C.byref(h)))
+        _copy_back(arr, views)
+        self.handle = h
+
+    def replay(self, seeds, samples, stream=None):
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        sm = np.ascontiguousarray(samples, dtype=np.uint32)
+        assert sd.shape[0] == len(self.views) and sm.shape[0] == len(self.views)
+        self.ctx.check(self.ctx.lib.occ_batch_launch(self.ctx.handle, self.handle, sd.ctypes.data,
+                                                     sm.ctypes.data, _stream_handle(stream)))
+
+    def free(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.occ_batch_free(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def occ_set_tuning(ctx: Context, reuse_tile_rows: int = 0, reuse_window_path: int = 0,
+                   batch_ctas_per_sm: int = 0):
+    t = N.occ_tuning(reuse_tile_rows, reuse_window_path, batch_ctas_per_sm)
+    ctx.check(ctx.lib.occ_set_tuning(ctx.handle, C.byref(t)))
+
+
+def occ_get_tuning(ctx: Context) -> dict:
+    t = N.occ_tuning()
+    ctx.check(ctx.lib.occ_get_tuning(ctx.handle, C.byref(t)))
+    return {f: getattr(t, f) for f, _ in t._fields_}

@@ -16,7 +16,7 @@ def oct_encode(n: np.ndarray) -> np.ndarray:
     x, y, z = n[..., 0], n[..., 1], n[..., 2]
     with np.errstate(divide="ignore", invalid="ignore"):   # zero vectors of empty records
         inv = np.float32(1.0) / ((np.abs(x) + np.abs(y)) + np.abs(z))
-    px, py = x * inv, y * inv
+        px, py = x * inv, y * inv
     sx = np.where(px >= 0, np.float32(1), np.float32(-1))
     sy = np.where(py >= 0, np.float32(1), np.float32(-1))
     fx = (np.float32(1) - np.abs(py)) * sx

@@ -1,0 +1,25 @@
+"""Host logic of the autotuner: cache file round trip and workload keys (no GPU)."""
+import json
+
+from paper_2607_23122_gb300 import autotune
+
+
+def test_cache_round_trip_and_bad_files(tmp_path, monkeypatch):
+    path = tmp_path / "sub" / "tune.json"
+    monkeypatch.setenv("OCC_TUNE_CACHE", str(path))
+    assert autotune.cache_path() == str(path)
+    assert autotune.load_cache() == {}                      # missing file
+    entry = {"best": {"reuse_tile_rows": 8, "reuse_window_path": 1},
+             "timings": [{"config": {}, "ms": 0.5}]}
+    autotune.save_cache({"k": entry})
+    assert autotune.load_cache() == {"k": entry}
+    assert json.loads(path.read_text()) == {"k": entry}
+    assert not [p for p in path.parent.iterdir() if ".tmp" in p.name]
+    path.write_text("{not json")
+    assert autotune.load_cache() == {}                      # corrupt file: start over
+
+
+def test_candidates_are_valid_tuning_values():
+    for c in autotune.REUSE_CANDIDATES:
+        assert c["reuse_tile_rows"] in (0, 4, 8, 16) and c["reuse_window_path"] in (1, 2)
+    assert all(0 <= c["batch_ctas_per_sm"] <= 16 for c in autotune.BATCH_CANDIDATES)

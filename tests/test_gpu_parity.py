@@ -324,7 +324,7 @@ def test_frame_host_matches_device_path(occ, ctx, c1):
 
 
 # --------------------------------------------------------------------------------------
-# Packed formats (octahedral normals, FP16 occluder offsets; FP32 arithmetic)
+# Packed formats (octahedral normals, 21-bit fixed-point occluder offsets; FP32 arithmetic)
 # --------------------------------------------------------------------------------------
 
 from tests import _packing as PK  # noqa: E402
