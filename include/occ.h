@@ -49,7 +49,9 @@ typedef enum {
     OCC_ERR_OOM = 3,
     OCC_ERR_TIMEOUT = 4,
     OCC_ERR_UNSUPPORTED = 5,
-    OCC_ERR_DEVICE_CHECK = 6
+    OCC_ERR_DEVICE_CHECK = 6,
+    OCC_ERR_BUSY = 7,        /* a serving queue is full (include/occ_serve.h) */
+    OCC_ERR_CANCELLED = 8    /* a queued request dropped when its server shut down */
 } occ_status;
 
 enum { OCC_EFFECT_AO = 0, OCC_EFFECT_SHADOW = 1 };
@@ -157,7 +159,9 @@ occ_status occ_bvh_info(const occ_bvh* bvh, occ_bvh_stats* out);
 /* Input stage (not part of the paper's method, which takes a raster
  * G-buffer): pinhole primary rays.  cam_host = eye[3], target[3], up[3],
  * vfov_deg.  Writes pos4/nrm4 (W*H float4 each); pos4 is the hit point moved
- * `eps` along the geometric normal turned toward the camera. */
+ * `eps` along the geometric normal turned toward the camera.  With nrm4 NULL
+ * it writes the PACKED G-buffer (one float4 plane, as occ_pack_gbuffer makes)
+ * into pos4. */
 occ_status occ_gbuffer_pinhole(occ_ctx* ctx, const occ_bvh* bvh, const float* cam_host,
                                float eps, int32_t W, int32_t H, float* pos4, float* nrm4,
                                void* stream);

@@ -15,7 +15,8 @@ c_float, c_double, c_void_p, c_char_p = C.c_float, C.c_double, C.c_void_p, C.c_c
 
 OCC_OK = 0
 STATUS_NAMES = {0: "OCC_OK", 1: "OCC_ERR_INVALID_ARG", 2: "OCC_ERR_CUDA", 3: "OCC_ERR_OOM",
-                4: "OCC_ERR_TIMEOUT", 5: "OCC_ERR_UNSUPPORTED", 6: "OCC_ERR_DEVICE_CHECK"}
+                4: "OCC_ERR_TIMEOUT", 5: "OCC_ERR_UNSUPPORTED", 6: "OCC_ERR_DEVICE_CHECK",
+                7: "OCC_ERR_BUSY", 8: "OCC_ERR_CANCELLED"}
 
 OCC_EFFECT_AO, OCC_EFFECT_SHADOW = 0, 1
 OCC_EST_NOREUSE, OCC_EST_BIASED, OCC_EST_UNBIASED, OCC_EST_BOXMEAN = 0, 1, 2, 3
@@ -63,7 +64,45 @@ class occ_bvh_stats(C.Structure):
                 ("build_seconds", c_double)]
 
 
-# name -> (restype, argtypes); every symbol declared in include/occ.h
+# include/occ_serve.h
+class occ_sched_config(C.Structure):
+    _fields_ = [("budget_bytes", c_int64), ("max_views_per_batch", c_int32),
+                ("max_inflight", c_int32), ("max_queued", c_int32)]
+
+
+class occ_sched_stats(C.Structure):
+    _fields_ = [(f, c_int64) for f in ("queued", "inflight_batches", "reserved_bytes",
+                                       "peak_reserved_bytes", "submitted", "admitted",
+                                       "completed_batches", "expired", "refused")]
+
+
+class occ_server_config(C.Structure):
+    _fields_ = [("budget_bytes", c_int64), ("max_views_per_batch", c_int32),
+                ("max_inflight", c_int32), ("max_queued", c_int32), ("poll_us", c_int32),
+                ("batch_max_px", c_int64), ("batch_window_us", c_int64)]
+
+
+class occ_request(C.Structure):
+    _fields_ = [("W", c_int32), ("H", c_int32), ("effect", c_int32), ("radius", c_float),
+                ("light", occ_rect_light), ("seed", c_uint64), ("sample", c_uint32),
+                ("pattern", occ_pattern), ("K", c_int32), ("estimator", c_int32),
+                ("packed", c_int32), ("camera", c_float * 10), ("eps", c_float),
+                ("pos4_host", c_void_p), ("nrm4_host", c_void_p), ("out_host", c_void_p),
+                ("out_device", c_void_p), ("deadline_ns", c_int64)]
+
+
+class occ_result(C.Structure):
+    _fields_ = [("id", c_uint64), ("status", c_int32), ("batch_views", c_int32),
+                ("t_submit_ns", c_int64), ("t_admit_ns", c_int64), ("t_done_ns", c_int64)]
+
+
+class occ_server_stats(C.Structure):
+    _fields_ = [("sched", occ_sched_stats), ("budget_bytes", c_int64), ("batches", c_int64),
+                ("views_batched", c_int64), ("views_single", c_int64),
+                ("pool_reserved_bytes", c_int64)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/*.h
 SIGNATURES = {
     "occ_create": (c_int32, [C.c_int, C.POINTER(c_void_p)]),
     "occ_destroy": (c_int32, [c_void_p]),
@@ -101,6 +140,23 @@ SIGNATURES = {
     "occ_batch_free": (c_int32, [c_void_p, c_void_p]),
     "occ_set_tuning": (c_int32, [c_void_p, C.POINTER(occ_tuning)]),
     "occ_get_tuning": (c_int32, [c_void_p, C.POINTER(occ_tuning)]),
+    "occ_sched_create": (c_int32, [C.POINTER(occ_sched_config), C.POINTER(c_void_p)]),
+    "occ_sched_destroy": (c_int32, [c_void_p]),
+    "occ_sched_submit": (c_int32, [c_void_p, c_uint64, c_int64, c_int64, c_int64]),
+    "occ_sched_next": (c_int32, [c_void_p, c_int64, c_void_p, c_int32, C.POINTER(c_int32),
+                                 C.POINTER(c_int32), c_void_p, c_int32, C.POINTER(c_int32)]),
+    "occ_sched_complete": (c_int32, [c_void_p, c_int32]),
+    "occ_sched_drain": (c_int32, [c_void_p, c_void_p, c_int32, C.POINTER(c_int32)]),
+    "occ_sched_get_stats": (c_int32, [c_void_p, C.POINTER(occ_sched_stats)]),
+    "occ_server_create": (c_int32, [c_void_p, c_void_p, C.POINTER(occ_server_config),
+                                    C.POINTER(c_void_p)]),
+    "occ_server_submit": (c_int32, [c_void_p, C.POINTER(occ_request), C.POINTER(c_uint64),
+                                    c_char_p, c_int32]),
+    "occ_server_poll": (c_int32, [c_void_p, C.POINTER(occ_result), c_int32, c_int64,
+                                  C.POINTER(c_int32)]),
+    "occ_server_get_stats": (c_int32, [c_void_p, C.POINTER(occ_server_stats)]),
+    "occ_server_shutdown": (c_int32, [c_void_p, c_int32]),
+    "occ_server_destroy": (c_int32, [c_void_p, c_int32]),
     "occ_debug_philox": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "occ_debug_rays": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_int32, c_float,
                                  C.POINTER(occ_rect_light), c_uint64, c_uint32, c_void_p,

@@ -1,4 +1,4 @@
-"""Builds liboccreuse.so (the C-ABI library of include/occ.h) in-tree with nvcc.
+"""Builds liboccreuse.so (the C-ABI library of include/*.h) in-tree with nvcc.
 
 One -gencode for sm_103a, translation units compiled in parallel, static cudart.
 Rebuilds only when a source or header is newer than the library.
@@ -36,7 +36,7 @@ def _sources():
 
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) \
-        + [os.path.join(INCLUDE, "occ.h"), os.path.abspath(__file__)]
+        + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:

@@ -172,15 +172,25 @@ __global__ void __launch_bounds__(128) k_gbuffer(DevBVH bvh, float3 eye, float3 
     const float3 d = normalize3(make_float3(f.x + sx * rt.x + sy * up.x, f.y + sx * rt.y + sy * up.y,
                                             f.z + sx * rt.z + sy * up.z));
     const Hit h = closest_hit(bvh, eye, d, 3.0e38f, status);
+    // nrm == nullptr: one packed plane (point, octahedral normal code in w)
     if (h.id == kNoHit) {
-        pos[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        nrm[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (nrm) {
+            pos[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            nrm[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        } else {
+            pos[p] = make_float4(0.0f, 0.0f, 0.0f, __uint_as_float(kOctInvalid));
+        }
         return;
     }
     const float3 n = hit_normal(bvh, h.slot, d);
-    pos[p] = make_float4(fmaf(h.t, d.x, eye.x) + eps * n.x, fmaf(h.t, d.y, eye.y) + eps * n.y,
-                         fmaf(h.t, d.z, eye.z) + eps * n.z, 1.0f);
-    nrm[p] = make_float4(n.x, n.y, n.z, 0.0f);
+    const float3 hp = make_float3(fmaf(h.t, d.x, eye.x) + eps * n.x, fmaf(h.t, d.y, eye.y) + eps * n.y,
+                                  fmaf(h.t, d.z, eye.z) + eps * n.z);
+    if (nrm) {
+        pos[p] = make_float4(hp.x, hp.y, hp.z, 1.0f);
+        nrm[p] = make_float4(n.x, n.y, n.z, 0.0f);
+    } else {
+        pos[p] = make_float4(hp.x, hp.y, hp.z, __uint_as_float(oct_encode(n)));
+    }
 }
 
 __global__ void k_debug_philox(const uint32_t* in, int64_t n, uint32_t* out) {

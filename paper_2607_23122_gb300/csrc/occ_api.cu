@@ -12,44 +12,8 @@
 
 #include <cuda_runtime.h>
 
-#include "occ.h"
 #include "occ_bvh_host.h"
-#include "occ_kernels.h"
-
-#define OCC_EXPORT extern "C" __attribute__((visibility("default")))
-
-struct occ_ctx {
-    int device = 0;
-    unsigned* status = nullptr;          // device status word (kStatus* bits)
-    std::string last_error;
-    // workspace of occ_frame_host: pos4, nrm4, records, output
-    void* ws = nullptr;
-    size_t ws_bytes = 0;
-    occ::Tuning tune;
-    // work table of occ_frame_batch: device copy, pinned staging, upload-done event
-    void* batch_dev = nullptr;
-    void* batch_host = nullptr;
-    size_t batch_bytes = 0;
-    cudaEvent_t batch_ev = nullptr;
-};
-
-struct occ_batch {
-    int device = 0;
-    occ::BatchView* views = nullptr;     // device
-    occ::BatchDyn* dyn = nullptr;        // device
-    occ::BatchDyn* dyn_host = nullptr;   // pinned
-    cudaEvent_t uploaded = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    int n_views = 0;
-};
-
-struct occ_bvh {
-    int device = 0;
-    occ::Node4* nodes = nullptr;
-    float4* tris = nullptr;
-    occ_bvh_stats stats{};
-    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // scene bounds
-};
+#include "occ_internal.h"
 
 namespace {
 
@@ -103,6 +67,10 @@ occ_status check_occluders(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occlud
         return fail(ctx, OCC_ERR_INVALID_ARG, "occluder data must be a 16-byte aligned pointer");
     return OCC_OK;
 }
+
+}  // namespace
+
+namespace occ {
 
 occ_status check_light(occ_ctx* ctx, const occ_rect_light* l) {
     if (!l) return fail(ctx, OCC_ERR_INVALID_ARG, "light is NULL");
@@ -176,6 +144,14 @@ occ_status make_pattern(occ_ctx* ctx, const occ_pattern* pat, int32_t K, occ::Pa
     }
     return OCC_OK;
 }
+
+}  // namespace occ
+
+namespace {
+
+using occ::check_light;
+using occ::make_pattern;
+using occ::to_params;
 
 occ::GBufView view(const occ_gbuffer* gb) {
     return occ::GBufView{gb->W, gb->H, reinterpret_cast<const float4*>(gb->pos4),
@@ -409,9 +385,9 @@ OCC_EXPORT occ_status occ_gbuffer_pinhole(occ_ctx* ctx, const occ_bvh* bvh, cons
                                           float* nrm4, void* stream) {
     occ_status st = check_ctx(ctx);
     if (st != OCC_OK) return st;
-    if (!bvh || !cam_host || !pos4 || !nrm4 || W <= 0 || H <= 0 || !std::isfinite(eps))
+    if (!bvh || !cam_host || !pos4 || W <= 0 || H <= 0 || !std::isfinite(eps))
         return fail(ctx, OCC_ERR_INVALID_ARG, "bad gbuffer_pinhole arguments");
-    if (!aligned16(pos4) || !aligned16(nrm4))
+    if (!aligned16(pos4) || (nrm4 && !aligned16(nrm4)))
         return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pointers must be 16-byte aligned");
     if (!(cam_host[9] > 0.0f && cam_host[9] < 180.0f))
         return fail(ctx, OCC_ERR_INVALID_ARG, "vertical fov must be in (0, 180) degrees");

@@ -245,13 +245,13 @@ class Pattern:
 
 
 def occ_gbuffer_pinhole(ctx: Context, bvh: BVH, camera, eps: float, W: int, H: int,
-                        stream=None) -> GBuffer:
+                        stream=None, packed: bool = False) -> GBuffer:
     cam = np.ascontiguousarray(camera, dtype=np.float32).reshape(10)
     dev = torch.device("cuda", ctx.device)
     gb = GBuffer(torch.empty((H, W, 4), dtype=torch.float32, device=dev),
-                 torch.empty((H, W, 4), dtype=torch.float32, device=dev))
+                 None if packed else torch.empty((H, W, 4), dtype=torch.float32, device=dev))
     ctx.check(ctx.lib.occ_gbuffer_pinhole(ctx.handle, bvh.handle, cam.ctypes.data, float(eps), W, H,
-                                          gb.pos4.data_ptr(), gb.nrm4.data_ptr(),
+                                          gb.pos4.data_ptr(), None if packed else gb.nrm4.data_ptr(),
                                           _stream_handle(stream)))
     return gb
 
@@ -478,3 +478,168 @@ def occ_get_tuning(ctx: Context) -> dict:
     t = N.occ_tuning()
     ctx.check(ctx.lib.occ_get_tuning(ctx.handle, C.byref(t)))
     return {f: getattr(t, f) for f, _ in t._fields_}
+
+
+# --------------------------------------------------------------------------------------
+# Serving loop (include/occ_serve.h)
+# --------------------------------------------------------------------------------------
+
+class Scheduler:
+    """The admission scheduler alone (host only; occ_sched_*)."""
+
+    def __init__(self, budget_bytes: int, max_views_per_batch: int = 64, max_inflight: int = 2,
+                 max_queued: int = 4096):
+        self.lib = N.load()
+        cfg = N.occ_sched_config(budget_bytes, max_views_per_batch, max_inflight, max_queued)
+        h = C.c_void_p()
+        st = self.lib.occ_sched_create(C.byref(cfg), C.byref(h))
+        if st != N.OCC_OK:
+            raise OccError(st, "occ_sched_create: invalid configuration")
+        self.handle = h
+        self.cap = max_views_per_batch
+
+    def submit(self, id: int, nbytes: int, now_ns: int, deadline_ns: int = 0) -> int:
+        """Returns the status (0 = queued)."""
+        return self.lib.occ_sched_submit(self.handle, id, nbytes, now_ns, deadline_ns)
+
+    def next(self, now_ns: int, exp_cap: int = 256):
+        """(slot or -1, admitted ids, expired ids)."""
+        ids = (C.c_uint64 * self.cap)()
+        exp = (C.c_uint64 * max(1, exp_cap))()
+        n, slot, ne = C.c_int32(), C.c_int32(), C.c_int32()
+        st = self.lib.occ_sched_next(self.handle, now_ns, ids, self.cap, C.byref(n), C.byref(slot),
+                                     exp, exp_cap, C.byref(ne))
+        if st != N.OCC_OK:
+            raise OccError(st, "occ_sched_next")
+        return slot.value, list(ids[:n.value]), list(exp[:ne.value])
+
+    def complete(self, slot: int) -> int:
+        return self.lib.occ_sched_complete(self.handle, slot)
+
+    def drain(self) -> list:
+        out = []
+        buf = (C.c_uint64 * 64)()
+        n = C.c_int32(64)
+        while n.value == 64:
+            self.lib.occ_sched_drain(self.handle, buf, 64, C.byref(n))
+            out += list(buf[:n.value])
+        return out
+
+    def stats(self) -> dict:
+        s = N.occ_sched_stats()
+        self.lib.occ_sched_get_stats(self.handle, C.byref(s))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.occ_sched_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A serving loop on ctx's device for one resident scene (occ_server_*).
+
+    submit() takes one frame (camera or host G-buffer in; pinned host or device tensor out)
+    and returns its id; poll() returns finished results as dicts with the server's own
+    timestamps (ns since the server started)."""
+
+    def __init__(self, ctx: Context, bvh: BVH, budget_bytes: int = 0, max_views_per_batch: int = 0,
+                 max_inflight: int = 0, max_queued: int = 0, poll_us: int = 0,
+                 batch_max_px: int = 0, batch_window_us: int = 0):
+        self.ctx, self.bvh = ctx, bvh          # the BVH must outlive the server
+        cfg = N.occ_server_config(budget_bytes, max_views_per_batch, max_inflight, max_queued,
+                                  poll_us, batch_max_px, batch_window_us)
+        h = C.c_void_p()
+        ctx.check(ctx.lib.occ_server_create(ctx.handle, bvh.handle, C.byref(cfg), C.byref(h)))
+        self.handle = h
+        self._keep = {}                        # id -> objects the request points into
+
+    def submit(self, W: int, H: int, effect: int, pattern: Pattern, estimator: int, out,
+               radius: float = 0.5, light=None, seed: int = 0, sample: int = 0,
+               packed: bool = False, camera=None, eps: float = 0.0, pos4_host=None,
+               nrm4_host=None, deadline_ns: int = 0) -> int:
+        r = N.occ_request()
+        r.W, r.H, r.effect, r.radius = W, H, effect, radius
+        r.light = _light(light if light is not None else np.zeros(9))
+        r.seed, r.sample = seed, sample
+        r.pattern = pattern.c()
+        r.K, r.estimator, r.packed = pattern.K, estimator, int(packed)
+        if camera is not None:
+            r.camera[:] = [float(v) for v in np.asarray(camera, dtype=np.float32).reshape(10)]
+        r.eps = eps
+        keep = [pattern]
+        if pos4_host is not None:
+            r.pos4_host = pos4_host.data_ptr()
+            keep.append(pos4_host)
+            if nrm4_host is not None:
+                r.nrm4_host = nrm4_host.data_ptr()
+                keep.append(nrm4_host)
+        if out.is_cuda:
+            r.out_device = out.data_ptr()
+        else:
+            r.out_host = out.data_ptr()
+        keep.append(out)
+        r.deadline_ns = deadline_ns
+        rid = C.c_uint64()
+        msg = C.create_string_buffer(256)
+        st = self.ctx.lib.occ_server_submit(self.handle, C.byref(r), C.byref(rid), msg, 256)
+        if st != N.OCC_OK:
+            raise OccError(st, msg.value.decode(errors="replace"))
+        self._keep[rid.value] = keep
+        return rid.value
+
+    def poll(self, max_results: int = 256, timeout_us: int = 0) -> list:
+        buf = (N.occ_result * max_results)()
+        n = C.c_int32()
+        self.ctx.check(self.ctx.lib.occ_server_poll(self.handle, buf, max_results, timeout_us,
+                                                    C.byref(n)))
+        out = []
+        for i in range(n.value):
+            r = buf[i]
+            self._keep.pop(r.id, None)
+            out.append({"id": r.id, "status": r.status, "batch_views": r.batch_views,
+                        "t_submit_ns": r.t_submit_ns, "t_admit_ns": r.t_admit_ns,
+                        "t_done_ns": r.t_done_ns})
+        return out
+
+    def wait(self, ids, timeout_s: float = 60.0) -> dict:
+        """Polls until every id in `ids` finished; returns {id: result}."""
+        import time
+        want, got = set(ids), {}
+        end = time.monotonic() + timeout_s
+        while want - got.keys():
+            left = end - time.monotonic()
+            if left <= 0:
+                raise TimeoutError(f"{len(want - got.keys())} requests still running")
+            for r in self.poll(timeout_us=int(min(left, 0.5) * 1e6)):
+                got[r["id"]] = r
+        return {i: got[i] for i in ids}
+
+    def stats(self) -> dict:
+        s = N.occ_server_stats()
+        self.ctx.check(self.ctx.lib.occ_server_get_stats(self.handle, C.byref(s)))
+        d = {f: getattr(s.sched, f) for f, _ in s.sched._fields_}
+        d.update({f: getattr(s, f) for f, _ in s._fields_ if f != "sched"})
+        return d
+
+    def shutdown(self, cancel_queued: bool = False):
+        """Stops accepting work; waits for the worker (results stay pollable)."""
+        self.ctx.check(self.ctx.lib.occ_server_shutdown(self.handle, int(cancel_queued)))
+
+    def close(self, cancel_queued: bool = False):
+        if getattr(self, "handle", None):
+            self.ctx.lib.occ_server_destroy(self.handle, int(cancel_queued))
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

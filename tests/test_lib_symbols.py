@@ -1,5 +1,6 @@
-"""The C-ABI library builds, loads without a GPU, and exports every symbol of include/occ.h."""
+"""The C-ABI library builds, loads without a GPU, and exports every symbol of include/*.h."""
 import ctypes
+import glob
 import os
 import re
 
@@ -7,9 +8,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared_functions():
-    src = open(os.path.join(ROOT, "include", "occ.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(occ_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(occ_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_hot_path():
@@ -52,3 +55,11 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(N.occ_bvh_stats) == 48
     # W H format (pad) data effect radius light(36) (pad) seed sample (pad)
     assert ctypes.sizeof(N.occ_occluders) == 88
+    assert ctypes.sizeof(N.occ_sched_config) == 24
+    assert ctypes.sizeof(N.occ_sched_stats) == 72
+    assert ctypes.sizeof(N.occ_server_config) == 40
+    # W H effect radius light(36) (pad) seed sample (pad) pattern(24) K estimator packed
+    # camera(40) eps 4 pointers deadline
+    assert ctypes.sizeof(N.occ_request) == 192
+    assert ctypes.sizeof(N.occ_result) == 40
+    assert ctypes.sizeof(N.occ_server_stats) == 112
