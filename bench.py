@@ -60,7 +60,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--profile-step", action="store_true",
+                    help="launch the hot kernels once each (1080p AO: trace, window reuse, "
+                         "4x2 group reuse) and exit: the case profiled with ncu")
     return ap.parse_args()
 
 
@@ -238,6 +242,23 @@ def packed_frame(occ, ctx, gb, bvh, pat, out, flush, stream) -> dict:
             "ms_per_frame": tr["ms"] + ru["ms"], "bytes_per_px_stored": 16 + 16 + 4}
 
 
+def quality_leg(occ, ctx, gb, bvh, pat) -> dict:
+    """Equal-time RelMSE (eps 1e-3) against a 4096-spp no-reuse reference on this frame:
+    AO at 2 ms and area-light shadows at 5 ms per image, the paper's 1080p budgets."""
+    import synth
+
+    from paper_2607_23122_gb300 import quality as Q
+    light = synth.light_c3().as_array()
+    out = {"reference": "no-reuse mean over 4096 spp (samples 0..4095); estimates use "
+                        "independent samples; frames per method = floor(budget / frame time)"}
+    for eff, budget, key in ((occ.OCC_EFFECT_AO, 2.0, "ao_2ms"), (occ.OCC_EFFECT_SHADOW, 5.0, "shadow_5ms")):
+        ref = Q.reference(ctx, gb, bvh, eff, radius=RADIUS, light=light, spp=4096)
+        out[key] = Q.equal_time(ctx, gb, bvh, eff, budget, ref, radius=RADIUS, light=light,
+                                extra=[("Occ(8) disk", pat, occ.OCC_EST_BIASED),
+                                       ("Occ(8)U", occ.Pattern.group(4, 2), occ.OCC_EST_UNBIASED)])
+    return out
+
+
 SERVE_RES = [(640, 360), (1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)]
 
 
@@ -249,80 +270,105 @@ def serving_mix(n: int, seed: int = 5) -> list:
              int(rng.integers(8))) for _ in range(n)]
 
 
-def serving(occ, ctx, bvh, scene, n_req: int) -> dict:
-    """Continuous-batching serving loop: the same request mix served with FP32 and with
-    packed formats; first as one burst (saturated throughput), then as Poisson arrivals at
-    0.8x the FP32 saturated rate.  Latency = submit -> estimate in pinned host memory, on
-    the server's own clock."""
-    import torch
+class _OutPool:
+    """Pinned host output buffers by resolution, recycled when their request completes."""
 
+    def __init__(self):
+        self.free, self.lock = {}, threading.Lock()
+
+    def take(self, w, h):
+        import torch
+        with self.lock:
+            lst = self.free.setdefault((w, h), [])
+            if lst:
+                return lst.pop()
+        return torch.empty((h, w), dtype=torch.float32, pin_memory=True)
+
+    def give(self, t):
+        with self.lock:
+            self.free.setdefault((t.shape[1], t.shape[0]), []).append(t)
+
+
+def serving(occ, ctx, bvh, scene, n_req: int) -> dict:
+    """Continuous-batching serving loop on the request mix, FP32 and packed formats:
+    (1) saturated: n_req requests submitted at once; (2) Poisson arrivals of 4 n_req
+    requests at 0.8x the FP32 saturated rate (same arrival times for both formats);
+    (3) saturated with a 2 GB device budget (admission by memory).  Latency = submit ->
+    estimate in pinned host memory, on the server's own clock."""
     import synth
-    mix = serving_mix(n_req)
+    n_poi = 4 * n_req
+    mix = serving_mix(n_poi)
     cams = [c.as_array() for c in synth.serving_views(8)]
     light = synth.light_c3().as_array()
     pats = {4: occ.Pattern.group(2, 2), 8: occ.Pattern.offsets_of(synth.disk_offsets(8, DISK_R, 3)),
             16: occ.Pattern.group(4, 4)}
-    sizes = [W_ * H_ for (W_, H_), _, _, _ in mix]
-    arena = torch.empty(sum(sizes), dtype=torch.float32, pin_memory=True)
-    outs, o = [], 0
-    for n in sizes:
-        outs.append(arena[o:o + n])
-        o += n
+    pool = _OutPool()
+    px = [w * h for (w, h), _, _, _ in mix]
 
-    def submit(srv, i, packed):
-        (w, h), eff, k, c = mix[i]
-        return srv.submit(w, h, eff, pats[k], occ.OCC_EST_BIASED, outs[i].view(h, w), radius=RADIUS,
-                          light=light if eff else None, seed=9, sample=i, packed=packed,
-                          camera=cams[c], eps=scene.eps)
+    def run(srv, idx, packed, gaps=None):
+        """Submits requests idx (at once, or after the given gaps) and collects them."""
+        res, outs, lock, stop = {}, {}, threading.Lock(), threading.Event()
 
-    def summarize(res, t_first, n):
+        def collect():
+            while not stop.is_set() or len(res) < len(idx):
+                for r in srv.poll(timeout_us=5000):
+                    with lock:
+                        res[r["id"]] = r
+                        pool.give(outs.pop(r["id"]))
+
+        th = threading.Thread(target=collect, daemon=True)
+        th.start()
+        due = time.perf_counter()
+        for n, i in enumerate(idx):
+            if gaps is not None:
+                due += gaps[n]
+                while True:
+                    left = due - time.perf_counter()
+                    if left <= 0:
+                        break
+                    time.sleep(left if left > 2e-4 else 0)
+            (w, h), eff, k, c = mix[i]
+            o = pool.take(w, h)
+            with lock:
+                rid = srv.submit(w, h, eff, pats[k], occ.OCC_EST_BIASED, o, radius=RADIUS,
+                                 light=light if eff else None, seed=9, sample=i, packed=packed,
+                                 camera=cams[c], eps=scene.eps)
+                outs[rid] = o
+        stop.set()
+        th.join(timeout=600)
+        t_first = min(r["t_submit_ns"] for r in res.values())
         lat = np.array([r["t_done_ns"] - r["t_submit_ns"] for r in res.values()]) * 1e-6
         span = (max(r["t_done_ns"] for r in res.values()) - t_first) * 1e-9
-        px = sum(sizes[:n])
-        return {"requests_per_s": n / span, "Mpx_per_s": px / span / 1e6,
+        return {"requests": len(idx), "requests_per_s": len(idx) / span,
+                "Mpx_per_s": sum(px[i] for i in idx) / span / 1e6,
                 "p50_ms": float(np.median(lat)), "p99_ms": float(np.quantile(lat, 0.99)),
                 "mean_batch_views": float(np.mean([r["batch_views"] for r in res.values()])),
                 "all_ok": all(r["status"] == 0 for r in res.values())}
 
-    out = {"requests": n_req,
-           "mix": "640x360..3840x2160 uniform, AO/shadow 50/50, K in {4 (group 2x2), "
+    out = {"mix": "640x360..3840x2160 uniform, AO/shadow 50/50, K in {4 (group 2x2), "
                   "8 (15-px disk), 16 (group 4x4)}, 8 cameras, biased; G-buffer rendered on the "
                   "device per request; estimate copied to pinned host memory"}
     rate = None
+    gaps = None
     for packed in (False, True):
+        key = "packed" if packed else "fp32"
         srv = occ.Server(ctx, bvh, max_views_per_batch=32, max_inflight=2)
-        # warm-up: every resolution once per effect (pool, kernels)
-        warm = [submit(srv, i, packed) for i in range(min(16, n_req))]
-        srv.wait(warm)
-        # saturated: all at once
-        ids = [submit(srv, i, packed) for i in range(n_req)]
-        res = srv.wait(ids, timeout_s=300)
-        t_first = min(r["t_submit_ns"] for r in res.values())
-        sat = summarize(res, t_first, n_req)
+        run(srv, list(range(16)), packed)                       # warm-up: pool, kernels
+        sat = run(srv, list(range(n_req)), packed)
         if rate is None:
             rate = 0.8 * sat["requests_per_s"]
-        # Poisson arrivals at the same rate for both formats
-        gaps = np.random.default_rng(55).exponential(1.0 / rate, size=n_req)
-        ids = []
-        t0 = time.perf_counter()
-        due = t0
-        for i in range(n_req):
-            due += gaps[i]
-            while True:
-                left = due - time.perf_counter()
-                if left <= 0:
-                    break
-                time.sleep(left if left > 2e-4 else 0)
-            ids.append(submit(srv, i, packed))
-        res = srv.wait(ids, timeout_s=300)
-        t_first = min(r["t_submit_ns"] for r in res.values())
-        poi = summarize(res, t_first, n_req)
+            gaps = np.random.default_rng(55).exponential(1.0 / rate, size=n_poi)
+        poi = run(srv, list(range(n_poi)), packed, gaps)
         st = srv.stats()
         srv.close()
-        out["packed" if packed else "fp32"] = {
-            "saturated": sat, "poisson": poi,
-            "peak_reserved_MB": st["peak_reserved_bytes"] / 2**20,
-            "views_batched": st["views_batched"], "views_single": st["views_single"]}
+        srv = occ.Server(ctx, bvh, budget_bytes=2 << 30, max_views_per_batch=32, max_inflight=2)
+        small = run(srv, list(range(n_req)), packed)
+        st_small = srv.stats()
+        srv.close()
+        out[key] = {"saturated": sat, "poisson": poi,
+                    "peak_reserved_MB": st["peak_reserved_bytes"] / 2**20,
+                    "views_batched": st["views_batched"], "views_single": st["views_single"],
+                    "budget_2GB_saturated": dict(small, peak_reserved_MB=st_small["peak_reserved_bytes"] / 2**20)}
     out["poisson_rate_req_s"] = rate
     return out
 
@@ -415,6 +461,8 @@ def run_ours(args):
                                         out=out, stream=st), flush, stream, 200)
         extra["shadow"] = shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream)
         extra["packed"] = packed_frame(occ, ctx, gb, bvh, pat, out, flush, stream)
+        if not args.no_quality:
+            extra["quality"] = quality_leg(occ, ctx, gb, bvh, pat)
         if not args.no_serving:
             extra["serving"] = serving(occ, ctx, bvh, scene, args.serve_requests)
 
@@ -468,8 +516,9 @@ def run_ours(args):
             "bvh": {"nodes": st["num_nodes"], "depth": st["depth"], "bytes": st["bytes"],
                     "build_s": st["build_seconds"]},
         }
-        if "serving" in extra:
-            line["serving"] = extra["serving"]
+        for key in ("quality", "serving"):
+            if key in extra:
+                line[key] = extra[key]
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(scene, cam, offs)
         print(json.dumps(line), flush=True)
@@ -531,8 +580,29 @@ def run_reference(args):
     }), flush=True)
 
 
+def profile_step():
+    """One launch of each hot kernel on the 1080p AO frame, untimed (ncu captures)."""
+    import torch
+
+    from paper_2607_23122_gb300 import occ
+    ctx = occ.Context(0)
+    scene, cam, offs = scene_inputs()
+    bvh = occ.BVH(ctx, scene.tris)
+    gb = occ.occ_gbuffer_pinhole(ctx, bvh, cam.as_array(), scene.eps, W, H)
+    rec = occ.Occluders.empty(H, W, gb.pos4.device)
+    out = torch.empty((H, W), dtype=torch.float32, device=gb.pos4.device)
+    occ.occ_trace_ao(ctx, gb, bvh, RADIUS, 1, 0, out=rec)
+    occ.occ_reuse_ao(ctx, gb, rec, occ.Pattern.offsets_of(offs), K, occ.OCC_EST_BIASED, out=out)
+    occ.occ_reuse_ao(ctx, gb, rec, occ.Pattern.group(4, 2), 8, occ.OCC_EST_BIASED, out=out)
+    ctx.sync()
+    print(json.dumps({"profile_step": "ok", "checksum": float(out.double().sum())}))
+
+
 def main():
     args = parse()
+    if args.profile_step:
+        profile_step()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
