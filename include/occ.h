@@ -73,11 +73,14 @@ enum { OCC_PAT_GROUP = 0, OCC_PAT_BOX = 1, OCC_PAT_OFFSETS = 2 };
  * per pixel each, FP32 arithmetic on the unpacked values):
  *  - G-buffer: one float4 plane (x.xyz, normal as octahedral 2 x 16-bit snorm code in the
  *    w bits; code 0x80008000 marks an invalid pixel);
- *  - records: one 16-byte plane: words 0-1 hold z - x_source as three 21-bit signed
- *    fixed-point numbers in units of offset_scale * 2^-20 (bits 0-20, 21-41, 42-62) and
- *    bit 63 = occluder present; word 2 the octahedral n_z code; word 3 the triangle
- *    id or -1.  offset_scale (written by the trace) bounds |z - x_source|: R for AO,
- *    for shadows the largest distance between the scene's bounding box and the light.
+ *  - records: one 16-byte plane: words 0-1 (a 64-bit little-endian word) hold
+ *    d = z - x_source as three 19-bit two's-complement mantissas m (bits 0-18, 19-37,
+ *    38-56) with a shared exponent E (bits 57-62), d = m * 2^(E - 60), and bit 63 =
+ *    occluder present; word 2 the octahedral n_z code; word 3 the triangle id or -1.
+ *    The writer takes E = floor(log2 max|d_i|) + 43 (clamped to 0..63) and rounds
+ *    d_i * 2^(60 - E) to nearest (even), clamped to +-(2^18 - 1); the reader rebuilds each
+ *    coordinate as fmaf(m, 2^(E - 60), x_source) in FP32 (one rounding), x_source being
+ *    the source receiver's G-buffer point.
  * Octahedral normals: Cigolle et al., "A Survey of Efficient Representations for
  * Independent Unit Vectors", JCGT 2014. */
 enum { OCC_GB_FP32 = 0, OCC_GB_PACKED = 1 };
@@ -117,7 +120,6 @@ typedef struct {
     occ_rect_light light;      /* light (shadow) */
     uint64_t seed;
     uint32_t sample;
-    float offset_scale;        /* PACKED: offset unit * 2^20 (written by trace) */
 } occ_occluders;
 
 typedef struct {

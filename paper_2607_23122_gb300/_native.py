@@ -38,7 +38,7 @@ class occ_rect_light(C.Structure):
 class occ_occluders(C.Structure):
     _fields_ = [("W", c_int32), ("H", c_int32), ("format", c_int32), ("data", c_void_p),
                 ("effect", c_int32), ("radius", c_float), ("light", occ_rect_light),
-                ("seed", c_uint64), ("sample", c_uint32), ("offset_scale", c_float)]
+                ("seed", c_uint64), ("sample", c_uint32)]
 
 
 class occ_pattern(C.Structure):

@@ -86,7 +86,7 @@ __device__ __forceinline__ int fetch_cand(const RecView& rec, int q, float3 xsrc
     const float4 r0 = __ldg(rec.r0 + q);
     const int tri = __float_as_int(r0.w);
     if (tri < 0) return tri;
-    if (rec.packed) return rec_unpack(r0, xsrc, rec.scale, z, nz);
+    if (rec.packed) return rec_unpack(r0, xsrc, z, nz);
     *z = f3(r0);
     *nz = f3(__ldg(rec.r1 + q));
     return tri;
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
         valid = inside && __float_as_uint(P.w) != kOctInvalid;
         hit = valid && __float_as_int(R0.w) >= 0;
         if (valid) nx = oct_decode(__float_as_uint(P.w));
-        if (hit) rec_unpack(R0, f3(P), a.rec.scale, &z, &nz);
+        if (hit) rec_unpack(R0, f3(P), &z, &nz);
     } else {
         if (inside) {
             P = group_load(a.gb.pos + i);

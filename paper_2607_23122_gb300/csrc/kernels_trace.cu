@@ -55,7 +55,7 @@ __device__ __forceinline__ float3 step1_ray(float3 x, float3 n, uint32_t p, floa
 __device__ __forceinline__ void write_record(const RecView& rec, uint32_t p, float3 xsrc, float3 z,
                                              float3 nz, float t, int tri) {
     if (rec.packed) {
-        rec.r0[p] = rec_pack(xsrc, z, nz, tri, rec.scale);
+        rec.r0[p] = rec_pack(xsrc, z, nz, tri);
     } else if (tri < 0) {
         rec.r0[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
         rec.r1[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);

@@ -160,33 +160,8 @@ occ::GBufView view(const occ_gbuffer* gb) {
 
 occ::RecView rec_view(const occ_occluders* o) {
     float4* base = reinterpret_cast<float4*>(o->data);
-    if (o->format == OCC_REC_PACKED) return occ::RecView{base, nullptr, 1, o->offset_scale};
-    return occ::RecView{base, base + (size_t)o->W * o->H, 0, 0.0f};
-}
-
-// Bound on |z - x_source| for packed records: R for AO; for shadows the largest distance
-// between the scene box (grown by 1% of its diagonal, covering the receiver offsets) and
-// the light rectangle -- both convex, so the maximum is found at their corners.
-float offset_scale_for(const occ_bvh* bvh, int effect, float radius, const occ_rect_light* L) {
-    if (effect == OCC_EFFECT_AO) return radius * (1.0f + 1.0f / 1024.0f);
-    double diag = 0.0;
-    for (int a = 0; a < 3; ++a) diag += (double)(bvh->hi[a] - bvh->lo[a]) * (bvh->hi[a] - bvh->lo[a]);
-    const double grow = 0.01 * std::sqrt(diag) + 1e-6;
-    double best = 0.0;
-    for (int c = 0; c < 8; ++c) {
-        double p[3];
-        for (int a = 0; a < 3; ++a) p[a] = ((c >> a) & 1) ? bvh->hi[a] + grow : bvh->lo[a] - grow;
-        for (int l = 0; l < 4; ++l) {
-            const double su = (l & 1) ? 0.5 : -0.5, sv = (l & 2) ? 0.5 : -0.5;
-            double d2 = 0.0;
-            for (int a = 0; a < 3; ++a) {
-                const double y = L->c[a] + su * L->eu[a] + sv * L->ev[a];
-                d2 += (y - p[a]) * (y - p[a]);
-            }
-            best = std::max(best, d2);
-        }
-    }
-    return (float)(std::sqrt(best) * (1.0 + 1.0 / 1024.0));
+    if (o->format == OCC_REC_PACKED) return occ::RecView{base, nullptr, 1};
+    return occ::RecView{base, base + (size_t)o->W * o->H, 0};
 }
 
 occ::DevBVH dev_bvh(const occ_bvh* b) { return occ::DevBVH{b->nodes, b->tris}; }
@@ -213,8 +188,6 @@ occ_status reuse_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
     if (estimator != OCC_EST_UNBIASED && bvh)
         return fail(ctx, OCC_ERR_INVALID_ARG, "bvh_or_null must be NULL unless the estimator is unbiased");
     if (!out) return fail(ctx, OCC_ERR_INVALID_ARG, "out is NULL");
-    if (occ->format == OCC_REC_PACKED && !(occ->offset_scale > 0.0f && std::isfinite(occ->offset_scale)))
-        return fail(ctx, OCC_ERR_INVALID_ARG, "packed records need a positive offset_scale");
     if (effect == OCC_EFFECT_SHADOW && (st = check_light(ctx, &occ->light)) != OCC_OK) return st;
     if (effect == OCC_EFFECT_AO && !(occ->radius > 0.0f && std::isfinite(occ->radius)))
         return fail(ctx, OCC_ERR_INVALID_ARG, "AO radius must be positive and finite");
@@ -251,7 +224,6 @@ occ_status trace_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
         std::memset(&out->light, 0, sizeof(out->light));
     out->seed = seed;
     out->sample = sample;
-    out->offset_scale = offset_scale_for(bvh, effect, radius, light);
     return launched(ctx,
                     occ::launch_trace(effect, view(gb), dev_bvh(bvh), radius, to_params(light), seed,
                                       sample, rec_view(out), ctx->status, (cudaStream_t)stream),
@@ -597,7 +569,6 @@ occ_status build_batch(occ_ctx* ctx, const occ_bvh* bvh, occ_view* views, int32_
         else std::memset(&v.rec.light, 0, sizeof(v.rec.light));
         v.rec.seed = v.seed;
         v.rec.sample = v.sample;
-        v.rec.offset_scale = offset_scale_for(bvh, v.effect, v.radius, &v.light);
         b.gb = view(&v.gb);
         b.rec = rec_view(&v.rec);
         b.effect = v.effect;

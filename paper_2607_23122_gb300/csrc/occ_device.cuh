@@ -127,32 +127,50 @@ __device__ __forceinline__ bool gb_valid(const float4* pos, bool packed, int p) 
 // Packed record: words 0-1 = 64 bits holding dz = z - x_source as three 21-bit signed
 // fixed-point numbers (units of scale * 2^-20; bits 0-20, 21-41, 42-62) and bit 63 set;
 // word 2 = octahedral n_z; word 3 = triangle id (-1: no occluder).
-__device__ __forceinline__ uint64_t fix21(float v, float inv_unit) {
-    const int q = max(-1048575, min(1048575, __float2int_rn(v * inv_unit)));
-    return (uint64_t)((uint32_t)q & 0x1FFFFFu);
+// Packed occluder offset d = z - x_source: three 19-bit two's-complement mantissas m with a
+// shared exponent E (6 bits), d = m * 2^(E - 60).  E = floor(log2 max|d_i|) + 43, so the
+// largest component uses 17-18 bits and every component is rounded to a unit of
+// 2^-17..2^-18 of max|d_i|: the precision follows |z - x|, which is what the density
+// and support tests are sensitive to.
+constexpr int kOffMantBits = 19;
+constexpr int kOffMantMax = (1 << (kOffMantBits - 1)) - 1;
+constexpr int kOffExpBias = 60;
+
+__device__ __forceinline__ uint64_t pack_offset(float3 d) {
+    const float M = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z)));
+    if (!(M > 0.0f)) return 0ull;
+    const int k = ((__float_as_int(M) >> 23) & 0xFF) - 127;   // floor(log2 M), M normal
+    const int E = max(0, min(63, k + 43));
+    const float inv_unit = __int_as_float((kOffExpBias - E + 127) << 23);   // 2^(60 - E)
+    const int mx = max(-kOffMantMax, min(kOffMantMax, __float2int_rn(d.x * inv_unit)));
+    const int my = max(-kOffMantMax, min(kOffMantMax, __float2int_rn(d.y * inv_unit)));
+    const int mz = max(-kOffMantMax, min(kOffMantMax, __float2int_rn(d.z * inv_unit)));
+    const uint64_t mask = (1ull << kOffMantBits) - 1ull;
+    return ((uint64_t)(uint32_t)mx & mask) | (((uint64_t)(uint32_t)my & mask) << 19) |
+           (((uint64_t)(uint32_t)mz & mask) << 38) | ((uint64_t)E << 57);
 }
 
-__device__ __forceinline__ float unfix21(uint64_t bits, float unit) {
-    const int q = (int)((uint32_t)(bits & 0x1FFFFFu) << 11) >> 11;   // sign-extend 21 bits
-    return (float)q * unit;
+// x + m * unit with one rounding (m: the sign-extended 19-bit field, exact as a float)
+__device__ __forceinline__ float unpack_coord(uint64_t bits, float unit, float x) {
+    const int m = (int)((uint32_t)(bits & 0x7FFFFu) << 13) >> 13;
+    return __fmaf_rn((float)m, unit, x);
 }
 
-__device__ __forceinline__ float4 rec_pack(float3 xsrc, float3 z, float3 nz, int tri, float scale) {
+__device__ __forceinline__ float4 rec_pack(float3 xsrc, float3 z, float3 nz, int tri) {
     if (tri < 0) return make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
-    const float inv_unit = 1048576.0f / scale;
-    const uint64_t w = fix21(z.x - xsrc.x, inv_unit) | (fix21(z.y - xsrc.y, inv_unit) << 21) |
-                       (fix21(z.z - xsrc.z, inv_unit) << 42) | (1ull << 63);
+    const uint64_t w = pack_offset(make_float3(z.x - xsrc.x, z.y - xsrc.y, z.z - xsrc.z)) |
+                       (1ull << 63);
     return make_float4(__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)(w >> 32)),
                        __uint_as_float(oct_encode(nz)), __int_as_float(tri));
 }
 
 // Unpacks a packed record of a source receiver at xsrc; returns its triangle id.
-__device__ __forceinline__ int rec_unpack(float4 r, float3 xsrc, float scale, float3* z,
-                                          float3* nz) {
+__device__ __forceinline__ int rec_unpack(float4 r, float3 xsrc, float3* z, float3* nz) {
     const uint64_t w = (uint64_t)__float_as_uint(r.x) | ((uint64_t)__float_as_uint(r.y) << 32);
-    const float unit = scale * (1.0f / 1048576.0f);
-    *z = make_float3(xsrc.x + unfix21(w, unit), xsrc.y + unfix21(w >> 21, unit),
-                     xsrc.z + unfix21(w >> 42, unit));
+    const int E = (int)((w >> 57) & 63u);
+    const float unit = __int_as_float((E - kOffExpBias + 127) << 23);   // 2^(E - 60)
+    *z = make_float3(unpack_coord(w, unit, xsrc.x), unpack_coord(w >> 19, unit, xsrc.y),
+                     unpack_coord(w >> 38, unit, xsrc.z));
     *nz = oct_decode(__float_as_uint(r.z));
     return __float_as_int(r.w);
 }

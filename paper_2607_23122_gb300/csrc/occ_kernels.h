@@ -21,7 +21,6 @@ struct RecView {
     float4* r0;
     float4* r1;
     int32_t packed;
-    float scale;       // packed: offset unit * 2^20
 };
 
 struct LightParams {

@@ -158,16 +158,14 @@ class Occluders:
         return o
 
     @staticmethod
-    def from_packed(plane: np.ndarray, effect: int, offset_scale: float, radius: float = 0.0,
-                    light=None, device="cuda") -> "Occluders":
-        """Packed records prepared elsewhere: [H, W, 4] float32 view of the 16-byte records,
-        offsets in units of offset_scale * 2^-20."""
+    def from_packed(plane: np.ndarray, effect: int, radius: float = 0.0, light=None,
+                    device="cuda") -> "Occluders":
+        """Packed records prepared elsewhere: [H, W, 4] float32 view of the 16-byte records."""
         H, W = plane.shape[:2]
         o = Occluders.empty(H, W, device, packed=True)
         o.data[0].copy_(torch.from_numpy(np.ascontiguousarray(plane, dtype=np.float32)))
         o.meta.effect = effect
         o.meta.radius = radius
-        o.meta.offset_scale = offset_scale
         if light is not None:
             o.meta.light = _light(light)
         return o

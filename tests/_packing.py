@@ -3,7 +3,7 @@
 Packs oracle-made inputs the way include/occ.h describes the PACKED formats, so the CUDA
 path can be fed packed data that it did not produce, and unpacks them again for the
 oracle.  Octahedral normals: Cigolle et al., JCGT 2014 (2 x 16-bit snorm); occluder
-points as 21-bit fixed-point offsets from the source receiver (unit scale * 2^-20).
+points as offsets from the source receiver, three 19-bit mantissas with a shared exponent.
 """
 import numpy as np
 
@@ -68,15 +68,29 @@ def unpack_gbuffer(packed: np.ndarray):
     return pos, nrm
 
 
-def pack_records(orec: np.ndarray, pos4: np.ndarray, scale: float) -> np.ndarray:
-    """Oracle records [H, W, 8] -> packed plane [H, W, 4] float32 (16-byte records)."""
+MANT_MAX = (1 << 18) - 1
+EXP_BIAS = 60
+
+
+def _offset_exponent(d: np.ndarray) -> np.ndarray:
+    """E = floor(log2 max|d_i|) + 43, clamped to 0..63 (0 for a zero offset)."""
+    M = np.abs(d).max(axis=-1)
+    with np.errstate(divide="ignore"):
+        _, e = np.frexp(M)                     # M = f 2^e, f in [0.5, 1): floor(log2 M) = e - 1
+    return np.where(M > 0, np.clip(e - 1 + 43, 0, 63), 0).astype(np.int64)
+
+
+def pack_records(orec: np.ndarray, pos4: np.ndarray) -> np.ndarray:
+    """Oracle records [H, W, 8] -> packed plane [H, W, 4] float32 (16-byte records):
+    d = z - x in FP64, shared exponent, mantissas rounded to nearest even."""
     H, W = orec.shape[:2]
     hit = orec[..., 7] >= 0
     off = orec[..., :3] - pos4[..., :3].astype(np.float64)
-    q = np.clip(np.rint(off * (2.0 ** 20 / np.float64(np.float32(scale)))), -1048575, 1048575)
-    q = (q.astype(np.int64) & 0x1FFFFF).astype(np.uint64)
-    w64 = (q[..., 0] | (q[..., 1] << np.uint64(21)) | (q[..., 2] << np.uint64(42))
-           | np.uint64(1 << 63))
+    E = _offset_exponent(off)
+    m = np.clip(np.rint(off * np.exp2(EXP_BIAS - E)[..., None]), -MANT_MAX, MANT_MAX)
+    m = (m.astype(np.int64) & 0x7FFFF).astype(np.uint64)
+    w64 = (m[..., 0] | (m[..., 1] << np.uint64(19)) | (m[..., 2] << np.uint64(38))
+           | (E.astype(np.uint64) << np.uint64(57)) | np.uint64(1 << 63))
     words = np.zeros((H, W, 4), dtype=np.uint32)
     words[..., 0] = (w64 & 0xFFFFFFFF).astype(np.uint32)
     words[..., 1] = (w64 >> np.uint64(32)).astype(np.uint32)
@@ -87,22 +101,44 @@ def pack_records(orec: np.ndarray, pos4: np.ndarray, scale: float) -> np.ndarray
     return words.view(np.float32)
 
 
-def unpack_records(packed: np.ndarray, pos4: np.ndarray, scale: float) -> np.ndarray:
-    """Packed plane -> the oracle's FP64 record layout (z rebuilt from the offsets)."""
+def fma_f32(a: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """fl32(a + x) of the exact real sum, for FP64 a and FP32-valued x (as an FMA with an
+    exact product a rounds it): TwoSum gives the exact sum as s + e in FP64; rounding s to
+    FP32 matches rounding s + e except when s lies exactly halfway between two FP32
+    values and e != 0, where e decides."""
+    s = a + x
+    bb = s - x
+    e = (x - (s - bb)) + (a - bb)
+    r = s.astype(np.float32)
+    r64 = r.astype(np.float64)
+    up = np.nextafter(r, np.float32(np.inf))
+    dn = np.nextafter(r, np.float32(-np.inf))
+    lo = np.where(r64 <= s, r, dn)
+    hi = np.where(r64 <= s, up, r)
+    mid = (s - lo.astype(np.float64)) == (hi.astype(np.float64) - s)
+    return np.where(mid & (e > 0), hi, np.where(mid & (e < 0), lo, r))
+
+
+def unpack_records(packed: np.ndarray, pos4: np.ndarray) -> np.ndarray:
+    """Packed plane -> the oracle's FP64 record layout, z rebuilt as the format defines it:
+    fmaf(m, 2^(E - 60), x) in FP32 (the product is exact, so this is one rounding of the
+    exact sum)."""
     w = packed.view(np.uint32)
     H, W = packed.shape[:2]
     rec = np.zeros((H, W, 8))
     tri = w[..., 3].view(np.int32)
     hit = tri >= 0
     w64 = w[..., 0].astype(np.uint64) | (w[..., 1].astype(np.uint64) << np.uint64(32))
-    unit = np.float64(np.float32(np.float32(scale) * np.float32(1.0 / 1048576.0)))
+    E = ((w64 >> np.uint64(57)) & np.uint64(63)).astype(np.int64)
+    unit = np.exp2(E - EXP_BIAS)
     comps = []
     for k in range(3):
-        v = ((w64 >> np.uint64(21 * k)) & np.uint64(0x1FFFFF)).astype(np.int64)
-        v = np.where(v >= (1 << 20), v - (1 << 21), v)
+        v = ((w64 >> np.uint64(19 * k)) & np.uint64(0x7FFFF)).astype(np.int64)
+        v = np.where(v >= (1 << 18), v - (1 << 19), v)
         comps.append(v.astype(np.float64) * unit)
-    x = pos4[..., :3].astype(np.float64)
-    z = x + np.stack(comps, axis=-1)
+    a = np.stack(comps, axis=-1)
+    x = pos4[..., :3].astype(np.float32).astype(np.float64)
+    z = fma_f32(a, x).astype(np.float64)
     n = oct_decode(w[..., 2])
     rec[..., :3] = np.where(hit[..., None], z, 0.0)
     rec[..., 3:6] = np.where(hit[..., None], n, 0.0)

@@ -1,0 +1,184 @@
+"""Parity at the benchmark sizes, whole frames, in the launch configurations bench.py times.
+
+  1080p AO      1M-triangle terrain, R = 0.5: trace; biased reuse with K = 8 shared disk
+                offsets (TMA window kernel) and 4x2 groups (warp group kernel)
+  1080p shadow  same scene, 1 x 0.5 light at z = 4: trace; biased disk-8 and 4x2-group
+                reuse; the light-sample averaging baseline (box mean over 4x2 groups)
+  4K packed     ~4M-triangle terrain, AO and shadows with packed G-buffer and records:
+                trace; biased reuse with K = 16 (4x4 groups and a 16-member disk)
+
+Both sides take the oracle's G-buffer.  Trace: ids bit-exact up to the listed grazing flips,
+distances and points within the FP32 bounds of tests/_parity.py.  Reuse is compared on the
+oracle's records (rounded to FP32, or packed), so a trace flip cannot move an estimate.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from tests import _packing as PK
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+AO, SH = 0, 1
+BIASED, BOXMEAN = 1, 3
+
+
+@pytest.fixture(scope="module")
+def occ():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_23122_gb300 import occ as occmod
+    return occmod
+
+
+@pytest.fixture(scope="module")
+def ctx(occ):
+    return occ.Context(0)
+
+
+def _frame(orc, occ, ctx, scene, cam, W, H):
+    osc = orc.OracleScene(scene.tris)
+    pos, nrm, _ = orc.gbuffer(osc, cam.as_array(), W, H, scene.eps)
+    return {"osc": osc, "bvh": occ.BVH(ctx, scene.tris), "pos": pos, "nrm": nrm,
+            "valid": pos[..., 3] > 0}
+
+
+@pytest.fixture(scope="module")
+def hd(orc, occ, ctx):
+    scene = synth.scene_terrain(grid=512, n_spheres=300, n_boxes=8000, seed=2)
+    f = _frame(orc, occ, ctx, scene, synth.camera_c2(), 1920, 1080)
+    f["gb"] = occ.GBuffer.from_numpy(f["pos"], f["nrm"])
+    return f
+
+
+@pytest.fixture(scope="module")
+def uhd(orc, occ, ctx):
+    scene = synth.scene_terrain(grid=1024, n_spheres=1200, n_boxes=30000, seed=4)
+    assert scene.num_tris > 3_900_000
+    return _frame(orc, occ, ctx, scene, synth.camera_c2(), 3840, 2160)
+
+
+def _pats(occ):
+    return {"disk8": occ.Pattern.offsets_of(synth.disk_offsets(8, 15.0, seed=3)),
+            "group4x2": occ.Pattern.group(4, 2), "group4x4": occ.Pattern.group(4, 4),
+            "disk16": occ.Pattern.offsets_of(synth.disk_offsets(16, 15.0, seed=3))}
+
+
+@pytest.mark.parametrize("effect", [AO, SH])
+def test_1080p_trace_and_reuse(orc, occ, ctx, hd, effect):
+    light = synth.light_c3().as_array()
+    o = (occ.occ_trace_ao(ctx, hd["gb"], hd["bvh"], 0.5, 1, 0) if effect == AO else
+         occ.occ_trace_shadow(ctx, hd["gb"], hd["bvh"], light, 1, 0))
+    ctx.sync()
+    orec, omg = orc.trace(hd["osc"], effect, hd["pos"], hd["nrm"], radius=0.5, light=light,
+                          seed=1, sample=0)
+    tr = P.compare_trace(o, orec, omg, hd["valid"], hd["pos"], f"1080p trace {effect}")
+    assert tr["hits"] > 0.05 * hd["valid"].sum()
+    r0, r1 = P.to_f32_records(orec)
+    orec32 = P.widen_records(r0, r1)
+    rec = occ.Occluders.from_numpy(r0, r1, effect, radius=0.5, light=light)
+    fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
+    cases = [("disk8", BIASED), ("group4x2", BIASED)] + ([("group4x2", BOXMEAN)] if effect == SH else [])
+    for pname, est in cases:
+        pat = _pats(occ)[pname]
+        g = fn(ctx, hd["gb"], rec, pat, pat.K, est)
+        ctx.sync()
+        ref, mg = orc.reuse(None, effect, hd["pos"], hd["nrm"], orec32, pat.as_tuple(), est,
+                            radius=0.5, light=light)
+        res = P.compare_out(g.cpu().numpy(), ref, mg, hd["valid"], f"1080p {pname} est {est}")
+        print(f"1080p effect {effect} {pname} est {est}: max err {res['max_err']:.2e}, "
+              f"{tr['mismatch']} trace flips")
+
+
+@pytest.mark.parametrize("effect", [AO, SH])
+def test_4k_packed_trace_and_reuse(orc, occ, ctx, uhd, effect):
+    import torch
+    light = synth.light_c3().as_array()
+    ppos = PK.pack_gbuffer(uhd["pos"], uhd["nrm"])
+    upos, unrm = PK.unpack_gbuffer(ppos)           # what the packed kernels see
+    valid = upos[..., 3] > 0
+    gb = occ.GBuffer(torch.from_numpy(ppos).cuda(), None)
+    o = (occ.occ_trace_ao(ctx, gb, uhd["bvh"], 0.5, 2, 0, packed=True) if effect == AO else
+         occ.occ_trace_shadow(ctx, gb, uhd["bvh"], light, 2, 0, packed=True))
+    ctx.sync()
+    grec = PK.unpack_records(o.data[0].cpu().numpy(), upos)
+    orec, omg = orc.trace(uhd["osc"], effect, upos, unrm, radius=0.5, light=light, seed=2, sample=0)
+    gtri, otri = grec[..., 7], orec[..., 7]
+    mism = (gtri != otri) & valid
+    assert not (mism & (omg >= P.TRACE_MARGIN)).any()
+    assert mism.sum() <= P.budget(int(valid.sum())), mism.sum()
+    both = valid & (gtri >= 0) & (gtri == otri)
+    assert both.sum() > 0.05 * valid.sum()
+    # the offset is rounded to 2^-17 of its largest component, then z to FP32
+    zerr = np.abs(grec[..., :3][both] - orec[..., :3][both]).max(axis=-1)
+    dmax = np.abs(orec[..., :3][both] - upos[..., :3][both]).max(axis=-1)
+    assert np.all(zerr <= 2.0 ** -17 * dmax + 1e-5 * (1 + np.abs(orec[..., :3][both]).max(axis=-1)))
+    # reuse on the oracle's records, packed
+    prec = PK.pack_records(orec, upos)
+    urec = PK.unpack_records(prec, upos)
+    rec = occ.Occluders.from_packed(prec, effect, radius=0.5, light=light)
+    fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
+    errs = []
+    for pname in ("group4x4", "disk16"):
+        pat = _pats(occ)[pname]
+        g = fn(ctx, gb, rec, pat, 16, BIASED)
+        ctx.sync()
+        g = g.cpu().numpy()
+        ref, mg = orc.reuse(None, effect, upos, unrm, urec, pat.as_tuple(), BIASED, radius=0.5,
+                            light=light)
+        P.compare_out(g, ref, mg, valid, f"4K packed {pname}")
+        # packing error against the full-precision oracle on the unpacked scene
+        full, _ = orc.reuse(None, effect, uhd["pos"], uhd["nrm"], orec, pat.as_tuple(), BIASED,
+                            radius=0.5, light=light)
+        e = np.abs(g - full)[valid]
+        errs.append(e)
+        print(f"4K packed effect {effect} {pname}: packing error max {e.max():.2e} "
+              f"p99.9 {np.quantile(e, 0.999):.2e} mean {e.mean():.2e} "
+              f"over 1e-3: {(e > 1e-3).mean():.2e}")
+    e = np.concatenate(errs)
+    # isolated support-test flips (a candidate's ray grazing the rectangle edge or the AO
+    # sphere) are the only pixels over 1e-3
+    assert np.quantile(e, 0.999) <= 1e-3 and (e > 1e-3).mean() <= 2e-4
+
+
+def test_1080p_sampled_blocks_through_the_bench_frame(orc, occ, ctx, hd):
+    """The bench's own frame: the GPU traces and reuses its own records; on random 32x32
+    blocks whose neighbourhoods hold no trace flip, the estimate matches the oracle's
+    end-to-end estimate (oracle trace + oracle reuse).  Each side reuses its own records,
+    which differ by the FP32 rounding of z = x + t w (close occluders turn it into up to
+    ~1e-4 on the estimate), so the bound is the end-to-end one: at most 2e-3 of the
+    pixels over 1e-5 and the 99.9th percentile under 1e-4."""
+    pat = _pats(occ)["disk8"]
+    o = occ.occ_trace_ao(ctx, hd["gb"], hd["bvh"], 0.5, 1, 7)
+    g = occ.occ_reuse_ao(ctx, hd["gb"], o, pat, 8, BIASED)
+    ctx.sync()
+    g = g.cpu().numpy()
+    _, _, gtri = P.gpu_records(o)
+    rng = np.random.default_rng(17)
+    offs = synth.disk_offsets(8, 15.0, seed=3)
+    hx0, hx1 = -offs[:, 0].min(), offs[:, 0].max()
+    hy0, hy1 = -offs[:, 1].min(), offs[:, 1].max()
+    checked, errs = 0, []
+    for _ in range(24):
+        x0 = int(rng.integers(hx0, 1920 - 32 - hx1))
+        y0 = int(rng.integers(hy0, 1080 - 32 - hy1))
+        reg = (x0 - hx0, y0 - hy0, 32 + hx0 + hx1, 32 + hy0 + hy1)
+        orec, _ = orc.trace(hd["osc"], AO, hd["pos"], hd["nrm"], radius=0.5, seed=1, sample=7,
+                            region=reg)
+        xs, ys = slice(reg[0], reg[0] + reg[2]), slice(reg[1], reg[1] + reg[3])
+        if np.any((orec[ys, xs, 7] != gtri[ys, xs]) & hd["valid"][ys, xs]):
+            continue                                   # a grazing flip in the neighbourhood
+        ref, mg = orc.reuse(None, AO, hd["pos"], hd["nrm"], orec, pat.as_tuple(), BIASED,
+                            radius=0.5, region=(x0, y0, 32, 32))
+        sl = (slice(y0, y0 + 32), slice(x0, x0 + 32))
+        v = hd["valid"][sl]
+        assert np.all(g[sl][~v] == 1.0)
+        errs.append(np.abs(g[sl].astype(np.float64) - ref[sl])[v])
+        checked += 1
+    assert checked >= 12
+    e = np.concatenate(errs)
+    print(f"sampled blocks: {checked}, max err {e.max():.2e}, over 1e-5: {(e > 1e-5).mean():.2e}")
+    assert (e > P.OUT_ATOL).mean() <= 2e-3 and np.quantile(e, 0.999) <= 1e-4

@@ -324,7 +324,7 @@ def test_frame_host_matches_device_path(occ, ctx, c1):
 
 
 # --------------------------------------------------------------------------------------
-# Packed formats (octahedral normals, 21-bit fixed-point occluder offsets; FP32 arithmetic)
+# Packed formats (octahedral normals, shared-exponent occluder offsets; FP32 arithmetic)
 # --------------------------------------------------------------------------------------
 
 from tests import _packing as PK  # noqa: E402
@@ -353,7 +353,7 @@ def test_packed_trace_matches_oracle(orc, occ, ctx, c1, effect):
         o = (occ.occ_trace_ao(ctx, gb, c1["bvh"], R_C1, 17, sample, packed=True) if effect == AO
              else occ.occ_trace_shadow(ctx, gb, c1["bvh"], LIGHT_C1, 17, sample, packed=True))
         ctx.sync()
-        grec = PK.unpack_records(o.data[0].cpu().numpy(), upos, o.meta.offset_scale)
+        grec = PK.unpack_records(o.data[0].cpu().numpy(), upos)
         orec, omg = orc.trace(c1["osc"], effect, upos, unrm, radius=R_C1, light=LIGHT_C1, seed=17,
                               sample=sample)
         gtri, otri = grec[..., 7], orec[..., 7]
@@ -365,9 +365,10 @@ def test_packed_trace_matches_oracle(orc, occ, ctx, c1, effect):
                                 unrm[py, px, :3].tolist()) for py, px in bad[:4]]
         assert mism.sum() <= P.budget(int(valid.sum()))
         both = valid & (gtri >= 0) & (gtri == otri)
-        unit = o.meta.offset_scale * 2.0 ** -20
-        zerr = np.abs(grec[..., :3][both] - orec[..., :3][both])
-        assert np.all(zerr <= unit + 1e-5 * (1 + np.abs(orec[..., :3][both]))), zerr.max()
+        # the offset is rounded to 2^-17 of its largest component, then z to FP32
+        zerr = np.abs(grec[..., :3][both] - orec[..., :3][both]).max(axis=-1)
+        dmax = np.abs(orec[..., :3][both] - upos[..., :3][both]).max(axis=-1)
+        assert np.all(zerr <= 2.0 ** -17 * dmax + 1e-5 * (1 + np.abs(orec[..., :3][both]).max(-1)))
         assert np.abs(grec[..., 3:6][both] - orec[..., 3:6][both]).max() < 2e-4
 
 
@@ -385,10 +386,9 @@ def test_packed_reuse(orc, occ, ctx, c1, effect, pname):
     for sample in range(2):
         orec, _ = orc.trace(c1["osc"], effect, c1["pos"], c1["nrm"], radius=R_C1, light=LIGHT_C1,
                             seed=41, sample=sample)
-        scale = 1.001 * R_C1 if effect == AO else 12.0     # bounds |z - x| in this scene
-        prec = PK.pack_records(orec, c1["pos"], scale)
-        urec = PK.unpack_records(prec, upos, scale)
-        o = occ.Occluders.from_packed(prec, effect, scale, radius=R_C1, light=LIGHT_C1)
+        prec = PK.pack_records(orec, c1["pos"])
+        urec = PK.unpack_records(prec, upos)
+        o = occ.Occluders.from_packed(prec, effect, radius=R_C1, light=LIGHT_C1)
         fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
         for est in (BIASED, UNBIASED):
             g = fn(ctx, gb, o, pat, pat.K, est, bvh=c1["bvh"] if est == UNBIASED else None)
