@@ -186,6 +186,12 @@ def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
 
 
 GROUP_BYTES_PER_PX = 52   # x 12, n 12, z 12, n_z 12, out 4
+# DRAM bytes (read + write) per launch from one `ncu --set full` capture of
+# `bench.py --profile-step` (cold L2; profiles/k_*_ao1080p*.md); None once a kernel changes
+NCU_TRAFFIC = {"k_trace<AO>": 72.545024e6 + 31.308288e6,
+               "k_reuse_tile<AO,9>": 132.796672e6 + 6.937344e6,
+               "k_reuse_group<AO,biased,4,2>": 114.1696e6 + 4.770048e6}
+NCU_TRACE_ISSUE_ACTIVE = 0.7097   # smsp__issue_active of k_trace<AO> in the same capture
 
 
 def time_kernel(fn, flush, stream, iters: int) -> dict:
@@ -478,13 +484,17 @@ def run_ours(args):
         alu_peak = sms * 128 * 2 * (clk["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
         trace_roof = {"kernel": "k_trace<AO>", "bound": "hbm",
                       "achieved": trace_bytes / tr / 1e9, "peak": hbm, "unit": "GB/s",
-                      "frac": trace_bytes / tr / 1e9 / hbm, "traffic": None,
-                      "peak_source": peak_kind,
-                      "algorithmic_bytes": trace_bytes}
+                      "frac": trace_bytes / tr / 1e9 / hbm,
+                      "traffic": NCU_TRAFFIC["k_trace<AO>"],
+                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                      "algorithmic_bytes": trace_bytes,
+                      "note": "software traversal is issue/latency bound: issue slots "
+                              f"{NCU_TRACE_ISSUE_ACTIVE:.0%} busy under ncu"}
         reuse_roof = {"kernel": "k_reuse_tile<AO,9> (TMA-staged window)", "bound": "alu",
                       "achieved": pairs * FLOPS_PER_PAIR_AO / ru / 1e12,
                       "peak": alu_peak / 1e12, "unit": "TFLOP/s",
-                      "frac": pairs * FLOPS_PER_PAIR_AO / ru / alu_peak, "traffic": None,
+                      "frac": pairs * FLOPS_PER_PAIR_AO / ru / alu_peak,
+                      "traffic": NCU_TRAFFIC["k_reuse_tile<AO,9>"],
                       "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x max SM clock"}
         dominant = trace_roof if tr >= ru else reuse_roof
         line = {
@@ -505,6 +515,7 @@ def run_ours(args):
             "gpu_launches": 2 * args.steps,
             "clocks": clk, "wall_s": wall,
             "reuse_group4x2": dict(extra["reuse_group4x2"], kernel="k_reuse_group<AO,biased,4,2>",
+                                   traffic=NCU_TRAFFIC["k_reuse_group<AO,biased,4,2>"],
                                    algorithmic_bytes=P * GROUP_BYTES_PER_PX,
                                    achieved_gbs=P * GROUP_BYTES_PER_PX / extra["reuse_group4x2"]["s"] / 1e9,
                                    frac_hbm=P * GROUP_BYTES_PER_PX / extra["reuse_group4x2"]["s"] / 1e9 / hbm,
