@@ -68,6 +68,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over the ranks of the default process group (x itself on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_step: float, steps: int, t_max: float) -> float:
+    """Whole-job rate: every rank processed units_per_step per step; the job took the
+    slowest rank's time."""
+    return world * units_per_step * steps / t_max
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -432,12 +449,8 @@ def run_ours(args):
     ctx.sync()
     t_trace = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]) * 1e-3
     t_reuse = np.array([ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]) * 1e-3
-    t_step = float((t_trace + t_reuse).sum())
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-    value = world * P * K * args.steps / t_step
+    t_step = max_over_ranks(float((t_trace + t_reuse).sum()), dev)
+    value = job_throughput(world, P * K, args.steps, t_step)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the region
     pos_h = gb.pos4.cpu().pin_memory()
@@ -448,16 +461,14 @@ def run_ours(args):
         occ.occ_frame_host(ctx, bvh, occ.OCC_EFFECT_AO, pos_h, nrm_h, RADIUS, None, 1, i, pat, K,
                            occ.OCC_EST_BIASED, out_h, stream=stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         occ.occ_frame_host(ctx, bvh, occ.OCC_EFFECT_AO, pos_h, nrm_h, RADIUS, None, 1, i, pat, K,
                            occ.OCC_EST_BIASED, out_h, stream=stream)
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dev)
 
     # the paper's own layout: 4x2 shared groups (K = 8) on warp lanes, HBM bound
     extra = {}
@@ -509,7 +520,7 @@ def run_ours(args):
             "reuse_pass": {"neighbour_samples_per_s": P * K / ru, "ms": ru * 1e3},
             "trace_pass": {"rays_per_s": P / tr, "ms": tr * 1e3},
             "roofline": dominant, "roofline_other": reuse_roof if dominant is trace_roof else trace_roof,
-            "e2e": {"value": world * P * K * e2e_steps / t_e2e, "unit": UNIT,
+            "e2e": {"value": job_throughput(world, P * K, e2e_steps, t_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": 2 * 16 * P, "d2h_bytes_per_step": 4 * P,
                     "ms_per_step": t_e2e / e2e_steps * 1e3},
             "gpu_launches": 2 * args.steps,
