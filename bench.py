@@ -205,7 +205,7 @@ def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
 GROUP_BYTES_PER_PX = 52   # x 12, n 12, z 12, n_z 12, out 4
 # DRAM bytes (read + write) per launch from one `ncu --set full` capture of
 # `bench.py --profile-step` (cold L2; profiles/k_*_ao1080p*.md); None once a kernel changes
-NCU_TRAFFIC = {"k_trace<AO>": 72.545024e6 + 31.308288e6,
+NCU_TRAFFIC = {"k_trace_dyn<AO>": None,
                "k_reuse_tile<AO,9>": 132.796672e6 + 6.937344e6,
                "k_reuse_group<AO,biased,4,2>": 114.1696e6 + 4.770048e6}
 NCU_TRACE_ISSUE_ACTIVE = 0.7097   # smsp__issue_active of k_trace<AO> in the same capture
@@ -493,10 +493,10 @@ def run_ours(args):
         # reuse (offset window, K^2 pair densities): FP32 ALU bound
         pairs = P * K * K
         alu_peak = sms * 128 * 2 * (clk["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        trace_roof = {"kernel": "k_trace<AO>", "bound": "hbm",
+        trace_roof = {"kernel": "k_trace_dyn<AO>", "bound": "hbm",
                       "achieved": trace_bytes / tr / 1e9, "peak": hbm, "unit": "GB/s",
                       "frac": trace_bytes / tr / 1e9 / hbm,
-                      "traffic": NCU_TRAFFIC["k_trace<AO>"],
+                      "traffic": NCU_TRAFFIC["k_trace_dyn<AO>"],
                       "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                       "algorithmic_bytes": trace_bytes,
                       "note": "software traversal is issue/latency bound: issue slots "

@@ -226,7 +226,8 @@ occ_status trace_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
     out->sample = sample;
     return launched(ctx,
                     occ::launch_trace(effect, view(gb), dev_bvh(bvh), radius, to_params(light), seed,
-                                      sample, rec_view(out), ctx->status, (cudaStream_t)stream),
+                                      sample, rec_view(out), ctx->status, (cudaStream_t)stream,
+                                      ctx->counter),
                     "trace launch");
 }
 
@@ -248,8 +249,10 @@ OCC_EXPORT occ_status occ_create(int device, occ_ctx** out) {
     if (cudaSetDevice(device) != cudaSuccess) return OCC_ERR_CUDA;
     occ_ctx* ctx = new occ_ctx();
     ctx->device = device;
-    cudaError_t e = cudaMalloc(&ctx->status, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(unsigned));
+    // status word and ray counter, 32 bytes apart
+    cudaError_t e = cudaMalloc(&ctx->status, 64);
+    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, 64);
+    ctx->counter = ctx->status + 8;
     if (e != cudaSuccess) {
         cudaFree(ctx->status);
         delete ctx;

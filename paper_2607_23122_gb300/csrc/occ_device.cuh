@@ -370,58 +370,85 @@ __device__ __forceinline__ uint32_t pop_next(const uint2* stack, int& sp, float 
 
 __device__ __forceinline__ bool is_leaf_ref(uint32_t ref) { return (ref & kLeafBit) != 0u; }
 
-// Closest hit on (0, tmax] (t in units of |d|), starting at `start`: the root (0), any
-// node or leaf reference whose subtree holds every triangle the ray can meet, or
-// kEmptyRef when none can be met.  While-while traversal: each lane walks internal
-// nodes until every active lane holds a postponed leaf, then all lanes test their
-// leaves together, which keeps the warp's lanes on the same code path.  Sets
-// kStatusStackOverflowBit in *status if the short stack would overflow (the builder
-// bounds the tree depth so that it cannot).
+// Resumable closest-hit traversal of one ray on (0, tmax] (t in units of |d|).  While-while
+// order: each round walks internal nodes until every active lane of the warp holds a
+// postponed leaf, then all lanes test their leaves together, which keeps the lanes on the
+// same code path.  The short stack lives outside the state (thread-local array).
+struct Traversal {
+    TraceRay r;
+    float tbest;
+    uint32_t best_id, best_slot;
+    uint32_t cur, leaf;
+    int sp;
+    bool overflow;
+};
+
+// Starts at `start`: the root (0), any node or leaf reference whose subtree holds every
+// triangle the ray can meet, or kEmptyRef when none can be met.
+__device__ __forceinline__ void trav_init(Traversal& t, float3 o, float3 d, float tmax,
+                                          uint32_t start) {
+    t.r = make_trace_ray(o, d);
+    t.tbest = tmax;
+    t.best_id = kNoHit;
+    t.best_slot = kNoHit;
+    t.sp = 0;
+    t.overflow = false;
+    t.cur = start;
+    t.leaf = kEmptyRef;
+    if (t.cur != kEmptyRef && is_leaf_ref(t.cur)) {
+        t.leaf = t.cur;
+        t.cur = kEmptyRef;
+    }
+}
+
+__device__ __forceinline__ bool trav_done(const Traversal& t) {
+    return t.cur == kEmptyRef && t.leaf == kEmptyRef;
+}
+
+// One round: internal nodes until the warp's active lanes all hold a leaf (or ran out),
+// then the leaves.  Call only while !trav_done.
+__device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, uint2* stack) {
+    while (t.cur != kEmptyRef && !is_leaf_ref(t.cur)) {
+        uint32_t next;
+        visit_node(bvh, t.cur, t.r, t.tbest, stack, t.sp, t.overflow, &next);
+        t.cur = next != kEmptyRef ? next : pop_next(stack, t.sp, t.tbest);
+        if (t.cur != kEmptyRef && is_leaf_ref(t.cur) && t.leaf == kEmptyRef) {
+            t.leaf = t.cur;   // postpone the leaf and keep walking internal nodes
+            t.cur = pop_next(stack, t.sp, t.tbest);
+        }
+        if (!__any_sync(__activemask(), t.leaf == kEmptyRef)) break;
+    }
+    while (t.leaf != kEmptyRef) {
+        const uint32_t first = t.leaf & kLeafFirstMask;
+        const uint32_t count = ((t.leaf & ~kLeafBit) >> kLeafCountShift) + 1u;
+        for (uint32_t i = 0; i < count; ++i) {
+            const float4* tr = bvh.tris + 3ull * (first + i);
+            triangle_test(t.r, __ldg(tr), __ldg(tr + 1), __ldg(tr + 2), first + i, t.tbest,
+                          t.best_id, t.best_slot);
+        }
+        if (t.cur != kEmptyRef && is_leaf_ref(t.cur)) {
+            t.leaf = t.cur;
+            t.cur = pop_next(stack, t.sp, t.tbest);
+        } else {
+            t.leaf = kEmptyRef;
+        }
+    }
+}
+
+// Closest hit on (0, tmax] from `start` (see trav_init).  Sets kStatusStackOverflowBit in
+// *status if the short stack would overflow (the builder bounds the tree depth so that it
+// cannot).
 __device__ __forceinline__ Hit closest_hit(const DevBVH& bvh, float3 o, float3 d, float tmax,
                                            unsigned int* status, uint32_t start = 0u) {
-    const TraceRay r = make_trace_ray(o, d);
-    float tbest = tmax;
-    uint32_t best_id = kNoHit, best_slot = kNoHit;
+    Traversal t;
     uint2 stack[kStackSize];
-    int sp = 0;
-    bool overflow = false;
-    uint32_t cur = start, leaf = kEmptyRef;
-    if (cur != kEmptyRef && is_leaf_ref(cur)) {
-        leaf = cur;
-        cur = kEmptyRef;
-    }
-    while (cur != kEmptyRef || leaf != kEmptyRef) {
-        while (cur != kEmptyRef && !is_leaf_ref(cur)) {
-            uint32_t next;
-            visit_node(bvh, cur, r, tbest, stack, sp, overflow, &next);
-            cur = next != kEmptyRef ? next : pop_next(stack, sp, tbest);
-            if (cur != kEmptyRef && is_leaf_ref(cur) && leaf == kEmptyRef) {
-                leaf = cur;   // postpone the leaf and keep walking internal nodes
-                cur = pop_next(stack, sp, tbest);
-            }
-            if (!__any_sync(__activemask(), leaf == kEmptyRef)) break;
-        }
-        while (leaf != kEmptyRef) {
-            const uint32_t first = leaf & kLeafFirstMask;
-            const uint32_t count = ((leaf & ~kLeafBit) >> kLeafCountShift) + 1u;
-            for (uint32_t i = 0; i < count; ++i) {
-                const float4* t = bvh.tris + 3ull * (first + i);
-                triangle_test(r, __ldg(t), __ldg(t + 1), __ldg(t + 2), first + i, tbest, best_id,
-                              best_slot);
-            }
-            if (cur != kEmptyRef && is_leaf_ref(cur)) {
-                leaf = cur;
-                cur = pop_next(stack, sp, tbest);
-            } else {
-                leaf = kEmptyRef;
-            }
-        }
-    }
-    if (overflow && status) atomicOr(status, kStatusStackOverflowBit);
+    trav_init(t, o, d, tmax, start);
+    while (!trav_done(t)) trav_round(t, bvh, stack);
+    if (t.overflow && status) atomicOr(status, kStatusStackOverflowBit);
     Hit h;
-    h.id = best_id;
-    h.slot = best_slot;
-    h.t = tbest;
+    h.id = t.best_id;
+    h.slot = t.best_slot;
+    h.t = t.tbest;
     return h;
 }
 

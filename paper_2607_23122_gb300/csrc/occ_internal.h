@@ -13,6 +13,7 @@
 struct occ_ctx {
     int device = 0;
     unsigned* status = nullptr;          // device status word (kStatus* bits)
+    unsigned* counter = nullptr;         // ray counter of the persistent trace kernel
     std::string last_error;
     // workspace of occ_frame_host: pos4, nrm4, records, output
     void* ws = nullptr;

@@ -64,9 +64,11 @@ enum Estimator { kNoReuse = 0, kBiased = 1, kUnbiased = 2, kBoxMean = 3 };
 
 cudaError_t launch_gbuffer(const DevBVH& bvh, const float* cam, float eps, int W, int H,
                            float4* pos, float4* nrm, unsigned* status, cudaStream_t s);
+// counter: a device word for the persistent dynamic-fetch kernel (reset on `s` before the
+// launch); nullptr selects the one-CTA-per-tile kernel.
 cudaError_t launch_trace(int effect, const GBufView& gb, const DevBVH& bvh, float radius,
                          const LightParams& light, uint64_t seed, uint32_t sample, RecView rec,
-                         unsigned* status, cudaStream_t s);
+                         unsigned* status, cudaStream_t s, unsigned* counter = nullptr);
 cudaError_t launch_pack_gbuffer(const GBufView& gb, float4* out, cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s);
 cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
