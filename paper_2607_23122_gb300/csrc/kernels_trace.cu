@@ -144,6 +144,9 @@ __global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS) k_trace(GBufView gb
 #ifndef OCC_TRACE_DYN_MIN_IDLE
 #define OCC_TRACE_DYN_MIN_IDLE 16
 #endif
+#ifndef OCC_TRACE_DYN_MIN_BLOCKS
+#define OCC_TRACE_DYN_MIN_BLOCKS OCC_TRACE_MIN_BLOCKS
+#endif
 
 __device__ __forceinline__ void index_pixel(uint32_t i, int tiles_x, int* x, int* y) {
     const uint32_t tile = i >> 7, within = i & 127u;
@@ -153,7 +156,7 @@ __device__ __forceinline__ void index_pixel(uint32_t i, int tiles_x, int* x, int
 }
 
 template <int EFFECT>
-__global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS)
+__global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
     k_trace_dyn(GBufView gb, DevBVH bvh, float radius, LightParams lp, uint64_t seed,
                 uint32_t sample, RecView rec, unsigned* status, unsigned* counter, int tiles_x,
                 uint32_t n_idx) {
