@@ -667,7 +667,7 @@ static int occ_pred(const scene_t* s, v3 xh, v3 z, int64_t tri, double* margin) 
     return h.tri == tri;
 }
 
-enum { EST_NOREUSE = 0, EST_BIASED = 1, EST_UNBIASED = 2, EST_BOXMEAN = 3 };
+enum { EST_NOREUSE = 0, EST_BIASED = 1, EST_UNBIASED = 2, EST_BOXMEAN = 3, EST_LIGHT_UNBIASED = 4 };
 
 typedef struct {
     const scene_t* s;
@@ -756,6 +756,56 @@ ORC_API void orc_reuse(const void* sc, int effect, int W, int H, const float* po
     }
 }
 
+/* ----------------------------------------------------------------------------------
+ * Unbiased light-sample reuse, Light(N U) of Sec. 6.2 (the comparison baseline for
+ * shadows): receiver i re-evaluates the visibility of every member j's light sample y_j
+ * (Eq. 5, drawn with j's own random numbers) from its own receiver point.  With the
+ * uniform area sampler every member's sample has the same density 1/|A|, so the balance
+ * heuristic weighs each of them 1/|N_i| and the estimate of Eq. 4 is the mean visibility
+ * of the |N_i| segments x_i -> y_j.  For j = i the segment is i's own step-1 shadow ray.
+ * -------------------------------------------------------------------------------- */
+static double light_reuse_px(const scene_t* s, int W, int H, const float* pos4, int px, int py,
+                             int kind, int gw, int gh, const int32_t* off, int n_off,
+                             const light_t* L, uint64_t seed, uint32_t sample, double* margin) {
+    int64_t i = (int64_t)py * W + px;
+    *margin = INFINITY;
+    if (pos4[4 * i + 3] == 0.0f) return 1.0;
+    int64_t m[MAX_MEMBERS];
+    int n = members(W, H, pos4, px, py, kind, gw, gh, off, n_off, m);
+    v3 xh = ldf(pos4 + 4 * i);
+    double vis = 0.0;
+    for (int q = 0; q < n; ++q) {
+        double u1, u2;
+        rng_pair(seed, (uint32_t)m[q], sample, ORC_STREAM_SHADOW, &u1, &u2);
+        v3 y = add(L->c, add(scl(L->eu, u1 - 0.5), scl(L->ev, u2 - 0.5)));
+        v3 dv = sub(y, xh);
+        double len = sqrt(dot(dv, dv));
+        hit_t h = closest_hit(s, xh, scl(dv, 1.0 / len), len, 0);
+        *margin = fmin(*margin, h.margin);
+        if (h.tri < 0) vis += 1.0;
+    }
+    return vis / n;
+}
+
+ORC_API void orc_reuse_light(const void* sc, int W, int H, const float* pos4, int kind, int gw,
+                             int gh, const int32_t* off, int n_off, const float* light,
+                             uint64_t seed, uint32_t sample, int x0, int y0, int w, int h,
+                             double* out, double* margin) {
+    const scene_t* s = (const scene_t*)sc;
+    light_t L = mk_light(light);
+    int64_t n = (int64_t)w * h;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < n; ++q) {
+        int px = x0 + (int)(q % w), py = y0 + (int)(q / w);
+        if (px < 0 || py < 0 || px >= W || py >= H) continue;
+        int64_t i = (int64_t)py * W + px;
+        double mg;
+        out[i] = light_reuse_px(s, W, H, pos4, px, py, kind, gw, gh, off, n_off, &L, seed, sample,
+                                &mg);
+        if (margin) margin[i] = mg;
+    }
+}
+
 /* Balance-heuristic weights (Eq. 11) seen by receiver i: for every member j
  * with an occluder and every member k, w[j][k] = p(z_j|x_k) / sum_e p(z_j|x_e)
  * (0 when the sum is 0).  Returns the member count; ids go to members_out. */
@@ -812,10 +862,15 @@ ORC_API void orc_accumulate(const void* sc, int effect, int W, int H, const floa
     double* out = (double*)calloc((size_t)P, sizeof(double));
     for (int64_t i = 0; i < (int64_t)w * h; ++i) { mean[i] = 0.0; var[i] = 0.0; }
     for (int m = 0; m < M; ++m) {
-        orc_trace(sc, effect, W, H, pos4, nrm4, radius, light, seed, sample0 + (uint32_t)m, hx0,
-                  hy0, hx1 - hx0, hy1 - hy0, rec, NULL);
-        orc_reuse(sc, effect, W, H, pos4, nrm4, rec, kind, gw, gh, off, n_off, estimator, radius,
-                  light, x0, y0, w, h, out, NULL);
+        if (estimator == EST_LIGHT_UNBIASED) {
+            orc_reuse_light(sc, W, H, pos4, kind, gw, gh, off, n_off, light, seed,
+                            sample0 + (uint32_t)m, x0, y0, w, h, out, NULL);
+        } else {
+            orc_trace(sc, effect, W, H, pos4, nrm4, radius, light, seed, sample0 + (uint32_t)m,
+                      hx0, hy0, hx1 - hx0, hy1 - hy0, rec, NULL);
+            orc_reuse(sc, effect, W, H, pos4, nrm4, rec, kind, gw, gh, off, n_off, estimator,
+                      radius, light, x0, y0, w, h, out, NULL);
+        }
         for (int64_t q = 0; q < (int64_t)w * h; ++q) {
             int px = x0 + (int)(q % w), py = y0 + (int)(q / w);
             double v = out[(int64_t)py * W + px];

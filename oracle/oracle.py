@@ -28,6 +28,7 @@ _lib = None
 EFFECT_AO, EFFECT_SHADOW = 0, 1
 PAT_GROUP, PAT_BOX, PAT_OFFSETS = 0, 1, 2
 EST_NOREUSE, EST_BIASED, EST_UNBIASED, EST_BOXMEAN = 0, 1, 2, 3
+EST_LIGHT_UNBIASED = 4       # shadows: unbiased light-sample reuse (Light(N U), Sec. 6.2)
 STREAM_AO, STREAM_SHADOW = 0, 1
 
 
@@ -74,6 +75,9 @@ def lib():
         L.orc_reuse.argtypes = [vp, C.c_int, C.c_int, C.c_int, f32, f32, f64, C.c_int, C.c_int,
                                 C.c_int, i32, C.c_int, C.c_int, C.c_float, f32, C.c_int, C.c_int,
                                 C.c_int, C.c_int, f64, f64]
+        L.orc_reuse_light.argtypes = [vp, C.c_int, C.c_int, f32, C.c_int, C.c_int, C.c_int, i32,
+                                      C.c_int, f32, C.c_uint64, C.c_uint32, C.c_int, C.c_int,
+                                      C.c_int, C.c_int, f64, f64]
         L.orc_mis_weights.argtypes = [vp, C.c_int, C.c_int, C.c_int, f32, f32, f64, C.c_int,
                                       C.c_int, C.c_int, i32, C.c_int, C.c_int, C.c_float, f32,
                                       C.c_int, C.c_int, i64, f64]
@@ -218,6 +222,23 @@ def reuse(scene, effect: int, pos4, nrm4, rec, pattern, estimator: int, radius: 
                     np.ascontiguousarray(nrm4, dtype=np.float32),
                     np.ascontiguousarray(rec, dtype=np.float64), kind, gw, gh, off, n_off,
                     estimator, radius, _light(light), x0, y0, w, h, out, mg)
+    return out, mg
+
+
+def reuse_light(scene, pos4, pattern, light, seed: int, sample: int, region=None, out=None):
+    """Unbiased light-sample reuse for shadows (Light(N U)): the mean visibility of the
+    segments from each receiver to its members' light samples (sample `sample`, key
+    `seed`).  Returns (out float64 [H, W], margin [H, W])."""
+    H, W = pos4.shape[:2]
+    x0, y0, w, h = region if region is not None else (0, 0, W, H)
+    kind, gw, gh, off, n_off = _pattern(pattern)
+    if out is not None:
+        out, mg = out
+    else:
+        out = np.full((H, W), np.nan)
+        mg = np.full((H, W), np.inf)
+    lib().orc_reuse_light(scene.handle, W, H, np.ascontiguousarray(pos4, dtype=np.float32), kind,
+                          gw, gh, off, n_off, _light(light), seed, sample, x0, y0, w, h, out, mg)
     return out, mg
 
 

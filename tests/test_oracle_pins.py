@@ -388,6 +388,8 @@ def test_shadow_fully_lit_is_one(orc, pattern):
     for est in (NOREUSE, BIASED, UNBIASED, BOXMEAN):
         out, _ = orc.reuse(sc, SH, pos, nrm, rec, pattern, est, light=light)
         assert np.all(out == 1.0)
+    out, _ = orc.reuse_light(sc, pos, pattern, light, seed=8, sample=0)
+    assert np.all(out == 1.0)
 
 
 @pytest.mark.parametrize("pattern", PATTERNS)
@@ -402,6 +404,8 @@ def test_shadow_fully_blocked(orc, pattern):
         for est in (NOREUSE, BIASED, BOXMEAN):
             out, _ = orc.reuse(sc, SH, pos, nrm, rec, pattern, est, light=light)
             assert np.all(out == 0.0), est   # the guard makes the biased estimate exactly 0
+        out, _ = orc.reuse_light(sc, pos, pattern, light, seed=8, sample=s)
+        assert np.all(out == 0.0)
     m, s = _image_mean_over_samples(orc, sc, SH, pos, nrm, pattern, UNBIASED, 48, seed=8,
                                     light=light)
     assert abs(m) < 4 * s + 1e-12
@@ -421,7 +425,7 @@ def _half_plane_case():
     return scene, light, pos, nrm, want
 
 
-@pytest.mark.parametrize("est", [NOREUSE, UNBIASED])
+@pytest.mark.parametrize("est", [NOREUSE, UNBIASED, 4])
 def test_shadow_half_plane_closed_form(orc, est):
     """Half-plane blocker: Shadow(x) = clamp((X* - a) / w, 0, 1), per pixel, in expectation."""
     scene, light, pos, nrm, want = _half_plane_case()
@@ -459,6 +463,49 @@ def test_k1_equals_noreuse(orc, effect):
                                     nrm[py, px, :3].astype(float), radius=R, light=light)
                     assert p == 0.0 and ref[py, px] == 0.0 and out[py, px] == 1.0
                 assert len(diff) <= 2
+
+
+def test_light_reuse_k1_equals_noreuse(orc):
+    """Unbiased light-sample reuse with N_i = {i}: the receiver's own light sample, i.e. the
+    step-1 shadow ray, bit for bit."""
+    scene = synth.scene_c1()
+    sc = orc.OracleScene(scene.tris)
+    pos, nrm, _ = orc.gbuffer(sc, synth.camera_c1().as_array(), 64, 64, scene.eps)
+    light = synth.light_c3().as_array()
+    for s in range(3):
+        rec, _ = orc.trace(sc, SH, pos, nrm, light=light, seed=31, sample=s)
+        ref, _ = orc.reuse(sc, SH, pos, nrm, rec, (GROUP, 1, 1, None), NOREUSE, light=light)
+        assert 0.0 < ref[pos[..., 3] > 0].mean() < 1.0
+        for pat in [(OFFS, 0, 0, None), (BOX, 1, 1, None), (GROUP, 1, 1, None)]:
+            out, _ = orc.reuse_light(sc, pos, pat, light, seed=31, sample=s)
+            assert np.array_equal(out, ref)
+
+
+def test_light_reuse_decomposes_into_member_segments(orc):
+    """Light(2U) on a 2x1 group is, per receiver, the mean of the visibility of its own light
+    sample and of its partner's: the partner's sample point is rebuilt from the partner's
+    step-1 ray (orc.ray) and the segment tested with the brute-force closest hit."""
+    scene = synth.scene_half_plane(2.0)
+    sc = orc.OracleScene(scene.tris)
+    light = np.array([0.5, 0.0, 4.0, 1.0, 0, 0, 0, -0.5, 0], dtype=np.float32)
+    pos, nrm = synth.receiver_grid(8, 1, 0.11, z=scene.eps, origin=(-0.4, 0.0))
+    mixed = 0
+    for s in range(48):
+        out, _ = orc.reuse_light(sc, pos, (GROUP, 2, 1, None), light, seed=5, sample=s)
+        for i in range(8):
+            j = i ^ 1
+            vis = []
+            for k in (i, j):
+                dv, tm = orc.ray(SH, pos[0, k], nrm[0, k], k, 0.0, light, 5, s)
+                y = pos[0, k, :3].astype(np.float64) + dv * tm
+                seg = y - pos[0, i, :3].astype(np.float64)
+                L = np.linalg.norm(seg)
+                tri, _, _ = sc.closest_hit(pos[0, i, :3].astype(np.float64)[None], (seg / L)[None],
+                                           np.array([L]), brute=True)
+                vis.append(1.0 if tri[0] < 0 else 0.0)
+            assert out[0, i] == 0.5 * (vis[0] + vis[1]), (s, i, out[0, i], vis)
+            mixed += vis[0] != vis[1]
+    assert mixed > 10          # the penumbra makes the two segments disagree often
 
 
 @pytest.mark.parametrize("effect", [AO, SH])
