@@ -278,7 +278,9 @@ def quality_leg(occ, ctx, gb, bvh, pat) -> dict:
         ref = Q.reference(ctx, gb, bvh, eff, radius=RADIUS, light=light, spp=4096)
         out[key] = Q.equal_time(ctx, gb, bvh, eff, budget, ref, radius=RADIUS, light=light,
                                 extra=[("Occ(8) disk", pat, occ.OCC_EST_BIASED),
-                                       ("Occ(8)U", occ.Pattern.group(4, 2), occ.OCC_EST_UNBIASED)])
+                                       ("Occ(8)U", occ.Pattern.group(4, 2), occ.OCC_EST_UNBIASED)]
+                                + ([("Light(8U)", occ.Pattern.group(4, 2), occ.OCC_EST_LIGHT_UNBIASED)]
+                                   if eff == occ.OCC_EFFECT_SHADOW else []))
     return out
 
 

@@ -61,8 +61,14 @@ enum { OCC_EFFECT_AO = 0, OCC_EFFECT_SHADOW = 1 };
 /* Estimators (Sec. 4.3-4.4): NOREUSE is Eq. 3 / Eq. 6 with one sample; BIASED
  * is Eq. 18 / Eq. 24 (shadow adds the all-blocked guard); UNBIASED is Eq. 17 /
  * Eq. 23 with first-hit validation rays; BOXMEAN averages the binary
- * visibility of N_i (final-value filtering / light-sample averaging). */
-enum { OCC_EST_NOREUSE = 0, OCC_EST_BIASED = 1, OCC_EST_UNBIASED = 2, OCC_EST_BOXMEAN = 3 };
+ * visibility of N_i (final-value filtering / light-sample averaging, the biased
+ * baselines Filter(N) and Light(N) of Sec. 6).  LIGHT_UNBIASED (shadows only) is
+ * the unbiased light-sample reuse baseline Light(N U) of Sec. 6.2: receiver i
+ * traces a segment to every member's light sample (drawn from the member's own
+ * random numbers of the records' seed and sample) and averages the visibility;
+ * the uniform area sampler gives every sample the same balance-heuristic weight. */
+enum { OCC_EST_NOREUSE = 0, OCC_EST_BIASED = 1, OCC_EST_UNBIASED = 2, OCC_EST_BOXMEAN = 3,
+       OCC_EST_LIGHT_UNBIASED = 4 };
 
 /* Neighbour patterns N_i (Eq. 8, Sec. 5 "Reuse Implementation", App. I):
  *  GROUP:   the screen is partitioned into gw x gh blocks; N_i is i's block.
@@ -191,8 +197,9 @@ occ_status occ_trace_shadow(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* 
 
 /* Alg. 1 steps 2-3: AO estimate per receiver into out (device float[H][W]).
  * K must equal the pattern's size (gw*gh, or n_offsets + 1), 1 <= K <= 64.
- * bvh_or_null is required for OCC_EST_UNBIASED and must be NULL otherwise.
- * Invalid receivers get 1.  Estimates are not clamped. */
+ * bvh_or_null is required for OCC_EST_UNBIASED (and, for shadows,
+ * OCC_EST_LIGHT_UNBIASED) and must be NULL otherwise.  Invalid receivers get 1.
+ * Estimates are not clamped.  The batched and served paths take estimators 0-3. */
 occ_status occ_reuse_ao(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occluders* occ,
                         const occ_pattern* pattern, int32_t K, int32_t estimator,
                         const occ_bvh* bvh_or_null, float* out, void* stream);

@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "OCC_OK", 1: "OCC_ERR_INVALID_ARG", 2: "OCC_ERR_CUDA", 3: "OC
 
 OCC_EFFECT_AO, OCC_EFFECT_SHADOW = 0, 1
 OCC_EST_NOREUSE, OCC_EST_BIASED, OCC_EST_UNBIASED, OCC_EST_BOXMEAN = 0, 1, 2, 3
+OCC_EST_LIGHT_UNBIASED = 4
 OCC_PAT_GROUP, OCC_PAT_BOX, OCC_PAT_OFFSETS = 0, 1, 2
 OCC_REC_FP32, OCC_REC_PACKED = 0, 1
 OCC_GB_FP32, OCC_GB_PACKED = 0, 1

@@ -261,6 +261,37 @@ __global__ void __launch_bounds__(128) k_reuse_simple(ReuseArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Unbiased light-sample reuse for shadows (Light(N U), Sec. 6.2): receiver i traces a
+// segment to every member j's light sample y_j (Eq. 5 with j's random numbers) and
+// averages the visibility.  For j = i the segment is i's own step-1 ray (same arithmetic
+// as the trace), so N_i = {i} reproduces no reuse.
+// ---------------------------------------------------------------------------------------
+template <int MAXK>
+__global__ void __launch_bounds__(128) k_reuse_light(ReuseArgs a, uint64_t seed, uint32_t sample) {
+    int x, y;
+    tile_pixel(&x, &y);
+    if (x >= a.gb.W || y >= a.gb.H) return;
+    const int i = y * a.gb.W + x;
+    if (!gb_valid(a.gb.pos, a.gb.packed != 0, i)) {
+        a.out[i] = 1.0f;
+        return;
+    }
+    const RectLight L = make_light_dev(a.lp);
+    int mem[MAXK];
+    int self;
+    const int n = gather_members<MAXK>(a.pat, a.gb, x, y, mem, &self);
+    const float3 xi = f3(__ldg(a.gb.pos + i));
+    int vis = 0;
+    for (int c = 0; c < n; ++c) {
+        float tmax;
+        const float3 d = light_direction(L, xi, uniform_pair(seed, (uint32_t)mem[c], sample, kStreamShadow),
+                                         &tmax);
+        if (!any_hit(a.bvh, xi, d, tmax, a.status)) ++vis;
+    }
+    a.out[i] = (float)vis / (float)n;
+}
+
+// ---------------------------------------------------------------------------------------
 // Batched reuse over views of different sizes, patterns, effects and estimators: the
 // persistent counterpart of k_trace_batch (same tile space and view lookup); each tile
 // runs the per-receiver evaluation of its view.
@@ -547,9 +578,17 @@ ReuseArgs make_args(const GBufView& gb, const RecView& rec, const PatternParams&
 cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const RecView& rec,
                          const PatternParams& pat, float radius, const LightParams& light,
                          const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s,
-                         const Tuning& tune) {
+                         const Tuning& tune, uint64_t seed, uint32_t sample) {
     if (gb.W <= 0 || gb.H <= 0) return cudaSuccess;
     const ReuseArgs a = make_args(gb, rec, pat, radius, light, bvh, out, status);
+    if (estimator == kLightUnbiased) {
+        const dim3 grid((unsigned)((gb.W + 15) / 16), (unsigned)((gb.H + 7) / 8));
+        if (pat.K <= 16)
+            k_reuse_light<16><<<grid, 128, 0, s>>>(a, seed, sample);
+        else
+            k_reuse_light<kMaxMembers><<<grid, 128, 0, s>>>(a, seed, sample);
+        return cudaGetLastError();
+    }
     const cudaError_t e = effect == kAO ? launch_effect<kAO>(estimator, a, s, tune)
                                         : launch_effect<kShadow>(estimator, a, s, tune);
     const cudaError_t l = cudaGetLastError();

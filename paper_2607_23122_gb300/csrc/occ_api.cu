@@ -181,11 +181,14 @@ occ_status reuse_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
     if (occ->effect != effect)
         return fail(ctx, OCC_ERR_INVALID_ARG, "occluder records were traced for effect %d, not %d",
                     occ->effect, effect);
-    if (estimator < OCC_EST_NOREUSE || estimator > OCC_EST_BOXMEAN)
+    if (estimator < OCC_EST_NOREUSE || estimator > OCC_EST_LIGHT_UNBIASED)
         return fail(ctx, OCC_ERR_INVALID_ARG, "estimator %d invalid", estimator);
-    if (estimator == OCC_EST_UNBIASED && !bvh)
-        return fail(ctx, OCC_ERR_INVALID_ARG, "the unbiased estimator needs the BVH");
-    if (estimator != OCC_EST_UNBIASED && bvh)
+    if (estimator == OCC_EST_LIGHT_UNBIASED && effect != OCC_EFFECT_SHADOW)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "light-sample reuse is defined for shadows only");
+    const bool traces = estimator == OCC_EST_UNBIASED || estimator == OCC_EST_LIGHT_UNBIASED;
+    if (traces && !bvh)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "the unbiased estimators need the BVH");
+    if (!traces && bvh)
         return fail(ctx, OCC_ERR_INVALID_ARG, "bvh_or_null must be NULL unless the estimator is unbiased");
     if (!out) return fail(ctx, OCC_ERR_INVALID_ARG, "out is NULL");
     if (effect == OCC_EFFECT_SHADOW && (st = check_light(ctx, &occ->light)) != OCC_OK) return st;
@@ -198,7 +201,7 @@ occ_status reuse_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
     return launched(ctx,
                     occ::launch_reuse(effect, estimator, view(gb), rec_view(occ), pat, occ->radius,
                                       lp, bvh ? &b : nullptr, out, ctx->status,
-                                      (cudaStream_t)stream, ctx->tune),
+                                      (cudaStream_t)stream, ctx->tune, occ->seed, occ->sample),
                     "reuse launch");
 }
 
@@ -454,7 +457,8 @@ OCC_EXPORT occ_status occ_frame_host(occ_ctx* ctx, const occ_bvh* bvh, int32_t e
     st = effect == OCC_EFFECT_AO ? occ_trace_ao(ctx, &gb, bvh, radius, seed, sample, &oc, stream)
                                  : occ_trace_shadow(ctx, &gb, bvh, light, seed, sample, &oc, stream);
     if (st != OCC_OK) return st;
-    const occ_bvh* vb = estimator == OCC_EST_UNBIASED ? bvh : nullptr;
+    const occ_bvh* vb =
+        estimator == OCC_EST_UNBIASED || estimator == OCC_EST_LIGHT_UNBIASED ? bvh : nullptr;
     st = effect == OCC_EFFECT_AO
              ? occ_reuse_ao(ctx, &gb, &oc, pattern, K, estimator, vb, out, stream)
              : occ_reuse_shadow(ctx, &gb, &oc, pattern, K, estimator, vb, out, stream);

@@ -406,7 +406,10 @@ __device__ __forceinline__ bool trav_done(const Traversal& t) {
 }
 
 // One round: internal nodes until the warp's active lanes all hold a leaf (or ran out),
-// then the leaves.  Call only while !trav_done.
+// then the leaves.  Call only while !trav_done.  ANY: stop at the first triangle accepted
+// on (0, tmax] (visibility queries need only whether one exists; the acceptance test is
+// the closest-hit one, so the answer is the same).
+template <bool ANY = false>
 __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, uint2* stack) {
     while (t.cur != kEmptyRef && !is_leaf_ref(t.cur)) {
         uint32_t next;
@@ -425,8 +428,11 @@ __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, uint
             const float4* tr = bvh.tris + 3ull * (first + i);
             triangle_test(t.r, __ldg(tr), __ldg(tr + 1), __ldg(tr + 2), first + i, t.tbest,
                           t.best_id, t.best_slot);
+            if (ANY && t.best_id != kNoHit) break;
         }
-        if (t.cur != kEmptyRef && is_leaf_ref(t.cur)) {
+        if (ANY && t.best_id != kNoHit) {
+            t.cur = t.leaf = kEmptyRef;
+        } else if (t.cur != kEmptyRef && is_leaf_ref(t.cur)) {
             t.leaf = t.cur;
             t.cur = pop_next(stack, t.sp, t.tbest);
         } else {
@@ -450,6 +456,17 @@ __device__ __forceinline__ Hit closest_hit(const DevBVH& bvh, float3 o, float3 d
     h.slot = t.best_slot;
     h.t = t.tbest;
     return h;
+}
+
+// Whether any triangle is hit on (0, tmax].
+__device__ __forceinline__ bool any_hit(const DevBVH& bvh, float3 o, float3 d, float tmax,
+                                        unsigned int* status) {
+    Traversal t;
+    uint2 stack[kStackSize];
+    trav_init(t, o, d, tmax, 0u);
+    while (!trav_done(t)) trav_round<true>(t, bvh, stack);
+    if (t.overflow && status) atomicOr(status, kStatusStackOverflowBit);
+    return t.best_id != kNoHit;
 }
 
 // Start reference for rays whose segments all lie inside the box [qlo, qhi]: walk down

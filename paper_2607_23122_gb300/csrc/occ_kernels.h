@@ -60,7 +60,7 @@ struct BatchDyn {
     uint32_t sample;
     uint32_t pad;
 };
-enum Estimator { kNoReuse = 0, kBiased = 1, kUnbiased = 2, kBoxMean = 3 };
+enum Estimator { kNoReuse = 0, kBiased = 1, kUnbiased = 2, kBoxMean = 3, kLightUnbiased = 4 };
 
 cudaError_t launch_gbuffer(const DevBVH& bvh, const float* cam, float eps, int W, int H,
                            float4* pos, float4* nrm, unsigned* status, cudaStream_t s);
@@ -85,7 +85,7 @@ struct Tuning {
 cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const RecView& rec,
                          const PatternParams& pat, float radius, const LightParams& light,
                          const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s,
-                         const Tuning& tune = Tuning());
+                         const Tuning& tune = Tuning(), uint64_t seed = 0, uint32_t sample = 0);
 // Batched frame over several views (persistent kernels over the concatenated tiles).
 cudaError_t launch_trace_batch(const BatchView* views, const BatchDyn* dyn, int n_views, int n_tiles,
                                const DevBVH& bvh, int ctas, unsigned* status, cudaStream_t s);

@@ -13,8 +13,8 @@ import torch
 
 from . import _native as N
 from ._native import (  # noqa: F401
-    OCC_EFFECT_AO, OCC_EFFECT_SHADOW, OCC_EST_BIASED, OCC_EST_BOXMEAN, OCC_EST_NOREUSE,
-    OCC_EST_UNBIASED, OCC_GB_FP32, OCC_GB_PACKED, OCC_PAT_BOX, OCC_PAT_GROUP, OCC_PAT_OFFSETS,
+    OCC_EFFECT_AO, OCC_EFFECT_SHADOW, OCC_EST_BIASED, OCC_EST_BOXMEAN, OCC_EST_LIGHT_UNBIASED,
+    OCC_EST_NOREUSE, OCC_EST_UNBIASED, OCC_GB_FP32, OCC_GB_PACKED, OCC_PAT_BOX, OCC_PAT_GROUP, OCC_PAT_OFFSETS,
     OCC_REC_FP32, OCC_REC_PACKED, MAX_MEMBERS)
 
 

@@ -39,8 +39,9 @@ def _trace(ctx, gb, bvh, effect, radius, light, seed, sample, rec, stream=None):
 
 def _reuse(ctx, gb, rec, effect, pattern, estimator, bvh, out, stream=None):
     fn = O.occ_reuse_ao if effect == O.OCC_EFFECT_AO else O.occ_reuse_shadow
-    return fn(ctx, gb, rec, pattern, pattern.K, estimator,
-              bvh=bvh if estimator == O.OCC_EST_UNBIASED else None, out=out, stream=stream)
+    traces = estimator in (O.OCC_EST_UNBIASED, O.OCC_EST_LIGHT_UNBIASED)
+    return fn(ctx, gb, rec, pattern, pattern.K, estimator, bvh=bvh if traces else None, out=out,
+              stream=stream)
 
 
 def reference(ctx, gb, bvh, effect, radius=0.5, light=None, spp=4096, seed=1) -> np.ndarray:

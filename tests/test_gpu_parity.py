@@ -405,3 +405,45 @@ def test_packed_reuse(orc, occ, ctx, c1, effect, pname):
     print(f"packing error vs FP64 oracle ({pname}, effect {effect}): max {e.max():.2e} "
           f"p99.9 {np.quantile(e, 0.999):.2e} mean {e.mean():.2e}")
     assert np.quantile(e, 0.999) <= 1e-3
+
+
+# --------------------------------------------------------------------------------------
+# Unbiased light-sample reuse (shadows, Light(N U))
+# --------------------------------------------------------------------------------------
+
+LIGHT_UNBIASED = 4
+
+
+@pytest.mark.parametrize("which", ["c1", "terrain_small"])
+def test_light_reuse_matches_oracle(orc, occ, ctx, which, request):
+    s = request.getfixturevalue(which)
+    light = LIGHT_C1 if which == "c1" else synth.light_c3().as_array()
+    valid = s["pos"][..., 3] > 0
+    pats = _patterns(occ)
+    for sample in range(2):
+        o = occ.occ_trace_shadow(ctx, s["gb"], s["bvh"], light, 23, sample)
+        own = occ.occ_reuse_shadow(ctx, s["gb"], o, occ.Pattern.group(1, 1), 1, NOREUSE)
+        g1 = occ.occ_reuse_shadow(ctx, s["gb"], o, occ.Pattern.group(1, 1), 1, LIGHT_UNBIASED,
+                                  bvh=s["bvh"])
+        ctx.sync()
+        # N_i = {i}: the receiver's own step-1 ray, the same bits as no reuse
+        assert np.array_equal(g1.cpu().numpy(), own.cpu().numpy())
+        for pname in ("group4x2", "box3x3", "disk8", "group2x2"):
+            pat = pats[pname]
+            g = occ.occ_reuse_shadow(ctx, s["gb"], o, pat, pat.K, LIGHT_UNBIASED, bvh=s["bvh"])
+            ctx.sync()
+            ref, mg = orc.reuse_light(s["osc"], s["pos"], pat.as_tuple(), light, 23, sample)
+            P.compare_out(g.cpu().numpy(), ref, mg, valid, f"light reuse {which} {pname}")
+
+
+def test_light_reuse_arguments(occ, ctx, c1):
+    o = occ.occ_trace_shadow(ctx, c1["gb"], c1["bvh"], LIGHT_C1, 1, 0)
+    a = occ.occ_trace_ao(ctx, c1["gb"], c1["bvh"], 1.0, 1, 0)
+    pat = occ.Pattern.group(4, 2)
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_reuse_shadow(ctx, c1["gb"], o, pat, 8, LIGHT_UNBIASED)              # no BVH
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_reuse_ao(ctx, c1["gb"], a, pat, 8, LIGHT_UNBIASED, bvh=c1["bvh"])   # AO
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_reuse_shadow(ctx, c1["gb"], o, pat, 8, 5, bvh=c1["bvh"])
+    ctx.sync()
