@@ -211,6 +211,18 @@ occ_status occ_reuse_shadow(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occlu
                             const occ_pattern* pattern, int32_t K, int32_t estimator,
                             const occ_bvh* bvh_or_null, float* out, void* stream);
 
+/* Several rectangular lights (Sec. 6.2, "Multiple Lights"): out = sum over l of
+ * weights_host[l] * V_l, where V_l is light l's shadow visibility from its own step-1
+ * trace (key seed + l, sample `sample`) into recs[l] and its own reuse with `estimator`
+ * over `pattern` into vis + l * W * H.  recs: n_lights caller-owned occluder buffers
+ * (W/H/format/data set, either format); vis: device float[n_lights][H][W]; out: device
+ * float[H][W]; 1 <= n_lights <= 16.  The per-light visibilities stay in vis. */
+occ_status occ_shadow_lights(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh,
+                             const occ_rect_light* lights_host, const float* weights_host,
+                             int32_t n_lights, uint64_t seed, uint32_t sample,
+                             const occ_pattern* pattern, int32_t K, int32_t estimator,
+                             occ_occluders* recs, float* vis, float* out, void* stream);
+
 /* One whole frame from host memory: copies pos4_host/nrm4_host (pinned host
  * memory recommended) to library-owned device buffers, traces (effect AO with
  * `radius`, or SHADOW with `light`), reuses, and copies the estimate to

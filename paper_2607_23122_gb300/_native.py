@@ -134,6 +134,10 @@ SIGNATURES = {
                                     C.POINTER(occ_rect_light), c_uint64, c_uint32,
                                     C.POINTER(occ_pattern), c_int32, c_int32, c_void_p, c_void_p,
                                     c_char_p, c_int32, c_void_p]),
+    "occ_shadow_lights": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p,
+                                    C.POINTER(occ_rect_light), c_void_p, c_int32, c_uint64,
+                                    c_uint32, C.POINTER(occ_pattern), c_int32, c_int32,
+                                    C.POINTER(occ_occluders), c_void_p, c_void_p, c_void_p]),
     "occ_frame_batch": (c_int32, [c_void_p, c_void_p, C.POINTER(occ_view), c_int32, c_void_p]),
     "occ_batch_capture": (c_int32, [c_void_p, c_void_p, C.POINTER(occ_view), c_int32,
                                     C.POINTER(c_void_p)]),

@@ -408,6 +408,22 @@ int trace_batch_ctas(int per_sm_wanted) {
     return per_sm * sms;
 }
 
+// out[p] = sum_l w[l] vis[l][p], accumulated in light order (one FMA per light).
+__global__ void k_weighted_sum(const float* vis, int64_t P, LightWeights w, float* out) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    float acc = 0.0f;
+    for (int l = 0; l < w.n; ++l) acc = fmaf(w.w[l], __ldg(vis + (size_t)l * P + p), acc);
+    out[p] = acc;
+}
+
+cudaError_t launch_weighted_sum(const float* vis, int64_t P, const LightWeights& w, float* out,
+                                cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    k_weighted_sum<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(vis, P, w, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_gbuffer(const GBufView& gb, float4* out, cudaStream_t s) {
     const int64_t n = (int64_t)gb.W * gb.H;
     if (n <= 0) return cudaSuccess;

@@ -468,6 +468,40 @@ OCC_EXPORT occ_status occ_frame_host(occ_ctx* ctx, const occ_bvh* bvh, int32_t e
     return occ_sync(ctx, stream);
 }
 
+OCC_EXPORT occ_status occ_shadow_lights(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh,
+                                        const occ_rect_light* lights_host, const float* weights_host,
+                                        int32_t n_lights, uint64_t seed, uint32_t sample,
+                                        const occ_pattern* pattern, int32_t K, int32_t estimator,
+                                        occ_occluders* recs, float* vis, float* out, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if ((st = check_gbuffer(ctx, gb)) != OCC_OK) return st;
+    if (!lights_host || !weights_host || !recs || !vis || !out)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "lights, weights, recs, vis and out must be set");
+    if (n_lights < 1 || n_lights > occ::kMaxLights)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "n_lights must be in [1, %d]", occ::kMaxLights);
+    occ::LightWeights w{};
+    w.n = n_lights;
+    for (int l = 0; l < n_lights; ++l) {
+        if (!std::isfinite(weights_host[l]))
+            return fail(ctx, OCC_ERR_INVALID_ARG, "weight %d is not finite", l);
+        if ((st = check_light(ctx, &lights_host[l])) != OCC_OK) return st;
+        w.w[l] = weights_host[l];
+    }
+    const int64_t P = (int64_t)gb->W * gb->H;
+    const bool traces = estimator == OCC_EST_UNBIASED || estimator == OCC_EST_LIGHT_UNBIASED;
+    for (int l = 0; l < n_lights; ++l) {
+        st = occ_trace_shadow(ctx, gb, bvh, &lights_host[l], seed + (uint64_t)l, sample, &recs[l],
+                              stream);
+        if (st == OCC_OK)
+            st = occ_reuse_shadow(ctx, gb, &recs[l], pattern, K, estimator, traces ? bvh : nullptr,
+                                  vis + (size_t)l * P, stream);
+        if (st != OCC_OK) return st;
+    }
+    return launched(ctx, occ::launch_weighted_sum(vis, P, w, out, (cudaStream_t)stream),
+                    "weighted sum");
+}
+
 OCC_EXPORT occ_status occ_debug_philox(occ_ctx* ctx, const uint32_t* in_dev, int64_t n,
                                        uint32_t* out_dev, void* stream) {
     occ_status st = check_ctx(ctx);

@@ -70,6 +70,13 @@ cudaError_t launch_trace(int effect, const GBufView& gb, const DevBVH& bvh, floa
                          const LightParams& light, uint64_t seed, uint32_t sample, RecView rec,
                          unsigned* status, cudaStream_t s, unsigned* counter = nullptr);
 cudaError_t launch_pack_gbuffer(const GBufView& gb, float4* out, cudaStream_t s);
+constexpr int kMaxLights = 16;
+struct LightWeights {
+    float w[kMaxLights];
+    int n;
+};
+cudaError_t launch_weighted_sum(const float* vis, int64_t P, const LightWeights& w, float* out,
+                                cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s);
 cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
                               const LightParams& light, uint64_t seed, uint32_t sample,

@@ -304,6 +304,30 @@ def occ_reuse_shadow(ctx: Context, gb: GBuffer, occ: Occluders, pattern: Pattern
     return _reuse(ctx.lib.occ_reuse_shadow, ctx, gb, occ, pattern, K, estimator, bvh, out, stream)
 
 
+def occ_shadow_lights(ctx: Context, gb: GBuffer, bvh: BVH, lights, weights, seed: int,
+                      sample: int, pattern: Pattern, estimator: int, packed: bool = False,
+                      stream=None):
+    """out = sum_l weights[l] * V_l over several lights (occ_shadow_lights); returns
+    (out [H, W], vis [n_lights, H, W], records)."""
+    lights = [np.asarray(l, dtype=np.float32).reshape(9) for l in lights]
+    n = len(lights)
+    dev = gb.pos4.device
+    recs = [Occluders.empty(gb.H, gb.W, dev, packed=packed) for _ in range(n)]
+    arr_l = (N.occ_rect_light * n)(*[_light(l) for l in lights])
+    arr_r = (N.occ_occluders * n)(*[r.c() for r in recs])
+    w = np.ascontiguousarray(weights, dtype=np.float32).reshape(n)
+    vis = torch.empty((n, gb.H, gb.W), dtype=torch.float32, device=dev)
+    out = torch.empty((gb.H, gb.W), dtype=torch.float32, device=dev)
+    g = gb.c()
+    ctx.check(ctx.lib.occ_shadow_lights(ctx.handle, C.byref(g), bvh.handle, arr_l, w.ctypes.data, n,
+                                        seed, sample, C.byref(pattern.c()), pattern.K, estimator,
+                                        arr_r, vis.data_ptr(), out.data_ptr(),
+                                        _stream_handle(stream)))
+    for r, m in zip(recs, arr_r):
+        r.meta = m
+    return out, vis, recs
+
+
 def occ_frame_host(ctx: Context, bvh: BVH, effect: int, pos4_host: torch.Tensor,
                    nrm4_host: torch.Tensor, radius: float, light, seed: int, sample: int,
                    pattern: Pattern, K: int, estimator: int, out_host: torch.Tensor,

@@ -447,3 +447,46 @@ def test_light_reuse_arguments(occ, ctx, c1):
     with pytest.raises(occ.OccError, match="INVALID_ARG"):
         occ.occ_reuse_shadow(ctx, c1["gb"], o, pat, 8, 5, bvh=c1["bvh"])
     ctx.sync()
+
+
+# --------------------------------------------------------------------------------------
+# Several lights
+# --------------------------------------------------------------------------------------
+
+def test_several_lights(occ, ctx, c1):
+    lights = [LIGHT_C1, np.array([1.5, -1.0, 3.5, 1.0, 0, 0, 0, -0.6, 0], dtype=np.float32),
+              synth.light_c3().as_array()]
+    w = np.array([0.5, 0.3, 0.2], dtype=np.float32)
+    for pname, est in (("group4x2", BIASED), ("disk8", BIASED), ("group2x2", UNBIASED)):
+        pat = _patterns(occ)[pname]
+        out, vis, recs = occ.occ_shadow_lights(ctx, c1["gb"], c1["bvh"], lights, w, 40, 2, pat, est)
+        ctx.sync()
+        v = vis.cpu().numpy()
+        for l, L in enumerate(lights):
+            o = occ.occ_trace_shadow(ctx, c1["gb"], c1["bvh"], L, 40 + l, 2)
+            g = occ.occ_reuse_shadow(ctx, c1["gb"], o, pat, pat.K, est,
+                                     bvh=c1["bvh"] if est == UNBIASED else None)
+            ctx.sync()
+            assert np.array_equal(g.cpu().numpy(), v[l]), (pname, l)
+            assert np.array_equal(P.gpu_records(o)[2], P.gpu_records(recs[l])[2])
+        want = (w[:, None, None].astype(np.float64) * v).sum(0)
+        assert np.abs(out.cpu().numpy() - want).max() <= 1e-6
+        assert not np.array_equal(v[0], v[1])
+
+
+def test_several_lights_fully_lit_and_arguments(occ, ctx):
+    pos, nrm = synth.receiver_grid(24, 16, 0.05, z=synth.scene_plane_only().eps)
+    gb = occ.GBuffer.from_numpy(pos, nrm)
+    bvh = occ.BVH(ctx, synth.scene_plane_only().tris)
+    lights = [synth.light_c3().as_array(), LIGHT_C1]
+    out, _, _ = occ.occ_shadow_lights(ctx, gb, bvh, lights, [0.25, 2.0], 1, 0,
+                                      occ.Pattern.group(4, 2), BIASED, packed=True)
+    ctx.sync()
+    assert np.all(out.cpu().numpy() == np.float32(2.25))
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_shadow_lights(ctx, gb, bvh, [lights[0]] * 17, [1.0] * 17, 1, 0,
+                              occ.Pattern.group(4, 2), BIASED)
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_shadow_lights(ctx, gb, bvh, lights, [1.0, float("nan")], 1, 0,
+                              occ.Pattern.group(4, 2), BIASED)
+    ctx.sync()
