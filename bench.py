@@ -167,10 +167,25 @@ def measured_peaks():
     return 6800.0, "fallback", {}
 
 
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
 def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
     """The FP64 oracle, as it stands, on this host: trace + reuse of square pixel blocks
-    (plus the halo their neighbour sets reach) until ~budget_s of work is done."""
+    (plus the halo their neighbour sets reach) until ~budget_s of work is done, on all the
+    cores this process may use, then on one core for a quarter of the time; trace and
+    reuse timed separately."""
     import oracle
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_num_threads(cores)
     osc = oracle.OracleScene(scene.tris)
     pos, nrm, _ = oracle.gbuffer(osc, cam.as_array(), W, H, scene.eps)
     rec = np.zeros((H, W, 8))
@@ -182,24 +197,40 @@ def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
     hx0, hx1 = max(0, -offs[:, 0].min()), max(0, offs[:, 0].max())
     hy0, hy1 = max(0, -offs[:, 1].min()), max(0, offs[:, 1].max())
     rng = np.random.default_rng(11)
-    B = 48
-    receivers, t_total, blocks = 0, 0.0, 0
-    while t_total < budget_s and blocks < 100000:
-        x0 = int(rng.integers(hx0, W - B - hx1))
-        y0 = int(rng.integers(hy0, H - B - hy1))
-        t0 = time.perf_counter()
-        oracle.trace(osc, 0, pos, nrm, radius=RADIUS, seed=1, sample=0,
-                     region=(x0 - hx0, y0 - hy0, B + hx0 + hx1, B + hy0 + hy1), out=(rec, mg))
-        oracle.reuse(None, 0, pos, nrm, rec, pat, oracle.EST_BIASED, radius=RADIUS,
-                     region=(x0, y0, B, B), out=(out, omg))
-        t_total += time.perf_counter() - t0
-        receivers += B * B
-        blocks += 1
-    return {"value": receivers * K / t_total, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": (f"{blocks} random {B}x{B} receiver blocks of the 1080p frame: trace of "
+
+    def run(B, budget):
+        receivers, t_tr, t_ru, blocks = 0, 0.0, 0.0, 0
+        while t_tr + t_ru < budget and blocks < 100000:
+            x0 = int(rng.integers(hx0, W - B - hx1))
+            y0 = int(rng.integers(hy0, H - B - hy1))
+            t0 = time.perf_counter()
+            oracle.trace(osc, 0, pos, nrm, radius=RADIUS, seed=1, sample=0,
+                         region=(x0 - hx0, y0 - hy0, B + hx0 + hx1, B + hy0 + hy1), out=(rec, mg))
+            t1 = time.perf_counter()
+            oracle.reuse(None, 0, pos, nrm, rec, pat, oracle.EST_BIASED, radius=RADIUS,
+                         region=(x0, y0, B, B), out=(out, omg))
+            t2 = time.perf_counter()
+            t_tr += t1 - t0
+            t_ru += t2 - t1
+            receivers += B * B
+            blocks += 1
+        return receivers, t_tr, t_ru, blocks
+
+    n, t_tr, t_ru, blocks = run(48, budget_s)
+    oracle.set_num_threads(1)
+    n1, t_tr1, t_ru1, blocks1 = run(48, budget_s / 4)
+    oracle.set_num_threads(cores)
+    return {"value": n * K / (t_tr + t_ru), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "cpu_model": cpu_model(),
+            "trace_rays_per_s": n / t_tr * ((48 + hx0 + hx1) * (48 + hy0 + hy1)) / (48 * 48),
+            "trace_s": t_tr, "reuse_s": t_ru,
+            "reuse_neighbour_samples_per_s": n * K / t_ru,
+            "single_core": {"value": n1 * K / (t_tr1 + t_ru1), "unit": UNIT, "cores": 1,
+                            "trace_s": t_tr1, "reuse_s": t_ru1,
+                            "sample": f"{blocks1} random 48x48 blocks with their halos"},
+            "sample": (f"{blocks} random 48x48 receiver blocks of the 1080p frame: trace of "
                        f"each block plus its {hx0}/{hx1}/{hy0}/{hy1}-px halo, then biased "
-                       f"K=8 reuse of the block ({t_total:.1f} s)")}
+                       f"K=8 reuse of the block ({t_tr + t_ru:.1f} s)")}
 
 
 GROUP_BYTES_PER_PX = 52   # x 12, n 12, z 12, n_z 12, out 4

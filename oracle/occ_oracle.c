@@ -884,6 +884,14 @@ ORC_API void orc_accumulate(const void* sc, int effect, int W, int H, const floa
     free(out);
 }
 
+ORC_API void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 ORC_API int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

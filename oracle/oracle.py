@@ -87,6 +87,7 @@ def lib():
                                      C.c_uint32, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                      f64, f64]
         L.orc_num_threads.restype = C.c_int
+        L.orc_set_num_threads.argtypes = [C.c_int]
         L.orc_density.argtypes = [C.c_int, f64, f64, f64, f64, C.c_float, f32]
         L.orc_density.restype = C.c_double
         _lib = L
@@ -95,6 +96,11 @@ def lib():
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (OpenMP)."""
+    lib().orc_set_num_threads(int(n))
 
 
 # ------------------------------------------------------------------------------------

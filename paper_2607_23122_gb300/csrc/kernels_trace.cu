@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     Traversal t;
-    uint2 stack[kStackSize];
+    StackEntry stack[kStackSize];
     t.cur = t.leaf = kEmptyRef;
     t.overflow = false;
     bool have = false, exhausted = false, overflow = false;

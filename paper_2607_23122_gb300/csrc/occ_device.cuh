@@ -310,10 +310,33 @@ struct Hit {
     float t;
 };
 
+// Traversal stack entries: the node reference alone (4 bytes; a popped node beyond the
+// current best hit is culled by its own box test), or with its entry distance so that it
+// is skipped without the fetch (OCC_STACK_KEYS=1, 8 bytes).  Measured at 1080p: equal for
+// AO, 1.7% faster shadows with 4-byte entries (half the local-memory stack).
+#ifndef OCC_STACK_KEYS
+#define OCC_STACK_KEYS 0
+#endif
+#if OCC_STACK_KEYS
+using StackEntry = uint2;
+__device__ __forceinline__ StackEntry stack_entry(uint32_t ref, float key) {
+    return make_uint2(ref, __float_as_uint(key));
+}
+__device__ __forceinline__ uint32_t entry_ref(StackEntry e) { return e.x; }
+__device__ __forceinline__ bool entry_live(StackEntry e, float tbest) {
+    return __uint_as_float(e.y) <= tbest;
+}
+#else
+using StackEntry = uint32_t;
+__device__ __forceinline__ StackEntry stack_entry(uint32_t ref, float) { return ref; }
+__device__ __forceinline__ uint32_t entry_ref(StackEntry e) { return e; }
+__device__ __forceinline__ bool entry_live(StackEntry, float) { return true; }
+#endif
+
 // Children of node `cur` hit by the ray before tbest, nearest first: the nearest goes to
 // *next, the others are pushed far-to-near.  *next = kEmptyRef if none is hit.
 __device__ __forceinline__ void visit_node(const DevBVH& bvh, uint32_t cur, const TraceRay& r,
-                                           float tbest, uint2* stack, int& sp, bool& overflow,
+                                           float tbest, StackEntry* stack, int& sp, bool& overflow,
                                            uint32_t* next) {
     // Slab test of the four children: near / far planes are picked by address (the ray's
     // direction signs), each plane distance is one FMA; boxes are grown at build time so
@@ -352,7 +375,7 @@ __device__ __forceinline__ void visit_node(const DevBVH& bvh, uint32_t cur, cons
 #pragma unroll
     for (int c = 3; c >= 1; --c) {
         if (key[c] != inf) {
-            if (sp < kStackSize) stack[sp++] = make_uint2(ref[c], __float_as_uint(key[c]));
+            if (sp < kStackSize) stack[sp++] = stack_entry(ref[c], key[c]);
             else overflow = true;
         }
     }
@@ -360,10 +383,10 @@ __device__ __forceinline__ void visit_node(const DevBVH& bvh, uint32_t cur, cons
 }
 
 // Pops the next entry that can still hold a hit before tbest (kEmptyRef when none).
-__device__ __forceinline__ uint32_t pop_next(const uint2* stack, int& sp, float tbest) {
+__device__ __forceinline__ uint32_t pop_next(const StackEntry* stack, int& sp, float tbest) {
     while (sp > 0) {
-        const uint2 e = stack[--sp];
-        if (__uint_as_float(e.y) <= tbest) return e.x;
+        const StackEntry e = stack[--sp];
+        if (entry_live(e, tbest)) return entry_ref(e);
     }
     return kEmptyRef;
 }
@@ -410,7 +433,7 @@ __device__ __forceinline__ bool trav_done(const Traversal& t) {
 // on (0, tmax] (visibility queries need only whether one exists; the acceptance test is
 // the closest-hit one, so the answer is the same).
 template <bool ANY = false>
-__device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, uint2* stack) {
+__device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, StackEntry* stack) {
     while (t.cur != kEmptyRef && !is_leaf_ref(t.cur)) {
         uint32_t next;
         visit_node(bvh, t.cur, t.r, t.tbest, stack, t.sp, t.overflow, &next);
@@ -447,7 +470,7 @@ __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, uint
 __device__ __forceinline__ Hit closest_hit(const DevBVH& bvh, float3 o, float3 d, float tmax,
                                            unsigned int* status, uint32_t start = 0u) {
     Traversal t;
-    uint2 stack[kStackSize];
+    StackEntry stack[kStackSize];
     trav_init(t, o, d, tmax, start);
     while (!trav_done(t)) trav_round(t, bvh, stack);
     if (t.overflow && status) atomicOr(status, kStatusStackOverflowBit);
@@ -462,7 +485,7 @@ __device__ __forceinline__ Hit closest_hit(const DevBVH& bvh, float3 o, float3 d
 __device__ __forceinline__ bool any_hit(const DevBVH& bvh, float3 o, float3 d, float tmax,
                                         unsigned int* status) {
     Traversal t;
-    uint2 stack[kStackSize];
+    StackEntry stack[kStackSize];
     trav_init(t, o, d, tmax, 0u);
     while (!trav_done(t)) trav_round<true>(t, bvh, stack);
     if (t.overflow && status) atomicOr(status, kStatusStackOverflowBit);
