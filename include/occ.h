@@ -318,6 +318,12 @@ occ_status occ_frame_noalloc(const occ_gbuffer* gb, const occ_bvh* bvh, int32_t 
 occ_status occ_debug_philox(occ_ctx* ctx, const uint32_t* in_dev, int64_t n, uint32_t* out_dev,
                             void* stream);
 
+/* Exercises the bounded-wait failure path of the TMA reuse kernel without a fault: one
+ * thread polls an mbarrier that nothing completes, gives up after `spins` polls
+ * (1 .. 2^24) and sets the wait-timeout flag, so that the next occ_sync() returns
+ * OCC_ERR_DEVICE_CHECK ("wait timeout") and clears it; the context stays usable. */
+occ_status occ_debug_wait_timeout(occ_ctx* ctx, uint32_t spins, void* stream);
+
 /* The step-1 ray of every receiver: out_dev[p] = (direction.xyz, tmax). */
 occ_status occ_debug_rays(occ_ctx* ctx, const occ_gbuffer* gb, int32_t effect, float radius,
                           const occ_rect_light* light, uint64_t seed, uint32_t sample,

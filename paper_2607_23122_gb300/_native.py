@@ -162,6 +162,7 @@ SIGNATURES = {
     "occ_server_get_stats": (c_int32, [c_void_p, C.POINTER(occ_server_stats)]),
     "occ_server_shutdown": (c_int32, [c_void_p, c_int32]),
     "occ_server_destroy": (c_int32, [c_void_p, c_int32]),
+    "occ_debug_wait_timeout": (c_int32, [c_void_p, c_uint32, c_void_p]),
     "occ_debug_philox": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "occ_debug_rays": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_int32, c_float,
                                  C.POINTER(occ_rect_light), c_uint64, c_uint32, c_void_p,

@@ -251,6 +251,18 @@ __global__ void __launch_bounds__(512, 1)
     }
 }
 
+// The bounded-wait path of the kernel above, exercised on purpose: one thread polls a barrier
+// that no arrival will ever complete, gives up after `spins` polls and records
+// kStatusWaitTimeoutBit, as every wait of k_reuse_tile does when it runs out.
+__global__ void k_debug_wait_timeout(uint32_t spins, unsigned* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar);
+    bool done = false;
+    for (uint32_t i = 0; i < spins && !done; ++i) done = mbar_try_wait(&bar, 0u);
+    if (!done) atomicOr(status, kStatusWaitTimeoutBit);
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
@@ -299,6 +311,11 @@ cudaError_t launch_t(const CUtensorMap* maps, const TileArgs& a, size_t smem, in
 // Returns false (nothing launched) when the pattern or the staging does not fit this
 // kernel: not a box / offsets pattern, K > 16, a halo wider than the TMA box allows, or a
 // tile that does not fit in shared memory.
+cudaError_t launch_debug_wait_timeout(uint32_t spins, unsigned* status, cudaStream_t s) {
+    k_debug_wait_timeout<<<1, 32, 0, s>>>(spins, status);
+    return cudaGetLastError();
+}
+
 bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const PatternParams& pat,
                        float R2s, const LightParams& light, float* out, unsigned* status,
                        cudaStream_t s, cudaError_t* err, int tile_rows) {

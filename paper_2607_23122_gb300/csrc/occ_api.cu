@@ -511,6 +511,14 @@ OCC_EXPORT occ_status occ_debug_philox(occ_ctx* ctx, const uint32_t* in_dev, int
                     "philox launch");
 }
 
+OCC_EXPORT occ_status occ_debug_wait_timeout(occ_ctx* ctx, uint32_t spins, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if (spins < 1 || spins > (1u << 24)) return fail(ctx, OCC_ERR_INVALID_ARG, "spins must be in [1, 2^24]");
+    return launched(ctx, occ::launch_debug_wait_timeout(spins, ctx->status, (cudaStream_t)stream),
+                    "wait-timeout launch");
+}
+
 OCC_EXPORT occ_status occ_debug_rays(occ_ctx* ctx, const occ_gbuffer* gb, int32_t effect,
                                      float radius, const occ_rect_light* light, uint64_t seed,
                                      uint32_t sample, float* out_dev, void* stream) {

@@ -78,6 +78,7 @@ struct LightWeights {
 cudaError_t launch_weighted_sum(const float* vis, int64_t P, const LightWeights& w, float* out,
                                 cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s);
+cudaError_t launch_debug_wait_timeout(uint32_t spins, unsigned* status, cudaStream_t s);
 cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
                               const LightParams& light, uint64_t seed, uint32_t sample,
                               float4* out, cudaStream_t s);

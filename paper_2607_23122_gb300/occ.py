@@ -369,6 +369,10 @@ def occ_frame_noalloc(gb: GBuffer, bvh: BVH, effect: int, radius: float, light, 
     return out
 
 
+def occ_debug_wait_timeout(ctx: Context, spins: int = 1000, stream=None):
+    ctx.check(ctx.lib.occ_debug_wait_timeout(ctx.handle, int(spins), _stream_handle(stream)))
+
+
 def occ_debug_philox(ctx: Context, ctr_key: np.ndarray, stream=None) -> np.ndarray:
     """Philox4x32-10 of rows (c0, c1, c2, c3, k0, k1) -> [n, 4] uint32 (synchronous)."""
     a = np.ascontiguousarray(ctr_key, dtype=np.uint32).reshape(-1, 6)

@@ -490,3 +490,19 @@ def test_several_lights_fully_lit_and_arguments(occ, ctx):
         occ.occ_shadow_lights(ctx, gb, bvh, lights, [1.0, float("nan")], 1, 0,
                               occ.Pattern.group(4, 2), BIASED)
     ctx.sync()
+
+
+def test_bounded_wait_timeout_is_reported_and_the_context_survives(occ, ctx, c1):
+    """A wait that runs out (a barrier nothing completes) sets the device flag; occ_sync
+    returns OCC_ERR_DEVICE_CHECK naming it, clears it, and the context keeps working."""
+    ctx.sync()
+    occ.occ_debug_wait_timeout(ctx, 1000)
+    with pytest.raises(occ.OccError, match="DEVICE_CHECK.*wait timeout"):
+        ctx.sync()
+    ctx.sync()                                              # flags were cleared
+    o = occ.occ_trace_ao(ctx, c1["gb"], c1["bvh"], R_C1, 3, 0)
+    g = occ.occ_reuse_ao(ctx, c1["gb"], o, occ.Pattern.box(3, 3), 9, BIASED)
+    ctx.sync()
+    assert np.isfinite(g.cpu().numpy()).all()
+    with pytest.raises(occ.OccError, match="INVALID_ARG"):
+        occ.occ_debug_wait_timeout(ctx, 0)
