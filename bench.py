@@ -236,7 +236,7 @@ def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
 GROUP_BYTES_PER_PX = 52   # x 12, n 12, z 12, n_z 12, out 4
 # DRAM bytes (read + write) per launch from one `ncu --set full` capture of
 # `bench.py --profile-step` (cold L2; profiles/k_*_ao1080p*.md); None once a kernel changes
-NCU_TRAFFIC = {"k_trace_dyn<AO>": 75.047936e6 + 31.301376e6,
+NCU_TRAFFIC = {"k_trace_dyn<AO>": None,
                "k_reuse_tile<AO,9>": 132.799744e6 + 6.98496e6,
                "k_reuse_group<AO,biased,4,2>": 114.168832e6 + 4.692736e6}
 NCU_TRACE_ISSUE_ACTIVE = 0.6594   # smsp__issue_active of k_trace_dyn<AO> in its capture

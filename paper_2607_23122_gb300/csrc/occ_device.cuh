@@ -224,7 +224,7 @@ struct TraceRay {
     float3 o;
     float3 idir;            // 1 / d with zero components replaced by a tiny value
     float3 oidir;           // o * idir: slab distances are lo * idir - oidir (one FMA)
-    int near[3], far[3];    // float4 index in Node4 of the near / far planes per axis
+    uint32_t nsel;          // bit a set: the high plane of axis a is entered first
     float3 rx, ry, rz;      // shear rows
     float3 d;
 };
@@ -260,12 +260,7 @@ __device__ __forceinline__ TraceRay make_trace_ray(float3 o, float3 d) {
     r.oidir = make_float3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
     // Node4 holds lox, hix, loy, hiy, loz, hiz as consecutive float4: for a positive
     // direction component the low plane is entered first.
-    r.near[0] = r.idir.x >= 0.0f ? 0 : 1;
-    r.near[1] = r.idir.y >= 0.0f ? 2 : 3;
-    r.near[2] = r.idir.z >= 0.0f ? 4 : 5;
-    r.far[0] = 1 - r.near[0];
-    r.far[1] = 5 - r.near[1];
-    r.far[2] = 9 - r.near[2];
+    r.nsel = (r.idir.x >= 0.0f ? 0u : 1u) | (r.idir.y >= 0.0f ? 0u : 2u) | (r.idir.z >= 0.0f ? 0u : 4u);
     return r;
 }
 
@@ -342,9 +337,11 @@ __device__ __forceinline__ void visit_node(const DevBVH& bvh, uint32_t cur, cons
     // direction signs), each plane distance is one FMA; boxes are grown at build time so
     // this is conservative.
     const float4* nb = reinterpret_cast<const float4*>(bvh.nodes + cur);
-    const float4 nx = __ldg(nb + r.near[0]), fx = __ldg(nb + r.far[0]);
-    const float4 ny = __ldg(nb + r.near[1]), fy = __ldg(nb + r.far[1]);
-    const float4 nz = __ldg(nb + r.near[2]), fz = __ldg(nb + r.far[2]);
+    // plane a of axis k sits at float4 2k + a; the far plane is the other one (index ^ 1)
+    const uint32_t ix = r.nsel & 1u, iy = 2u + ((r.nsel >> 1) & 1u), iz = 4u + ((r.nsel >> 2) & 1u);
+    const float4 nx = __ldg(nb + ix), fx = __ldg(nb + (ix ^ 1u));
+    const float4 ny = __ldg(nb + iy), fy = __ldg(nb + (iy ^ 1u));
+    const float4 nz = __ldg(nb + iz), fz = __ldg(nb + (iz ^ 1u));
     const uint4 ch = __ldg(reinterpret_cast<const uint4*>(nb + 6));
     const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, fxs[4] = {fx.x, fx.y, fx.z, fx.w};
     const float nys[4] = {ny.x, ny.y, ny.z, ny.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w};
