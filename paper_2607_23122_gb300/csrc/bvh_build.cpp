@@ -1,8 +1,9 @@
-// bvh_build.cpp -- host construction of the 4-wide BVH used by the traversal kernels.
+// bvh_build.cpp -- host construction of the wide BVH (4 or 8 children per node,
+// OCC_BVH_WIDTH) used by the traversal kernels.
 //
 // A binary BVH is built top-down with binned SAH (16 bins per axis over the
 // centroid bounds; the top levels run in parallel threads), then collapsed into
-// 4-wide nodes by repeatedly opening the child with the largest surface area.
+// wide nodes by repeatedly opening the child with the largest surface area.
 // Leaves keep their triangles contiguous, so the triangle array is stored in leaf
 // order as three float4 per triangle with the input id in v0.w.
 #include <algorithm>
@@ -185,9 +186,35 @@ struct Builder {
     }
 };
 
+// Component c (child index) of plane p of a node.
+inline float& plane_at(BvhNode& n, int p, int c) {
+    float4& v = n.plane[p * kPlaneVecs + c / 4];
+    return (&v.x)[c % 4];
+}
+
+inline void set_child(BvhNode& n, int c, uint32_t ref) {
+    uint4& v = n.child[c / 4];
+    (&v.x)[c % 4] = ref;
+}
+
+// An empty node: every child slot empty (inverted box, kEmptyRef).
+inline BvhNode empty_node() {
+    BvhNode n;
+    std::memset(&n, 0, sizeof(n));
+    const float inf = std::numeric_limits<float>::infinity();
+    for (int c = 0; c < kWidth; ++c) {
+        for (int a = 0; a < 3; ++a) {
+            plane_at(n, 2 * a, c) = inf;
+            plane_at(n, 2 * a + 1, c) = -inf;
+        }
+        set_child(n, c, kEmptyRef);
+    }
+    return n;
+}
+
 struct Collapser {
     const std::vector<BNode>& bn;
-    std::vector<Node4>& nodes;
+    std::vector<BvhNode>& nodes;
     float pad;          // absolute growth of every child box (see build_bvh4)
     int max_depth = 0;
     int64_t leaves = 0;
@@ -197,11 +224,13 @@ struct Collapser {
         return kLeafBit | ((b.count - 1u) << kLeafCountShift) | b.first;
     }
 
-    // Emits the 4-wide node standing for binary node `b` (internal) and returns its index.
+    // Emits the kWidth-wide node standing for binary node `b` (internal) and returns its
+    // index: the binary subtree's children are opened largest-area first until kWidth
+    // children (or only leaves) remain.
     uint32_t emit(int32_t b, int depth) {
         max_depth = std::max(max_depth, depth);
         std::vector<int32_t> kids = {bn[b].left, bn[b].right};
-        while (kids.size() < 4) {
+        while ((int)kids.size() < kWidth) {
             int pick = -1;
             float best = -1.0f;
             for (int i = 0; i < (int)kids.size(); ++i) {
@@ -219,22 +248,10 @@ struct Collapser {
             kids.push_back(bn[open].right);
         }
         const uint32_t me = (uint32_t)nodes.size();
-        nodes.emplace_back();
-        float lo[3][4], hi[3][4];
-        uint32_t ref[4];
-        for (int c = 0; c < 4; ++c) {
-            ref[c] = kEmptyRef;
-            for (int a = 0; a < 3; ++a) {
-                lo[a][c] = std::numeric_limits<float>::infinity();
-                hi[a][c] = -std::numeric_limits<float>::infinity();
-            }
-        }
+        nodes.push_back(empty_node());
+        uint32_t ref[kWidth];
         for (int c = 0; c < (int)kids.size(); ++c) {
             const BNode& k = bn[kids[c]];
-            for (int a = 0; a < 3; ++a) {
-                lo[a][c] = k.box.lo[a] - pad;
-                hi[a][c] = k.box.hi[a] + pad;
-            }
             if (k.left < 0) {
                 ref[c] = leaf_ref(k);
                 ++leaves;
@@ -243,15 +260,15 @@ struct Collapser {
                 ref[c] = emit(kids[c], depth + 1);
             }
         }
-        Node4& n = nodes[me];
-        n.lox = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
-        n.hix = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
-        n.loy = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
-        n.hiy = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
-        n.loz = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
-        n.hiz = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
-        n.child = make_uint4(ref[0], ref[1], ref[2], ref[3]);
-        n.pad = make_uint4(0, 0, 0, 0);
+        BvhNode& n = nodes[me];   // after the recursion: the vector may have moved
+        for (int c = 0; c < (int)kids.size(); ++c) {
+            const BNode& k = bn[kids[c]];
+            for (int a = 0; a < 3; ++a) {
+                plane_at(n, 2 * a, c) = k.box.lo[a] - pad;
+                plane_at(n, 2 * a + 1, c) = k.box.hi[a] + pad;
+            }
+            set_child(n, c, ref[c]);
+        }
         return me;
     }
 };
@@ -298,17 +315,13 @@ bool build_bvh4(const float* tris, int64_t T, HostBVH* out, std::string* err) {
     Collapser col{bn, out->nodes, std::ldexp(mag, -17)};
     if (bn[0].left < 0) {
         // the whole scene is one leaf: a root node with that single child
-        Node4 n;
-        std::memset(&n, 0, sizeof(n));
-        const float inf = std::numeric_limits<float>::infinity();
+        BvhNode n = empty_node();
         const float p = col.pad;
-        n.lox = make_float4(bn[0].box.lo[0] - p, inf, inf, inf);
-        n.hix = make_float4(bn[0].box.hi[0] + p, -inf, -inf, -inf);
-        n.loy = make_float4(bn[0].box.lo[1] - p, inf, inf, inf);
-        n.hiy = make_float4(bn[0].box.hi[1] + p, -inf, -inf, -inf);
-        n.loz = make_float4(bn[0].box.lo[2] - p, inf, inf, inf);
-        n.hiz = make_float4(bn[0].box.hi[2] + p, -inf, -inf, -inf);
-        n.child = make_uint4(Collapser::leaf_ref(bn[0]), kEmptyRef, kEmptyRef, kEmptyRef);
+        for (int a = 0; a < 3; ++a) {
+            plane_at(n, 2 * a, 0) = bn[0].box.lo[a] - p;
+            plane_at(n, 2 * a + 1, 0) = bn[0].box.hi[a] + p;
+        }
+        set_child(n, 0, Collapser::leaf_ref(bn[0]));
         out->nodes.push_back(n);
         col.leaves = 1;
         col.max_leaf = bn[0].count;
@@ -316,7 +329,7 @@ bool build_bvh4(const float* tris, int64_t T, HostBVH* out, std::string* err) {
     } else {
         col.emit(0, 0);
     }
-    if (3 * (col.max_depth + 1) > kStackSize) {
+    if ((kWidth - 1) * (col.max_depth + 1) > kStackSize) {
         *err = "BVH too deep for the traversal stack";
         return false;
     }

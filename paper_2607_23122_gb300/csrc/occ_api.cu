@@ -311,7 +311,7 @@ OCC_EXPORT occ_status occ_bvh_build(occ_ctx* ctx, const float* tris_host, int64_
     if (!occ::build_bvh4(tris_host, T, &hb, &err)) return fail(ctx, OCC_ERR_INVALID_ARG, "%s", err.c_str());
     occ_bvh* b = new occ_bvh();
     b->device = ctx->device;
-    const size_t nb = hb.nodes.size() * sizeof(occ::Node4), tb = hb.tris.size() * sizeof(float4);
+    const size_t nb = hb.nodes.size() * sizeof(occ::BvhNode), tb = hb.tris.size() * sizeof(float4);
     cudaError_t e = cudaMalloc(&b->nodes, nb);
     if (e == cudaSuccess) e = cudaMalloc(&b->tris, tb);
     if (e == cudaSuccess) e = cudaMemcpy(b->nodes, hb.nodes.data(), nb, cudaMemcpyHostToDevice);

@@ -12,14 +12,14 @@
 namespace occ {
 
 struct HostBVH {
-    std::vector<Node4> nodes;     // root at index 0
+    std::vector<BvhNode> nodes;   // root at index 0
     std::vector<float4> tris;     // 3 per triangle, leaf order, v0.w = input id bits
     int64_t num_leaves = 0;
     int depth = 0;
     int max_leaf_tris = 0;
 };
 
-// Builds the 4-wide BVH of T triangles (tris: [T][3][3] floats).  Returns false with
+// Builds the kWidth-wide BVH of T triangles (tris: [T][3][3] floats).  Returns false with
 // a message for invalid input or a tree too deep for the traversal stack.
 bool build_bvh4(const float* tris, int64_t T, HostBVH* out, std::string* err);
 

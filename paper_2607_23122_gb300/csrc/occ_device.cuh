@@ -258,7 +258,7 @@ __device__ __forceinline__ TraceRay make_trace_ray(float3 o, float3 d) {
                          __frcp_rn(fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
                          __frcp_rn(fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
     r.oidir = make_float3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
-    // Node4 holds lox, hix, loy, hiy, loz, hiz as consecutive float4: for a positive
+    // a node holds planes lox, hix, loy, hiy, loz, hiz in that order: for a positive
     // direction component the low plane is entered first.
     r.nsel = (r.idir.x >= 0.0f ? 0u : 1u) | (r.idir.y >= 0.0f ? 0u : 2u) | (r.idir.z >= 0.0f ? 0u : 4u);
     return r;
@@ -330,47 +330,59 @@ __device__ __forceinline__ bool entry_live(StackEntry, float) { return true; }
 
 // Children of node `cur` hit by the ray before tbest, nearest first: the nearest goes to
 // *next, the others are pushed far-to-near.  *next = kEmptyRef if none is hit.
-__device__ __forceinline__ void visit_node(const DevBVH& bvh, uint32_t cur, const TraceRay& r,
-                                           float tbest, StackEntry* stack, int& sp, bool& overflow,
-                                           uint32_t* next) {
-    // Slab test of the four children: near / far planes are picked by address (the ray's
-    // direction signs), each plane distance is one FMA; boxes are grown at build time so
-    // this is conservative.
-    const float4* nb = reinterpret_cast<const float4*>(bvh.nodes + cur);
-    // plane a of axis k sits at float4 2k + a; the far plane is the other one (index ^ 1)
-    const uint32_t ix = r.nsel & 1u, iy = 2u + ((r.nsel >> 1) & 1u), iz = 4u + ((r.nsel >> 2) & 1u);
-    const float4 nx = __ldg(nb + ix), fx = __ldg(nb + (ix ^ 1u));
-    const float4 ny = __ldg(nb + iy), fy = __ldg(nb + (iy ^ 1u));
-    const float4 nz = __ldg(nb + iz), fz = __ldg(nb + (iz ^ 1u));
-    const uint4 ch = __ldg(reinterpret_cast<const uint4*>(nb + 6));
-    const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, fxs[4] = {fx.x, fx.y, fx.z, fx.w};
-    const float nys[4] = {ny.x, ny.y, ny.z, ny.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w};
-    const float nzs[4] = {nz.x, nz.y, nz.z, nz.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
-    const uint32_t cref[4] = {ch.x, ch.y, ch.z, ch.w};
-    const float inf = __int_as_float(0x7f800000);
-    float key[4];
-    uint32_t ref[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const float tn = fmaxf(fmaxf(fmaf(nxs[c], r.idir.x, -r.oidir.x), fmaf(nys[c], r.idir.y, -r.oidir.y)),
-                               fmaxf(fmaf(nzs[c], r.idir.z, -r.oidir.z), 0.0f));
-        const float tf = fminf(fminf(fmaf(fxs[c], r.idir.x, -r.oidir.x), fmaf(fys[c], r.idir.y, -r.oidir.y)),
-                               fminf(fmaf(fzs[c], r.idir.z, -r.oidir.z), tbest));
-        const bool hit = cref[c] != kEmptyRef && tn <= tf;
-        key[c] = hit ? tn : inf;
-        ref[c] = cref[c];
-    }
-    // near-to-far order (sorting network (0,1)(2,3)(0,2)(1,3)(1,2)): the nearest child is
-    // visited next, the others are pushed far-to-near so closer ones pop first
 #define OCC_CSWAP(a, b)                                                          \
     if (key[b] < key[a]) {                                                      \
         const float tk = key[a]; key[a] = key[b]; key[b] = tk;                  \
         const uint32_t tr = ref[a]; ref[a] = ref[b]; ref[b] = tr;               \
     }
-    OCC_CSWAP(0, 1) OCC_CSWAP(2, 3) OCC_CSWAP(0, 2) OCC_CSWAP(1, 3) OCC_CSWAP(1, 2)
-#undef OCC_CSWAP
+__device__ __forceinline__ void visit_node(const DevBVH& bvh, uint32_t cur, const TraceRay& r,
+                                           float tbest, StackEntry* stack, int& sp, bool& overflow,
+                                           uint32_t* next) {
+    // Slab test of the children: near / far planes are picked by address (the ray's
+    // direction signs), each plane distance is one FMA; boxes are grown at build time so
+    // this is conservative.
+    const float4* nb = reinterpret_cast<const float4*>(bvh.nodes + cur);
+    // plane a of axis k is plane 2k + a; its children 4h .. 4h + 3 sit at float4
+    // (2k + a) * kPlaneVecs + h, the far plane is the other one of the axis
+    const uint32_t ix = r.nsel & 1u, iy = 2u + ((r.nsel >> 1) & 1u), iz = 4u + ((r.nsel >> 2) & 1u);
+    const float inf = __int_as_float(0x7f800000);
+    float key[kWidth];
+    uint32_t ref[kWidth];
 #pragma unroll
-    for (int c = 3; c >= 1; --c) {
+    for (int h = 0; h < kPlaneVecs; ++h) {
+        const float4 nx = __ldg(nb + ix * kPlaneVecs + h), fx = __ldg(nb + (ix ^ 1u) * kPlaneVecs + h);
+        const float4 ny = __ldg(nb + iy * kPlaneVecs + h), fy = __ldg(nb + (iy ^ 1u) * kPlaneVecs + h);
+        const float4 nz = __ldg(nb + iz * kPlaneVecs + h), fz = __ldg(nb + (iz ^ 1u) * kPlaneVecs + h);
+        const uint4 ch = __ldg(reinterpret_cast<const uint4*>(nb + 6 * kPlaneVecs + h));
+        const float nxs[4] = {nx.x, nx.y, nx.z, nx.w}, fxs[4] = {fx.x, fx.y, fx.z, fx.w};
+        const float nys[4] = {ny.x, ny.y, ny.z, ny.w}, fys[4] = {fy.x, fy.y, fy.z, fy.w};
+        const float nzs[4] = {nz.x, nz.y, nz.z, nz.w}, fzs[4] = {fz.x, fz.y, fz.z, fz.w};
+        const uint32_t cref[4] = {ch.x, ch.y, ch.z, ch.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float tn = fmaxf(fmaxf(fmaf(nxs[c], r.idir.x, -r.oidir.x), fmaf(nys[c], r.idir.y, -r.oidir.y)),
+                                   fmaxf(fmaf(nzs[c], r.idir.z, -r.oidir.z), 0.0f));
+            const float tf = fminf(fminf(fmaf(fxs[c], r.idir.x, -r.oidir.x), fmaf(fys[c], r.idir.y, -r.oidir.y)),
+                                   fminf(fmaf(fzs[c], r.idir.z, -r.oidir.z), tbest));
+            const bool hit = cref[c] != kEmptyRef && tn <= tf;
+            key[4 * h + c] = hit ? tn : inf;
+            ref[4 * h + c] = cref[c];
+        }
+    }
+    // near-to-far order by a sorting network: 4 keys (0,1)(2,3)(0,2)(1,3)(1,2); 8 keys the
+    // 19-comparator network (pairs, quadruples, merge).  The nearest child is visited next,
+    // the others are pushed far-to-near so closer ones pop first.
+    if (kWidth == 4) {
+        OCC_CSWAP(0, 1) OCC_CSWAP(2, 3) OCC_CSWAP(0, 2) OCC_CSWAP(1, 3) OCC_CSWAP(1, 2)
+    } else {
+        OCC_CSWAP(0, 2) OCC_CSWAP(1, 3) OCC_CSWAP(4, 6) OCC_CSWAP(5, 7)
+        OCC_CSWAP(0, 4) OCC_CSWAP(1, 5) OCC_CSWAP(2, 6) OCC_CSWAP(3, 7)
+        OCC_CSWAP(0, 1) OCC_CSWAP(2, 3) OCC_CSWAP(4, 5) OCC_CSWAP(6, 7)
+        OCC_CSWAP(2, 4) OCC_CSWAP(3, 5) OCC_CSWAP(1, 4) OCC_CSWAP(3, 6)
+        OCC_CSWAP(1, 2) OCC_CSWAP(3, 4) OCC_CSWAP(5, 6)
+    }
+#pragma unroll
+    for (int c = kWidth - 1; c >= 1; --c) {
         if (key[c] != inf) {
             if (sp < kStackSize) stack[sp++] = stack_entry(ref[c], key[c]);
             else overflow = true;
@@ -378,6 +390,7 @@ __device__ __forceinline__ void visit_node(const DevBVH& bvh, uint32_t cur, cons
     }
     *next = key[0] != inf ? ref[0] : kEmptyRef;
 }
+#undef OCC_CSWAP
 
 // Pops the next entry that can still hold a hit before tbest (kEmptyRef when none).
 __device__ __forceinline__ uint32_t pop_next(const StackEntry* stack, int& sp, float tbest) {
@@ -497,24 +510,27 @@ __device__ __forceinline__ bool any_hit(const DevBVH& bvh, float3 o, float3 d, f
 __device__ __forceinline__ uint32_t start_node(const DevBVH& bvh, float3 qlo, float3 qhi) {
     uint32_t cur = 0;
     for (int level = 0; level < kStackSize; ++level) {
-        const Node4* n = bvh.nodes + cur;
-        const float4 lox = __ldg(&n->lox), hix = __ldg(&n->hix);
-        const float4 loy = __ldg(&n->loy), hiy = __ldg(&n->hiy);
-        const float4 loz = __ldg(&n->loz), hiz = __ldg(&n->hiz);
-        const uint4 ch = __ldg(&n->child);
-        const float lx[4] = {lox.x, lox.y, lox.z, lox.w}, hx[4] = {hix.x, hix.y, hix.z, hix.w};
-        const float ly[4] = {loy.x, loy.y, loy.z, loy.w}, hy[4] = {hiy.x, hiy.y, hiy.z, hiy.w};
-        const float lz[4] = {loz.x, loz.y, loz.z, loz.w}, hz[4] = {hiz.x, hiz.y, hiz.z, hiz.w};
-        const uint32_t cref[4] = {ch.x, ch.y, ch.z, ch.w};
+        const float4* nb = reinterpret_cast<const float4*>(bvh.nodes + cur);
         int count = 0;
         uint32_t only = kEmptyRef;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const bool ov = cref[c] != kEmptyRef && lx[c] <= qhi.x && hx[c] >= qlo.x &&
-                            ly[c] <= qhi.y && hy[c] >= qlo.y && lz[c] <= qhi.z && hz[c] >= qlo.z;
-            if (ov) {
-                ++count;
-                only = cref[c];
+        for (int h = 0; h < kPlaneVecs; ++h) {
+            const float4 lox = __ldg(nb + 0 * kPlaneVecs + h), hix = __ldg(nb + 1 * kPlaneVecs + h);
+            const float4 loy = __ldg(nb + 2 * kPlaneVecs + h), hiy = __ldg(nb + 3 * kPlaneVecs + h);
+            const float4 loz = __ldg(nb + 4 * kPlaneVecs + h), hiz = __ldg(nb + 5 * kPlaneVecs + h);
+            const uint4 ch = __ldg(reinterpret_cast<const uint4*>(nb + 6 * kPlaneVecs + h));
+            const float lx[4] = {lox.x, lox.y, lox.z, lox.w}, hx[4] = {hix.x, hix.y, hix.z, hix.w};
+            const float ly[4] = {loy.x, loy.y, loy.z, loy.w}, hy[4] = {hiy.x, hiy.y, hiy.z, hiy.w};
+            const float lz[4] = {loz.x, loz.y, loz.z, loz.w}, hz[4] = {hiz.x, hiz.y, hiz.z, hiz.w};
+            const uint32_t cref[4] = {ch.x, ch.y, ch.z, ch.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const bool ov = cref[c] != kEmptyRef && lx[c] <= qhi.x && hx[c] >= qlo.x &&
+                                ly[c] <= qhi.y && hy[c] >= qlo.y && lz[c] <= qhi.z && hz[c] >= qlo.z;
+                if (ov) {
+                    ++count;
+                    only = cref[c];
+                }
             }
         }
         if (count == 0) return kEmptyRef;

@@ -38,7 +38,7 @@ struct occ_batch {
 
 struct occ_bvh {
     int device = 0;
-    occ::Node4* nodes = nullptr;
+    occ::BvhNode* nodes = nullptr;
     float4* tris = nullptr;
     occ_bvh_stats stats{};
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // scene bounds

@@ -7,26 +7,36 @@
 namespace occ {
 
 // ---------------------------------------------------------------------------------------
-// BVH layout.  One node = 128 bytes: the bounds of its (up to) four children in
-// structure-of-arrays form, then four packed child references.
+// BVH layout.  A node of width W (4 or 8, OCC_BVH_WIDTH) is W/4 cache lines: the bounds
+// of its (up to) W children in structure-of-arrays form -- planes lox, hix, loy, hiy,
+// loz, hiz, each W/4 float4 -- then W/4 uint4 of packed child references.
 //   internal child : node index (bit 31 clear)
 //   leaf child     : bit 31 | (count - 1) << 26 | first triangle (count <= 32)
 //   empty slot     : kEmptyRef with an empty box
+// Plane p (0..5) of children 4h .. 4h + 3 is float4 p * W/4 + h; the far plane of an axis
+// is the near one's index xor W/4.
 // Triangles: three float4 per triangle in leaf order; v0.w holds the input id.
 // ---------------------------------------------------------------------------------------
-struct __align__(16) Node4 {
-    float4 lox, hix, loy, hiy, loz, hiz;
-    uint4 child;
-    uint4 pad;
+#ifndef OCC_BVH_WIDTH
+#define OCC_BVH_WIDTH 4
+#endif
+constexpr int kWidth = OCC_BVH_WIDTH;
+constexpr int kPlaneVecs = kWidth / 4;
+static_assert(kWidth == 4 || kWidth == 8, "BVH width must be 4 or 8");
+
+struct __align__(16) BvhNode {
+    float4 plane[6 * kPlaneVecs];
+    uint4 child[kPlaneVecs];
+    uint4 pad[kPlaneVecs];
 };
-static_assert(sizeof(Node4) == 128, "Node4 must be 128 bytes");
+static_assert(sizeof(BvhNode) == 128 * kPlaneVecs, "a node is W/4 cache lines");
 
 constexpr uint32_t kEmptyRef = 0x7FFFFFFFu;
 constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr int kLeafCountShift = 26;
 constexpr uint32_t kLeafFirstMask = (1u << kLeafCountShift) - 1u;
 constexpr int kMaxLeafTris = 32;
-constexpr int kStackSize = 64;
+constexpr int kStackSize = kWidth == 8 ? 96 : 64;
 constexpr uint32_t kNoHit = 0xFFFFFFFFu;
 
 // Device status word bits (set by kernels, read back and cleared by occ_sync).
@@ -35,7 +45,7 @@ constexpr uint32_t kStatusWaitTimeoutBit = 1u << 1;
 constexpr uint32_t kStatusBadIndexBit = 1u << 2;
 
 struct DevBVH {
-    const Node4* nodes;
+    const BvhNode* nodes;
     const float4* tris;
 };
 
