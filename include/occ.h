@@ -324,6 +324,14 @@ occ_status occ_debug_philox(occ_ctx* ctx, const uint32_t* in_dev, int64_t n, uin
  * OCC_ERR_DEVICE_CHECK ("wait timeout") and clears it; the context stays usable. */
 occ_status occ_debug_wait_timeout(occ_ctx* ctx, uint32_t spins, void* stream);
 
+/* The traversal on arbitrary rays: rays_dev holds 8 floats per ray (o.xyz, tmax,
+ * d.xyz, unused), t in units of |d| on (0, tmax].  any = 0: tri_dev[i] = the closest
+ * hit's input triangle id (-1 none) and t_dev[i] its t (-1 none); any = 1: tri_dev[i] = 1
+ * if some triangle is hit, else 0. */
+occ_status occ_debug_closest_hit(occ_ctx* ctx, const occ_bvh* bvh, const float* rays_dev,
+                                 int64_t n, int32_t any, int32_t* tri_dev, float* t_dev,
+                                 void* stream);
+
 /* The step-1 ray of every receiver: out_dev[p] = (direction.xyz, tmax). */
 occ_status occ_debug_rays(occ_ctx* ctx, const occ_gbuffer* gb, int32_t effect, float radius,
                           const occ_rect_light* light, uint64_t seed, uint32_t sample,

@@ -107,6 +107,10 @@ typedef struct {
     int64_t batch_window_us;      /* 0: a free slot takes whatever is queued at once; > 0: it
                                      waits until max_views_per_batch requests are queued or
                                      the oldest has waited this long */
+    int32_t inject_alloc_failures; /* host-side fault injection: the first N batches find the
+                                      device memory pool exhausted; their requests finish with
+                                      OCC_ERR_OOM and the server goes on (0 in production) */
+    int32_t reserved;
 } occ_server_config;
 
 /* One frame to serve.  The G-buffer comes either from a pinhole camera

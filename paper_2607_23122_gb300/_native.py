@@ -80,7 +80,8 @@ class occ_sched_stats(C.Structure):
 class occ_server_config(C.Structure):
     _fields_ = [("budget_bytes", c_int64), ("max_views_per_batch", c_int32),
                 ("max_inflight", c_int32), ("max_queued", c_int32), ("poll_us", c_int32),
-                ("batch_max_px", c_int64), ("batch_window_us", c_int64)]
+                ("batch_max_px", c_int64), ("batch_window_us", c_int64),
+                ("inject_alloc_failures", c_int32), ("reserved", c_int32)]
 
 
 class occ_request(C.Structure):
@@ -163,6 +164,8 @@ SIGNATURES = {
     "occ_server_shutdown": (c_int32, [c_void_p, c_int32]),
     "occ_server_destroy": (c_int32, [c_void_p, c_int32]),
     "occ_debug_wait_timeout": (c_int32, [c_void_p, c_uint32, c_void_p]),
+    "occ_debug_closest_hit": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p,
+                                        c_void_p, c_void_p]),
     "occ_debug_philox": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "occ_debug_rays": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_int32, c_float,
                                  C.POINTER(occ_rect_light), c_uint64, c_uint32, c_void_p,

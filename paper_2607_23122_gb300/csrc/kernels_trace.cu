@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
     StackEntry stack[kStackSize];
     t.cur = t.leaf = kEmptyRef;
     t.overflow = false;
-    bool have = false, exhausted = false, overflow = false;
+    t.bad = false;
+    bool have = false, exhausted = false, overflow = false, bad = false;
     uint32_t p = 0;
     for (;;) {
         // lanes without a ray take the next indices (warp-uniform loop; ends when every
@@ -207,6 +208,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
             trav_round(t, bvh, stack);
             if (trav_done(t)) {
                 overflow |= t.overflow;
+                bad |= t.bad;
                 const float3 o = t.r.o, d = t.r.d;
                 if (t.best_id == kNoHit) {
                     write_record(rec, p, o, o, o, 0.0f, -1);
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
         }
     }
     if (overflow && status) atomicOr(status, kStatusStackOverflowBit);
+    if (OCC_CHECKS && bad && status) atomicOr(status, kStatusBadIndexBit);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -297,6 +300,22 @@ __global__ void k_debug_philox(const uint32_t* in, int64_t n, uint32_t* out) {
     out[4 * i + 1] = w.y;
     out[4 * i + 2] = w.z;
     out[4 * i + 3] = w.w;
+}
+
+// Closest (or any) hit of arbitrary rays: rays[2i] = (o.xyz, tmax), rays[2i+1] = (d.xyz, -).
+__global__ void k_debug_closest_hit(DevBVH bvh, const float4* rays, int64_t n, int any, int32_t* tri,
+                                    float* t, unsigned* status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 a = rays[2 * i], b = rays[2 * i + 1];
+    if (any) {
+        tri[i] = any_hit(bvh, f3(a), f3(b), a.w, status) ? 1 : 0;
+        t[i] = 0.0f;
+        return;
+    }
+    const Hit h = closest_hit(bvh, f3(a), f3(b), a.w, status);
+    tri[i] = h.id == kNoHit ? -1 : (int32_t)h.id;
+    t[i] = h.id == kNoHit ? -1.0f : h.t;
 }
 
 template <int EFFECT>
@@ -428,6 +447,13 @@ cudaError_t launch_pack_gbuffer(const GBufView& gb, float4* out, cudaStream_t s)
     const int64_t n = (int64_t)gb.W * gb.H;
     if (n <= 0) return cudaSuccess;
     k_pack_gbuffer<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(gb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_closest_hit(const DevBVH& bvh, const float4* rays, int64_t n, int any,
+                                     int32_t* tri, float* t, unsigned* status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_debug_closest_hit<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(bvh, rays, n, any, tri, t, status);
     return cudaGetLastError();
 }
 

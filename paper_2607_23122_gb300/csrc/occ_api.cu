@@ -164,7 +164,9 @@ occ::RecView rec_view(const occ_occluders* o) {
     return occ::RecView{base, base + (size_t)o->W * o->H, 0};
 }
 
-occ::DevBVH dev_bvh(const occ_bvh* b) { return occ::DevBVH{b->nodes, b->tris}; }
+occ::DevBVH dev_bvh(const occ_bvh* b) {
+    return occ::DevBVH{b->nodes, b->tris, (uint32_t)b->stats.num_nodes, (uint32_t)b->stats.num_tris};
+}
 
 occ_status launched(occ_ctx* ctx, cudaError_t e, const char* what) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, what);
@@ -509,6 +511,20 @@ OCC_EXPORT occ_status occ_debug_philox(occ_ctx* ctx, const uint32_t* in_dev, int
     if (n < 0 || (n > 0 && (!in_dev || !out_dev))) return fail(ctx, OCC_ERR_INVALID_ARG, "bad arguments");
     return launched(ctx, occ::launch_debug_philox(in_dev, n, out_dev, (cudaStream_t)stream),
                     "philox launch");
+}
+
+OCC_EXPORT occ_status occ_debug_closest_hit(occ_ctx* ctx, const occ_bvh* bvh, const float* rays_dev,
+                                            int64_t n, int32_t any, int32_t* tri_dev, float* t_dev,
+                                            void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if (!bvh || n < 0 || (n > 0 && (!rays_dev || !tri_dev || !t_dev)) || !aligned16(rays_dev))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "bad debug_closest_hit arguments");
+    return launched(ctx,
+                    occ::launch_debug_closest_hit(dev_bvh(bvh), reinterpret_cast<const float4*>(rays_dev),
+                                                  n, any != 0, tri_dev, t_dev, ctx->status,
+                                                  (cudaStream_t)stream),
+                    "debug_closest_hit launch");
 }
 
 OCC_EXPORT occ_status occ_debug_wait_timeout(occ_ctx* ctx, uint32_t spins, void* stream) {

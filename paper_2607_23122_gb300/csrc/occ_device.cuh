@@ -414,6 +414,7 @@ struct Traversal {
     uint32_t cur, leaf;
     int sp;
     bool overflow;
+    bool bad;               // OCC_CHECKS: an index outside the BVH was met
 };
 
 // Starts at `start`: the root (0), any node or leaf reference whose subtree holds every
@@ -426,6 +427,7 @@ __device__ __forceinline__ void trav_init(Traversal& t, float3 o, float3 d, floa
     t.best_slot = kNoHit;
     t.sp = 0;
     t.overflow = false;
+    t.bad = false;
     t.cur = start;
     t.leaf = kEmptyRef;
     if (t.cur != kEmptyRef && is_leaf_ref(t.cur)) {
@@ -445,6 +447,13 @@ __device__ __forceinline__ bool trav_done(const Traversal& t) {
 template <bool ANY = false>
 __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, StackEntry* stack) {
     while (t.cur != kEmptyRef && !is_leaf_ref(t.cur)) {
+#if OCC_CHECKS
+        if (t.cur >= bvh.n_nodes) {
+            t.bad = true;
+            t.cur = t.leaf = kEmptyRef;
+            return;
+        }
+#endif
         uint32_t next;
         visit_node(bvh, t.cur, t.r, t.tbest, stack, t.sp, t.overflow, &next);
         t.cur = next != kEmptyRef ? next : pop_next(stack, t.sp, t.tbest);
@@ -457,6 +466,13 @@ __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, Stac
     while (t.leaf != kEmptyRef) {
         const uint32_t first = t.leaf & kLeafFirstMask;
         const uint32_t count = ((t.leaf & ~kLeafBit) >> kLeafCountShift) + 1u;
+#if OCC_CHECKS
+        if ((uint64_t)first + count > bvh.n_tris) {
+            t.bad = true;
+            t.cur = t.leaf = kEmptyRef;
+            return;
+        }
+#endif
         for (uint32_t i = 0; i < count; ++i) {
             const float4* tr = bvh.tris + 3ull * (first + i);
             triangle_test(t.r, __ldg(tr), __ldg(tr + 1), __ldg(tr + 2), first + i, t.tbest,
@@ -484,6 +500,7 @@ __device__ __forceinline__ Hit closest_hit(const DevBVH& bvh, float3 o, float3 d
     trav_init(t, o, d, tmax, start);
     while (!trav_done(t)) trav_round(t, bvh, stack);
     if (t.overflow && status) atomicOr(status, kStatusStackOverflowBit);
+    if (OCC_CHECKS && t.bad && status) atomicOr(status, kStatusBadIndexBit);
     Hit h;
     h.id = t.best_id;
     h.slot = t.best_slot;
@@ -499,6 +516,7 @@ __device__ __forceinline__ bool any_hit(const DevBVH& bvh, float3 o, float3 d, f
     trav_init(t, o, d, tmax, 0u);
     while (!trav_done(t)) trav_round<true>(t, bvh, stack);
     if (t.overflow && status) atomicOr(status, kStatusStackOverflowBit);
+    if (OCC_CHECKS && t.bad && status) atomicOr(status, kStatusBadIndexBit);
     return t.best_id != kNoHit;
 }
 

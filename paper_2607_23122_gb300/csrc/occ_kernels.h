@@ -79,6 +79,8 @@ cudaError_t launch_weighted_sum(const float* vis, int64_t P, const LightWeights&
                                 cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t* in, int64_t n, uint32_t* out, cudaStream_t s);
 cudaError_t launch_debug_wait_timeout(uint32_t spins, unsigned* status, cudaStream_t s);
+cudaError_t launch_debug_closest_hit(const DevBVH& bvh, const float4* rays, int64_t n, int any,
+                                     int32_t* tri, float* t, unsigned* status, cudaStream_t s);
 cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
                               const LightParams& light, uint64_t seed, uint32_t sample,
                               float4* out, cudaStream_t s);

@@ -47,6 +47,13 @@ constexpr uint32_t kStatusBadIndexBit = 1u << 2;
 struct DevBVH {
     const BvhNode* nodes;
     const float4* tris;
+    uint32_t n_nodes = 0, n_tris = 0;   // bounds the OCC_CHECKS build verifies
 };
+
+// OCC_CHECKS=1: the traversal checks every node and triangle index it follows against the
+// BVH's sizes; a bad one sets kStatusBadIndexBit and ends that ray (no trap).
+#ifndef OCC_CHECKS
+#define OCC_CHECKS 0
+#endif
 
 }  // namespace occ

@@ -84,6 +84,7 @@ struct occ_server {
     uint64_t next_id = 1;
     Clock::time_point t0;
     int64_t batches = 0, views_batched = 0, views_single = 0;
+    int32_t inject_left = 0;           // allocation failures still to inject (worker only)
 
     int64_t now() const {
         return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t0).count();
@@ -116,6 +117,10 @@ occ_status launch_batch(occ_server* S, Slot& sl, const std::vector<Req*>& rs) {
     cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return OCC_ERR_CUDA;
     size_t allocated = 0;
+    if (S->inject_left > 0) {
+        --S->inject_left;   // injected fault: the pool has no room for this batch
+        return OCC_ERR_OOM;
+    }
     for (Req* q : rs) {
         e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&q->mem), (size_t)q->bytes, S->pool, s);
         if (e != cudaSuccess) {
@@ -354,7 +359,8 @@ OCC_EXPORT occ_status occ_server_create(occ_ctx* ctx, const occ_bvh* bvh,
     occ_server_config cfg = cfg_in ? *cfg_in : occ_server_config{};
     if (cfg.budget_bytes < 0 || cfg.max_views_per_batch < 0 || cfg.max_views_per_batch > 256 ||
         cfg.max_inflight < 0 || cfg.max_inflight > occ::Scheduler::kMaxInflight ||
-        cfg.max_queued < 0 || cfg.poll_us < 0 || cfg.batch_max_px < 0 || cfg.batch_window_us < 0)
+        cfg.max_queued < 0 || cfg.poll_us < 0 || cfg.batch_max_px < 0 || cfg.batch_window_us < 0 ||
+        cfg.inject_alloc_failures < 0)
         return OCC_ERR_INVALID_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return OCC_ERR_CUDA;
     size_t free_b = 0, total_b = 0;
@@ -371,6 +377,7 @@ OCC_EXPORT occ_status occ_server_create(occ_ctx* ctx, const occ_bvh* bvh,
     S->bvh = bvh;
     S->cfg = cfg;
     S->tune = ctx->tune;
+    S->inject_left = cfg.inject_alloc_failures;
     S->t0 = Clock::now();
     occ_sched_config sc{cfg.budget_bytes, cfg.max_views_per_batch, cfg.max_inflight, cfg.max_queued};
     S->sched = new occ::Scheduler(sc);

@@ -369,6 +369,24 @@ def occ_frame_noalloc(gb: GBuffer, bvh: BVH, effect: int, radius: float, light, 
     return out
 
 
+def occ_debug_closest_hit(ctx: Context, bvh: BVH, o, d, tmax, any_hit: bool = False,
+                          stream=None):
+    """(tri [n] int32, t [n] float32) of arbitrary rays (occ_debug_closest_hit)."""
+    o = np.asarray(o, dtype=np.float32).reshape(-1, 3)
+    d = np.asarray(d, dtype=np.float32).reshape(-1, 3)
+    n = o.shape[0]
+    rays = np.zeros((n, 8), dtype=np.float32)
+    rays[:, :3], rays[:, 3], rays[:, 4:7] = o, np.broadcast_to(np.asarray(tmax, np.float32), (n,)), d
+    dev = torch.device("cuda", ctx.device)
+    r = torch.from_numpy(rays).to(dev)
+    tri = torch.empty(n, dtype=torch.int32, device=dev)
+    t = torch.empty(n, dtype=torch.float32, device=dev)
+    ctx.check(ctx.lib.occ_debug_closest_hit(ctx.handle, bvh.handle, r.data_ptr(), n, int(any_hit),
+                                            tri.data_ptr(), t.data_ptr(), _stream_handle(stream)))
+    ctx.sync(stream)
+    return tri.cpu().numpy(), t.cpu().numpy()
+
+
 def occ_debug_wait_timeout(ctx: Context, spins: int = 1000, stream=None):
     ctx.check(ctx.lib.occ_debug_wait_timeout(ctx.handle, int(spins), _stream_handle(stream)))
 
@@ -577,10 +595,11 @@ class Server:
 
     def __init__(self, ctx: Context, bvh: BVH, budget_bytes: int = 0, max_views_per_batch: int = 0,
                  max_inflight: int = 0, max_queued: int = 0, poll_us: int = 0,
-                 batch_max_px: int = 0, batch_window_us: int = 0):
+                 batch_max_px: int = 0, batch_window_us: int = 0,
+                 inject_alloc_failures: int = 0):
         self.ctx, self.bvh = ctx, bvh          # the BVH must outlive the server
         cfg = N.occ_server_config(budget_bytes, max_views_per_batch, max_inflight, max_queued,
-                                  poll_us, batch_max_px, batch_window_us)
+                                  poll_us, batch_max_px, batch_window_us, inject_alloc_failures, 0)
         h = C.c_void_p()
         ctx.check(ctx.lib.occ_server_create(ctx.handle, bvh.handle, C.byref(cfg), C.byref(h)))
         self.handle = h

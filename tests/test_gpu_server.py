@@ -304,3 +304,18 @@ def test_poisson_arrivals_with_concurrent_polling(occ, ctx, c1):
     finally:
         done.set()
         srv.close()
+
+
+def test_injected_allocation_failures_fail_their_requests_only(occ, ctx, c1):
+    """Host-side fault injection: the first two batches find the pool exhausted; their
+    requests finish with OCC_ERR_OOM, later ones run, the server keeps serving."""
+    srv = occ.Server(ctx, c1["bvh"], max_views_per_batch=1, max_inflight=1,
+                     inject_alloc_failures=2)
+    try:
+        ids = [_submit(occ, srv, c1, MIX[k % 3], seed=k)[0] for k in range(6)]
+        res = srv.wait(ids)
+        st = [res[i]["status"] for i in ids]
+        assert st == [OOM, OOM, OK, OK, OK, OK], st
+        assert srv.stats()["reserved_bytes"] == 0
+    finally:
+        srv.close()
