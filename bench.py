@@ -63,8 +63,9 @@ def parse():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--profile-step", action="store_true",
-                    help="launch the hot kernels once each (1080p AO: trace, window reuse, "
-                         "4x2 group reuse) and exit: the case profiled with ncu")
+                    help="launch the hot kernels once each (1080p: AO trace, window reuse, "
+                         "4x2 group reuse, shadow trace, fused AO and shadow trace + 4x2 "
+                         "group reuse) and exit: the case profiled with ncu")
     return ap.parse_args()
 
 
@@ -276,6 +277,38 @@ def shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream) -> dict:
     return {"trace_ms": tr["ms"], "reuse_offsets_k8_ms": ru["ms"], "light8_boxmean_ms": lb["ms"],
             "reuse_group4x2_ms": gr["ms"], "ms_per_frame": tr["ms"] + ru["ms"],
             "light": "1 x 0.5 rectangle at z=4 facing down"}
+
+
+def fused_frame(occ, ctx, gb, bvh, rec, out, flush, stream) -> dict:
+    """Steps 1-3 with 4x2 shared groups (K = 8, biased) on the same frame: the separate
+    trace + group-reuse launches against the fused kernel that keeps the occluders on chip
+    (AO on both of its launch paths, and shadows)."""
+    import synth
+    light = synth.light_c3().as_array()
+    g, B = occ.Pattern.group(4, 2), occ.OCC_EST_BIASED
+
+    def ao_separate(st):
+        occ.occ_trace_ao(ctx, gb, bvh, RADIUS, 1, 0, out=rec, stream=st)
+        occ.occ_reuse_ao(ctx, gb, rec, g, 8, B, out=out, stream=st)
+
+    def sh_separate(st):
+        occ.occ_trace_shadow(ctx, gb, bvh, light, 1, 0, out=rec, stream=st)
+        occ.occ_reuse_shadow(ctx, gb, rec, g, 8, B, out=out, stream=st)
+
+    res = {"ao_separate_ms": time_kernel(ao_separate, flush, stream, 100)["ms"]}
+    try:
+        for path in (1, 2):
+            occ.occ_set_tuning(ctx, fused_ao_path=path)
+            res[f"ao_fused_path{path}_ms"] = time_kernel(
+                lambda st: occ.occ_trace_reuse_ao(ctx, gb, bvh, RADIUS, 1, 0, g, 8, B, out=out,
+                                                  stream=st), flush, stream, 100)["ms"]
+    finally:
+        occ.occ_set_tuning(ctx)
+    res["shadow_separate_ms"] = time_kernel(sh_separate, flush, stream, 100)["ms"]
+    res["shadow_fused_ms"] = time_kernel(
+        lambda st: occ.occ_trace_reuse_shadow(ctx, gb, bvh, light, 1, 0, g, 8, B, out=out,
+                                              stream=st), flush, stream, 100)["ms"]
+    return res
 
 
 PACKED_GROUP_BYTES_PER_PX = 30   # x 12, octahedral n 4, offsets 6, octahedral n_z 4, out 4
@@ -540,6 +573,7 @@ def run_ours(args):
                                         out=out, stream=st), flush, stream, 200)
         extra["shadow"] = shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream)
         extra["packed"] = packed_frame(occ, ctx, gb, bvh, pat, out, flush, stream)
+        extra["fused"] = fused_frame(occ, ctx, gb, bvh, rec, out, flush, stream)
         if not args.no_quality:
             extra["quality"] = quality_leg(occ, ctx, gb, bvh, pat)
         if not args.no_serving:
@@ -597,6 +631,7 @@ def run_ours(args):
             "packed_frame": dict(extra["packed"],
                                  group_frac_hbm=P * PACKED_GROUP_BYTES_PER_PX
                                  / (extra["packed"]["reuse_group4x2_ms"] * 1e-3) / 1e9 / hbm),
+            "fused_group4x2_frame": extra["fused"],
             "bvh": {"nodes": st["num_nodes"], "depth": st["depth"], "bytes": st["bytes"],
                     "build_s": st["build_seconds"]},
         }
@@ -668,6 +703,7 @@ def profile_step():
     """One launch of each hot kernel on the 1080p AO frame, untimed (ncu captures)."""
     import torch
 
+    import synth
     from paper_2607_23122_gb300 import occ
     ctx = occ.Context(0)
     scene, cam, offs = scene_inputs()
@@ -678,6 +714,11 @@ def profile_step():
     occ.occ_trace_ao(ctx, gb, bvh, RADIUS, 1, 0, out=rec)
     occ.occ_reuse_ao(ctx, gb, rec, occ.Pattern.offsets_of(offs), K, occ.OCC_EST_BIASED, out=out)
     occ.occ_reuse_ao(ctx, gb, rec, occ.Pattern.group(4, 2), 8, occ.OCC_EST_BIASED, out=out)
+    occ.occ_trace_shadow(ctx, gb, bvh, synth.light_c3().as_array(), 1, 0, out=rec)
+    occ.occ_trace_reuse_ao(ctx, gb, bvh, RADIUS, 1, 0, occ.Pattern.group(4, 2), 8,
+                           occ.OCC_EST_BIASED, out=out)
+    occ.occ_trace_reuse_shadow(ctx, gb, bvh, synth.light_c3().as_array(), 1, 0,
+                               occ.Pattern.group(4, 2), 8, occ.OCC_EST_BIASED, out=out)
     ctx.sync()
     print(json.dumps({"profile_step": "ok", "checksum": float(out.double().sum())}))
 

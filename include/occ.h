@@ -211,6 +211,28 @@ occ_status occ_reuse_shadow(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occlu
                             const occ_pattern* pattern, int32_t K, int32_t estimator,
                             const occ_bvh* bvh_or_null, float* out, void* stream);
 
+/* Alg. 1 steps 1-3 in one kernel for a shared-group pattern (Sec. 5, "Reuse
+ * Implementation": a group's rays run in neighbouring lanes of a warp and exchange their
+ * occluders there).  The estimate equals occ_trace_ao followed by occ_reuse_ao with FP32
+ * records, without storing the records in device memory.  pattern: OCC_PAT_GROUP with
+ * gw x gh = 2x1, 2x2, 4x2 or 4x4 (K = gw * gh), anything else OCC_ERR_UNSUPPORTED;
+ * estimator NOREUSE, BIASED, UNBIASED or BOXMEAN (UNBIASED traces its validation rays
+ * in the same kernel).  occ_or_null: NULL, or a record buffer (W/H/format/data set as for
+ * occ_trace_ao) that also receives the step-1 records, header filled; the estimate
+ * uses the FP32 occluders either way.  out: device float[H][W].  Uses the context's work
+ * counter like occ_trace_ao. */
+occ_status occ_trace_reuse_ao(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh,
+                              float radius, uint64_t seed, uint32_t sample,
+                              const occ_pattern* pattern, int32_t K, int32_t estimator,
+                              occ_occluders* occ_or_null, float* out, void* stream);
+
+/* Alg. 2 steps 1-3 in one kernel (shadow counterpart of occ_trace_reuse_ao; BIASED keeps
+ * the all-blocked guard of Sec. 4.4). */
+occ_status occ_trace_reuse_shadow(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh,
+                                  const occ_rect_light* light, uint64_t seed, uint32_t sample,
+                                  const occ_pattern* pattern, int32_t K, int32_t estimator,
+                                  occ_occluders* occ_or_null, float* out, void* stream);
+
 /* Several rectangular lights (Sec. 6.2, "Multiple Lights"): out = sum over l of
  * weights_host[l] * V_l, where V_l is light l's shadow visibility from its own step-1
  * trace (key seed + l, sample `sample`) into recs[l] and its own reuse with `estimator`
@@ -275,6 +297,8 @@ typedef struct {
     int32_t reuse_tile_rows;     /* TMA window kernel: receiver rows per tile (4, 8, 16) */
     int32_t reuse_window_path;   /* window patterns: 1 TMA tile kernel, 2 per-receiver kernel */
     int32_t batch_ctas_per_sm;   /* persistent batched kernels: CTAs per SM (1 .. 16) */
+    int32_t fused_ao_path;       /* occ_trace_reuse_ao: 1 one CTA per 16 x 8 tile, 2 persistent
+                                    CTAs refilling whole groups from the context's counter */
 } occ_tuning;
 occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t);
 occ_status occ_get_tuning(const occ_ctx* ctx, occ_tuning* t);

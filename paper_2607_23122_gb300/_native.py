@@ -56,7 +56,7 @@ class occ_view(C.Structure):
 
 class occ_tuning(C.Structure):
     _fields_ = [("reuse_tile_rows", c_int32), ("reuse_window_path", c_int32),
-                ("batch_ctas_per_sm", c_int32)]
+                ("batch_ctas_per_sm", c_int32), ("fused_ao_path", c_int32)]
 
 
 class occ_bvh_stats(C.Structure):
@@ -128,6 +128,13 @@ SIGNATURES = {
     "occ_reuse_shadow": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), C.POINTER(occ_occluders),
                                    C.POINTER(occ_pattern), c_int32, c_int32, c_void_p, c_void_p,
                                    c_void_p]),
+    "occ_trace_reuse_ao": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p, c_float,
+                                     c_uint64, c_uint32, C.POINTER(occ_pattern), c_int32, c_int32,
+                                     c_void_p, c_void_p, c_void_p]),
+    "occ_trace_reuse_shadow": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p,
+                                         C.POINTER(occ_rect_light), c_uint64, c_uint32,
+                                         C.POINTER(occ_pattern), c_int32, c_int32, c_void_p,
+                                         c_void_p, c_void_p]),
     "occ_frame_host": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
                                  c_int32, c_float, C.POINTER(occ_rect_light), c_uint64, c_uint32,
                                  C.POINTER(occ_pattern), c_int32, c_int32, c_void_p, c_void_p]),

@@ -20,12 +20,10 @@
 
 #include "occ_device.cuh"
 #include "occ_kernels.h"
+#include "occ_path.cuh"
 
 namespace occ {
 namespace {
-
-constexpr float kSupportSlack = 1.0f + 1.0f / 65536.0f;
-constexpr float kValidateTmax = 1.0f + 1.0f / 1024.0f;
 
 struct ReuseArgs {
     GBufView gb;
@@ -37,39 +35,6 @@ struct ReuseArgs {
     float* out;
     unsigned* status;
 };
-
-__device__ __forceinline__ RectLight make_light_dev(const LightParams& p) {
-    RectLight L;
-    L.c = make_float3(p.c[0], p.c[1], p.c[2]);
-    L.eu = make_float3(p.eu[0], p.eu[1], p.eu[2]);
-    L.ev = make_float3(p.ev[0], p.ev[1], p.ev[2]);
-    L.n = normalize3(cross3(L.eu, L.ev));
-    L.inv_eu2 = 1.0f / dot3(L.eu, L.eu);
-    L.inv_ev2 = 1.0f / dot3(L.ev, L.ev);
-    L.lim = 0.5f * kSupportSlack;
-    return L;
-}
-
-// Receiver data needed by the density of each effect.
-struct Recv {
-    float3 x;
-    float3 n;       // AO: normal.  Shadow: (n_L.(c - x), (x - c).eu, (x - c).ev)
-    bool valid;
-};
-
-template <int EFFECT>
-__device__ __forceinline__ Recv make_recv(float3 x, float3 n, bool valid, const RectLight& L) {
-    Recv r;
-    r.x = x;
-    r.valid = valid;
-    if (EFFECT == kAO) {
-        r.n = n;
-    } else {
-        const float3 xc = sub3(r.x, L.c);
-        r.n = make_float3(-dot3(L.n, xc), dot3(xc, L.eu), dot3(xc, L.ev));
-    }
-    return r;
-}
 
 // Receiver data of pixel q, from either G-buffer format.
 template <int EFFECT>
@@ -90,48 +55,6 @@ __device__ __forceinline__ int fetch_cand(const RecView& rec, int q, float3 xsrc
     *z = f3(r0);
     *nz = f3(__ldg(rec.r1 + q));
     return tri;
-}
-
-// Eq. 15 without Occ and 1/pi: max(0, n_x.d) max(0, -n_z.d) / r^4 inside the radius.
-__device__ __forceinline__ float dens_ao(float3 z, float3 nz, const Recv& r, float R2s) {
-    const float3 d = sub3(z, r.x);
-    const float r2 = dot3(d, d);
-    const float a = dot3(r.n, d);
-    const float b = -dot3(nz, d);
-    const bool ok = (a > 0.0f) & (b > 0.0f) & (r2 > 0.0f) & (r2 <= R2s);
-    return ok ? __fdividef(a * b, r2 * r2) : 0.0f;
-}
-
-// Eqs. 20-21 without Occ and 1/Area: the ray x + s d meets the light plane at
-// s_L = n_L.(c - x) / n_L.d (> 1, hitting the emitting side); y' = x + s_L d must lie
-// in the rectangle; J = s_L^2 (-n_z.d) / (-n_L.d).
-__device__ __forceinline__ float dens_sh(float3 z, float3 nz, const Recv& r, const RectLight& L) {
-    const float3 d = sub3(z, r.x);
-    const float nd = dot3(L.n, d);
-    const float cz = -dot3(nz, d);
-    if (!(nd < 0.0f) || !(cz > 0.0f)) return 0.0f;
-    const float inv = 1.0f / nd;
-    const float sL = r.n.x * inv;
-    if (!(sL > 1.0f)) return 0.0f;
-    const float a = fmaf(sL, dot3(d, L.eu), r.n.y) * L.inv_eu2;
-    const float b = fmaf(sL, dot3(d, L.ev), r.n.z) * L.inv_ev2;
-    if (fabsf(a) > L.lim || fabsf(b) > L.lim) return 0.0f;
-    return sL * sL * cz * (-inv);
-}
-
-template <int EFFECT>
-__device__ __forceinline__ float density(float3 z, float3 nz, const Recv& r, float R2s,
-                                         const RectLight& L) {
-    if (EFFECT == kAO) return dens_ao(z, nz, r, R2s);
-    return dens_sh(z, nz, r, L);
-}
-
-// Eq. 7 for a reused candidate: the closest hit from x toward z (t in (0, 1 + 2^-10]
-// in units of z - x) is z's own triangle.
-__device__ __forceinline__ bool first_hit(const DevBVH& bvh, float3 x, float3 z, uint32_t tri,
-                                          unsigned* status) {
-    const Hit h = closest_hit(bvh, x, sub3(z, x), kValidateTmax, status);
-    return h.id == tri;
 }
 
 int sm_count() {
@@ -189,7 +112,7 @@ __device__ __forceinline__ void reuse_pixel(const ReuseArgs& a, int x, int y) {
         return;
     }
     RectLight L;
-    if (EFFECT == kShadow) L = make_light_dev(a.lp);
+    if (EFFECT == kShadow) L = make_light(a.lp);
     int mem[MAXK];
     int self;
     const int n = gather_members<MAXK>(a.pat, a.gb, x, y, mem, &self);
@@ -276,7 +199,7 @@ __global__ void __launch_bounds__(128) k_reuse_light(ReuseArgs a, uint64_t seed,
         a.out[i] = 1.0f;
         return;
     }
-    const RectLight L = make_light_dev(a.lp);
+    const RectLight L = make_light(a.lp);
     int mem[MAXK];
     int self;
     const int n = gather_members<MAXK>(a.pat, a.gb, x, y, mem, &self);
@@ -347,7 +270,7 @@ __global__ void k_debug_mis(ReuseArgs a, const int32_t* pix, int32_t npix, int32
     const int i = pix[t];
     const int x = i % a.gb.W, y = i / a.gb.W;
     RectLight L;
-    if (EFFECT == kShadow) L = make_light_dev(a.lp);
+    if (EFFECT == kShadow) L = make_light(a.lp);
     int mem[kMaxMembers];
     int self;
     int n = 0;
@@ -418,7 +341,7 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
     const bool inside = x < a.gb.W && y < a.gb.H;
     const int i = inside ? y * a.gb.W + x : 0;
     RectLight L;
-    if (EFFECT == kShadow) L = make_light_dev(a.lp);
+    if (EFFECT == kShadow) L = make_light(a.lp);
 
     float4 P = make_float4(0.0f, 0.0f, 0.0f, 0.0f), N = P;
     float4 R0 = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1)), R1 = P;

@@ -8,6 +8,7 @@
 
 #include "occ_device.cuh"
 #include "occ_kernels.h"
+#include "occ_path.cuh"
 
 namespace occ {
 namespace {
@@ -24,68 +25,6 @@ __device__ __forceinline__ void tile_pixel(int* x, int* y) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     *x = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
     *y = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
-}
-
-__device__ __forceinline__ RectLight make_light(const LightParams& p) {
-    RectLight L;
-    L.c = make_float3(p.c[0], p.c[1], p.c[2]);
-    L.eu = make_float3(p.eu[0], p.eu[1], p.eu[2]);
-    L.ev = make_float3(p.ev[0], p.ev[1], p.ev[2]);
-    L.n = normalize3(cross3(L.eu, L.ev));
-    L.inv_eu2 = 1.0f / dot3(L.eu, L.eu);
-    L.inv_ev2 = 1.0f / dot3(L.ev, L.ev);
-    L.lim = 0.5f * (1.0f + 1.0f / 65536.0f);
-    return L;
-}
-
-// Step-1 ray of receiver p: origin x, direction, tmax.
-template <int EFFECT>
-__device__ __forceinline__ float3 step1_ray(float3 x, float3 n, uint32_t p, float radius,
-                                            const RectLight& L, uint64_t seed, uint32_t sample,
-                                            float* tmax) {
-    if (EFFECT == kAO) {
-        *tmax = radius;
-        return cosine_direction(n, uniform_pair(seed, p, sample, kStreamAO));
-    } else {
-        return light_direction(L, x, uniform_pair(seed, p, sample, kStreamShadow), tmax);
-    }
-}
-
-// Record of receiver p (tri < 0: no occluder) in the buffer's format.
-__device__ __forceinline__ void write_record(const RecView& rec, uint32_t p, float3 xsrc, float3 z,
-                                             float3 nz, float t, int tri) {
-    if (rec.packed) {
-        rec.r0[p] = rec_pack(xsrc, z, nz, tri);
-    } else if (tri < 0) {
-        rec.r0[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
-        rec.r1[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    } else {
-        rec.r0[p] = make_float4(z.x, z.y, z.z, __int_as_float(tri));
-        rec.r1[p] = make_float4(nz.x, nz.y, nz.z, t);
-    }
-}
-
-// Box holding every AO segment of the warp: the valid origins widened by the radius
-// (with slack for the rounding of |direction| and of the box test), reduced over lanes.
-__device__ __forceinline__ uint32_t warp_start_node(const DevBVH& bvh, bool valid, float3 x,
-                                                    float radius) {
-    const float inf = __int_as_float(0x7f800000);
-    float lo[3] = {valid ? x.x : inf, valid ? x.y : inf, valid ? x.z : inf};
-    float hi[3] = {valid ? x.x : -inf, valid ? x.y : -inf, valid ? x.z : -inf};
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = fminf(lo[a], __shfl_xor_sync(0xFFFFFFFFu, lo[a], o));
-            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xFFFFFFFFu, hi[a], o));
-        }
-    }
-    if (!(lo[0] <= hi[0])) return kEmptyRef;   // no valid receiver in this warp
-    const float mag = fmaxf(fmaxf(fmaxf(fabsf(lo[0]), fabsf(hi[0])), fmaxf(fabsf(lo[1]), fabsf(hi[1]))),
-                            fmaxf(fabsf(lo[2]), fabsf(hi[2])));
-    const float pad = radius * 1.001f + 1e-5f * (1.0f + mag);
-    return start_node(bvh, make_float3(lo[0] - pad, lo[1] - pad, lo[2] - pad),
-                      make_float3(hi[0] + pad, hi[1] + pad, hi[2] + pad));
 }
 
 // Step 1 for pixel (x, y) of a view.  Warp-collective (the warp shares its start node):

@@ -236,6 +236,50 @@ occ_status trace_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
                     "trace launch");
 }
 
+occ_status trace_reuse_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const occ_bvh* bvh,
+                              float radius, const occ_rect_light* light, uint64_t seed,
+                              uint32_t sample, const occ_pattern* pattern, int32_t K,
+                              int32_t estimator, occ_occluders* rec, float* out, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if ((st = check_gbuffer(ctx, gb)) != OCC_OK) return st;
+    if (!bvh) return fail(ctx, OCC_ERR_INVALID_ARG, "bvh is NULL");
+    if (bvh->device != ctx->device)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "bvh lives on device %d, context on %d", bvh->device,
+                    ctx->device);
+    if (rec && (st = check_occluders(ctx, gb, rec)) != OCC_OK) return st;
+    if (!out) return fail(ctx, OCC_ERR_INVALID_ARG, "out is NULL");
+    if (effect == OCC_EFFECT_AO && !(radius > 0.0f && std::isfinite(radius)))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "AO radius must be positive and finite");
+    if (effect == OCC_EFFECT_SHADOW && (st = check_light(ctx, light)) != OCC_OK) return st;
+    if (estimator < OCC_EST_NOREUSE || estimator > OCC_EST_BOXMEAN)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "estimator %d invalid for the fused pass", estimator);
+    occ::PatternParams pat;
+    if ((st = make_pattern(ctx, pattern, K, &pat)) != OCC_OK) return st;
+    if (pat.kind != OCC_PAT_GROUP || !occ::frame_group_shape(pat.gw, pat.gh))
+        return fail(ctx, OCC_ERR_UNSUPPORTED,
+                    "the fused pass takes GROUP patterns 2x1, 2x2, 4x2 or 4x4 (got kind %d, %dx%d)",
+                    pat.kind, pat.gw, pat.gh);
+    occ::RecView rv{nullptr, nullptr, 0};
+    if (rec) {
+        rec->effect = effect;
+        rec->radius = effect == OCC_EFFECT_AO ? radius : 0.0f;
+        if (effect == OCC_EFFECT_SHADOW)
+            rec->light = *light;
+        else
+            std::memset(&rec->light, 0, sizeof(rec->light));
+        rec->seed = seed;
+        rec->sample = sample;
+        rv = rec_view(rec);
+    }
+    return launched(ctx,
+                    occ::launch_trace_reuse(effect, estimator, view(gb), dev_bvh(bvh), radius,
+                                            to_params(light), seed, sample, pat.gw, pat.gh, rv, out,
+                                            ctx->status, (cudaStream_t)stream, ctx->counter,
+                                            ctx->tune.fused_ao_path),
+                    "fused trace + reuse launch");
+}
+
 }  // namespace
 
 OCC_EXPORT const char* occ_version(void) { return "occreuse 0.1 (sm_103a)"; }
@@ -300,6 +344,24 @@ OCC_EXPORT occ_status occ_sync(occ_ctx* ctx, void* stream) {
                     (flags & occ::kStatusBadIndexBit) ? "bad index" : "");
     }
     return OCC_OK;
+}
+
+OCC_EXPORT occ_status occ_trace_reuse_ao(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh,
+                                         float radius, uint64_t seed, uint32_t sample,
+                                         const occ_pattern* pattern, int32_t K, int32_t estimator,
+                                         occ_occluders* occ_or_null, float* out, void* stream) {
+    return trace_reuse_common(ctx, OCC_EFFECT_AO, gb, bvh, radius, nullptr, seed, sample, pattern,
+                              K, estimator, occ_or_null, out, stream);
+}
+
+OCC_EXPORT occ_status occ_trace_reuse_shadow(occ_ctx* ctx, const occ_gbuffer* gb,
+                                             const occ_bvh* bvh, const occ_rect_light* light,
+                                             uint64_t seed, uint32_t sample,
+                                             const occ_pattern* pattern, int32_t K,
+                                             int32_t estimator, occ_occluders* occ_or_null,
+                                             float* out, void* stream) {
+    return trace_reuse_common(ctx, OCC_EFFECT_SHADOW, gb, bvh, 0.0f, light, seed, sample, pattern,
+                              K, estimator, occ_or_null, out, stream);
 }
 
 OCC_EXPORT occ_status occ_bvh_build(occ_ctx* ctx, const float* tris_host, int64_t T, occ_bvh** out) {
@@ -788,9 +850,12 @@ OCC_EXPORT occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t) {
         return fail(ctx, OCC_ERR_INVALID_ARG, "reuse_window_path must be 0, 1 or 2");
     if (t->batch_ctas_per_sm < 0 || t->batch_ctas_per_sm > 16)
         return fail(ctx, OCC_ERR_INVALID_ARG, "batch_ctas_per_sm must be in [0, 16]");
+    if (t->fused_ao_path < 0 || t->fused_ao_path > 2)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "fused_ao_path must be 0, 1 or 2");
     ctx->tune.tile_rows = t->reuse_tile_rows;
     ctx->tune.window_path = t->reuse_window_path;
     ctx->tune.batch_per_sm = t->batch_ctas_per_sm;
+    ctx->tune.fused_ao_path = t->fused_ao_path;
     return OCC_OK;
 }
 
@@ -799,6 +864,7 @@ OCC_EXPORT occ_status occ_get_tuning(const occ_ctx* ctx, occ_tuning* t) {
     t->reuse_tile_rows = ctx->tune.tile_rows;
     t->reuse_window_path = ctx->tune.window_path;
     t->batch_ctas_per_sm = ctx->tune.batch_per_sm;
+    t->fused_ao_path = ctx->tune.fused_ao_path;
     return OCC_OK;
 }
 

@@ -90,6 +90,7 @@ struct Tuning {
     int tile_rows = 0;
     int window_path = 0;
     int batch_per_sm = 0;
+    int fused_ao_path = 0;
 };
 
 cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const RecView& rec,
@@ -109,6 +110,16 @@ cudaError_t launch_reuse_batch(const BatchView* views, int n_views, int n_tiles,
 bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const PatternParams& pat,
                        float R2s, const LightParams& light, float* out, unsigned* status,
                        cudaStream_t s, cudaError_t* err, int tile_rows);
+
+// Steps 1-3 in one kernel for GROUP patterns gw x gh in {2x1, 2x2, 4x2, 4x4}
+// (frame_group_shape) and estimators NOREUSE, BIASED, UNBIASED, BOXMEAN; rec.r0 == nullptr
+// stores no records.  mode (AO): 0 default, 1 one CTA per tile, 2 persistent group refill
+// (needs `counter`, reset on `s` before the launch; unbiased always takes mode 1).
+bool frame_group_shape(int gw, int gh);
+cudaError_t launch_trace_reuse(int effect, int estimator, const GBufView& gb, const DevBVH& bvh,
+                               float radius, const LightParams& light, uint64_t seed,
+                               uint32_t sample, int gw, int gh, RecView rec, float* out,
+                               unsigned* status, cudaStream_t s, unsigned* counter, int mode);
 
 cudaError_t launch_debug_mis(int effect, int estimator, const GBufView& gb, const RecView& rec,
                              const PatternParams& pat, float radius, const LightParams& light,

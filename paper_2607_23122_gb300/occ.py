@@ -304,6 +304,38 @@ def occ_reuse_shadow(ctx: Context, gb: GBuffer, occ: Occluders, pattern: Pattern
     return _reuse(ctx.lib.occ_reuse_shadow, ctx, gb, occ, pattern, K, estimator, bvh, out, stream)
 
 
+def occ_trace_reuse_ao(ctx: Context, gb: GBuffer, bvh: BVH, radius: float, seed: int,
+                       sample: int, pattern: Pattern, K: int, estimator: int,
+                       rec: Occluders | None = None, out: torch.Tensor | None = None,
+                       stream=None) -> torch.Tensor:
+    """Steps 1-3 in one kernel for a group pattern (occ_trace_reuse_ao); `rec`, when given,
+    also receives the step-1 records."""
+    if out is None:
+        out = torch.empty((gb.H, gb.W), dtype=torch.float32, device=gb.pos4.device)
+    g = gb.c()
+    ctx.check(ctx.lib.occ_trace_reuse_ao(ctx.handle, C.byref(g), bvh.handle, float(radius),
+                                         int(seed), int(sample), C.byref(pattern.c()), int(K),
+                                         int(estimator), C.byref(rec.c()) if rec is not None else None,
+                                         out.data_ptr(), _stream_handle(stream)))
+    return out
+
+
+def occ_trace_reuse_shadow(ctx: Context, gb: GBuffer, bvh: BVH, light, seed: int, sample: int,
+                           pattern: Pattern, K: int, estimator: int, rec: Occluders | None = None,
+                           out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Shadow counterpart of occ_trace_reuse_ao."""
+    if out is None:
+        out = torch.empty((gb.H, gb.W), dtype=torch.float32, device=gb.pos4.device)
+    g = gb.c()
+    L = _light(light)
+    ctx.check(ctx.lib.occ_trace_reuse_shadow(ctx.handle, C.byref(g), bvh.handle, C.byref(L),
+                                             int(seed), int(sample), C.byref(pattern.c()), int(K),
+                                             int(estimator),
+                                             C.byref(rec.c()) if rec is not None else None,
+                                             out.data_ptr(), _stream_handle(stream)))
+    return out
+
+
 def occ_shadow_lights(ctx: Context, gb: GBuffer, bvh: BVH, lights, weights, seed: int,
                       sample: int, pattern: Pattern, estimator: int, packed: bool = False,
                       stream=None):
@@ -513,8 +545,8 @@ class Batch:
 
 
 def occ_set_tuning(ctx: Context, reuse_tile_rows: int = 0, reuse_window_path: int = 0,
-                   batch_ctas_per_sm: int = 0):
-    t = N.occ_tuning(reuse_tile_rows, reuse_window_path, batch_ctas_per_sm)
+                   batch_ctas_per_sm: int = 0, fused_ao_path: int = 0):
+    t = N.occ_tuning(reuse_tile_rows, reuse_window_path, batch_ctas_per_sm, fused_ao_path)
     ctx.check(ctx.lib.occ_set_tuning(ctx.handle, C.byref(t)))
 
 
