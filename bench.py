@@ -238,7 +238,7 @@ GROUP_BYTES_PER_PX = 52   # x 12, n 12, z 12, n_z 12, out 4
 # DRAM bytes (read + write) per launch from one `ncu --set full` capture of
 # `bench.py --profile-step` (cold L2; profiles/k_*_ao1080p*.md); None once a kernel changes
 NCU_TRAFFIC = {"k_trace_dyn<AO>": None,
-               "k_reuse_tile<AO,9>": 132.799744e6 + 6.98496e6,
+               "k_reuse_tile<AO,8>": None,
                "k_reuse_group<AO,biased,4,2>": 114.168832e6 + 4.692736e6}
 NCU_TRACE_ISSUE_ACTIVE = 0.6594   # smsp__issue_active of k_trace_dyn<AO> in its capture
 
@@ -597,11 +597,11 @@ def run_ours(args):
                       "algorithmic_bytes": trace_bytes,
                       "note": "software traversal is issue/latency bound: issue slots "
                               f"{NCU_TRACE_ISSUE_ACTIVE:.0%} busy under ncu"}
-        reuse_roof = {"kernel": "k_reuse_tile<AO,9> (TMA-staged window)", "bound": "alu",
+        reuse_roof = {"kernel": "k_reuse_tile<AO,8> (TMA-staged window)", "bound": "alu",
                       "achieved": pairs * FLOPS_PER_PAIR_AO / ru / 1e12,
                       "peak": alu_peak / 1e12, "unit": "TFLOP/s",
                       "frac": pairs * FLOPS_PER_PAIR_AO / ru / alu_peak,
-                      "traffic": NCU_TRAFFIC["k_reuse_tile<AO,9>"],
+                      "traffic": NCU_TRAFFIC["k_reuse_tile<AO,8>"],
                       "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x max SM clock"}
         dominant = trace_roof if tr >= ru else reuse_roof
         line = {

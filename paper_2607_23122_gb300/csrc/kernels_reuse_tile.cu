@@ -7,7 +7,9 @@
 // planes -- (TW + halo) x (TH + halo) float4 each, zero-filled outside the image --
 // completing on an mbarrier; every thread then evaluates its receiver's K x K pair
 // densities from shared memory (K receivers held in registers, K candidate records
-// read once each), normalises by P_j = sum_k p(z_j|x_k) and writes 1 - B_i.
+// read once each), normalises by P_j = sum_k p(z_j|x_k) and writes 1 - B_i.  Missing
+// members carry zero receiver terms, whose densities are 0, so the pair loop has no
+// per-member test.
 // Waits on the mbarrier are bounded: on expiry the CTA records kStatusWaitTimeoutBit,
 // drains its copies (again bounded) and returns.
 #include <cuda.h>
@@ -191,18 +193,22 @@ __global__ void __launch_bounds__(512, 1)
             const int sc = (ly + a.hy0) * a.SW + (lx + a.hx0);
             float res = 1.0f;
             if (s_pos[sc].w != 0.0f) {
-                // member slots: fixed order, invalid or outside members masked out
+                // member slots: the receiver first, then the other members in a fixed order;
+                // invalid, outside and unused slots get zero receiver terms, for which
+                // every pair density is 0 (AO: n_x.d = 0; shadow: s_L = 0)
                 int sidx[MAXK];
                 uint32_t vmask = 0;
-                int self = 0;
 #pragma unroll
                 for (int s = 0; s < MAXK; ++s) {
                     sidx[s] = sc;
                     if (s < a.K) {
                         int dx, dy;
                         if (a.kind == 1) {
-                            dx = s % a.gw - (a.gw - 1) / 2;
-                            dy = s / a.gw - (a.gh - 1) / 2;
+                            // the box's centre cell first, then the other cells row-major
+                            const int centre = ((a.gh - 1) / 2) * a.gw + (a.gw - 1) / 2;
+                            const int cell = s == 0 ? centre : (s <= centre ? s - 1 : s);
+                            dx = cell % a.gw - (a.gw - 1) / 2;
+                            dy = cell / a.gw - (a.gh - 1) / 2;
                         } else {
                             dx = s == 0 ? 0 : a.off[s - 1].x;
                             dy = s == 0 ? 0 : a.off[s - 1].y;
@@ -213,13 +219,14 @@ __global__ void __launch_bounds__(512, 1)
                             vmask |= 1u << s;
                             sidx[s] = q;
                         }
-                        if (dx == 0 && dy == 0) self = s;
                     }
                 }
                 float3 rx[MAXK], rt[MAXK];
 #pragma unroll
-                for (int s = 0; s < MAXK; ++s)
+                for (int s = 0; s < MAXK; ++s) {
                     recv_terms<EFFECT>(s_pos[sidx[s]], s_nrm[sidx[s]], L, &rx[s], &rt[s]);
+                    if (!((vmask >> s) & 1u)) rt[s] = make_float3(0.0f, 0.0f, 0.0f);
+                }
                 float B = 0.0f;
                 uint32_t blocked = 0;
 #pragma unroll 1
@@ -229,15 +236,12 @@ __global__ void __launch_bounds__(512, 1)
                     if (__float_as_int(r0.w) < 0) continue;
                     blocked |= 1u << c;
                     const float3 z = f3(r0), nz = f3(s_r1[sidx[c]]);
-                    float Psum = 0.0f, pi = 0.0f;
+                    // slot 0 is the receiver: its density is the numerator
+                    const float pi = pair_density<EFFECT>(z, nz, rx[0], rt[0], a.R2s, L);
+                    float Psum = pi;
 #pragma unroll
-                    for (int s = 0; s < MAXK; ++s) {
-                        if ((vmask >> s) & 1u) {
-                            const float q = pair_density<EFFECT>(z, nz, rx[s], rt[s], a.R2s, L);
-                            Psum += q;
-                            if (s == self) pi = q;
-                        }
-                    }
+                    for (int s = 1; s < MAXK; ++s)
+                        Psum += pair_density<EFFECT>(z, nz, rx[s], rt[s], a.R2s, L);
                     if (pi > 0.0f) B += pi / Psum;
                 }
                 res = 1.0f - B;
@@ -374,11 +378,17 @@ bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const
         !make_map(&maps[2], rec.r0, gb.W, gb.H, a.SW, a.SH) ||
         !make_map(&maps[3], rec.r1, gb.W, gb.H, a.SW, a.SH))
         return false;
+    // slot counts: every slot beyond K costs a density, so the common sizes get their own
     if (effect == kAO)
-        *err = pat.K <= 9 ? launch_t<kAO, 9>(maps, a, smem, sms, s) : launch_t<kAO, 16>(maps, a, smem, sms, s);
+        *err = pat.K <= 4 ? launch_t<kAO, 4>(maps, a, smem, sms, s)
+               : pat.K <= 8 ? launch_t<kAO, 8>(maps, a, smem, sms, s)
+               : pat.K <= 9 ? launch_t<kAO, 9>(maps, a, smem, sms, s)
+                            : launch_t<kAO, 16>(maps, a, smem, sms, s);
     else
-        *err = pat.K <= 9 ? launch_t<kShadow, 9>(maps, a, smem, sms, s)
-                          : launch_t<kShadow, 16>(maps, a, smem, sms, s);
+        *err = pat.K <= 4 ? launch_t<kShadow, 4>(maps, a, smem, sms, s)
+               : pat.K <= 8 ? launch_t<kShadow, 8>(maps, a, smem, sms, s)
+               : pat.K <= 9 ? launch_t<kShadow, 9>(maps, a, smem, sms, s)
+                            : launch_t<kShadow, 16>(maps, a, smem, sms, s);
     return true;
 }
 
