@@ -116,10 +116,25 @@ __device__ __forceinline__ void reuse_pixel(const ReuseArgs& a, int x, int y) {
     int mem[MAXK];
     int self;
     const int n = gather_members<MAXK>(a.pat, a.gb, x, y, mem, &self);
+    // the receiver first, then the other members in pattern order
+#pragma unroll
+    for (int b = MAXK - 1; b >= 1; --b)
+        if (b <= self) mem[b] = mem[b - 1];
+    mem[0] = i;
+    // up to 16 slots every slot is evaluated: unused ones carry zero receiver terms, whose
+    // densities are 0 (AO: n_x.d = 0; shadow: s_L = 0); larger sets test the member count
+    constexpr bool kPadded = MAXK <= 16;
     Recv rk[MAXK];
 #pragma unroll
-    for (int b = 0; b < MAXK; ++b)
-        if (b < n) rk[b] = fetch_recv<EFFECT>(a.gb, mem[b], L);
+    for (int b = 0; b < MAXK; ++b) {
+        if (b < n) {
+            rk[b] = fetch_recv<EFFECT>(a.gb, mem[b], L);
+        } else {
+            rk[b].x = make_float3(0.0f, 0.0f, 0.0f);
+            rk[b].n = rk[b].x;
+            rk[b].valid = false;
+        }
+    }
     float B = 0.0f;
     int blocked = 0;
 #pragma unroll 1
@@ -131,12 +146,12 @@ __device__ __forceinline__ void reuse_pixel(const ReuseArgs& a, int x, int y) {
         float Psum = 0.0f, pi = 0.0f;
 #pragma unroll
         for (int b = 0; b < MAXK; ++b) {
-            if (b < n) {
+            if (kPadded || b < n) {
                 float q = density<EFFECT>(z, nz, rk[b], a.R2s, L);
                 if (EST == kUnbiased && q > 0.0f && b != c)
                     if (!first_hit(a.bvh, rk[b].x, z, (uint32_t)tri, a.status)) q = 0.0f;
                 Psum += q;
-                if (b == self) pi = q;
+                if (b == 0) pi = q;
             }
         }
         if (pi > 0.0f) B += pi / Psum;
@@ -450,6 +465,12 @@ bool launch_group(const ReuseArgs& a, cudaStream_t s) {
 template <int EFFECT, int EST>
 void launch_generic(const ReuseArgs& a, cudaStream_t s) {
     const dim3 grid((unsigned)((a.gb.W + 15) / 16), (unsigned)((a.gb.H + 7) / 8));
+    if constexpr (EST != kUnbiased) {
+        if (a.pat.K <= 8) {
+            k_reuse_generic<EFFECT, EST, 8><<<grid, 128, 0, s>>>(a);
+            return;
+        }
+    }
     if (a.pat.K <= 9)
         k_reuse_generic<EFFECT, EST, 9><<<grid, 128, 0, s>>>(a);
     else if (a.pat.K <= 16)
