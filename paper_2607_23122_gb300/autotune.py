@@ -22,6 +22,7 @@ _LOCK = threading.Lock()
 
 REUSE_CANDIDATES = [
     {"reuse_tile_rows": 16, "reuse_window_path": 1},
+    {"reuse_tile_rows": 16, "reuse_window_path": 3},
     {"reuse_tile_rows": 8, "reuse_window_path": 1},
     {"reuse_tile_rows": 4, "reuse_window_path": 1},
     {"reuse_tile_rows": 0, "reuse_window_path": 2},

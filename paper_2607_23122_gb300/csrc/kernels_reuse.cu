@@ -491,7 +491,7 @@ cudaError_t launch_effect(int est, const ReuseArgs& a, cudaStream_t s, const Tun
             cudaError_t e = cudaSuccess;
             if (!a.gb.packed && !a.rec.packed && tune.window_path != 2 &&
                 launch_reuse_tile(EFFECT, a.gb, a.rec, a.pat, a.R2s, a.lp, a.out, a.status, s, &e,
-                                  tune.tile_rows))
+                                  tune.tile_rows, tune.window_path == 3))
                 return e;
             launch_generic<EFFECT, kBiased>(a, s);
         } else if (!launch_group<EFFECT, kBiased>(a, s)) {

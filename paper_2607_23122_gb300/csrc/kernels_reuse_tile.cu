@@ -136,11 +136,157 @@ __device__ __forceinline__ float pair_density(float3 z, float3 nz, float3 x, flo
     }
 }
 
+// Offset of member slot s of a window: slot 0 is the receiver; a box lists its other cells
+// row-major, an offsets pattern its offsets in order.
+__device__ __forceinline__ int2 member_offset(const TileArgs& a, int s) {
+    if (a.kind == 1) {
+        const int centre = ((a.gh - 1) / 2) * a.gw + (a.gw - 1) / 2;
+        const int cell = s == 0 ? centre : (s <= centre ? s - 1 : s);
+        return make_int2(cell % a.gw - (a.gw - 1) / 2, cell / a.gw - (a.gh - 1) / 2);
+    }
+    return s == 0 ? make_int2(0, 0) : a.off[s - 1];
+}
+
+// Members of the receiver at (x, y), staged index sc: bit s set when slot s is inside the
+// image and a valid receiver.
+template <int MAXK>
+__device__ __forceinline__ uint32_t member_mask(const TileArgs& a, const float4* s_pos, int x,
+                                                int y, int sc) {
+    uint32_t vmask = 0;
+#pragma unroll
+    for (int s = 0; s < MAXK; ++s) {
+        if (s < a.K) {
+            const int2 o = member_offset(a, s);
+            const int px = x + o.x, py = y + o.y;
+            if (px >= 0 && py >= 0 && px < a.W && py < a.H && s_pos[sc + o.y * a.SW + o.x].w != 0.0f)
+                vmask |= 1u << s;
+        }
+    }
+    return vmask;
+}
+
+struct Staged {
+    const float4 *pos, *nrm, *r0, *r1;
+};
+
+// One thread per receiver: its K receivers in registers (missing members carry zero
+// receiver terms, whose densities are 0, so the pair loop has no per-member test).
 template <int EFFECT, int MAXK>
-__global__ void __launch_bounds__(512, 1)
-    k_reuse_tile(const __grid_constant__ CUtensorMap tm_pos, const __grid_constant__ CUtensorMap tm_nrm,
-                 const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ CUtensorMap tm_r1,
-                 const __grid_constant__ TileArgs a) {
+__device__ __forceinline__ void tile_single(const TileArgs& a, const RectLight& L, const Staged& st,
+                                            int x0, int y0) {
+    const int lx = threadIdx.x % a.TW, ly = threadIdx.x / a.TW;
+    const int x = x0 + lx, y = y0 + ly;
+    if (ly >= a.TH || x >= a.W || y >= a.H) return;
+    const int sc = (ly + a.hy0) * a.SW + (lx + a.hx0);
+    float res = 1.0f;
+    if (st.pos[sc].w != 0.0f) {
+        const uint32_t vmask = member_mask<MAXK>(a, st.pos, x, y, sc);
+        float3 rx[MAXK], rt[MAXK];
+#pragma unroll
+        for (int s = 0; s < MAXK; ++s) {
+            const bool v = (vmask >> s) & 1u;
+            int q = sc;
+            if (v) {
+                const int2 o = member_offset(a, s);
+                q = sc + o.y * a.SW + o.x;
+            }
+            recv_terms<EFFECT>(st.pos[q], st.nrm[q], L, &rx[s], &rt[s]);
+            if (!v) rt[s] = make_float3(0.0f, 0.0f, 0.0f);
+        }
+        float B = 0.0f;
+        uint32_t blocked = 0;
+#pragma unroll 1
+        for (int c = 0; c < a.K; ++c) {
+            if (!((vmask >> c) & 1u)) continue;
+            const int2 o = member_offset(a, c);
+            const int q = sc + o.y * a.SW + o.x;
+            const float4 r0 = st.r0[q];
+            if (__float_as_int(r0.w) < 0) continue;
+            blocked |= 1u << c;
+            const float3 z = f3(r0), nz = f3(st.r1[q]);
+            // slot 0 is the receiver: its density is the numerator
+            const float pi = pair_density<EFFECT>(z, nz, rx[0], rt[0], a.R2s, L);
+            float Psum = pi;
+#pragma unroll
+            for (int s = 1; s < MAXK; ++s) Psum += pair_density<EFFECT>(z, nz, rx[s], rt[s], a.R2s, L);
+            if (pi > 0.0f) B += pi / Psum;
+        }
+        res = 1.0f - B;
+        if (EFFECT == kShadow && blocked == vmask) res = 0.0f;   // all-blocked guard
+    }
+    a.out[y * a.W + x] = res;
+}
+
+// Two threads per receiver (twice the resident warps at half the registers each): thread h
+// of the pair holds the member slots 2j + h, and the pair adds its halves of P_j with one
+// shuffle.  Candidates that no lane of the warp has are skipped warp-uniformly, so every
+// lane reaches the shuffle.  A tuning choice (reuse_window_path 3), not the default: at
+// 1080p with 8 disk offsets it measured 0.179 ms for AO against 0.137 ms for tile_single
+// (the doubled candidate loads, member masks and shuffles outweigh the extra warps) and
+// 0.205 against 0.207 ms for shadows.
+template <int EFFECT, int MAXK>
+__device__ __forceinline__ void tile_pairs(const TileArgs& a, const RectLight& L, const Staged& st,
+                                           int x0, int y0) {
+    constexpr int HALF = (MAXK + 1) / 2;
+    const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
+    const int lx = r % a.TW, ly = r / a.TW;
+    const int x = x0 + lx, y = y0 + ly;
+    const bool inside = ly < a.TH && x < a.W && y < a.H;
+    const int sc = (min(ly, a.TH - 1) + a.hy0) * a.SW + (lx + a.hx0);
+    const bool rvalid = inside && st.pos[sc].w != 0.0f;
+    const uint32_t vmask = rvalid ? member_mask<MAXK>(a, st.pos, x, y, sc) : 0u;
+    float3 rx[HALF], rt[HALF];
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) {
+        const int s = 2 * j + h;
+        const bool v = (vmask >> s) & 1u;
+        int q = sc;
+        if (v) {
+            const int2 o = member_offset(a, s);
+            q = sc + o.y * a.SW + o.x;
+        }
+        recv_terms<EFFECT>(st.pos[q], st.nrm[q], L, &rx[j], &rt[j]);
+        if (!v) rt[j] = make_float3(0.0f, 0.0f, 0.0f);
+    }
+    float B = 0.0f;
+    uint32_t blocked = 0;
+#pragma unroll 1
+    for (int c = 0; c < a.K; ++c) {
+        const int2 o = member_offset(a, c);
+        const int q = sc + o.y * a.SW + o.x;
+        bool cand = (vmask >> c) & 1u;
+        float4 r0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (cand) {
+            r0 = st.r0[q];
+            cand = __float_as_int(r0.w) >= 0;
+        }
+        if (!__any_sync(0xFFFFFFFFu, cand)) continue;
+        blocked |= (uint32_t)cand << c;
+        const float3 z = f3(r0), nz = cand ? f3(st.r1[q]) : make_float3(0.0f, 0.0f, 0.0f);
+        float pi = 0.0f, part = 0.0f;
+#pragma unroll
+        for (int j = 0; j < HALF; ++j) {
+            const float d = pair_density<EFFECT>(z, nz, rx[j], rt[j], a.R2s, L);
+            part += d;
+            if (j == 0) pi = d;   // slot 0 (the receiver) on the pair's first thread
+        }
+        const float Psum = part + __shfl_xor_sync(0xFFFFFFFFu, part, 1);
+        if (cand && h == 0 && pi > 0.0f) B += pi / Psum;
+    }
+    if (h == 0 && inside) {
+        float res = 1.0f;
+        if (rvalid) {
+            res = 1.0f - B;
+            if (EFFECT == kShadow && blocked == vmask) res = 0.0f;   // all-blocked guard
+        }
+        a.out[y * a.W + x] = res;
+    }
+}
+
+template <int EFFECT, int MAXK, bool PAIRS>
+__device__ __forceinline__ void reuse_tile_body(const CUtensorMap* tm_pos, const CUtensorMap* tm_nrm,
+                                                const CUtensorMap* tm_r0, const CUtensorMap* tm_r1,
+                                                const TileArgs& a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     // bulk-tensor copies need 128-byte aligned shared destinations: align the base (the
@@ -155,8 +301,6 @@ __global__ void __launch_bounds__(512, 1)
     __syncthreads();
     RectLight L;
     if (EFFECT == kShadow) L = tile_light(a.lp);
-    const int lx = threadIdx.x % a.TW, ly = threadIdx.x / a.TW;
-    const bool active_thread = ly < a.TH;
     // buffer b holds the G-buffer and record planes of one staged tile
     auto issue = [&](int tile, int b) {
         float4* base = reinterpret_cast<float4*>(smem) + (size_t)b * 4 * plane;
@@ -164,10 +308,10 @@ __global__ void __launch_bounds__(512, 1)
         const int gx = 4 * (x0 - a.hx0), gy = y0 - a.hy0;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bar[b], bytes);
-        tma_load_2d(base, &tm_pos, gx, gy, &bar[b]);
-        tma_load_2d(base + plane, &tm_nrm, gx, gy, &bar[b]);
-        tma_load_2d(base + 2 * plane, &tm_r0, gx, gy, &bar[b]);
-        tma_load_2d(base + 3 * plane, &tm_r1, gx, gy, &bar[b]);
+        tma_load_2d(base, tm_pos, gx, gy, &bar[b]);
+        tma_load_2d(base + plane, tm_nrm, gx, gy, &bar[b]);
+        tma_load_2d(base + 2 * plane, tm_r0, gx, gy, &bar[b]);
+        tma_load_2d(base + 3 * plane, tm_r1, gx, gy, &bar[b]);
     };
     uint32_t parity[2] = {0u, 0u};
     if (threadIdx.x == 0 && (int)blockIdx.x < a.n_tiles) issue(blockIdx.x, 0);
@@ -183,76 +327,37 @@ __global__ void __launch_bounds__(512, 1)
             return;
         }
         parity[b] ^= 1u;
-        const float4* s_pos = reinterpret_cast<const float4*>(smem) + (size_t)b * 4 * plane;
-        const float4* s_nrm = s_pos + plane;
-        const float4* s_r0 = s_pos + 2 * plane;
-        const float4* s_r1 = s_pos + 3 * plane;
+        Staged st;
+        st.pos = reinterpret_cast<const float4*>(smem) + (size_t)b * 4 * plane;
+        st.nrm = st.pos + plane;
+        st.r0 = st.pos + 2 * plane;
+        st.r1 = st.pos + 3 * plane;
         const int x0 = (tile % a.tiles_x) * a.TW, y0 = (tile / a.tiles_x) * a.TH;
-        const int x = x0 + lx, y = y0 + ly;
-        if (active_thread && x < a.W && y < a.H) {
-            const int sc = (ly + a.hy0) * a.SW + (lx + a.hx0);
-            float res = 1.0f;
-            if (s_pos[sc].w != 0.0f) {
-                // member slots: the receiver first, then the other members in a fixed order;
-                // invalid, outside and unused slots get zero receiver terms, for which
-                // every pair density is 0 (AO: n_x.d = 0; shadow: s_L = 0)
-                int sidx[MAXK];
-                uint32_t vmask = 0;
-#pragma unroll
-                for (int s = 0; s < MAXK; ++s) {
-                    sidx[s] = sc;
-                    if (s < a.K) {
-                        int dx, dy;
-                        if (a.kind == 1) {
-                            // the box's centre cell first, then the other cells row-major
-                            const int centre = ((a.gh - 1) / 2) * a.gw + (a.gw - 1) / 2;
-                            const int cell = s == 0 ? centre : (s <= centre ? s - 1 : s);
-                            dx = cell % a.gw - (a.gw - 1) / 2;
-                            dy = cell / a.gw - (a.gh - 1) / 2;
-                        } else {
-                            dx = s == 0 ? 0 : a.off[s - 1].x;
-                            dy = s == 0 ? 0 : a.off[s - 1].y;
-                        }
-                        const int px = x + dx, py = y + dy;
-                        const int q = sc + dy * a.SW + dx;
-                        if (px >= 0 && py >= 0 && px < a.W && py < a.H && s_pos[q].w != 0.0f) {
-                            vmask |= 1u << s;
-                            sidx[s] = q;
-                        }
-                    }
-                }
-                float3 rx[MAXK], rt[MAXK];
-#pragma unroll
-                for (int s = 0; s < MAXK; ++s) {
-                    recv_terms<EFFECT>(s_pos[sidx[s]], s_nrm[sidx[s]], L, &rx[s], &rt[s]);
-                    if (!((vmask >> s) & 1u)) rt[s] = make_float3(0.0f, 0.0f, 0.0f);
-                }
-                float B = 0.0f;
-                uint32_t blocked = 0;
-#pragma unroll 1
-                for (int c = 0; c < a.K; ++c) {
-                    if (!((vmask >> c) & 1u)) continue;
-                    const float4 r0 = s_r0[sidx[c]];
-                    if (__float_as_int(r0.w) < 0) continue;
-                    blocked |= 1u << c;
-                    const float3 z = f3(r0), nz = f3(s_r1[sidx[c]]);
-                    // slot 0 is the receiver: its density is the numerator
-                    const float pi = pair_density<EFFECT>(z, nz, rx[0], rt[0], a.R2s, L);
-                    float Psum = pi;
-#pragma unroll
-                    for (int s = 1; s < MAXK; ++s)
-                        Psum += pair_density<EFFECT>(z, nz, rx[s], rt[s], a.R2s, L);
-                    if (pi > 0.0f) B += pi / Psum;
-                }
-                res = 1.0f - B;
-                if (EFFECT == kShadow && blocked == vmask) res = 0.0f;   // all-blocked guard
-            }
-            a.out[y * a.W + x] = res;
-        }
+        if (PAIRS)
+            tile_pairs<EFFECT, MAXK>(a, L, st, x0, y0);
+        else
+            tile_single<EFFECT, MAXK>(a, L, st, x0, y0);
         __syncthreads();   // buffer b is free for the copies issued next
         if (a.stages == 1 && threadIdx.x == 0 && tile + (int)gridDim.x < a.n_tiles)
             issue(tile + gridDim.x, 0);
     }
+}
+
+template <int EFFECT, int MAXK>
+__global__ void __launch_bounds__(512, 1)
+    k_reuse_tile(const __grid_constant__ CUtensorMap tm_pos, const __grid_constant__ CUtensorMap tm_nrm,
+                 const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ CUtensorMap tm_r1,
+                 const __grid_constant__ TileArgs a) {
+    reuse_tile_body<EFFECT, MAXK, false>(&tm_pos, &tm_nrm, &tm_r0, &tm_r1, a);
+}
+
+template <int EFFECT, int MAXK>
+__global__ void __launch_bounds__(1024, 1)
+    k_reuse_tile_pairs(const __grid_constant__ CUtensorMap tm_pos,
+                       const __grid_constant__ CUtensorMap tm_nrm,
+                       const __grid_constant__ CUtensorMap tm_r0,
+                       const __grid_constant__ CUtensorMap tm_r1, const __grid_constant__ TileArgs a) {
+    reuse_tile_body<EFFECT, MAXK, true>(&tm_pos, &tm_nrm, &tm_r0, &tm_r1, a);
 }
 
 // The bounded-wait path of the kernel above, exercised on purpose: one thread polls a barrier
@@ -300,13 +405,13 @@ bool make_map(CUtensorMap* m, const void* base, int W, int H, int SW, int SH) {
 }
 
 template <int EFFECT, int MAXK>
-cudaError_t launch_t(const CUtensorMap* maps, const TileArgs& a, size_t smem, int sms,
+cudaError_t launch_t(const CUtensorMap* maps, const TileArgs& a, size_t smem, int sms, bool pairs,
                      cudaStream_t s) {
-    auto k = k_reuse_tile<EFFECT, MAXK>;
+    auto k = pairs ? k_reuse_tile_pairs<EFFECT, MAXK> : k_reuse_tile<EFFECT, MAXK>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = a.n_tiles < sms ? a.n_tiles : sms;
-    k<<<grid, a.TW * a.TH, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
+    k<<<grid, a.TW * a.TH * (pairs ? 2 : 1), smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
     return cudaPeekAtLastError();
 }
 
@@ -322,7 +427,7 @@ cudaError_t launch_debug_wait_timeout(uint32_t spins, unsigned* status, cudaStre
 
 bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const PatternParams& pat,
                        float R2s, const LightParams& light, float* out, unsigned* status,
-                       cudaStream_t s, cudaError_t* err, int tile_rows) {
+                       cudaStream_t s, cudaError_t* err, int tile_rows, bool pairs) {
     *err = cudaSuccess;
     if (pat.kind != 1 && pat.kind != 2) return false;
     if (pat.K > 16) return false;
@@ -380,15 +485,15 @@ bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const
         return false;
     // slot counts: every slot beyond K costs a density, so the common sizes get their own
     if (effect == kAO)
-        *err = pat.K <= 4 ? launch_t<kAO, 4>(maps, a, smem, sms, s)
-               : pat.K <= 8 ? launch_t<kAO, 8>(maps, a, smem, sms, s)
-               : pat.K <= 9 ? launch_t<kAO, 9>(maps, a, smem, sms, s)
-                            : launch_t<kAO, 16>(maps, a, smem, sms, s);
+        *err = pat.K <= 4 ? launch_t<kAO, 4>(maps, a, smem, sms, pairs, s)
+               : pat.K <= 8 ? launch_t<kAO, 8>(maps, a, smem, sms, pairs, s)
+               : pat.K <= 9 ? launch_t<kAO, 9>(maps, a, smem, sms, pairs, s)
+                            : launch_t<kAO, 16>(maps, a, smem, sms, pairs, s);
     else
-        *err = pat.K <= 4 ? launch_t<kShadow, 4>(maps, a, smem, sms, s)
-               : pat.K <= 8 ? launch_t<kShadow, 8>(maps, a, smem, sms, s)
-               : pat.K <= 9 ? launch_t<kShadow, 9>(maps, a, smem, sms, s)
-                            : launch_t<kShadow, 16>(maps, a, smem, sms, s);
+        *err = pat.K <= 4 ? launch_t<kShadow, 4>(maps, a, smem, sms, pairs, s)
+               : pat.K <= 8 ? launch_t<kShadow, 8>(maps, a, smem, sms, pairs, s)
+               : pat.K <= 9 ? launch_t<kShadow, 9>(maps, a, smem, sms, pairs, s)
+                            : launch_t<kShadow, 16>(maps, a, smem, sms, pairs, s);
     return true;
 }
 

@@ -846,8 +846,8 @@ OCC_EXPORT occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t) {
     if (t->reuse_tile_rows != 0 && t->reuse_tile_rows != 4 && t->reuse_tile_rows != 8 &&
         t->reuse_tile_rows != 16)
         return fail(ctx, OCC_ERR_INVALID_ARG, "reuse_tile_rows must be 0, 4, 8 or 16");
-    if (t->reuse_window_path < 0 || t->reuse_window_path > 2)
-        return fail(ctx, OCC_ERR_INVALID_ARG, "reuse_window_path must be 0, 1 or 2");
+    if (t->reuse_window_path < 0 || t->reuse_window_path > 3)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "reuse_window_path must be 0, 1, 2 or 3");
     if (t->batch_ctas_per_sm < 0 || t->batch_ctas_per_sm > 16)
         return fail(ctx, OCC_ERR_INVALID_ARG, "batch_ctas_per_sm must be in [0, 16]");
     if (t->fused_ao_path < 0 || t->fused_ao_path > 2)

@@ -109,7 +109,7 @@ cudaError_t launch_reuse_batch(const BatchView* views, int n_views, int n_tiles,
 // the pattern or its staging does not fit that kernel.
 bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const PatternParams& pat,
                        float R2s, const LightParams& light, float* out, unsigned* status,
-                       cudaStream_t s, cudaError_t* err, int tile_rows);
+                       cudaStream_t s, cudaError_t* err, int tile_rows, bool pairs);
 
 // Steps 1-3 in one kernel for GROUP patterns gw x gh in {2x1, 2x2, 4x2, 4x4}
 // (frame_group_shape) and estimators NOREUSE, BIASED, UNBIASED, BOXMEAN; rec.r0 == nullptr

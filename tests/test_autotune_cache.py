@@ -21,5 +21,5 @@ def test_cache_round_trip_and_bad_files(tmp_path, monkeypatch):
 
 def test_candidates_are_valid_tuning_values():
     for c in autotune.REUSE_CANDIDATES:
-        assert c["reuse_tile_rows"] in (0, 4, 8, 16) and c["reuse_window_path"] in (1, 2)
+        assert c["reuse_tile_rows"] in (0, 4, 8, 16) and c["reuse_window_path"] in (1, 2, 3)
     assert all(0 <= c["batch_ctas_per_sm"] <= 16 for c in autotune.BATCH_CANDIDATES)

@@ -229,6 +229,9 @@ def test_batch_arguments_rejected(occ, ctx, c1):
 @pytest.mark.parametrize("cfg", [dict(reuse_window_path=1, reuse_tile_rows=4),
                                  dict(reuse_window_path=1, reuse_tile_rows=8),
                                  dict(reuse_window_path=1, reuse_tile_rows=16),
+                                 dict(reuse_window_path=3, reuse_tile_rows=4),
+                                 dict(reuse_window_path=3, reuse_tile_rows=8),
+                                 dict(reuse_window_path=3, reuse_tile_rows=16),
                                  dict(reuse_window_path=2)])
 @pytest.mark.parametrize("pname", ["box3x3", "disk8"])
 @pytest.mark.parametrize("effect", [AO, SH])
