@@ -4,6 +4,7 @@
                 offsets (TMA window kernel) and 4x2 groups (warp group kernel)
   1080p shadow  same scene, 1 x 0.5 light at z = 4: trace; biased disk-8 and 4x2-group
                 reuse; the light-sample averaging baseline (box mean over 4x2 groups)
+  1080p fused   AO and shadow trace + 4x2 group reuse in one kernel (occ_trace_reuse_*)
   4K packed     ~4M-triangle terrain, AO and shadows with packed G-buffer and records:
                 trace; biased reuse with K = 16 (4x4 groups and a 16-member disk)
 
@@ -67,14 +68,22 @@ def _pats(occ):
             "disk16": occ.Pattern.offsets_of(synth.disk_offsets(16, 15.0, seed=3))}
 
 
+def _oracle_trace(orc, hd, effect):
+    """The oracle's step 1 of the 1080p frame (seed 1, sample 0), computed once per effect."""
+    cache = hd.setdefault("orec", {})
+    if effect not in cache:
+        cache[effect] = orc.trace(hd["osc"], effect, hd["pos"], hd["nrm"], radius=0.5,
+                                  light=synth.light_c3().as_array(), seed=1, sample=0)
+    return cache[effect]
+
+
 @pytest.mark.parametrize("effect", [AO, SH])
 def test_1080p_trace_and_reuse(orc, occ, ctx, hd, effect):
     light = synth.light_c3().as_array()
     o = (occ.occ_trace_ao(ctx, hd["gb"], hd["bvh"], 0.5, 1, 0) if effect == AO else
          occ.occ_trace_shadow(ctx, hd["gb"], hd["bvh"], light, 1, 0))
     ctx.sync()
-    orec, omg = orc.trace(hd["osc"], effect, hd["pos"], hd["nrm"], radius=0.5, light=light,
-                          seed=1, sample=0)
+    orec, omg = _oracle_trace(orc, hd, effect)
     tr = P.compare_trace(o, orec, omg, hd["valid"], hd["pos"], f"1080p trace {effect}")
     assert tr["hits"] > 0.05 * hd["valid"].sum()
     r0, r1 = P.to_f32_records(orec)
@@ -91,6 +100,36 @@ def test_1080p_trace_and_reuse(orc, occ, ctx, hd, effect):
         res = P.compare_out(g.cpu().numpy(), ref, mg, hd["valid"], f"1080p {pname} est {est}")
         print(f"1080p effect {effect} {pname} est {est}: max err {res['max_err']:.2e}, "
               f"{tr['mismatch']} trace flips")
+
+
+@pytest.mark.parametrize("effect", [AO, SH])
+def test_1080p_fused_trace_and_group_reuse(orc, occ, ctx, hd, effect):
+    """The fused kernel on the bench's 1080p frame (4x2 groups, biased, default launch path):
+    its step-1 records against the oracle's trace, its estimate against the oracle on those
+    records and against the separate group reuse of the same records."""
+    light = synth.light_c3().as_array()
+    pat = _pats(occ)["group4x2"]
+    rec = occ.Occluders.empty(1080, 1920, hd["gb"].pos4.device)
+    if effect == AO:
+        g = occ.occ_trace_reuse_ao(ctx, hd["gb"], hd["bvh"], 0.5, 1, 0, pat, 8, BIASED, rec=rec)
+    else:
+        g = occ.occ_trace_reuse_shadow(ctx, hd["gb"], hd["bvh"], light, 1, 0, pat, 8, BIASED,
+                                       rec=rec)
+    ctx.sync()
+    orec, omg = _oracle_trace(orc, hd, effect)
+    tr = P.compare_trace(rec, orec, omg, hd["valid"], hd["pos"], f"1080p fused trace {effect}")
+    assert tr["hits"] > 0.05 * hd["valid"].sum()
+    r0, r1, _ = P.gpu_records(rec)
+    g = g.cpu().numpy()
+    ref, mg = orc.reuse(None, effect, hd["pos"], hd["nrm"], P.widen_records(r0, r1),
+                        pat.as_tuple(), BIASED, radius=0.5, light=light)
+    res = P.compare_out(g, ref, mg, hd["valid"], f"1080p fused est {effect}")
+    fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
+    sep = fn(ctx, hd["gb"], rec, pat, 8, BIASED)
+    ctx.sync()
+    d = np.abs(g - sep.cpu().numpy())
+    assert d.max() <= 1e-6, float(d.max())
+    print(f"1080p fused effect {effect}: max err {res['max_err']:.2e}, {tr['mismatch']} trace flips")
 
 
 @pytest.mark.parametrize("effect", [AO, SH])
