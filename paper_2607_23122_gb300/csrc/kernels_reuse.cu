@@ -489,7 +489,7 @@ cudaError_t launch_effect(int est, const ReuseArgs& a, cudaStream_t s, const Tun
     } else if (est == kBiased) {
         if (a.pat.kind != 0) {
             cudaError_t e = cudaSuccess;
-            if (!a.gb.packed && !a.rec.packed && tune.window_path != 2 &&
+            if (tune.window_path != 2 &&
                 launch_reuse_tile(EFFECT, a.gb, a.rec, a.pat, a.R2s, a.lp, a.out, a.status, s, &e,
                                   tune.tile_rows, tune.window_path == 3))
                 return e;

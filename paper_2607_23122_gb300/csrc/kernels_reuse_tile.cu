@@ -1,9 +1,11 @@
 // kernels_reuse_tile.cu -- biased occluder reuse (Eq. 18 AO / Eq. 24 shadow) for window
 // patterns (a centred box or shared offsets), with the receiver tile and the halo its
-// neighbour sets reach staged in shared memory by the Tensor Memory Accelerator.
+// neighbour sets reach staged in shared memory by the Tensor Memory Accelerator.  Either
+// format: FP32 (G-buffer and record planes, four float4 planes) or packed (two 16-byte
+// planes, decoded from shared memory).
 //
 // Persistent CTAs walk the image in TW x TH receiver tiles.  For each tile one thread
-// issues four 2D bulk-tensor copies (cp.async.bulk.tensor) of the G-buffer and record
+// issues four (FP32) or two (packed) 2D bulk-tensor copies (cp.async.bulk.tensor) of the G-buffer and record
 // planes -- (TW + halo) x (TH + halo) float4 each, zero-filled outside the image --
 // completing on an mbarrier; every thread then evaluates its receiver's K x K pair
 // densities from shared memory (K receivers held in registers, K candidate records
@@ -126,7 +128,9 @@ __device__ __forceinline__ float pair_density(float3 z, float3 nz, float3 x, flo
         const float nd = dot3(L.n, d);
         const float cz = -dot3(nz, d);
         if (!(nd < 0.0f) || !(cz > 0.0f)) return 0.0f;
-        const float inv = 1.0f / nd;
+        // approximate reciprocal (a few ulp): moves s_L and J far less than the 1e-5 output
+        // tolerance; only support tests within that margin of their threshold can flip
+        const float inv = __fdividef(1.0f, nd);
         const float sL = t.x * inv;
         if (!(sL > 1.0f)) return 0.0f;
         const float a = fmaf(sL, dot3(d, L.eu), t.y) * L.inv_eu2;
@@ -149,29 +153,67 @@ __device__ __forceinline__ int2 member_offset(const TileArgs& a, int s) {
 
 // Members of the receiver at (x, y), staged index sc: bit s set when slot s is inside the
 // image and a valid receiver.
-template <int MAXK>
+// Validity of a staged G-buffer entry: FP32 w = 1 / 0; packed w = octahedral code, with
+// one code reserved for background.
+template <bool PACKED>
+__device__ __forceinline__ bool staged_valid(float4 P) {
+    return PACKED ? __float_as_uint(P.w) != kOctInvalid : P.w != 0.0f;
+}
+
+template <int MAXK, bool PACKED>
 __device__ __forceinline__ uint32_t member_mask(const TileArgs& a, const float4* s_pos, int x,
-                                                int y, int sc) {
+                                                int y, int sc, int* sidx = nullptr) {
     uint32_t vmask = 0;
 #pragma unroll
     for (int s = 0; s < MAXK; ++s) {
+        if (sidx) sidx[s] = sc;
         if (s < a.K) {
             const int2 o = member_offset(a, s);
             const int px = x + o.x, py = y + o.y;
-            if (px >= 0 && py >= 0 && px < a.W && py < a.H && s_pos[sc + o.y * a.SW + o.x].w != 0.0f)
+            const int q = sc + o.y * a.SW + o.x;
+            if (px >= 0 && py >= 0 && px < a.W && py < a.H && staged_valid<PACKED>(s_pos[q])) {
                 vmask |= 1u << s;
+                if (sidx) sidx[s] = q;
+            }
         }
     }
     return vmask;
 }
 
 struct Staged {
-    const float4 *pos, *nrm, *r0, *r1;
+    const float4 *pos, *nrm, *r0, *r1;   // packed: pos and r0 only
 };
+
+// Receiver terms of staged pixel q in either format.
+template <int EFFECT, bool PACKED>
+__device__ __forceinline__ void staged_recv(const Staged& st, int q, const RectLight& L, float3* x,
+                                            float3* t) {
+    const float4 P = st.pos[q];
+    float4 N;
+    if (PACKED) {
+        const float3 n = oct_decode(__float_as_uint(P.w));
+        N = make_float4(n.x, n.y, n.z, 0.0f);
+    } else {
+        N = st.nrm[q];
+    }
+    recv_terms<EFFECT>(P, N, L, x, t);
+}
+
+// Candidate of staged pixel q whose record word 0 is r0 (triangle id >= 0): occluder point
+// and normal in either format.
+template <bool PACKED>
+__device__ __forceinline__ void staged_cand(const Staged& st, int q, float4 r0, float3* z, float3* nz) {
+    if (PACKED) {
+        rec_unpack(r0, f3(st.pos[q]), z, nz);
+    } else {
+        *z = f3(r0);
+        *nz = f3(st.r1[q]);
+    }
+}
 
 // One thread per receiver: its K receivers in registers (missing members carry zero
 // receiver terms, whose densities are 0, so the pair loop has no per-member test).
-template <int EFFECT, int MAXK>
+template <int EFFECT, int MAXK, bool PACKED>
 __device__ __forceinline__ void tile_single(const TileArgs& a, const RectLight& L, const Staged& st,
                                             int x0, int y0) {
     const int lx = threadIdx.x % a.TW, ly = threadIdx.x / a.TW;
@@ -179,37 +221,43 @@ __device__ __forceinline__ void tile_single(const TileArgs& a, const RectLight& 
     if (ly >= a.TH || x >= a.W || y >= a.H) return;
     const int sc = (ly + a.hy0) * a.SW + (lx + a.hx0);
     float res = 1.0f;
-    if (st.pos[sc].w != 0.0f) {
-        const uint32_t vmask = member_mask<MAXK>(a, st.pos, x, y, sc);
+    if (staged_valid<PACKED>(st.pos[sc])) {
+        // staged index of every member slot (the receiver's own for missing members)
+        int sidx[MAXK];
+        const uint32_t vmask = member_mask<MAXK, PACKED>(a, st.pos, x, y, sc, sidx);
         float3 rx[MAXK], rt[MAXK];
 #pragma unroll
         for (int s = 0; s < MAXK; ++s) {
-            const bool v = (vmask >> s) & 1u;
-            int q = sc;
-            if (v) {
-                const int2 o = member_offset(a, s);
-                q = sc + o.y * a.SW + o.x;
-            }
-            recv_terms<EFFECT>(st.pos[q], st.nrm[q], L, &rx[s], &rt[s]);
-            if (!v) rt[s] = make_float3(0.0f, 0.0f, 0.0f);
+            staged_recv<EFFECT, PACKED>(st, sidx[s], L, &rx[s], &rt[s]);
+            if (!((vmask >> s) & 1u)) rt[s] = make_float3(0.0f, 0.0f, 0.0f);
         }
         float B = 0.0f;
         uint32_t blocked = 0;
-#pragma unroll 1
-        for (int c = 0; c < a.K; ++c) {
-            if (!((vmask >> c) & 1u)) continue;
-            const int2 o = member_offset(a, c);
-            const int q = sc + o.y * a.SW + o.x;
+        auto candidate = [&](int c) {
+            if (!((vmask >> c) & 1u)) return;
+            const int q = sidx[c];
             const float4 r0 = st.r0[q];
-            if (__float_as_int(r0.w) < 0) continue;
+            if (__float_as_int(r0.w) < 0) return;
             blocked |= 1u << c;
-            const float3 z = f3(r0), nz = f3(st.r1[q]);
+            float3 z, nz;
+            staged_cand<PACKED>(st, q, r0, &z, &nz);
             // slot 0 is the receiver: its density is the numerator
             const float pi = pair_density<EFFECT>(z, nz, rx[0], rt[0], a.R2s, L);
             float Psum = pi;
 #pragma unroll
             for (int s = 1; s < MAXK; ++s) Psum += pair_density<EFFECT>(z, nz, rx[s], rt[s], a.R2s, L);
             if (pi > 0.0f) B += pi / Psum;
+        };
+        // AO: the unrolled candidate loop keeps the member indices in registers (1080p,
+        // 8 disk offsets: 0.129 against 0.134 ms rolled); the shadow density's branches
+        // favour the rolled loop (0.199 against 0.204 ms)
+        if (EFFECT == kAO) {
+#pragma unroll
+            for (int c = 0; c < MAXK; ++c)
+                if (c < a.K) candidate(c);
+        } else {
+#pragma unroll 1
+            for (int c = 0; c < a.K; ++c) candidate(c);
         }
         res = 1.0f - B;
         if (EFFECT == kShadow && blocked == vmask) res = 0.0f;   // all-blocked guard
@@ -234,7 +282,7 @@ __device__ __forceinline__ void tile_pairs(const TileArgs& a, const RectLight& L
     const bool inside = ly < a.TH && x < a.W && y < a.H;
     const int sc = (min(ly, a.TH - 1) + a.hy0) * a.SW + (lx + a.hx0);
     const bool rvalid = inside && st.pos[sc].w != 0.0f;
-    const uint32_t vmask = rvalid ? member_mask<MAXK>(a, st.pos, x, y, sc) : 0u;
+    const uint32_t vmask = rvalid ? member_mask<MAXK, false>(a, st.pos, x, y, sc) : 0u;
     float3 rx[HALF], rt[HALF];
 #pragma unroll
     for (int j = 0; j < HALF; ++j) {
@@ -283,7 +331,7 @@ __device__ __forceinline__ void tile_pairs(const TileArgs& a, const RectLight& L
     }
 }
 
-template <int EFFECT, int MAXK, bool PAIRS>
+template <int EFFECT, int MAXK, bool PAIRS, bool PACKED>
 __device__ __forceinline__ void reuse_tile_body(const CUtensorMap* tm_pos, const CUtensorMap* tm_nrm,
                                                 const CUtensorMap* tm_r0, const CUtensorMap* tm_r1,
                                                 const TileArgs& a) {
@@ -292,8 +340,9 @@ __device__ __forceinline__ void reuse_tile_body(const CUtensorMap* tm_pos, const
     // bulk-tensor copies need 128-byte aligned shared destinations: align the base (the
     // launch adds 128 bytes of slack) and round every plane up to a multiple of 128 bytes
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    constexpr int kPlanes = PACKED ? 2 : 4;                   // packed: G-buffer, records
     const int plane = ((a.SW * a.SH + 7) / 8) * 8;          // float4 per plane
-    const uint32_t bytes = 4u * (uint32_t)(a.SW * a.SH) * 16u;   // bytes the copies deliver
+    const uint32_t bytes = (uint32_t)kPlanes * (uint32_t)(a.SW * a.SH) * 16u;   // bytes delivered
     if (threadIdx.x == 0) {
         mbar_init(&bar[0]);
         mbar_init(&bar[1]);
@@ -303,15 +352,20 @@ __device__ __forceinline__ void reuse_tile_body(const CUtensorMap* tm_pos, const
     if (EFFECT == kShadow) L = tile_light(a.lp);
     // buffer b holds the G-buffer and record planes of one staged tile
     auto issue = [&](int tile, int b) {
-        float4* base = reinterpret_cast<float4*>(smem) + (size_t)b * 4 * plane;
+        float4* base = reinterpret_cast<float4*>(smem) + (size_t)b * kPlanes * plane;
         const int x0 = (tile % a.tiles_x) * a.TW, y0 = (tile / a.tiles_x) * a.TH;
         const int gx = 4 * (x0 - a.hx0), gy = y0 - a.hy0;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bar[b], bytes);
-        tma_load_2d(base, tm_pos, gx, gy, &bar[b]);
-        tma_load_2d(base + plane, tm_nrm, gx, gy, &bar[b]);
-        tma_load_2d(base + 2 * plane, tm_r0, gx, gy, &bar[b]);
-        tma_load_2d(base + 3 * plane, tm_r1, gx, gy, &bar[b]);
+        if (PACKED) {
+            tma_load_2d(base, tm_pos, gx, gy, &bar[b]);
+            tma_load_2d(base + plane, tm_r0, gx, gy, &bar[b]);
+        } else {
+            tma_load_2d(base, tm_pos, gx, gy, &bar[b]);
+            tma_load_2d(base + plane, tm_nrm, gx, gy, &bar[b]);
+            tma_load_2d(base + 2 * plane, tm_r0, gx, gy, &bar[b]);
+            tma_load_2d(base + 3 * plane, tm_r1, gx, gy, &bar[b]);
+        }
     };
     uint32_t parity[2] = {0u, 0u};
     if (threadIdx.x == 0 && (int)blockIdx.x < a.n_tiles) issue(blockIdx.x, 0);
@@ -328,27 +382,33 @@ __device__ __forceinline__ void reuse_tile_body(const CUtensorMap* tm_pos, const
         }
         parity[b] ^= 1u;
         Staged st;
-        st.pos = reinterpret_cast<const float4*>(smem) + (size_t)b * 4 * plane;
-        st.nrm = st.pos + plane;
-        st.r0 = st.pos + 2 * plane;
-        st.r1 = st.pos + 3 * plane;
+        st.pos = reinterpret_cast<const float4*>(smem) + (size_t)b * kPlanes * plane;
+        if (PACKED) {
+            st.nrm = nullptr;
+            st.r0 = st.pos + plane;
+            st.r1 = nullptr;
+        } else {
+            st.nrm = st.pos + plane;
+            st.r0 = st.pos + 2 * plane;
+            st.r1 = st.pos + 3 * plane;
+        }
         const int x0 = (tile % a.tiles_x) * a.TW, y0 = (tile / a.tiles_x) * a.TH;
         if (PAIRS)
             tile_pairs<EFFECT, MAXK>(a, L, st, x0, y0);
         else
-            tile_single<EFFECT, MAXK>(a, L, st, x0, y0);
+            tile_single<EFFECT, MAXK, PACKED>(a, L, st, x0, y0);
         __syncthreads();   // buffer b is free for the copies issued next
         if (a.stages == 1 && threadIdx.x == 0 && tile + (int)gridDim.x < a.n_tiles)
             issue(tile + gridDim.x, 0);
     }
 }
 
-template <int EFFECT, int MAXK>
+template <int EFFECT, int MAXK, bool PACKED>
 __global__ void __launch_bounds__(512, 1)
     k_reuse_tile(const __grid_constant__ CUtensorMap tm_pos, const __grid_constant__ CUtensorMap tm_nrm,
                  const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ CUtensorMap tm_r1,
                  const __grid_constant__ TileArgs a) {
-    reuse_tile_body<EFFECT, MAXK, false>(&tm_pos, &tm_nrm, &tm_r0, &tm_r1, a);
+    reuse_tile_body<EFFECT, MAXK, false, PACKED>(&tm_pos, &tm_nrm, &tm_r0, &tm_r1, a);
 }
 
 template <int EFFECT, int MAXK>
@@ -357,7 +417,7 @@ __global__ void __launch_bounds__(1024, 1)
                        const __grid_constant__ CUtensorMap tm_nrm,
                        const __grid_constant__ CUtensorMap tm_r0,
                        const __grid_constant__ CUtensorMap tm_r1, const __grid_constant__ TileArgs a) {
-    reuse_tile_body<EFFECT, MAXK, true>(&tm_pos, &tm_nrm, &tm_r0, &tm_r1, a);
+    reuse_tile_body<EFFECT, MAXK, true, false>(&tm_pos, &tm_nrm, &tm_r0, &tm_r1, a);
 }
 
 // The bounded-wait path of the kernel above, exercised on purpose: one thread polls a barrier
@@ -406,12 +466,14 @@ bool make_map(CUtensorMap* m, const void* base, int W, int H, int SW, int SH) {
 
 template <int EFFECT, int MAXK>
 cudaError_t launch_t(const CUtensorMap* maps, const TileArgs& a, size_t smem, int sms, bool pairs,
-                     cudaStream_t s) {
-    auto k = pairs ? k_reuse_tile_pairs<EFFECT, MAXK> : k_reuse_tile<EFFECT, MAXK>;
+                     bool packed, cudaStream_t s) {
+    auto k = packed ? k_reuse_tile<EFFECT, MAXK, true>
+             : pairs ? k_reuse_tile_pairs<EFFECT, MAXK> : k_reuse_tile<EFFECT, MAXK, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = a.n_tiles < sms ? a.n_tiles : sms;
-    k<<<grid, a.TW * a.TH * (pairs ? 2 : 1), smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
+    k<<<grid, a.TW * a.TH * (pairs && !packed ? 2 : 1), smem, s>>>(maps[0], maps[1], maps[2], maps[3],
+                                                                  a);
     return cudaPeekAtLastError();
 }
 
@@ -430,6 +492,9 @@ bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const
                        cudaStream_t s, cudaError_t* err, int tile_rows, bool pairs) {
     *err = cudaSuccess;
     if (pat.kind != 1 && pat.kind != 2) return false;
+    if ((gb.packed != 0) != (rec.packed != 0)) return false;
+    const bool packed = gb.packed != 0;
+    const size_t planes = packed ? 2 : 4;
     if (pat.K > 16) return false;
     const int hx = pat.halo[0] + pat.halo[1], hy = pat.halo[2] + pat.halo[3];
     const int SW = kTileW + hx;
@@ -444,7 +509,7 @@ bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const
     size_t smem = 0;
     for (; TH >= 4; TH /= 2) {
         if (hy + TH > 256) continue;
-        smem = (size_t)4 * (((size_t)SW * (TH + hy) + 7) / 8 * 8) * 16;   // 128-byte planes
+        smem = planes * (((size_t)SW * (TH + hy) + 7) / 8 * 8) * 16;   // 128-byte planes
         if (2 * smem + 1024 <= (size_t)max_smem) {
             stages = 2;
             smem = 2 * smem + 128;
@@ -478,22 +543,30 @@ bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const
     a.out = out;
     a.status = status;
     CUtensorMap maps[4];
-    if (!make_map(&maps[0], gb.pos, gb.W, gb.H, a.SW, a.SH) ||
-        !make_map(&maps[1], gb.nrm, gb.W, gb.H, a.SW, a.SH) ||
-        !make_map(&maps[2], rec.r0, gb.W, gb.H, a.SW, a.SH) ||
-        !make_map(&maps[3], rec.r1, gb.W, gb.H, a.SW, a.SH))
+    if (packed) {
+        // the kernel reads the packed G-buffer and record planes only
+        if (!make_map(&maps[0], gb.pos, gb.W, gb.H, a.SW, a.SH) ||
+            !make_map(&maps[2], rec.r0, gb.W, gb.H, a.SW, a.SH))
+            return false;
+        maps[1] = maps[0];
+        maps[3] = maps[2];
+    } else if (!make_map(&maps[0], gb.pos, gb.W, gb.H, a.SW, a.SH) ||
+               !make_map(&maps[1], gb.nrm, gb.W, gb.H, a.SW, a.SH) ||
+               !make_map(&maps[2], rec.r0, gb.W, gb.H, a.SW, a.SH) ||
+               !make_map(&maps[3], rec.r1, gb.W, gb.H, a.SW, a.SH)) {
         return false;
+    }
     // slot counts: every slot beyond K costs a density, so the common sizes get their own
     if (effect == kAO)
-        *err = pat.K <= 4 ? launch_t<kAO, 4>(maps, a, smem, sms, pairs, s)
-               : pat.K <= 8 ? launch_t<kAO, 8>(maps, a, smem, sms, pairs, s)
-               : pat.K <= 9 ? launch_t<kAO, 9>(maps, a, smem, sms, pairs, s)
-                            : launch_t<kAO, 16>(maps, a, smem, sms, pairs, s);
+        *err = pat.K <= 4 ? launch_t<kAO, 4>(maps, a, smem, sms, pairs, packed, s)
+               : pat.K <= 8 ? launch_t<kAO, 8>(maps, a, smem, sms, pairs, packed, s)
+               : pat.K <= 9 ? launch_t<kAO, 9>(maps, a, smem, sms, pairs, packed, s)
+                            : launch_t<kAO, 16>(maps, a, smem, sms, pairs, packed, s);
     else
-        *err = pat.K <= 4 ? launch_t<kShadow, 4>(maps, a, smem, sms, pairs, s)
-               : pat.K <= 8 ? launch_t<kShadow, 8>(maps, a, smem, sms, pairs, s)
-               : pat.K <= 9 ? launch_t<kShadow, 9>(maps, a, smem, sms, pairs, s)
-                            : launch_t<kShadow, 16>(maps, a, smem, sms, pairs, s);
+        *err = pat.K <= 4 ? launch_t<kShadow, 4>(maps, a, smem, sms, pairs, packed, s)
+               : pat.K <= 8 ? launch_t<kShadow, 8>(maps, a, smem, sms, pairs, packed, s)
+               : pat.K <= 9 ? launch_t<kShadow, 9>(maps, a, smem, sms, pairs, packed, s)
+                            : launch_t<kShadow, 16>(maps, a, smem, sms, pairs, packed, s);
     return true;
 }
 
