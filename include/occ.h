@@ -255,6 +255,19 @@ occ_status occ_frame_host(occ_ctx* ctx, const occ_bvh* bvh, int32_t effect,
                           uint32_t sample, const occ_pattern* pattern, int32_t K,
                           int32_t estimator, float* out_host, void* stream);
 
+/* occ_frame_host without the final wait: enqueues the same copies and launches on
+ * `stream` and returns.  out_host holds the estimate once `stream` has completed;
+ * occ_sync(ctx, stream) waits for it and reports device checks.  The context's frame
+ * workspace stays in use until then, so one context carries one such frame at a time: to
+ * overlap consecutive frames (the copies of one with the kernels of the other), give each
+ * frame in flight its own context and stream.  The host buffers must stay valid (pinned,
+ * for the copies to run asynchronously) until the stream completes. */
+occ_status occ_frame_host_async(occ_ctx* ctx, const occ_bvh* bvh, int32_t effect,
+                                const float* pos4_host, const float* nrm4_host, int32_t W,
+                                int32_t H, float radius, const occ_rect_light* light,
+                                uint64_t seed, uint32_t sample, const occ_pattern* pattern,
+                                int32_t K, int32_t estimator, float* out_host, void* stream);
+
 /* ---- batched frames, captured batches and tuning ----------------------------- */
 
 /* One view of a batched frame.  gb and rec describe caller-owned buffers (either

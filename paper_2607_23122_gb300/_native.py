@@ -138,6 +138,10 @@ SIGNATURES = {
     "occ_frame_host": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
                                  c_int32, c_float, C.POINTER(occ_rect_light), c_uint64, c_uint32,
                                  C.POINTER(occ_pattern), c_int32, c_int32, c_void_p, c_void_p]),
+    "occ_frame_host_async": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_int32,
+                                       c_int32, c_float, C.POINTER(occ_rect_light), c_uint64,
+                                       c_uint32, C.POINTER(occ_pattern), c_int32, c_int32,
+                                       c_void_p, c_void_p]),
     "occ_frame_noalloc": (c_int32, [C.POINTER(occ_gbuffer), c_void_p, c_int32, c_float,
                                     C.POINTER(occ_rect_light), c_uint64, c_uint32,
                                     C.POINTER(occ_pattern), c_int32, c_int32, c_void_p, c_void_p,

@@ -20,6 +20,8 @@
 // receives a copy of step 1 in its own format.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "occ_device.cuh"
 #include "occ_kernels.h"
 #include "occ_path.cuh"
@@ -277,13 +279,17 @@ cudaError_t launch_shape(const FrameArgs& a, int mode, unsigned* counter, cudaSt
     const unsigned tx = (unsigned)((a.gb.W + 15) / 16), ty = (unsigned)((a.gb.H + 7) / 8);
     if (EFFECT == kAO && mode == 2 && a.est != kUnbiased && counter) {
         constexpr int K = GW * GH;
-        static int ctas = 0;   // persistent grid: resident CTAs per SM x SMs
+        // persistent grid: resident CTAs per SM x SMs (computed once; threads that race
+        // here compute the same value)
+        static std::atomic<int> cached{0};
+        int ctas = cached.load(std::memory_order_relaxed);
         if (!ctas) {
             int per_sm = 1;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_frame_group_dyn<GW, GH>, 128,
                                                               0) != cudaSuccess || per_sm < 1)
                 per_sm = 1;
             ctas = per_sm * sms();
+            cached.store(ctas, std::memory_order_relaxed);
         }
         const uint32_t n_groups = tx * ty * 4u * (uint32_t)(32 / K);
         const unsigned blocks = (unsigned)ctas < tx * ty ? (unsigned)ctas : tx * ty;

@@ -6,6 +6,8 @@
 // receivers and touch the same BVH nodes (short AO rays stay local).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "occ_device.cuh"
 #include "occ_kernels.h"
 #include "occ_path.cuh"
@@ -298,17 +300,21 @@ cudaError_t launch_trace(int effect, const GBufView& gb, const DevBVH& bvh, floa
     const dim3 grid = tile_grid(gb.W, gb.H);
     if (OCC_TRACE_DYN && counter && effect == kAO) {
         const uint32_t n_idx = grid.x * grid.y * 128u;
-        static int ctas[2] = {0, 0};   // persistent grid: resident CTAs per SM x SMs
+        // persistent grid: resident CTAs per SM x SMs (computed once; threads that race
+        // here compute the same value)
+        static std::atomic<int> ctas[2];
         const int ei = effect == kAO ? 0 : 1;
-        if (!ctas[ei]) {
+        int n = ctas[ei].load(std::memory_order_relaxed);
+        if (!n) {
             int dev = 0, sms = 1, per_sm = 1;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &per_sm, effect == kAO ? k_trace_dyn<kAO> : k_trace_dyn<kShadow>, 128, 0);
-            ctas[ei] = (per_sm > 0 ? per_sm : 1) * sms;
+            n = (per_sm > 0 ? per_sm : 1) * sms;
+            ctas[ei].store(n, std::memory_order_relaxed);
         }
-        const unsigned blocks = (unsigned)ctas[ei] < grid.x * grid.y ? (unsigned)ctas[ei] : grid.x * grid.y;
+        const unsigned blocks = (unsigned)n < grid.x * grid.y ? (unsigned)n : grid.x * grid.y;
         cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
         if (effect == kAO)

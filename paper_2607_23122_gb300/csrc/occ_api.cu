@@ -482,11 +482,14 @@ OCC_EXPORT occ_status occ_reuse_shadow(occ_ctx* ctx, const occ_gbuffer* gb,
                         stream);
 }
 
-OCC_EXPORT occ_status occ_frame_host(occ_ctx* ctx, const occ_bvh* bvh, int32_t effect,
-                                     const float* pos4_host, const float* nrm4_host, int32_t W,
-                                     int32_t H, float radius, const occ_rect_light* light,
-                                     uint64_t seed, uint32_t sample, const occ_pattern* pattern,
-                                     int32_t K, int32_t estimator, float* out_host, void* stream) {
+namespace {
+
+// Copies, trace, reuse and the estimate's download of one host frame, enqueued on `stream`.
+occ_status frame_host_enqueue(occ_ctx* ctx, const occ_bvh* bvh, int32_t effect,
+                              const float* pos4_host, const float* nrm4_host, int32_t W, int32_t H,
+                              float radius, const occ_rect_light* light, uint64_t seed,
+                              uint32_t sample, const occ_pattern* pattern, int32_t K,
+                              int32_t estimator, float* out_host, void* stream) {
     occ_status st = check_ctx(ctx);
     if (st != OCC_OK) return st;
     if (!bvh || !pos4_host || !nrm4_host || !out_host || W <= 0 || H <= 0)
@@ -529,7 +532,31 @@ OCC_EXPORT occ_status occ_frame_host(occ_ctx* ctx, const occ_bvh* bvh, int32_t e
     if (st != OCC_OK) return st;
     e = cudaMemcpyAsync(out_host, out, 4 * P, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "frame download");
+    return OCC_OK;
+}
+
+}  // namespace
+
+OCC_EXPORT occ_status occ_frame_host(occ_ctx* ctx, const occ_bvh* bvh, int32_t effect,
+                                     const float* pos4_host, const float* nrm4_host, int32_t W,
+                                     int32_t H, float radius, const occ_rect_light* light,
+                                     uint64_t seed, uint32_t sample, const occ_pattern* pattern,
+                                     int32_t K, int32_t estimator, float* out_host, void* stream) {
+    const occ_status st = frame_host_enqueue(ctx, bvh, effect, pos4_host, nrm4_host, W, H, radius,
+                                             light, seed, sample, pattern, K, estimator, out_host,
+                                             stream);
+    if (st != OCC_OK) return st;
     return occ_sync(ctx, stream);
+}
+
+OCC_EXPORT occ_status occ_frame_host_async(occ_ctx* ctx, const occ_bvh* bvh, int32_t effect,
+                                           const float* pos4_host, const float* nrm4_host,
+                                           int32_t W, int32_t H, float radius,
+                                           const occ_rect_light* light, uint64_t seed,
+                                           uint32_t sample, const occ_pattern* pattern, int32_t K,
+                                           int32_t estimator, float* out_host, void* stream) {
+    return frame_host_enqueue(ctx, bvh, effect, pos4_host, nrm4_host, W, H, radius, light, seed,
+                              sample, pattern, K, estimator, out_host, stream);
 }
 
 OCC_EXPORT occ_status occ_shadow_lights(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh,

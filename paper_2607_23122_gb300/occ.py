@@ -374,6 +374,22 @@ def occ_frame_host(ctx: Context, bvh: BVH, effect: int, pos4_host: torch.Tensor,
     return out_host
 
 
+def occ_frame_host_async(ctx: Context, bvh: BVH, effect: int, pos4_host: torch.Tensor,
+                         nrm4_host: torch.Tensor, radius: float, light, seed: int, sample: int,
+                         pattern: Pattern, K: int, estimator: int, out_host: torch.Tensor,
+                         stream=None) -> torch.Tensor:
+    """occ_frame_host without the wait: out_host is valid once `stream` has completed
+    (ctx.sync(stream)); one frame in flight per context."""
+    H, W = int(pos4_host.shape[0]), int(pos4_host.shape[1])
+    L = _light(light if light is not None else np.zeros(9))
+    ctx.check(ctx.lib.occ_frame_host_async(ctx.handle, bvh.handle, int(effect),
+                                           pos4_host.data_ptr(), nrm4_host.data_ptr(), W, H,
+                                           float(radius), C.byref(L), int(seed), int(sample),
+                                           C.byref(pattern.c()), int(K), int(estimator),
+                                           out_host.data_ptr(), _stream_handle(stream)))
+    return out_host
+
+
 NOALLOC_MAX_PIXELS = 1 << 20
 
 

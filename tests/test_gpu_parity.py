@@ -323,6 +323,34 @@ def test_frame_host_matches_device_path(occ, ctx, c1):
     assert torch.equal(out_h, d.cpu())
 
 
+def test_frame_host_async_two_frames_in_flight(occ, ctx, c1):
+    """Frames alternating over two contexts and streams (each frame's copies overlapping the
+    other's kernels) give the same estimates as the synchronous call, frame by frame."""
+    import torch
+    pat = _patterns(occ)["disk8"]
+    pos_h = torch.from_numpy(c1["pos"]).pin_memory()
+    nrm_h = torch.from_numpy(c1["nrm"]).pin_memory()
+    ctxs = [ctx, occ.Context(0)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [torch.empty((64, 64), dtype=torch.float32).pin_memory() for _ in range(2)]
+    got = []
+    for i in range(6):
+        j = i & 1
+        if i >= 2:
+            ctxs[j].sync(streams[j])
+            got.append(outs[j].clone())
+        occ.occ_frame_host_async(ctxs[j], c1["bvh"], AO, pos_h, nrm_h, R_C1, None, 5, i, pat, 8,
+                                 BIASED, outs[j], stream=streams[j])
+    for i in (4, 5):
+        ctxs[i & 1].sync(streams[i & 1])
+        got.append(outs[i & 1].clone())
+    want = torch.empty((64, 64), dtype=torch.float32).pin_memory()
+    for i in range(6):
+        occ.occ_frame_host(ctx, c1["bvh"], AO, pos_h, nrm_h, R_C1, None, 5, i, pat, 8, BIASED, want)
+        assert torch.equal(got[i], want), i
+    assert not torch.equal(got[0], got[1])      # different samples, different estimates
+
+
 # --------------------------------------------------------------------------------------
 # Packed formats (octahedral normals, shared-exponent occluder offsets; FP32 arithmetic)
 # --------------------------------------------------------------------------------------
