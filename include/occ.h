@@ -30,8 +30,9 @@
  *    OCC_ERR_DEVICE_CHECK by the next occ_sync().  No entry point aborts,
  *    traps or throws across the ABI.
  *  - A context may be used by one host thread at a time.  Its AO trace calls share one
- *    device work counter, so they must not overlap on the device: use one context per
- *    stream that traces concurrently.
+ *    device work counter and its unbiased group reuse calls one validation workspace, so
+ *    they must not overlap on the device: use one context per stream that traces or
+ *    reuses concurrently.
  *
  * Images are row-major, pixel (x, y) at linear index y * W + x.
  */

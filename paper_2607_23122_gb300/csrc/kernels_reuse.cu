@@ -5,12 +5,13 @@
 // Densities are evaluated in FP32 without the constant factors 1/pi and 1/Area,
 // which cancel in every ratio p(z_j|x_i) / sum_k p(z_j|x_k).
 //
-//  k_reuse_group    GROUP patterns with power-of-two blocks (the paper's shared
-//                   groups mapped onto warp lanes).  Lane j owns candidate z_j and
-//                   evaluates its column p(z_j|x_k) for all K receivers (receiver data
-//                   exchanged through shared memory), normalises by P_j, and a
-//                   recursive-halving shuffle reduce-scatter (K-1 shuffles) hands lane
-//                   i its B_i = sum_j p(z_j|x_i)/P_j.
+//  k_reuse_group    (kernels_reuse_group.cu) GROUP patterns with power-of-two blocks
+//                   (the paper's shared groups mapped onto warp lanes).  Lane j owns
+//                   candidate z_j and evaluates its column p(z_j|x_k) for all K receivers
+//                   (receiver data exchanged through shared memory), normalises by P_j,
+//                   and a recursive-halving shuffle reduce-scatter (K-1 shuffles) hands
+//                   lane i its B_i = sum_j p(z_j|x_i)/P_j.  Unbiased: the pairs that need
+//                   Eq. 7 are queued and traced by the persistent k_validate.
 //  k_reuse_tile     (kernels_reuse_tile.cu) biased box / offset windows with the tile
 //                   and its halo staged in shared memory by TMA.
 //  k_reuse_generic  any pattern: one thread per receiver, members' receiver data held
@@ -18,52 +19,10 @@
 //  k_reuse_simple   NOREUSE / BOXMEAN.
 #include <cuda_runtime.h>
 
-#include "occ_device.cuh"
-#include "occ_kernels.h"
-#include "occ_path.cuh"
+#include "occ_reuse.cuh"
 
 namespace occ {
 namespace {
-
-struct ReuseArgs {
-    GBufView gb;
-    RecView rec;
-    PatternParams pat;
-    float R2s;          // AO: R^2 (1 + 2^-16)
-    LightParams lp;
-    DevBVH bvh;         // unbiased only
-    float* out;
-    unsigned* status;
-};
-
-// Receiver data of pixel q, from either G-buffer format.
-template <int EFFECT>
-__device__ __forceinline__ Recv fetch_recv(const GBufView& gb, int q, const RectLight& L) {
-    float3 x = make_float3(0.0f, 0.0f, 0.0f), n = x;
-    const bool v = gb_fetch(gb.pos, gb.nrm, gb.packed != 0, q, &x, &n);
-    return make_recv<EFFECT>(x, n, v, L);
-}
-
-// Candidate of pixel q whose own receiver point is xsrc: occluder point and normal; returns
-// the triangle id (< 0: no occluder).  Either record format.
-__device__ __forceinline__ int fetch_cand(const RecView& rec, int q, float3 xsrc, float3* z,
-                                          float3* nz) {
-    const float4 r0 = __ldg(rec.r0 + q);
-    const int tri = __float_as_int(r0.w);
-    if (tri < 0) return tri;
-    if (rec.packed) return rec_unpack(r0, xsrc, z, nz);
-    *z = f3(r0);
-    *nz = f3(__ldg(rec.r1 + q));
-    return tri;
-}
-
-int sm_count() {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return 1;
-    return n;
-}
 
 __device__ __forceinline__ void tile_pixel(int* x, int* y) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -313,155 +272,6 @@ __global__ void k_debug_mis(ReuseArgs a, const int32_t* pix, int32_t npix, int32
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// Warp-cooperative GROUP kernel.  K = GW * GH lanes per group, 32 / K groups per warp
-// laid side by side (warp block = (32/K * GW) x GH pixels), 8 warps side by side per CTA.
-// ---------------------------------------------------------------------------------------
-// Loading the hit-normal plane only for rays that hit saves bytes but adds a dependent
-// round trip; OCC_GROUP_EAGER_R1=1 loads it together with the other planes (measured
-// slower for AO at 1080p: 32.2 vs 28.8 us).
-#ifndef OCC_GROUP_EAGER_R1
-#define OCC_GROUP_EAGER_R1 0
-#endif
-// warps per CTA of the group kernel (side by side) and the load flavour: every byte of
-// the G-buffer and records is read exactly once, so streaming loads (evict-first) can be
-// used instead of read-only cached loads.
-#ifndef OCC_GROUP_WARPS
-#define OCC_GROUP_WARPS 8
-#endif
-#ifndef OCC_GROUP_STREAM_LOADS
-#define OCC_GROUP_STREAM_LOADS 0
-#endif
-template <typename T>
-__device__ __forceinline__ T group_load(const T* p) {
-    if (OCC_GROUP_STREAM_LOADS) return __ldcs(p);
-    return __ldg(p);
-}
-
-template <int EFFECT, int EST, int GW, int GH, bool PACKED>
-__global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs a) {
-    constexpr int K = GW * GH;
-    constexpr int GPW = 32 / K;
-    constexpr int BW = GPW * GW;
-    // receiver exchange buffer; group slots are K + 2 float4 apart so that the groups of a
-    // warp reading their k-th member hit different shared-memory banks
-    constexpr int GS = K + 2;
-    __shared__ float4 s_x[OCC_GROUP_WARPS][GPW * GS];
-    __shared__ float4 s_n[OCC_GROUP_WARPS][GPW * GS];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane / K, m = lane % K;
-    // the CTA's warps sit side by side: each row of the CTA is contiguous pixels
-    const int x = (blockIdx.x * OCC_GROUP_WARPS + warp) * BW + g * GW + m % GW;
-    const int y = blockIdx.y * GH + m / GW;
-    const bool inside = x < a.gb.W && y < a.gb.H;
-    const int i = inside ? y * a.gb.W + x : 0;
-    RectLight L;
-    if (EFFECT == kShadow) L = make_light(a.lp);
-
-    float4 P = make_float4(0.0f, 0.0f, 0.0f, 0.0f), N = P;
-    float4 R0 = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1)), R1 = P;
-    float3 z = make_float3(0.0f, 0.0f, 0.0f), nz = z, nx = z;
-    bool valid, hit;
-    if (PACKED) {
-        // 16 + 16 bytes per pixel: (x, octahedral normal) and the packed record
-        if (inside) {
-            P = group_load(a.gb.pos + i);
-            R0 = group_load(a.rec.r0 + i);
-        }
-        valid = inside && __float_as_uint(P.w) != kOctInvalid;
-        hit = valid && __float_as_int(R0.w) >= 0;
-        if (valid) nx = oct_decode(__float_as_uint(P.w));
-        if (hit) rec_unpack(R0, f3(P), &z, &nz);
-    } else {
-        if (inside) {
-            P = group_load(a.gb.pos + i);
-            N = group_load(a.gb.nrm + i);
-            R0 = group_load(a.rec.r0 + i);
-            if (OCC_GROUP_EAGER_R1) R1 = group_load(a.rec.r1 + i);
-        }
-        valid = inside && P.w != 0.0f;
-        hit = valid && __float_as_int(R0.w) >= 0;
-        // a ray that missed provides no candidate, so its hit normal is not needed
-        if (!OCC_GROUP_EAGER_R1 && hit) R1 = group_load(a.rec.r1 + i);
-        nx = f3(N);
-        z = f3(R0);
-        nz = f3(R1);
-    }
-    // receiver data for the density: AO (x, n); shadow (x, precomputed plane terms)
-    const Recv me = make_recv<EFFECT>(f3(P), nx, valid, L);
-    s_x[warp][g * GS + m] = make_float4(me.x.x, me.x.y, me.x.z, valid ? 1.0f : 0.0f);
-    s_n[warp][g * GS + m] = make_float4(me.n.x, me.n.y, me.n.z, 0.0f);
-    __syncwarp();
-
-    const unsigned gmask = (K == 32 ? 0xFFFFFFFFu : ((1u << K) - 1u)) << (g * K);
-    const unsigned vmask = __ballot_sync(0xFFFFFFFFu, valid) & gmask;
-    const unsigned hmask = __ballot_sync(0xFFFFFFFFu, hit) & gmask;
-
-    // column of candidate z_m: densities at every receiver of the group
-    float r[K];
-    float Psum = 0.0f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const float4 sx = s_x[warp][g * GS + k];
-        const float4 sn = s_n[warp][g * GS + k];
-        Recv rk;
-        rk.x = f3(sx);
-        rk.n = f3(sn);
-        float q = 0.0f;
-        if (hit && sx.w != 0.0f) q = density<EFFECT>(z, nz, rk, a.R2s, L);
-        if (EST == kUnbiased && q > 0.0f && k != m)
-            if (!first_hit(a.bvh, rk.x, z, (uint32_t)__float_as_int(R0.w), a.status)) q = 0.0f;
-        r[k] = q;
-        Psum += q;
-    }
-    const float inv = Psum > 0.0f ? 1.0f / Psum : 0.0f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r[k] *= inv;
-
-    // reduce-scatter over the group's lanes: lane m ends with sum_j r_j[m]
-#pragma unroll
-    for (int h = K / 2; h >= 1; h >>= 1) {
-        const bool upper = (m & h) != 0;
-#pragma unroll
-        for (int e = 0; e < h; ++e) {
-            const float keep = upper ? r[e + h] : r[e];
-            const float send = upper ? r[e] : r[e + h];
-            r[e] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, h);
-        }
-    }
-    if (!inside) return;
-    float res = 1.0f;
-    if (valid) {
-        res = 1.0f - r[0];
-        if (EFFECT == kShadow && EST == kBiased && vmask == hmask) res = 0.0f;
-    }
-    a.out[i] = res;
-}
-
-template <int EFFECT, int EST, int GW, int GH>
-void launch_group_t(const ReuseArgs& a, cudaStream_t s) {
-    constexpr int K = GW * GH;
-    constexpr int BW = (32 / K) * GW;
-    constexpr int CW = OCC_GROUP_WARPS * BW;
-    const dim3 grid((unsigned)((a.gb.W + CW - 1) / CW), (unsigned)((a.gb.H + GH - 1) / GH));
-    if (a.gb.packed && a.rec.packed)
-        k_reuse_group<EFFECT, EST, GW, GH, true><<<grid, 32 * OCC_GROUP_WARPS, 0, s>>>(a);
-    else if (!a.gb.packed && !a.rec.packed)
-        k_reuse_group<EFFECT, EST, GW, GH, false><<<grid, 32 * OCC_GROUP_WARPS, 0, s>>>(a);
-}
-
-
-template <int EFFECT, int EST>
-bool launch_group(const ReuseArgs& a, cudaStream_t s) {
-    const int gw = a.pat.gw, gh = a.pat.gh;
-    if ((a.gb.packed != 0) != (a.rec.packed != 0)) return false;
-    if (gw == 2 && gh == 1) { launch_group_t<EFFECT, EST, 2, 1>(a, s); return true; }
-    if (gw == 2 && gh == 2) { launch_group_t<EFFECT, EST, 2, 2>(a, s); return true; }
-    if (gw == 4 && gh == 2) { launch_group_t<EFFECT, EST, 4, 2>(a, s); return true; }
-    if (gw == 4 && gh == 4) { launch_group_t<EFFECT, EST, 4, 4>(a, s); return true; }
-    return false;
-}
-
 template <int EFFECT, int EST>
 void launch_generic(const ReuseArgs& a, cudaStream_t s) {
     const dim3 grid((unsigned)((a.gb.W + 15) / 16), (unsigned)((a.gb.H + 7) / 8));
@@ -494,11 +304,18 @@ cudaError_t launch_effect(int est, const ReuseArgs& a, cudaStream_t s, const Tun
                                   tune.tile_rows, tune.window_path == 3))
                 return e;
             launch_generic<EFFECT, kBiased>(a, s);
-        } else if (!launch_group<EFFECT, kBiased>(a, s)) {
+        } else if (!launch_group_reuse(EFFECT, kBiased, a, s)) {
             launch_generic<EFFECT, kBiased>(a, s);
         }
+    } else if (a.pat.kind == 0 && a.vq && launch_group_reuse(EFFECT, kUnbCollect, a, s)) {
+        // queued validation: the pairs that need Eq. 7 are traced by the persistent
+        // k_validate, then the group kernel estimates with the validated pairs
+        const cudaError_t e = launch_validate(a, s);
+        if (e != cudaSuccess) return e;
+        launch_group_reuse(EFFECT, kUnbFinal, a, s);
     } else {
-        if (a.pat.kind != 0 || !launch_group<EFFECT, kUnbiased>(a, s)) launch_generic<EFFECT, kUnbiased>(a, s);
+        if (a.pat.kind != 0 || !launch_group_reuse(EFFECT, kUnbiased, a, s))
+            launch_generic<EFFECT, kUnbiased>(a, s);
     }
     return cudaSuccess;
 }
@@ -514,6 +331,9 @@ ReuseArgs make_args(const GBufView& gb, const RecView& rec, const PatternParams&
     a.bvh = bvh ? *bvh : DevBVH{nullptr, nullptr};
     a.out = out;
     a.status = status;
+    a.vq = nullptr;
+    a.vcount = nullptr;
+    a.vbits = nullptr;
     return a;
 }
 
@@ -522,9 +342,20 @@ ReuseArgs make_args(const GBufView& gb, const RecView& rec, const PatternParams&
 cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const RecView& rec,
                          const PatternParams& pat, float radius, const LightParams& light,
                          const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s,
-                         const Tuning& tune, uint64_t seed, uint32_t sample) {
+                         const Tuning& tune, uint64_t seed, uint32_t sample,
+                         const ValidateWs* vws) {
     if (gb.W <= 0 || gb.H <= 0) return cudaSuccess;
-    const ReuseArgs a = make_args(gb, rec, pat, radius, light, bvh, out, status);
+    ReuseArgs a = make_args(gb, rec, pat, radius, light, bvh, out, status);
+    const size_t P = (size_t)gb.W * gb.H;
+    if (estimator == kUnbiased && vws && vws->queue && pat.kind == 0 && pat.K <= 16 &&
+        P < (1u << 28) && vws->queue_cap >= (size_t)(pat.K - 1) * P && vws->bits_cap >= P) {
+        cudaError_t e = cudaMemsetAsync(vws->bits, 0, P * sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(vws->counters, 0, 2 * sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        a.vq = vws->queue;
+        a.vcount = vws->counters;
+        a.vbits = vws->bits;
+    }
     if (estimator == kLightUnbiased) {
         const dim3 grid((unsigned)((gb.W + 15) / 16), (unsigned)((gb.H + 7) / 8));
         if (pat.K <= 16)

@@ -173,6 +173,12 @@ occ_status launched(occ_ctx* ctx, cudaError_t e, const char* what) {
     return OCC_OK;
 }
 
+// 1: unbiased group reuse queues its first-hit validation rays for a persistent trace
+// kernel; 0: the group kernel traces them inline.
+#ifndef OCC_VALIDATE_QUEUE
+#define OCC_VALIDATE_QUEUE 1
+#endif
+
 occ_status reuse_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const occ_occluders* occ,
                         const occ_pattern* pattern, int32_t K, int32_t estimator,
                         const occ_bvh* bvh, float* out, void* stream) {
@@ -200,10 +206,36 @@ occ_status reuse_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
     if ((st = make_pattern(ctx, pattern, K, &pat)) != OCC_OK) return st;
     const occ::DevBVH b = bvh ? dev_bvh(bvh) : occ::DevBVH{nullptr, nullptr};
     const occ::LightParams lp = to_params(&occ->light);
+    occ::ValidateWs vws{nullptr, 0, nullptr, 0, nullptr};
+    if (OCC_VALIDATE_QUEUE && estimator == OCC_EST_UNBIASED && pat.kind == OCC_PAT_GROUP &&
+        pat.K <= 16) {
+        // queued validation: (K - 1) query words and one validation word per pixel, grown
+        // on demand (a context's calls run in order on the device, so the previous contents
+        // are no longer needed once cudaFree returns)
+        const size_t P = (size_t)gb->W * gb->H, nq = (size_t)(pat.K - 1) * P;
+        if (nq > ctx->vq_cap || P > ctx->vbits_cap) {
+            cudaFree(ctx->vq);
+            cudaFree(ctx->vbits);
+            ctx->vq = nullptr;
+            ctx->vbits = nullptr;
+            ctx->vq_cap = ctx->vbits_cap = 0;
+            cudaError_t e = cudaMalloc(&ctx->vq, (nq > 0 ? nq : 1) * sizeof(uint32_t));
+            if (e == cudaSuccess) e = cudaMalloc(&ctx->vbits, P * sizeof(uint32_t));
+            if (e != cudaSuccess) {
+                cudaFree(ctx->vq);
+                ctx->vq = nullptr;
+                return cuda_fail(ctx, e, "validation workspace");
+            }
+            ctx->vq_cap = nq;
+            ctx->vbits_cap = P;
+        }
+        vws = occ::ValidateWs{ctx->vq, ctx->vq_cap, ctx->vbits, ctx->vbits_cap, ctx->counter + 1};
+    }
     return launched(ctx,
                     occ::launch_reuse(effect, estimator, view(gb), rec_view(occ), pat, occ->radius,
                                       lp, bvh ? &b : nullptr, out, ctx->status,
-                                      (cudaStream_t)stream, ctx->tune, occ->seed, occ->sample),
+                                      (cudaStream_t)stream, ctx->tune, occ->seed, occ->sample,
+                                      vws.queue ? &vws : nullptr),
                     "reuse launch");
 }
 
@@ -298,7 +330,7 @@ OCC_EXPORT occ_status occ_create(int device, occ_ctx** out) {
     if (cudaSetDevice(device) != cudaSuccess) return OCC_ERR_CUDA;
     occ_ctx* ctx = new occ_ctx();
     ctx->device = device;
-    // status word and ray counter, 32 bytes apart
+    // status word (word 0), ray counter (word 8), validation counters (words 9, 10)
     cudaError_t e = cudaMalloc(&ctx->status, 64);
     if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, 64);
     ctx->counter = ctx->status + 8;
@@ -315,6 +347,8 @@ OCC_EXPORT occ_status occ_destroy(occ_ctx* ctx) {
     if (!ctx) return OCC_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     cudaFree(ctx->status);
+    cudaFree(ctx->vq);
+    cudaFree(ctx->vbits);
     cudaFree(ctx->ws);
     cudaFree(ctx->batch_dev);
     cudaFreeHost(ctx->batch_host);

@@ -14,6 +14,12 @@ struct occ_ctx {
     int device = 0;
     unsigned* status = nullptr;          // device status word (kStatus* bits)
     unsigned* counter = nullptr;         // ray counter of the persistent trace kernel
+    // queued first-hit validation of unbiased group reuse: query list and validation words
+    // (its two counters live in the status allocation, after the ray counter)
+    uint32_t* vq = nullptr;
+    size_t vq_cap = 0;
+    uint32_t* vbits = nullptr;
+    size_t vbits_cap = 0;
     std::string last_error;
     // workspace of occ_frame_host: pos4, nrm4, records, output
     void* ws = nullptr;

@@ -93,10 +93,22 @@ struct Tuning {
     int fused_ao_path = 0;
 };
 
+// Workspace of the queued first-hit validation (unbiased group reuse): up to (K - 1) W H
+// query words, W H validation words, two counters.  Without it the group kernel traces
+// its validation rays inline.
+struct ValidateWs {
+    uint32_t* queue;
+    size_t queue_cap;
+    uint32_t* bits;
+    size_t bits_cap;
+    unsigned* counters;
+};
+
 cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const RecView& rec,
                          const PatternParams& pat, float radius, const LightParams& light,
                          const DevBVH* bvh, float* out, unsigned* status, cudaStream_t s,
-                         const Tuning& tune = Tuning(), uint64_t seed = 0, uint32_t sample = 0);
+                         const Tuning& tune = Tuning(), uint64_t seed = 0, uint32_t sample = 0,
+                         const ValidateWs* vws = nullptr);
 // Batched frame over several views (persistent kernels over the concatenated tiles).
 cudaError_t launch_trace_batch(const BatchView* views, const BatchDyn* dyn, int n_views, int n_tiles,
                                const DevBVH& bvh, int ctas, unsigned* status, cudaStream_t s);
