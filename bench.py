@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--no-uhd", action="store_true",
+                    help="skip the 4K packed K = 16 leg (~4M-triangle scene)")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--profile-step", action="store_true",
                     help="launch the hot kernels once each (1080p: AO trace, window reuse, "
@@ -308,6 +310,70 @@ def fused_frame(occ, ctx, gb, bvh, rec, out, flush, stream) -> dict:
     res["shadow_fused_ms"] = time_kernel(
         lambda st: occ.occ_trace_reuse_shadow(ctx, gb, bvh, light, 1, 0, g, 8, B, out=out,
                                               stream=st), flush, stream, 100)["ms"]
+    return res
+
+
+def uhd_frame(occ, flush, stream) -> dict:
+    """The 4K configuration: ~4M-triangle scene (1024^2 heightfield, 1,200 spheres, 30,000
+    boxes, seed 4), 3840 x 2160, packed G-buffer and records, K = 16 in 4x4 groups and in a
+    16-member disk (window tuning picked by the autotuner), AO and shadows."""
+    import tempfile
+
+    import torch
+
+    import synth
+    from paper_2607_23122_gb300 import autotune
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = occ.Context(dev.index)
+    t0 = time.perf_counter()
+    scene = synth.scene_terrain(grid=1024, n_spheres=1200, n_boxes=30000, seed=4)
+    bvh = occ.BVH(ctx, scene.tris)
+    build_s = time.perf_counter() - t0
+    Wu, Hu = 3840, 2160
+    P = Wu * Hu
+    gb = occ.occ_gbuffer_pinhole(ctx, bvh, synth.camera_c2().as_array(), scene.eps, Wu, Hu,
+                                 packed=True)
+    rec = occ.Occluders.empty(Hu, Wu, dev, packed=True)
+    out = torch.empty((Hu, Wu), dtype=torch.float32, device=dev)
+    light = synth.light_c3().as_array()
+    g16 = occ.Pattern.group(4, 4)
+    d16 = occ.Pattern.offsets_of(synth.disk_offsets(16, 15.0, seed=3))
+    res = {"W": Wu, "H": Hu, "tris": scene.num_tris, "scene_and_bvh_s": build_s,
+           "formats": "packed G-buffer and records (16 + 16 B/px)"}
+    old_cache = os.environ.get("OCC_TUNE_CACHE")
+    with tempfile.TemporaryDirectory() as tmp:
+        os.environ["OCC_TUNE_CACHE"] = os.path.join(tmp, "tuning.json")
+        try:
+            for name, eff in (("ao", occ.OCC_EFFECT_AO), ("shadow", occ.OCC_EFFECT_SHADOW)):
+                if eff == occ.OCC_EFFECT_AO:
+                    def trace(st):
+                        occ.occ_trace_ao(ctx, gb, bvh, RADIUS, 1, 0, out=rec, stream=st)
+                    fn = occ.occ_reuse_ao
+                else:
+                    def trace(st):
+                        occ.occ_trace_shadow(ctx, gb, bvh, light, 1, 0, out=rec, stream=st)
+                    fn = occ.occ_reuse_shadow
+                tr = time_kernel(trace, flush, stream, 30)["ms"]
+                trace(stream)
+                ctx.sync()
+                tuned = autotune.tune_reuse(ctx, gb, rec, d16, occ.OCC_EST_BIASED, out,
+                                            use_cache=False)
+                gr = time_kernel(lambda st: fn(ctx, gb, rec, g16, 16, occ.OCC_EST_BIASED, out=out,
+                                               stream=st), flush, stream, 30)["ms"]
+                dk = time_kernel(lambda st: fn(ctx, gb, rec, d16, 16, occ.OCC_EST_BIASED, out=out,
+                                               stream=st), flush, stream, 30)["ms"]
+                occ.occ_set_tuning(ctx)
+                res[name] = {"trace_ms": tr, "reuse_group4x4_ms": gr, "reuse_disk16_ms": dk,
+                             "disk16_tuning": tuned["best"],
+                             "ms_per_frame_group4x4": tr + gr, "ms_per_frame_disk16": tr + dk,
+                             "neighbour_samples_per_s_group4x4": P * 16 / ((tr + gr) * 1e-3),
+                             "neighbour_samples_per_s_disk16": P * 16 / ((tr + dk) * 1e-3)}
+        finally:
+            if old_cache is None:
+                os.environ.pop("OCC_TUNE_CACHE", None)
+            else:
+                os.environ["OCC_TUNE_CACHE"] = old_cache
+    ctx.sync()
     return res
 
 
@@ -600,6 +666,8 @@ def run_ours(args):
         extra["shadow"] = shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream)
         extra["packed"] = packed_frame(occ, ctx, gb, bvh, pat, out, flush, stream)
         extra["fused"] = fused_frame(occ, ctx, gb, bvh, rec, out, flush, stream)
+        if not args.no_uhd:
+            extra["uhd"] = uhd_frame(occ, flush, stream)
         if not args.no_quality:
             extra["quality"] = quality_leg(occ, ctx, gb, bvh, pat)
         if not args.no_serving:
@@ -666,6 +734,8 @@ def run_ours(args):
             "bvh": {"nodes": st["num_nodes"], "depth": st["depth"], "bytes": st["bytes"],
                     "build_s": st["build_seconds"]},
         }
+        if "uhd" in extra:
+            line["uhd_packed_k16_frame"] = extra["uhd"]
         for key in ("quality", "serving"):
             if key in extra:
                 line[key] = extra[key]
