@@ -311,7 +311,8 @@ typedef struct {
     int32_t reuse_tile_rows;     /* TMA window kernel: receiver rows per tile (4, 8, 16) */
     int32_t reuse_window_path;   /* window patterns: 1 TMA tile kernel (one thread per receiver),
                                     2 per-receiver kernel, 3 TMA tile kernel with two threads
-                                    per receiver */
+                                    per receiver; 0: TMA tile kernel, two threads per receiver
+                                    for AO windows of more than 9 members */
     int32_t batch_ctas_per_sm;   /* persistent batched kernels: CTAs per SM (1 .. 16) */
     int32_t fused_ao_path;       /* occ_trace_reuse_ao: 1 one CTA per 16 x 8 tile, 2 persistent
                                     CTAs refilling whole groups from the context's counter */

@@ -289,6 +289,15 @@ void launch_generic(const ReuseArgs& a, cudaStream_t s) {
         k_reuse_generic<EFFECT, EST, kMaxMembers><<<grid, 128, 0, s>>>(a);
 }
 
+// Two threads per receiver in the TMA window kernel: on request (window path 3), and by
+// default for AO windows of more than 9 members, where one thread's 16 receivers crowd its
+// registers (4K, 16 disk offsets: 1.82 against 2.13 ms FP32, 1.89 against 2.74 ms packed;
+// shadows and K <= 9 are faster with one thread per receiver).
+bool window_pairs(int effect, int K, const Tuning& tune) {
+    if (tune.window_path == 3) return true;
+    return tune.window_path == 0 && effect == kAO && K > 9;
+}
+
 template <int EFFECT>
 cudaError_t launch_effect(int est, const ReuseArgs& a, cudaStream_t s, const Tuning& tune) {
     const dim3 grid((unsigned)((a.gb.W + 15) / 16), (unsigned)((a.gb.H + 7) / 8));
@@ -301,7 +310,7 @@ cudaError_t launch_effect(int est, const ReuseArgs& a, cudaStream_t s, const Tun
             cudaError_t e = cudaSuccess;
             if (tune.window_path != 2 &&
                 launch_reuse_tile(EFFECT, a.gb, a.rec, a.pat, a.R2s, a.lp, a.out, a.status, s, &e,
-                                  tune.tile_rows, tune.window_path == 3))
+                                  tune.tile_rows, window_pairs(EFFECT, a.pat.K, tune)))
                 return e;
             launch_generic<EFFECT, kBiased>(a, s);
         } else if (!launch_group_reuse(EFFECT, kBiased, a, s)) {

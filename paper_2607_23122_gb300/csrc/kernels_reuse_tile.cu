@@ -270,11 +270,10 @@ __device__ __forceinline__ void tile_single(const TileArgs& a, const RectLight& 
 // Two threads per receiver (twice the resident warps at half the registers each): thread h
 // of the pair holds the member slots 2j + h, and the pair adds its halves of P_j with one
 // shuffle.  Candidates that no lane of the warp has are skipped warp-uniformly, so every
-// lane reaches the shuffle.  A tuning choice (reuse_window_path 3), not the default: at
-// 1080p with 8 disk offsets it measured 0.179 ms for AO against 0.137 ms for tile_single
-// (the doubled candidate loads, member masks and shuffles outweigh the extra warps) and
-// 0.205 against 0.207 ms for shadows.
-template <int EFFECT, int MAXK>
+// lane reaches the shuffle.  The default for AO windows of more than 9 members (4K, 16 disk
+// offsets: 1.82 against 2.13 ms); with 8 offsets the doubled candidate loads, member masks
+// and shuffles outweigh the extra warps (1080p: 0.179 against 0.137 ms).
+template <int EFFECT, int MAXK, bool PACKED>
 __device__ __forceinline__ void tile_pairs(const TileArgs& a, const RectLight& L, const Staged& st,
                                            int x0, int y0) {
     constexpr int HALF = (MAXK + 1) / 2;
@@ -283,8 +282,8 @@ __device__ __forceinline__ void tile_pairs(const TileArgs& a, const RectLight& L
     const int x = x0 + lx, y = y0 + ly;
     const bool inside = ly < a.TH && x < a.W && y < a.H;
     const int sc = (min(ly, a.TH - 1) + a.hy0) * a.SW + (lx + a.hx0);
-    const bool rvalid = inside && st.pos[sc].w != 0.0f;
-    const uint32_t vmask = rvalid ? member_mask<MAXK, false>(a, st.pos, x, y, sc) : 0u;
+    const bool rvalid = inside && staged_valid<PACKED>(st.pos[sc]);
+    const uint32_t vmask = rvalid ? member_mask<MAXK, PACKED>(a, st.pos, x, y, sc) : 0u;
     float3 rx[HALF], rt[HALF];
 #pragma unroll
     for (int j = 0; j < HALF; ++j) {
@@ -295,7 +294,7 @@ __device__ __forceinline__ void tile_pairs(const TileArgs& a, const RectLight& L
             const int2 o = member_offset(a, s);
             q = sc + o.y * a.SW + o.x;
         }
-        recv_terms<EFFECT>(st.pos[q], st.nrm[q], L, &rx[j], &rt[j]);
+        staged_recv<EFFECT, PACKED>(st, q, L, &rx[j], &rt[j]);
         if (!v) rt[j] = make_float3(0.0f, 0.0f, 0.0f);
     }
     float B = 0.0f;
@@ -312,7 +311,8 @@ __device__ __forceinline__ void tile_pairs(const TileArgs& a, const RectLight& L
         }
         if (!__any_sync(0xFFFFFFFFu, cand)) continue;
         blocked |= (uint32_t)cand << c;
-        const float3 z = f3(r0), nz = cand ? f3(st.r1[q]) : make_float3(0.0f, 0.0f, 0.0f);
+        float3 z = make_float3(0.0f, 0.0f, 0.0f), nz = z;
+        if (cand) staged_cand<PACKED>(st, q, r0, &z, &nz);
         float pi = 0.0f, part = 0.0f;
 #pragma unroll
         for (int j = 0; j < HALF; ++j) {
@@ -396,7 +396,7 @@ __device__ __forceinline__ void reuse_tile_body(const CUtensorMap* tm_pos, const
         }
         const int x0 = (tile % a.tiles_x) * a.TW, y0 = (tile / a.tiles_x) * a.TH;
         if (PAIRS)
-            tile_pairs<EFFECT, MAXK>(a, L, st, x0, y0);
+            tile_pairs<EFFECT, MAXK, PACKED>(a, L, st, x0, y0);
         else
             tile_single<EFFECT, MAXK, PACKED>(a, L, st, x0, y0);
         __syncthreads();   // buffer b is free for the copies issued next
@@ -413,13 +413,13 @@ __global__ void __launch_bounds__(512, 1)
     reuse_tile_body<EFFECT, MAXK, false, PACKED>(&tm_pos, &tm_nrm, &tm_r0, &tm_r1, a);
 }
 
-template <int EFFECT, int MAXK>
+template <int EFFECT, int MAXK, bool PACKED>
 __global__ void __launch_bounds__(1024, 1)
     k_reuse_tile_pairs(const __grid_constant__ CUtensorMap tm_pos,
                        const __grid_constant__ CUtensorMap tm_nrm,
                        const __grid_constant__ CUtensorMap tm_r0,
                        const __grid_constant__ CUtensorMap tm_r1, const __grid_constant__ TileArgs a) {
-    reuse_tile_body<EFFECT, MAXK, true, false>(&tm_pos, &tm_nrm, &tm_r0, &tm_r1, a);
+    reuse_tile_body<EFFECT, MAXK, true, PACKED>(&tm_pos, &tm_nrm, &tm_r0, &tm_r1, a);
 }
 
 // The bounded-wait path of the kernel above, exercised on purpose: one thread polls a barrier
@@ -469,13 +469,12 @@ bool make_map(CUtensorMap* m, const void* base, int W, int H, int SW, int SH) {
 template <int EFFECT, int MAXK>
 cudaError_t launch_t(const CUtensorMap* maps, const TileArgs& a, size_t smem, int sms, bool pairs,
                      bool packed, cudaStream_t s) {
-    auto k = packed ? k_reuse_tile<EFFECT, MAXK, true>
-             : pairs ? k_reuse_tile_pairs<EFFECT, MAXK> : k_reuse_tile<EFFECT, MAXK, false>;
+    auto k = packed ? (pairs ? k_reuse_tile_pairs<EFFECT, MAXK, true> : k_reuse_tile<EFFECT, MAXK, true>)
+                    : (pairs ? k_reuse_tile_pairs<EFFECT, MAXK, false> : k_reuse_tile<EFFECT, MAXK, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = a.n_tiles < sms ? a.n_tiles : sms;
-    k<<<grid, a.TW * a.TH * (pairs && !packed ? 2 : 1), smem, s>>>(maps[0], maps[1], maps[2], maps[3],
-                                                                  a);
+    k<<<grid, a.TW * a.TH * (pairs ? 2 : 1), smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
     return cudaPeekAtLastError();
 }
 
