@@ -452,7 +452,8 @@ def serving(occ, ctx, bvh, scene, n_req: int) -> dict:
     the G-buffer either rendered on the device per request ("device_gbuffer") or sent from
     pinned host memory by the client ("host_gbuffer": 32 B/px FP32, 16 B/px packed,
     copied inside the request).  Per mode: the saturated rate of each format (median of
-    3 bursts of n_req requests), then Poisson arrivals of 4 n_req requests at 0.8x the
+    3 bursts of n_req requests after one untimed burst), then Poisson arrivals of 4 n_req
+    requests at 0.8x the
     slower format's rate (same arrival times for both formats); for the device mode also a
     saturated run under a 2 GB budget (admission by memory).  Latency = submit -> estimate
     in pinned host memory, on the server's own clock."""
@@ -531,7 +532,9 @@ def serving(occ, ctx, bvh, scene, n_req: int) -> dict:
         servers = {}
         for packed in (False, True):
             srv = occ.Server(ctx, bvh, max_views_per_batch=32, max_inflight=2)
-            run(srv, list(range(16)), packed, host)                 # warm-up
+            # warm-up: a whole burst, so that the server's memory pool has grown to the
+            # mix's working set before the timed bursts
+            run(srv, list(range(n_req)), packed, host)
             bursts = [run(srv, list(range(n_req)), packed, host) for _ in range(3)]
             bursts.sort(key=lambda b: b["requests_per_s"])
             m["packed" if packed else "fp32"] = {"saturated": bursts[1],
