@@ -453,10 +453,9 @@ def serving(occ, ctx, bvh, scene, n_req: int) -> dict:
     pinned host memory by the client ("host_gbuffer": 32 B/px FP32, 16 B/px packed,
     copied inside the request).  Per mode: the saturated rate of each format (median of
     3 bursts of n_req requests after one untimed burst), then Poisson arrivals of 4 n_req
-    requests at 0.8x the
-    slower format's rate (same arrival times for both formats); for the device mode also a
-    saturated run under a 2 GB budget (admission by memory).  Latency = submit -> estimate
-    in pinned host memory, on the server's own clock."""
+    requests at 0.8x the slower format's rate (same arrival times for both formats); for
+    the device mode also a saturated run under a 2 GB budget (admission by memory).
+    Latency = submit -> estimate in pinned host memory, on the server's own clock."""
     import torch
 
     import synth
