@@ -67,7 +67,8 @@ def parse():
     ap.add_argument("--profile-step", action="store_true",
                     help="launch the hot kernels once each (1080p: AO trace, window reuse, "
                          "4x2 group reuse, shadow trace, fused AO and shadow trace + 4x2 "
-                         "group reuse) and exit: the case profiled with ncu")
+                         "group reuse, then an AO trace and unbiased 4x2 group reuse) and "
+                         "exit: the case profiled with ncu")
     return ap.parse_args()
 
 
@@ -822,6 +823,9 @@ def profile_step():
                            occ.OCC_EST_BIASED, out=out)
     occ.occ_trace_reuse_shadow(ctx, gb, bvh, synth.light_c3().as_array(), 1, 0,
                                occ.Pattern.group(4, 2), 8, occ.OCC_EST_BIASED, out=out)
+    # unbiased 4x2 groups on the AO records: collect pass, k_validate, final pass
+    occ.occ_trace_ao(ctx, gb, bvh, RADIUS, 1, 0, out=rec)
+    occ.occ_reuse_ao(ctx, gb, rec, occ.Pattern.group(4, 2), 8, occ.OCC_EST_UNBIASED, bvh=bvh, out=out)
     ctx.sync()
     print(json.dumps({"profile_step": "ok", "checksum": float(out.double().sum())}))
 
