@@ -244,6 +244,7 @@ NCU_TRAFFIC = {"k_trace_dyn<AO>": 74.984192e6 + 29.916416e6,
                "k_reuse_tile<AO,8>": 132.794624e6 + 6.783488e6,
                "k_reuse_group<AO,biased,4,2>": 114.168832e6 + 4.530688e6}
 NCU_TRACE_ISSUE_ACTIVE = 0.7107   # smsp__issue_active of k_trace_dyn<AO> in its capture
+NCU_TRACE_WARP_INSTR = 309.363657e6   # smsp__inst_executed.sum of k_trace_dyn<AO>, same capture
 
 
 def time_kernel(fn, flush, stream, iters: int) -> dict:
@@ -685,7 +686,8 @@ def run_ours(args):
         trace_bytes = P * (32 + 32) + st["bytes"]
         # reuse (offset window, K^2 pair densities): FP32 ALU bound
         pairs = P * K * K
-        alu_peak = sms * 128 * 2 * (clk["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        issue_mhz = clk["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+        alu_peak = sms * 128 * 2 * issue_mhz * 1e6
         trace_roof = {"kernel": "k_trace_dyn<AO>", "bound": "hbm",
                       "achieved": trace_bytes / tr / 1e9, "peak": hbm, "unit": "GB/s",
                       "frac": trace_bytes / tr / 1e9 / hbm,
@@ -693,7 +695,13 @@ def run_ours(args):
                       "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                       "algorithmic_bytes": trace_bytes,
                       "note": "software traversal is issue/latency bound: issue slots "
-                              f"{NCU_TRACE_ISSUE_ACTIVE:.0%} busy under ncu"}
+                              f"{NCU_TRACE_ISSUE_ACTIVE:.0%} busy under ncu",
+                      # the resource that binds it: warp-instruction issue (4 schedulers per
+                      # SM, one instruction per cycle each, at the max SM clock)
+                      "issue": {"warp_instructions": NCU_TRACE_WARP_INSTR,
+                                "achieved": NCU_TRACE_WARP_INSTR / tr,
+                                "peak": sms * 4 * issue_mhz * 1e6, "unit": "warp-instr/s",
+                                "frac": NCU_TRACE_WARP_INSTR / tr / (sms * 4 * issue_mhz * 1e6)}}
         reuse_roof = {"kernel": "k_reuse_tile<AO,8> (TMA-staged window)", "bound": "alu",
                       "achieved": pairs * FLOPS_PER_PAIR_AO / ru / 1e12,
                       "peak": alu_peak / 1e12, "unit": "TFLOP/s",
