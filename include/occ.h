@@ -200,7 +200,10 @@ occ_status occ_trace_shadow(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* 
  * K must equal the pattern's size (gw*gh, or n_offsets + 1), 1 <= K <= 64.
  * bvh_or_null is required for OCC_EST_UNBIASED (and, for shadows,
  * OCC_EST_LIGHT_UNBIASED) and must be NULL otherwise.  Invalid receivers get 1.
- * Estimates are not clamped.  The batched and served paths take estimators 0-3. */
+ * Estimates are not clamped.  The batched and served paths take estimators 0-3.
+ * UNBIASED over GROUP patterns of up to 16 members queues its first-hit validation rays
+ * (Eq. 7) in a context workspace of 4 K bytes per pixel, allocated on first use and
+ * grown with the image (the estimate is the same as tracing them inline). */
 occ_status occ_reuse_ao(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occluders* occ,
                         const occ_pattern* pattern, int32_t K, int32_t estimator,
                         const occ_bvh* bvh_or_null, float* out, void* stream);
