@@ -455,7 +455,7 @@ def serving(occ, ctx, bvh, scene, n_req: int) -> dict:
     pinned host memory by the client ("host_gbuffer": 32 B/px FP32, 16 B/px packed,
     copied inside the request).  Per mode: the saturated rate of each format (median of
     3 bursts of n_req requests after one untimed burst), then Poisson arrivals of 4 n_req
-    requests at 0.8x the slower format's rate (same arrival times for both formats); for
+    requests at 0.8x the slowest burst of either format (same arrival times for both); for
     the device mode also a saturated run under a 2 GB budget (admission by memory).
     Latency = submit -> estimate in pinned host memory, on the server's own clock."""
     import torch
@@ -541,8 +541,11 @@ def serving(occ, ctx, bvh, scene, n_req: int) -> dict:
             m["packed" if packed else "fp32"] = {"saturated": bursts[1],
                                                  "saturated_runs_req_s": [b["requests_per_s"] for b in bursts]}
             servers[packed] = srv
-        rate = 0.8 * min(m["fp32"]["saturated"]["requests_per_s"],
-                         m["packed"]["saturated"]["requests_per_s"])
+        # 0.8x the slower format's slowest burst: bursts of the same requests vary by up to
+        # ~1.6x on this host (submission thread, pinned copies), and a rate above the
+        # sustained one measures queue growth, not latency
+        rate = 0.8 * min(min(m["fp32"]["saturated_runs_req_s"]),
+                         min(m["packed"]["saturated_runs_req_s"]))
         gaps = np.random.default_rng(55).exponential(1.0 / rate, size=n_poi)
         for packed in (False, True):
             srv = servers[packed]
