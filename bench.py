@@ -240,11 +240,11 @@ def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
 GROUP_BYTES_PER_PX = 52   # x 12, n 12, z 12, n_z 12, out 4
 # DRAM bytes (read + write) per launch from one `ncu --set full` capture of
 # `bench.py --profile-step` (cold L2); None once a kernel changes
-NCU_TRAFFIC = {"k_trace_dyn<AO>": 74.984192e6 + 29.916416e6,
+NCU_TRAFFIC = {"k_trace_dyn<AO>": 72.457472e6 + 28.906496e6,
                "k_reuse_tile<AO,8>": 132.794624e6 + 6.783488e6,
                "k_reuse_group<AO,biased,4,2>": 114.168832e6 + 4.530688e6}
-NCU_TRACE_ISSUE_ACTIVE = 0.7107   # smsp__issue_active of k_trace_dyn<AO> in its capture
-NCU_TRACE_WARP_INSTR = 309.363657e6   # smsp__inst_executed.sum of k_trace_dyn<AO>, same capture
+NCU_TRACE_ISSUE_ACTIVE = 0.6923   # smsp__issue_active of k_trace_dyn<AO> in its capture
+NCU_TRACE_WARP_INSTR = 300.359031e6   # smsp__inst_executed.sum of k_trace_dyn<AO>, same capture
 
 
 def time_kernel(fn, flush, stream, iters: int) -> dict:
