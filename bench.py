@@ -3,13 +3,18 @@
 Workload (one step = one frame): 1920x1080 ambient occlusion, 1 cosine ray per pixel,
 radius 0.5, over the seeded ~1M-triangle terrain scene (512^2 heightfield + 300
 icospheres + 8000 boxes, seed 2), then biased occluder reuse with K = 8 (the receiver
-plus 7 shared random offsets in a 15-pixel disk).  Metric: neighbour-samples/s =
-pixels * K / frame time (trace + reuse); ms_per_step is the frame time.
+plus 7 shared random offsets in a 15-pixel disk).  Metric: reuse-pass neighbour-samples/s
+= pixels * K / reuse time, summed over the timed steps; ms_per_step is the whole frame
+(trace + reuse), and frame_neighbour_samples_per_s = pixels * K / frame time beside it.
 
   python bench.py [--gpus N --steps K --warmup W]    this library (CUDA, sm_103a)
   python bench.py --impl reference ...               the FP64 CPU oracle on host cores
+  OCC_LIB_VARIANT=counters python bench.py --count-touch
+                                                     traversal counters of the trace
+                                                     (instrumented library)
 
-N > 1 runs one independent replica per GPU (the path needs no exchange between GPUs).
+N > 1 runs one independent replica per GPU (the path needs no exchange between GPUs); run
+without torchrun, --gpus N relaunches itself as N ranks on this node.
 """
 from __future__ import annotations
 
@@ -28,7 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 W, H, K, RADIUS, SEED_SCENE, SEED_OFF, DISK_R = 1920, 1080, 8, 0.5, 2, 3, 15.0
-METRIC = "reuse neighbour-samples/s (1080p AO frame: trace + biased K=8 reuse)"
+METRIC = "reuse-pass neighbour-samples/s and ms/frame (1080p AO, biased K=8 reuse)"
 UNIT = "neighbour-samples/s"
 WORKLOAD = ("1920x1080 AO, 1 spp, R=0.5, ~1M-tri terrain (seed 2); biased occluder reuse, "
             "K=8 (receiver + 7 shared offsets in a 15-px disk), FP32 records")
@@ -64,6 +69,9 @@ def parse():
     ap.add_argument("--no-uhd", action="store_true",
                     help="skip the 4K packed K = 16 leg (~4M-triangle scene)")
     ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--count-touch", action="store_true",
+                    help="with OCC_LIB_VARIANT=counters: node visits, triangle tests and the "
+                         "distinct BVH bytes touched by the 1080p AO and shadow traces")
     ap.add_argument("--profile-step", action="store_true",
                     help="launch the hot kernels once each (1080p: AO trace, window reuse, "
                          "4x2 group reuse, shadow trace, fused AO and shadow trace + 4x2 "
@@ -94,6 +102,27 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def bench_config(world: int, tris: int) -> dict:
+    """The workload description both arms print (the same dict, key for key)."""
+    return {"workload": WORKLOAD, "W": W, "H": H, "K": K, "radius": RADIUS, "tris": tris,
+            "pattern": "offsets", "estimator": "biased",
+            "l2": f"GPU arm: flushed before every step ({L2_FLUSH_BYTES >> 20} MB written, then "
+                  "read back)",
+            "parallelism": f"replicas x{world}"}
+
+
+def relaunch_as_ranks(n: int) -> int:
+    """Runs this script as n ranks on this node (torchrun), when started without it."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__),
+           *sys.argv[1:]]
+    return subprocess.call(cmd)
 
 
 def scene_inputs():
@@ -224,12 +253,14 @@ def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
     oracle.set_num_threads(1)
     n1, t_tr1, t_ru1, blocks1 = run(48, budget_s / 4)
     oracle.set_num_threads(cores)
-    return {"value": n * K / (t_tr + t_ru), "unit": UNIT, "cores": oracle.num_threads(),
+    return {"value": n * K / t_ru, "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle", "cpu_model": cpu_model(),
+            "frame_neighbour_samples_per_s": n * K / (t_tr + t_ru),
             "trace_rays_per_s": n / t_tr * ((48 + hx0 + hx1) * (48 + hy0 + hy1)) / (48 * 48),
             "trace_s": t_tr, "reuse_s": t_ru,
             "reuse_neighbour_samples_per_s": n * K / t_ru,
-            "single_core": {"value": n1 * K / (t_tr1 + t_ru1), "unit": UNIT, "cores": 1,
+            "single_core": {"value": n1 * K / t_ru1, "unit": UNIT, "cores": 1,
+                            "frame_neighbour_samples_per_s": n1 * K / (t_tr1 + t_ru1),
                             "trace_s": t_tr1, "reuse_s": t_ru1,
                             "sample": f"{blocks1} random 48x48 blocks with their halos"},
             "sample": (f"{blocks} random 48x48 receiver blocks of the 1080p frame: trace of "
@@ -245,6 +276,37 @@ NCU_TRAFFIC = {"k_trace_dyn<AO>": 72.457472e6 + 28.906496e6,
                "k_reuse_group<AO,biased,4,2>": 114.168832e6 + 4.530688e6}
 NCU_TRACE_ISSUE_ACTIVE = 0.6923   # smsp__issue_active of k_trace_dyn<AO> in its capture
 NCU_TRACE_WARP_INSTR = 300.359031e6   # smsp__inst_executed.sum of k_trace_dyn<AO>, same capture
+
+
+def fp32_peak(occ, ctx, dev, stream) -> dict:
+    """Measured FP32 peak: the library's FMA-chain probe over 8 CTAs of 256 threads per SM
+    (scalar fma.rn.f32 and paired fma.rn.f32x2), best of 10 CUDA-event timings each, with
+    the SM clock sampled during the runs."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = 8 * sms, 4096
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    clk = ClockSampler(dev.index)
+    clk.start()
+    res = {}
+    for paired in (False, True):
+        flop = occ.occ_debug_fp32_peak(ctx, paired, iters, blocks, sink, stream=stream)
+        best = None
+        for _ in range(10):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            occ.occ_debug_fp32_peak(ctx, paired, iters, blocks, sink, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            t = a.elapsed_time(b) * 1e-3
+            best = t if best is None else min(best, t)
+        res["paired_f32x2" if paired else "scalar"] = flop / best / 1e12
+    c = clk.stop()
+    ctx.sync()
+    res.update(unit="TFLOP/s", sm_mhz=c["sm_mhz"], sm_max_mhz=c["sm_max_mhz"],
+               probe=f"{blocks} CTAs x 256 threads x 16 FMA chains x {iters} iterations")
+    res["peak"] = max(res["scalar"], res["paired_f32x2"])
+    return res
 
 
 def time_kernel(fn, flush, stream, iters: int) -> dict:
@@ -621,7 +683,8 @@ def run_ours(args):
     t_trace = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]) * 1e-3
     t_reuse = np.array([ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]) * 1e-3
     t_step = max_over_ranks(float((t_trace + t_reuse).sum()), dev)
-    value = job_throughput(world, P * K, args.steps, t_step)
+    t_reuse_all = max_over_ranks(float(t_reuse.sum()), dev)
+    value = job_throughput(world, P * K, args.steps, t_reuse_all)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the region:
     # every frame uploads its G-buffer and downloads its estimate.  Pipelined: E2E_DEPTH
@@ -683,6 +746,7 @@ def run_ours(args):
             extra["quality"] = quality_leg(occ, ctx, gb, bvh, pat)
 
     if rank == 0:
+        fp32 = fp32_peak(occ, ctx, dev, stream)
         hbm, peak_kind, peaks = measured_peaks()
         st = bvh.stats
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -692,7 +756,7 @@ def run_ours(args):
         # reuse (offset window, K^2 pair densities): FP32 ALU bound
         pairs = P * K * K
         issue_mhz = clk["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-        alu_peak = sms * 128 * 2 * issue_mhz * 1e6
+        alu_peak = fp32["peak"] * 1e12
         trace_roof = {"kernel": "k_trace_dyn<AO>", "bound": "hbm",
                       "achieved": trace_bytes / tr / 1e9, "peak": hbm, "unit": "GB/s",
                       "frac": trace_bytes / tr / 1e9 / hbm,
@@ -712,19 +776,18 @@ def run_ours(args):
                       "peak": alu_peak / 1e12, "unit": "TFLOP/s",
                       "frac": pairs * FLOPS_PER_PAIR_AO / ru / alu_peak,
                       "traffic": NCU_TRAFFIC["k_reuse_tile<AO,8>"],
-                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x max SM clock"}
+                      "peak_source": "measured: FP32 FMA-chain probe (fp32_peak)"}
         dominant = trace_roof if tr >= ru else reuse_roof
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_step / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "W": W, "H": H, "K": K, "radius": RADIUS,
-                       "tris": scene.num_tris, "pattern": "offsets", "estimator": "biased",
-                       "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB written, then read back)",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(world, scene.num_tris),
+            "frame_neighbour_samples_per_s": job_throughput(world, P * K, args.steps, t_step),
             "reuse_pass": {"neighbour_samples_per_s": P * K / ru, "ms": ru * 1e3},
             "trace_pass": {"rays_per_s": P / tr, "ms": tr * 1e3},
+            "fp32_peak": fp32,
             "roofline": dominant, "roofline_other": reuse_roof if dominant is trace_roof else trace_roof,
             "e2e": {"value": job_throughput(world, P * K, e2e_steps, t_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": 2 * 16 * P, "d2h_bytes_per_step": 4 * P,
@@ -786,21 +849,28 @@ def run_reference(args):
     B = 32
     rng = np.random.default_rng(5)
 
+    t_reuse = [0.0]
+
     def step(i):
         x0 = int(rng.integers(hx0, W - B - hx1))
         y0 = int(rng.integers(hy0, H - B - hy1))
         oracle.trace(osc, 0, pos, nrm, radius=RADIUS, seed=1, sample=i,
                      region=(x0 - hx0, y0 - hy0, B + hx0 + hx1, B + hy0 + hy1), out=(rec, mg))
+        t1 = time.perf_counter()
         oracle.reuse(None, 0, pos, nrm, rec, pat, oracle.EST_BIASED, radius=RADIUS,
                      region=(x0, y0, B, B), out=(out, omg))
+        t_reuse[0] += time.perf_counter() - t1
 
     for i in range(args.warmup):
         step(i)
+    t_reuse[0] = 0.0
     t0 = time.perf_counter()
     for i in range(args.steps):
         step(args.warmup + i)
     t = time.perf_counter() - t0
-    value = B * B * K * args.steps / t
+    # the same metric as the GPU arm: neighbour-samples over the reuse time; the frame rate
+    # (trace + reuse) beside it
+    value = B * B * K * args.steps / t_reuse[0]
     sample = (f"each step: one random {B}x{B} receiver block of the 1080p frame, traced with "
               f"its {hx0}/{hx1}/{hy0}/{hy1}-px halo, then biased K=8 reuse")
     print(json.dumps({
@@ -808,12 +878,43 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "W": W, "H": H, "K": K, "radius": RADIUS,
-                   "tris": scene.num_tris, "pattern": "offsets", "estimator": "biased"},
+        "config": bench_config(world, scene.num_tris),
+        "frame_neighbour_samples_per_s": B * B * K * args.steps / t,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def count_touch():
+    """Traversal counters of the 1080p AO trace (the bench step's) and shadow trace, from the
+    instrumented library: node visits and triangle tests per ray, and the distinct nodes and
+    triangles touched (their bytes are the BVH part of the trace's compulsory traffic)."""
+    from paper_2607_23122_gb300 import _native
+    if _native.variant() != "counters":
+        raise SystemExit("--count-touch needs OCC_LIB_VARIANT=counters")
+    import synth
+    from paper_2607_23122_gb300 import occ
+    ctx = occ.Context(0)
+    scene, cam, _ = scene_inputs()
+    bvh = occ.BVH(ctx, scene.tris)
+    gb = occ.occ_gbuffer_pinhole(ctx, bvh, cam.as_array(), scene.eps, W, H)
+    rec = occ.Occluders.empty(H, W, gb.pos4.device)
+    ctx.sync()
+    occ.occ_debug_bvh_counters(ctx, bvh, reset=True)
+    res = {"bvh_bytes": bvh.stats["bytes"], "bvh_nodes": bvh.stats["num_nodes"], "tris": scene.num_tris}
+    valid = int((gb.pos4[..., 3] != 0).sum())
+    for name, fn in (("ao", lambda: occ.occ_trace_ao(ctx, gb, bvh, RADIUS, 1, 0, out=rec)),
+                     ("shadow", lambda: occ.occ_trace_shadow(ctx, gb, bvh, synth.light_c3().as_array(),
+                                                             1, 0, out=rec))):
+        fn()
+        ctx.sync()
+        c = occ.occ_debug_bvh_counters(ctx, bvh, reset=True)
+        c["rays"] = valid
+        c["node_visits_per_ray"] = c["node_visits"] / valid
+        c["triangle_tests_per_ray"] = c["triangle_tests"] / valid
+        res[name] = c
+    print(json.dumps(res), flush=True)
 
 
 def profile_step():
@@ -848,6 +949,14 @@ def main():
     if args.profile_step:
         profile_step()
         return
+    if args.count_touch:
+        count_touch()
+        return
+    _, world, _ = dist_env()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch_as_ranks(args.gpus))
+    if world != args.gpus:
+        raise SystemExit(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -333,16 +333,20 @@ occ_status occ_get_tuning(const occ_ctx* ctx, occ_tuning* t);
  *
  * One frame on the current device: the step-1 trace of `effect` (AO with `radius`,
  * or SHADOW with `light`) for every receiver of gb, then the reuse of `estimator`
- * over `pattern` into out (device float[H][W]).  The caller passes the G-buffer,
- * the BVH and `out`; the occluder records and the device status word live in a
- * static device array inside the library (calls no cudaMalloc, cudaFree or other
- * allocating routine).  Limits and behaviour:
+ * over `pattern` into out (device float[H][W]).  The caller passes the G-buffer
+ * (either format), the BVH and `out`; the occluder records, the device status word
+ * and the trace's work counter live in a static device array inside the library
+ * (calls no cudaMalloc, cudaFree or other allocating routine).  Limits and behaviour:
+ *  - estimator NOREUSE, BIASED, UNBIASED (validation rays traced inline) or BOXMEAN;
+ *    LIGHT_UNBIASED returns OCC_ERR_INVALID_ARG;
+ *  - the records are always FP32 (32 bytes per pixel), whatever the G-buffer format;
  *  - frames of at most 1,048,576 pixels (e.g. 1280x720, 1024x1024); larger ones
  *    return OCC_ERR_INVALID_ARG with a message and launch nothing;
  *  - the array (32 MiB) is held by every GPU that loads the library until exit;
  *  - the first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current: make that first call before
- *    any stream capture;
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the life of the
+ *    process: make that first call before any stream capture, and do not call this
+ *    entry point again on a device after cudaDeviceReset (the kept address is stale);
  *  - every call shares the array and overwrites the previous call's records; calls
  *    that overlap on the GPU (other streams or host threads) race on it;
  *  - the status word is cleared at the start of each call; if flags_host is not
@@ -367,6 +371,25 @@ occ_status occ_debug_philox(occ_ctx* ctx, const uint32_t* in_dev, int64_t n, uin
  * (1 .. 2^24) and sets the wait-timeout flag, so that the next occ_sync() returns
  * OCC_ERR_DEVICE_CHECK ("wait timeout") and clears it; the context stays usable. */
 occ_status occ_debug_wait_timeout(occ_ctx* ctx, uint32_t spins, void* stream);
+
+/* Measurement aid (not part of the method): a throughput probe of the FP32 pipe, the peak
+ * that FP32-bound kernels (the window reuse with its K^2 pair densities) are rated against.
+ * `blocks` CTAs of 256 threads each run 16 independent chains of `iters` (1 .. 2^24) fused
+ * multiply-adds: paired = 0 scalar fma.rn.f32, paired = 1 fma.rn.f32x2 (two FMAs per
+ * instruction).  sink_dev (device float[blocks * 256], caller-owned) receives one value per
+ * thread so that nothing is optimised away; *flop_host receives the launch's FLOP count
+ * (2 per FMA).  Asynchronous on `stream`: time it with events there. */
+occ_status occ_debug_fp32_peak(occ_ctx* ctx, int32_t paired, int32_t iters, int32_t blocks,
+                               float* sink_dev, double* flop_host, void* stream);
+
+/* Measurement aid for the instrumented library only (built with OCC_COUNTERS=1; the product
+ * library returns OCC_ERR_UNSUPPORTED): what the traversal of every launch since the last
+ * reset did on `bvh` (Alg. 1/2 step 1 and the Eq. 7 validation rays).  out_host[5] =
+ * {node visits, triangle tests, distinct nodes touched, distinct triangles touched, bytes of
+ * those distinct nodes and triangles}.  Waits for the device; reset = 1 then zeroes the
+ * counters. */
+occ_status occ_debug_bvh_counters(occ_ctx* ctx, const occ_bvh* bvh, int32_t reset,
+                                  uint64_t* out_host);
 
 /* The traversal on arbitrary rays: rays_dev holds 8 floats per ray (o.xyz, tmax,
  * d.xyz, unused), t in units of |d| on (0, tmax].  any = 0: tri_dev[i] = the closest

@@ -1,6 +1,8 @@
 """ctypes declarations of include/occ.h and the loader of liboccreuse.so.
 
 The library must exist (``build()`` makes it); there is no fallback of any kind.
+OCC_LIB_VARIANT=counters (environment) loads the instrumented build instead (see
+build.VARIANTS), which only measurement runs use.
 """
 from __future__ import annotations
 
@@ -8,7 +10,7 @@ import ctypes as C
 import os
 import threading
 
-from .build import LIB as _LIB, build as _do_build, up_to_date as _up_to_date
+from .build import build as _do_build, lib_path as _lib_path, up_to_date as _up_to_date
 
 c_int32, c_int64, c_uint32, c_uint64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
 c_float, c_double, c_void_p, c_char_p = C.c_float, C.c_double, C.c_void_p, C.c_char_p
@@ -175,6 +177,9 @@ SIGNATURES = {
     "occ_server_shutdown": (c_int32, [c_void_p, c_int32]),
     "occ_server_destroy": (c_int32, [c_void_p, c_int32]),
     "occ_debug_wait_timeout": (c_int32, [c_void_p, c_uint32, c_void_p]),
+    "occ_debug_fp32_peak": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p,
+                                      C.POINTER(c_double), c_void_p]),
+    "occ_debug_bvh_counters": (c_int32, [c_void_p, c_void_p, c_int32, C.POINTER(c_uint64)]),
     "occ_debug_closest_hit": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p,
                                         c_void_p, c_void_p]),
     "occ_debug_philox": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
@@ -190,8 +195,12 @@ _lock = threading.Lock()
 _lib = None
 
 
+def variant() -> str:
+    return os.environ.get("OCC_LIB_VARIANT", "")
+
+
 def library_path() -> str:
-    return _LIB
+    return _lib_path(variant())
 
 
 def load(build_if_missing: bool = True) -> C.CDLL:
@@ -200,11 +209,12 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     with _lock:
         if _lib is not None:
             return _lib
-        path = _LIB
-        if not os.path.exists(path) or not _up_to_date():
+        var = variant()
+        path = _lib_path(var)
+        if not os.path.exists(path) or not _up_to_date(var):
             if not build_if_missing:
-                raise RuntimeError(f"liboccreuse.so is not built ({path}); run build()")
-            _do_build()
+                raise RuntimeError(f"{os.path.basename(path)} is not built ({path}); run build()")
+            _do_build(variant=var)
         lib = C.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)

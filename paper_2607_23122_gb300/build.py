@@ -17,6 +17,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "liboccreuse.so")
+# Library variants: "" is the product library; "counters" is the instrumented build whose
+# traversal counts node visits, triangle tests and the distinct nodes and triangles it
+# touched (occ_debug_bvh_counters), used to measure the bytes a trace launch must read.
+VARIANTS = {"": [], "counters": ["-DOCC_COUNTERS=1"]}
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden,-O3",
@@ -39,24 +43,33 @@ def _deps():
         + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def lib_path(variant: str = "") -> str:
+    if variant not in VARIANTS:
+        raise ValueError(f"unknown library variant {variant!r} (known: {sorted(VARIANTS)})")
+    return LIB if not variant else os.path.join(OUT_DIR, f"liboccreuse_{variant}.so")
+
+
+def up_to_date(variant: str = "") -> bool:
+    lib = lib_path(variant)
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
-    """Compiles the library.  OCC_NVCC_EXTRA (environment) appends nvcc flags, e.g. a
-    tuning define such as -DOCC_TRACE_MIN_BLOCKS=10; set it with force=True."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=None, variant: str = "") -> str:
+    """Compiles the library (or one of VARIANTS).  OCC_NVCC_EXTRA (environment) appends nvcc
+    flags, e.g. a tuning define such as -DOCC_TRACE_MIN_BLOCKS=10; set it with force=True."""
+    lib = lib_path(variant)
+    if not force and up_to_date(variant):
+        return lib
+    obj_dir = OUT_DIR if not variant else os.path.join(OUT_DIR, variant)
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
-    extra = list(extra or []) + os.environ.get("OCC_NVCC_EXTRA", "").split()
+    extra = list(extra or []) + VARIANTS[variant] + os.environ.get("OCC_NVCC_EXTRA", "").split()
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd = [cc, *FLAGS, *extra, "-x", "c++", "-c", src, "-o", obj]
@@ -70,16 +83,17 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"], capture_output=True,
                        text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
+    var = next((a.split("=", 1)[1] for a in sys.argv if a.startswith("--variant=")), "")
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None, variant=var))

@@ -5,6 +5,7 @@
 
 #include <atomic>
 
+#include "occ_f32x2.cuh"
 #include "occ_reuse.cuh"
 
 namespace occ {
@@ -35,16 +36,81 @@ __device__ __forceinline__ T group_load(const T* p) {
     return __ldg(p);
 }
 
+// AO column of candidate (z, n_z) against two receivers at once with paired FP32
+// instructions: the densities of Eq. 15 (without Occ and 1/pi) of members k, k + 1 given
+// their coordinates (xs, ys, zs) and normals (nxs, nys, nzs) as lane pairs.  The operation
+// order is dens_ao's, so each lane equals dens_ao bit for bit; an invalid member carries a
+// zero normal (n_x.d = 0 fails the support test).
+__device__ __forceinline__ float2 dens_ao_x2(f32x2 zx, f32x2 zy, f32x2 zz, f32x2 mnx, f32x2 mny,
+                                             f32x2 mnz, float2 xs, float2 ys, float2 zs,
+                                             float2 nxs, float2 nys, float2 nzs, float R2s) {
+    const f32x2 dx = sub2(zx, pk2(xs.x, xs.y));
+    const f32x2 dy = sub2(zy, pk2(ys.x, ys.y));
+    const f32x2 dz = sub2(zz, pk2(zs.x, zs.y));
+    const f32x2 r2 = dot3x2(dx, dy, dz, dx, dy, dz);
+    const f32x2 a = dot3x2(pk2(nxs.x, nxs.y), pk2(nys.x, nys.y), pk2(nzs.x, nzs.y), dx, dy, dz);
+    const f32x2 b = dot3x2(mnx, mny, mnz, dx, dy, dz);   // -(n_z . d), exactly
+    const float2 A = up2(a), B = up2(b), R = up2(r2), AB = up2(mul2(a, b)), R4 = up2(mul2(r2, r2));
+    const bool ok0 = (A.x > 0.0f) & (B.x > 0.0f) & (R.x > 0.0f) & (R.x <= R2s);
+    const bool ok1 = (A.y > 0.0f) & (B.y > 0.0f) & (R.y > 0.0f) & (R.y <= R2s);
+    return make_float2(ok0 ? __fdividef(AB.x, R4.x) : 0.0f, ok1 ? __fdividef(AB.y, R4.y) : 0.0f);
+}
+
+// Shadow counterpart (Eqs. 20-21 without Occ and 1/Area, dens_sh's operation order): the
+// receivers' precomputed plane terms (n_L.(c - x), (x - c).e_u, (x - c).e_v) come in
+// (nxs, nys, nzs); an invalid member carries zero terms (s_L = 0 fails s_L > 1).  Every
+// term is evaluated for both lanes and the support tests are combined at the end.
+__device__ __forceinline__ float2 dens_sh_x2(f32x2 zx, f32x2 zy, f32x2 zz, f32x2 mnx, f32x2 mny,
+                                             f32x2 mnz, float2 xs, float2 ys, float2 zs,
+                                             float2 hs, float2 us, float2 vs, const RectLight& L) {
+    const f32x2 dx = sub2(zx, pk2(xs.x, xs.y));
+    const f32x2 dy = sub2(zy, pk2(ys.x, ys.y));
+    const f32x2 dz = sub2(zz, pk2(zs.x, zs.y));
+    const float2 nd = up2(dot3x2(bc2(L.n.x), bc2(L.n.y), bc2(L.n.z), dx, dy, dz));
+    const float2 cz = up2(dot3x2(mnx, mny, mnz, dx, dy, dz));   // -(n_z . d), exactly
+    const float2 inv = make_float2(__fdividef(1.0f, nd.x), __fdividef(1.0f, nd.y));
+    const f32x2 inv2 = pk2(inv.x, inv.y);
+    const f32x2 sL = mul2(pk2(hs.x, hs.y), inv2);
+    const f32x2 du = dot3x2(dx, dy, dz, bc2(L.eu.x), bc2(L.eu.y), bc2(L.eu.z));
+    const f32x2 dv = dot3x2(dx, dy, dz, bc2(L.ev.x), bc2(L.ev.y), bc2(L.ev.z));
+    const float2 A = up2(mul2(fma2(sL, du, pk2(us.x, us.y)), bc2(L.inv_eu2)));
+    const float2 B = up2(mul2(fma2(sL, dv, pk2(vs.x, vs.y)), bc2(L.inv_ev2)));
+    const f32x2 neg_inv = pk2(-inv.x, -inv.y);
+    const float2 J = up2(mul2(mul2(mul2(sL, sL), pk2(cz.x, cz.y)), neg_inv));
+    const float2 S = up2(sL);
+    const bool ok0 = (nd.x < 0.0f) & (cz.x > 0.0f) & (S.x > 1.0f) & (fabsf(A.x) <= L.lim) &
+                     (fabsf(B.x) <= L.lim);
+    const bool ok1 = (nd.y < 0.0f) & (cz.y > 0.0f) & (S.y > 1.0f) & (fabsf(A.y) <= L.lim) &
+                     (fabsf(B.y) <= L.lim);
+    return make_float2(ok0 ? J.x : 0.0f, ok1 ? J.y : 0.0f);
+}
+
+template <int EFFECT>
+__device__ __forceinline__ float2 dens_x2(f32x2 zx, f32x2 zy, f32x2 zz, f32x2 mnx, f32x2 mny,
+                                          f32x2 mnz, float2 xs, float2 ys, float2 zs, float2 ns0,
+                                          float2 ns1, float2 ns2, float R2s, const RectLight& L) {
+    if (EFFECT == kAO) return dens_ao_x2(zx, zy, zz, mnx, mny, mnz, xs, ys, zs, ns0, ns1, ns2, R2s);
+    return dens_sh_x2(zx, zy, zz, mnx, mny, mnz, xs, ys, zs, ns0, ns1, ns2, L);
+}
+
 template <int EFFECT, int EST, int GW, int GH, bool PACKED>
 __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs a) {
     constexpr int K = GW * GH;
     constexpr int GPW = 32 / K;
     constexpr int BW = GPW * GW;
+    // Columns without inline validation rays run on paired FP32 instructions, reading the
+    // group's receivers from a structure-of-arrays block (x, y, z and the three receiver
+    // terms, rows of K floats); the inline-validation columns read (x, valid) and receiver
+    // term float4 slots.
+    constexpr bool PAIRED = EST != kUnbiased;
     // receiver exchange buffer; group slots are K + 2 float4 apart so that the groups of a
-    // warp reading their k-th member hit different shared-memory banks
+    // warp reading their k-th member hit different shared-memory banks; the paired blocks
+    // are 6K + 4 (K >= 4) or 6K + 2 floats apart for the same reason
     constexpr int GS = K + 2;
-    __shared__ float4 s_x[OCC_GROUP_WARPS][GPW * GS];
-    __shared__ float4 s_n[OCC_GROUP_WARPS][GPW * GS];
+    constexpr int SS = 6 * K + (K >= 4 ? 4 : 2);
+    __shared__ float4 s_x[OCC_GROUP_WARPS][PAIRED ? 1 : GPW * GS];
+    __shared__ float4 s_n[OCC_GROUP_WARPS][PAIRED ? 1 : GPW * GS];
+    __shared__ __align__(16) float s_soa[OCC_GROUP_WARPS][PAIRED ? GPW * SS : 4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane / K, m = lane % K;
     // the CTA's warps sit side by side: each row of the CTA is contiguous pixels
@@ -86,8 +152,18 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
     }
     // receiver data for the density: AO (x, n); shadow (x, precomputed plane terms)
     const Recv me = make_recv<EFFECT>(f3(P), nx, valid, L);
-    s_x[warp][g * GS + m] = make_float4(me.x.x, me.x.y, me.x.z, valid ? 1.0f : 0.0f);
-    s_n[warp][g * GS + m] = make_float4(me.n.x, me.n.y, me.n.z, 0.0f);
+    if (PAIRED) {
+        float* sg = &s_soa[warp][g * SS];
+        sg[0 * K + m] = me.x.x;
+        sg[1 * K + m] = me.x.y;
+        sg[2 * K + m] = me.x.z;
+        sg[3 * K + m] = valid ? me.n.x : 0.0f;
+        sg[4 * K + m] = valid ? me.n.y : 0.0f;
+        sg[5 * K + m] = valid ? me.n.z : 0.0f;
+    } else {
+        s_x[warp][g * GS + m] = make_float4(me.x.x, me.x.y, me.x.z, valid ? 1.0f : 0.0f);
+        s_n[warp][g * GS + m] = make_float4(me.n.x, me.n.y, me.n.z, 0.0f);
+    }
     __syncwarp();
 
     const unsigned gmask = (K == 32 ? 0xFFFFFFFFu : ((1u << K) - 1u)) << (g * K);
@@ -99,8 +175,53 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
     float Psum = 0.0f;
     uint32_t need = 0;                                     // kUnbCollect: members to validate
     const uint32_t vb = EST == kUnbFinal && hit ? __ldg(a.vbits + i) : 0u;
+    if (PAIRED) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+        for (int k = 0; k < K; ++k) r[k] = 0.0f;
+        if (hit) {
+            const float* sg = &s_soa[warp][g * SS];
+            const f32x2 zx = bc2(z.x), zy = bc2(z.y), zz = bc2(z.z);
+            const f32x2 mnx = bc2(-nz.x), mny = bc2(-nz.y), mnz = bc2(-nz.z);
+            float2 q[K / 2];
+            if (K >= 4) {
+#pragma unroll
+                for (int k = 0; k < K; k += 4) {
+                    const float4 X = *reinterpret_cast<const float4*>(sg + 0 * K + k);
+                    const float4 Y = *reinterpret_cast<const float4*>(sg + 1 * K + k);
+                    const float4 Z = *reinterpret_cast<const float4*>(sg + 2 * K + k);
+                    const float4 NX = *reinterpret_cast<const float4*>(sg + 3 * K + k);
+                    const float4 NY = *reinterpret_cast<const float4*>(sg + 4 * K + k);
+                    const float4 NZ = *reinterpret_cast<const float4*>(sg + 5 * K + k);
+                    q[k / 2] = dens_x2<EFFECT>(zx, zy, zz, mnx, mny, mnz, make_float2(X.x, X.y),
+                                               make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+                                               make_float2(NX.x, NX.y), make_float2(NY.x, NY.y),
+                                               make_float2(NZ.x, NZ.y), a.R2s, L);
+                    q[k / 2 + 1] = dens_x2<EFFECT>(zx, zy, zz, mnx, mny, mnz, make_float2(X.z, X.w),
+                                                   make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+                                                   make_float2(NX.z, NX.w), make_float2(NY.z, NY.w),
+                                                   make_float2(NZ.z, NZ.w), a.R2s, L);
+                }
+            } else {
+                q[0] = dens_x2<EFFECT>(zx, zy, zz, mnx, mny, mnz,
+                                       *reinterpret_cast<const float2*>(sg + 0 * K),
+                                       *reinterpret_cast<const float2*>(sg + 1 * K),
+                                       *reinterpret_cast<const float2*>(sg + 2 * K),
+                                       *reinterpret_cast<const float2*>(sg + 3 * K),
+                                       *reinterpret_cast<const float2*>(sg + 4 * K),
+                                       *reinterpret_cast<const float2*>(sg + 5 * K), a.R2s, L);
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float qk = (k & 1) ? q[k / 2].y : q[k / 2].x;
+                if (EST == kUnbCollect && qk > 0.0f && k != m) need |= 1u << k;
+                if (EST == kUnbFinal && k != m && !((vb >> k) & 1u)) qk = 0.0f;
+                r[k] = qk;
+                Psum += qk;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < (PAIRED ? 0 : K); ++k) {
         const float4 sx = s_x[warp][g * GS + k];
         const float4 sn = s_n[warp][g * GS + k];
         Recv rk;
@@ -136,8 +257,18 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
         return;
     }
     const float inv = Psum > 0.0f ? 1.0f / Psum : 0.0f;
+    if (PAIRED) {
+        const f32x2 inv2 = bc2(inv);
 #pragma unroll
-    for (int k = 0; k < K; ++k) r[k] *= inv;
+        for (int k = 0; k < K; k += 2) {
+            const float2 v = up2(mul2(pk2(r[k], r[k + 1]), inv2));
+            r[k] = v.x;
+            r[k + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) r[k] *= inv;
+    }
 
     // reduce-scatter over the group's lanes: lane m ends with sum_j r_j[m]
 #pragma unroll

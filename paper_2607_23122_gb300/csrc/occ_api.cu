@@ -165,7 +165,15 @@ occ::RecView rec_view(const occ_occluders* o) {
 }
 
 occ::DevBVH dev_bvh(const occ_bvh* b) {
-    return occ::DevBVH{b->nodes, b->tris, (uint32_t)b->stats.num_nodes, (uint32_t)b->stats.num_tris};
+    occ::DevBVH d{b->nodes, b->tris, (uint32_t)b->stats.num_nodes, (uint32_t)b->stats.num_tris};
+#if OCC_COUNTERS
+    if (b->ctr) {
+        d.ctr = b->ctr;
+        d.node_bits = reinterpret_cast<uint32_t*>(b->ctr + 2);
+        d.tri_bits = d.node_bits + (b->stats.num_nodes + 31) / 32;
+    }
+#endif
+    return d;
 }
 
 occ_status launched(occ_ctx* ctx, cudaError_t e, const char* what) {
@@ -437,6 +445,19 @@ OCC_EXPORT occ_status occ_bvh_build(occ_ctx* ctx, const float* tris_host, int64_
     b->stats.bytes = (int64_t)(nb + tb);
     b->stats.build_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (OCC_COUNTERS) {
+        // two 64-bit counters, then one bit per node and one per triangle slot
+        b->ctr_bytes = 16 + 4 * (size_t)((b->stats.num_nodes + 31) / 32 + (T + 31) / 32);
+        e = cudaMalloc(&b->ctr, b->ctr_bytes);
+        if (e == cudaSuccess) e = cudaMemset(b->ctr, 0, b->ctr_bytes);
+        if (e != cudaSuccess) {
+            cudaFree(b->ctr);
+            cudaFree(b->nodes);
+            cudaFree(b->tris);
+            delete b;
+            return cuda_fail(ctx, e, "bvh counters");
+        }
+    }
     *out = b;
     return OCC_OK;
 }
@@ -446,6 +467,7 @@ OCC_EXPORT occ_status occ_bvh_free(occ_ctx* ctx, occ_bvh* bvh) {
     cudaSetDevice(bvh->device);
     cudaFree(bvh->nodes);
     cudaFree(bvh->tris);
+    cudaFree(bvh->ctr);
     delete bvh;
     return OCC_OK;
 }
@@ -648,6 +670,51 @@ OCC_EXPORT occ_status occ_debug_closest_hit(occ_ctx* ctx, const occ_bvh* bvh, co
                                                   n, any != 0, tri_dev, t_dev, ctx->status,
                                                   (cudaStream_t)stream),
                     "debug_closest_hit launch");
+}
+
+OCC_EXPORT occ_status occ_debug_fp32_peak(occ_ctx* ctx, int32_t paired, int32_t iters,
+                                          int32_t blocks, float* sink_dev, double* flop_host,
+                                          void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if ((paired != 0 && paired != 1) || iters < 1 || iters > (1 << 24) || blocks < 1 ||
+        blocks > (1 << 20) || !sink_dev || !flop_host)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "bad fp32_peak arguments");
+    return launched(ctx,
+                    occ::launch_fp32_peak(paired, iters, blocks, sink_dev, flop_host,
+                                          (cudaStream_t)stream),
+                    "fp32 probe launch");
+}
+
+OCC_EXPORT occ_status occ_debug_bvh_counters(occ_ctx* ctx, const occ_bvh* bvh, int32_t reset,
+                                             uint64_t* out_host) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if (!bvh || !out_host) return fail(ctx, OCC_ERR_INVALID_ARG, "bad bvh_counters arguments");
+    if (!OCC_COUNTERS || !bvh->ctr)
+        return fail(ctx, OCC_ERR_UNSUPPORTED,
+                    "traversal counters need the instrumented library (OCC_COUNTERS=1)");
+    cudaError_t e = cudaDeviceSynchronize();
+    std::vector<uint32_t> words(bvh->ctr_bytes / 4);
+    if (e == cudaSuccess) e = cudaMemcpy(words.data(), bvh->ctr, bvh->ctr_bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "counter read");
+    uint64_t visits[2];
+    std::memcpy(visits, words.data(), 16);
+    const size_t nw = (size_t)(bvh->stats.num_nodes + 31) / 32;
+    uint64_t nodes = 0, tris = 0;
+    for (size_t i = 0; i < nw; ++i) nodes += (uint64_t)__builtin_popcount(words[4 + i]);
+    for (size_t i = 4 + nw; i < words.size(); ++i) tris += (uint64_t)__builtin_popcount(words[i]);
+    out_host[0] = visits[0];
+    out_host[1] = visits[1];
+    out_host[2] = nodes;
+    out_host[3] = tris;
+    out_host[4] = nodes * sizeof(occ::BvhNode) + tris * 3 * sizeof(float4);
+    if (reset) {
+        e = cudaMemset(bvh->ctr, 0, bvh->ctr_bytes);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "counter reset");
+    }
+    return OCC_OK;
 }
 
 OCC_EXPORT occ_status occ_debug_wait_timeout(occ_ctx* ctx, uint32_t spins, void* stream) {
@@ -945,7 +1012,8 @@ namespace {
 constexpr int64_t kNoAllocMaxPixels = int64_t(1) << 20;   // e.g. 1280x720 or 1024x1024
 constexpr int kNoAllocMaxDevices = 64;
 
-// [0, 2 * max) : two float4 record planes; [2 * max] : device status word (+ padding)
+// [0, 2 * max) : two float4 record planes; [2 * max] : device status word; [2 * max + 1] :
+// work counter of the persistent AO trace (the rest is padding)
 static __device__ __align__(256) float4 g_noalloc_scratch[2 * kNoAllocMaxPixels + 16];
 
 std::mutex g_noalloc_mutex;
@@ -1007,12 +1075,15 @@ OCC_EXPORT occ_status occ_frame_noalloc(const occ_gbuffer* gb, const occ_bvh* bv
     }
     const occ::RecView rec{base, base + P};
     unsigned* status = reinterpret_cast<unsigned*>(base + 2 * kNoAllocMaxPixels);
+    unsigned* counter = reinterpret_cast<unsigned*>(base + 2 * kNoAllocMaxPixels + 1);
     cudaStream_t s = (cudaStream_t)stream;
     const occ::LightParams lp = to_params(effect == OCC_EFFECT_SHADOW ? light : nullptr);
     const occ::DevBVH b = dev_bvh(bvh);
     e = cudaMemsetAsync(status, 0, sizeof(unsigned), s);
+    // the counter selects the same trace kernels as occ_trace_ao / occ_trace_shadow
     if (e == cudaSuccess)
-        e = occ::launch_trace(effect, view(gb), b, radius, lp, seed, sample, rec, status, s);
+        e = occ::launch_trace(effect, view(gb), b, radius, lp, seed, sample, rec, status, s,
+                              counter);
     if (e == cudaSuccess)
         e = occ::launch_reuse(effect, estimator, view(gb), rec, pat, radius, lp,
                               estimator == OCC_EST_UNBIASED ? &b : nullptr, out, status, s);

@@ -124,9 +124,8 @@ __device__ __forceinline__ bool gb_valid(const float4* pos, bool packed, int p) 
     return packed ? __float_as_uint(q.w) != kOctInvalid : q.w != 0.0f;
 }
 
-// Packed record: words 0-1 = 64 bits holding dz = z - x_source as three 21-bit signed
-// fixed-point numbers (units of scale * 2^-20; bits 0-20, 21-41, 42-62) and bit 63 set;
-// word 2 = octahedral n_z; word 3 = triangle id (-1: no occluder).
+// Packed record: words 0-1 = a 64-bit word holding the occluder offset (below) in bits
+// 0-62 and bit 63 set; word 2 = octahedral n_z; word 3 = triangle id (-1: no occluder).
 // Packed occluder offset d = z - x_source: three 19-bit two's-complement mantissas m with a
 // shared exponent E (6 bits), d = m * 2^(E - 60).  E = floor(log2 max|d_i|) + 43, so the
 // largest component uses 17-18 bits and every component is rounded to a unit of
@@ -403,6 +402,24 @@ __device__ __forceinline__ uint32_t pop_next(const StackEntry* stack, int& sp, f
 
 __device__ __forceinline__ bool is_leaf_ref(uint32_t ref) { return (ref & kLeafBit) != 0u; }
 
+// Instrumented build (OCC_COUNTERS): a visit of node n / a test of triangle slot s.
+__device__ __forceinline__ void count_node(const DevBVH& bvh, uint32_t n) {
+#if OCC_COUNTERS
+    if (bvh.ctr) {
+        atomicAdd(bvh.ctr + 0, 1ull);
+        atomicOr(bvh.node_bits + (n >> 5), 1u << (n & 31u));
+    }
+#endif
+}
+__device__ __forceinline__ void count_tri(const DevBVH& bvh, uint32_t s) {
+#if OCC_COUNTERS
+    if (bvh.ctr) {
+        atomicAdd(bvh.ctr + 1, 1ull);
+        atomicOr(bvh.tri_bits + (s >> 5), 1u << (s & 31u));
+    }
+#endif
+}
+
 // Resumable closest-hit traversal of one ray on (0, tmax] (t in units of |d|).  While-while
 // order: each round walks internal nodes until every active lane of the warp holds a
 // postponed leaf, then all lanes test their leaves together, which keeps the lanes on the
@@ -455,6 +472,7 @@ __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, Stac
         }
 #endif
         uint32_t next;
+        count_node(bvh, t.cur);
         visit_node(bvh, t.cur, t.r, t.tbest, stack, t.sp, t.overflow, &next);
         t.cur = next != kEmptyRef ? next : pop_next(stack, t.sp, t.tbest);
         if (t.cur != kEmptyRef && is_leaf_ref(t.cur) && t.leaf == kEmptyRef) {
@@ -475,6 +493,7 @@ __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, Stac
 #endif
         for (uint32_t i = 0; i < count; ++i) {
             const float4* tr = bvh.tris + 3ull * (first + i);
+            count_tri(bvh, first + i);
             triangle_test(t.r, __ldg(tr), __ldg(tr + 1), __ldg(tr + 2), first + i, t.tbest,
                           t.best_id, t.best_slot);
             if (ANY && t.best_id != kNoHit) break;
@@ -528,6 +547,7 @@ __device__ __forceinline__ bool any_hit(const DevBVH& bvh, float3 o, float3 d, f
 __device__ __forceinline__ uint32_t start_node(const DevBVH& bvh, float3 qlo, float3 qhi) {
     uint32_t cur = 0;
     for (int level = 0; level < kStackSize; ++level) {
+        count_node(bvh, cur);
         const float4* nb = reinterpret_cast<const float4*>(bvh.nodes + cur);
         int count = 0;
         uint32_t only = kEmptyRef;

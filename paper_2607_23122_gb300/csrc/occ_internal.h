@@ -48,6 +48,10 @@ struct occ_bvh {
     float4* tris = nullptr;
     occ_bvh_stats stats{};
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // scene bounds
+    // instrumented build only (OCC_COUNTERS): visit counters and touched-node / triangle
+    // bitmaps, one allocation
+    unsigned long long* ctr = nullptr;
+    size_t ctr_bytes = 0;
 };
 
 namespace occ {

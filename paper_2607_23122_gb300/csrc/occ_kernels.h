@@ -16,7 +16,9 @@ struct GBufView {
 };
 
 // Occluder records.  FP32: plane 0 (z.xyz, tri id bits), plane 1 (n_z.xyz, t).
-// Packed: plane 0 only, (half3 z - x_source, flags, octahedral n_z, tri id).
+// Packed: plane 0 only, 16 bytes per pixel: the 64-bit offset word (z - x_source as three
+// 19-bit mantissas with a shared exponent, bit 63 = occluder present), the octahedral n_z
+// code and the tri id.
 struct RecView {
     float4* r0;
     float4* r1;
@@ -84,6 +86,9 @@ cudaError_t launch_debug_closest_hit(const DevBVH& bvh, const float4* rays, int6
 cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
                               const LightParams& light, uint64_t seed, uint32_t sample,
                               float4* out, cudaStream_t s);
+// FP32 throughput probe (kernels_probe.cu): *flop = FLOPs of the launch.
+cudaError_t launch_fp32_peak(int paired, int iters, int blocks, float* sink, double* flop,
+                             cudaStream_t s);
 
 // Launch choices (0 = default); see occ_tuning.
 struct Tuning {

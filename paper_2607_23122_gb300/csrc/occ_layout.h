@@ -44,10 +44,23 @@ constexpr uint32_t kStatusStackOverflowBit = 1u << 0;
 constexpr uint32_t kStatusWaitTimeoutBit = 1u << 1;
 constexpr uint32_t kStatusBadIndexBit = 1u << 2;
 
+// OCC_COUNTERS=1 (the "counters" library variant): every node visit and triangle test of
+// the traversal is counted, and the distinct nodes and triangles touched are marked in
+// bitmaps, so that the bytes a launch must read from the BVH can be measured.  The product
+// library is built without it.
+#ifndef OCC_COUNTERS
+#define OCC_COUNTERS 0
+#endif
+
 struct DevBVH {
     const BvhNode* nodes;
     const float4* tris;
     uint32_t n_nodes = 0, n_tris = 0;   // bounds the OCC_CHECKS build verifies
+#if OCC_COUNTERS
+    unsigned long long* ctr = nullptr;   // [0] node visits, [1] triangle tests
+    uint32_t* node_bits = nullptr;       // one bit per node touched
+    uint32_t* tri_bits = nullptr;        // one bit per triangle slot touched
+#endif
 };
 
 // OCC_CHECKS=1: the traversal checks every node and triangle index it follows against the

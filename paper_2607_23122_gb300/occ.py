@@ -435,6 +435,25 @@ def occ_debug_closest_hit(ctx: Context, bvh: BVH, o, d, tmax, any_hit: bool = Fa
     return tri.cpu().numpy(), t.cpu().numpy()
 
 
+def occ_debug_fp32_peak(ctx: Context, paired: bool, iters: int, blocks: int, sink: torch.Tensor,
+                        stream=None) -> float:
+    """Launches the FP32 throughput probe on `stream`; returns the launch's FLOP count."""
+    assert sink.dtype == torch.float32 and sink.is_cuda and sink.numel() >= blocks * 256
+    flop = C.c_double()
+    ctx.check(ctx.lib.occ_debug_fp32_peak(ctx.handle, int(bool(paired)), int(iters), int(blocks),
+                                          sink.data_ptr(), C.byref(flop), _stream_handle(stream)))
+    return float(flop.value)
+
+
+def occ_debug_bvh_counters(ctx: Context, bvh: BVH, reset: bool = True) -> dict:
+    """Traversal counters of the instrumented library since the last reset."""
+    out = (C.c_uint64 * 5)()
+    ctx.check(ctx.lib.occ_debug_bvh_counters(ctx.handle, bvh.handle, int(bool(reset)), out))
+    return {"node_visits": int(out[0]), "triangle_tests": int(out[1]),
+            "distinct_nodes": int(out[2]), "distinct_triangles": int(out[3]),
+            "distinct_bytes": int(out[4])}
+
+
 def occ_debug_wait_timeout(ctx: Context, spins: int = 1000, stream=None):
     ctx.check(ctx.lib.occ_debug_wait_timeout(ctx.handle, int(spins), _stream_handle(stream)))
 

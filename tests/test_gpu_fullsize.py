@@ -24,6 +24,10 @@ pytestmark = pytest.mark.gpu
 
 AO, SH = 0, 1
 BIASED, BOXMEAN = 1, 3
+# a support test (AO radius, light plane, rectangle edge) this close to its threshold, in
+# the oracle's relative margin, can be moved across it by the packing: offsets keep 2^-17 of
+# |z - x|, which the shadow tests amplify by the extension factor s_L to the light
+PACK_MARGIN = 2e-3
 
 
 @pytest.fixture(scope="module")
@@ -170,54 +174,65 @@ def test_4k_packed_trace_and_reuse(orc, occ, ctx, uhd, effect):
                             light=light)
         P.compare_out(g, ref, mg, valid, f"4K packed {pname}")
         # packing error against the full-precision oracle on the unpacked scene
-        full, _ = orc.reuse(None, effect, uhd["pos"], uhd["nrm"], orec, pat.as_tuple(), BIASED,
-                            radius=0.5, light=light)
-        e = np.abs(g - full)[valid]
-        errs.append(e)
-        print(f"4K packed effect {effect} {pname}: packing error max {e.max():.2e} "
-              f"p99.9 {np.quantile(e, 0.999):.2e} mean {e.mean():.2e} "
-              f"over 1e-3: {(e > 1e-3).mean():.2e}")
-    e = np.concatenate(errs)
-    # isolated support-test flips (a candidate's ray grazing the rectangle edge or the AO
-    # sphere) are the only pixels over 1e-3
-    assert np.quantile(e, 0.999) <= 1e-3 and (e > 1e-3).mean() <= 2e-4
+        full, mgf = orc.reuse(None, effect, uhd["pos"], uhd["nrm"], orec, pat.as_tuple(), BIASED,
+                              radius=0.5, light=light)
+        e = np.where(valid, np.abs(g - full), 0.0)
+        over = e > 1e-3
+        # conditioning at packing precision: the full-precision estimate on the unpacked
+        # records and G-buffer (what the packed kernels read), computed by the oracle
+        kap = np.where(valid, np.abs(ref - full), 0.0)
+        errs.append((pname, e, over, mgf, kap))
+        ev = e[valid]
+        print(f"4K packed effect {effect} {pname}: packing error max {ev.max():.2e} "
+              f"p99.9 {np.quantile(ev, 0.999):.2e} mean {ev.mean():.2e} "
+              f"over 1e-3: {over.sum()} ({over.sum() / valid.sum():.2e})")
+    # every pixel over 1e-3 against the full-precision oracle is listed with its support
+    # margin there; each must be a support test within packing reach of its threshold
+    # (margin < PACK_MARGIN) or ill-conditioned at packing precision, and there may be at
+    # most 1e-4 of the pixels per pattern
+    for (pname, e, over, mgf, kap) in errs:
+        expl = (mgf < PACK_MARGIN) | (kap >= 2.5e-4)
+        print(f"4K packed effect {effect} {pname}: listed over 1e-3: "
+              f"{[(int(y), int(x), float(e[y, x]), float(mgf[y, x]), float(kap[y, x])) for y, x in np.argwhere(over)][:12]}")
+        assert not (over & ~expl).any(), f"{pname}: unexplained packing errors over 1e-3"
+        assert over.sum() <= P.budget(int(valid.sum())), f"{pname}: {over.sum()} pixels over 1e-3"
 
 
-def test_1080p_sampled_blocks_through_the_bench_frame(orc, occ, ctx, hd):
-    """The bench's own frame: the GPU traces and reuses its own records; on random 32x32
-    blocks whose neighbourhoods hold no trace flip, the estimate matches the oracle's
-    end-to-end estimate (oracle trace + oracle reuse).  Each side reuses its own records,
-    which differ by the FP32 rounding of z = x + t w (close occluders turn it into up to
-    ~1e-4 on the estimate), so the bound is the end-to-end one: at most 2e-3 of the
-    pixels over 1e-5 and the 99.9th percentile under 1e-4."""
-    pat = _pats(occ)["disk8"]
-    o = occ.occ_trace_ao(ctx, hd["gb"], hd["bvh"], 0.5, 1, 7)
-    g = occ.occ_reuse_ao(ctx, hd["gb"], o, pat, 8, BIASED)
+@pytest.mark.parametrize("effect", [AO, SH])
+def test_1080p_end_to_end_bench_frame(orc, occ, ctx, hd, effect):
+    """The bench's own frame, whole: the GPU traces and reuses its own records (disk-8 window
+    and 4x2 groups, biased), the oracle traces and reuses its own.  P5 as in
+    tests/_parity.compare_end_to_end: pixels next to a trace disagreement excluded; every other
+    pixel within 1e-5, or listed and explained by the oracle's own conditioning (its FP64
+    estimate moves by >= 2.5e-6 when the records move by 2 FP32 ulps) or a support margin;
+    at most 1e-4 of the pixels unexplained."""
+    light = synth.light_c3().as_array()
+    o = (occ.occ_trace_ao(ctx, hd["gb"], hd["bvh"], 0.5, 1, 7) if effect == AO else
+         occ.occ_trace_shadow(ctx, hd["gb"], hd["bvh"], light, 1, 7))
     ctx.sync()
-    g = g.cpu().numpy()
-    _, _, gtri = P.gpu_records(o)
-    rng = np.random.default_rng(17)
-    offs = synth.disk_offsets(8, 15.0, seed=3)
-    hx0, hx1 = -offs[:, 0].min(), offs[:, 0].max()
-    hy0, hy1 = -offs[:, 1].min(), offs[:, 1].max()
-    checked, errs = 0, []
-    for _ in range(24):
-        x0 = int(rng.integers(hx0, 1920 - 32 - hx1))
-        y0 = int(rng.integers(hy0, 1080 - 32 - hy1))
-        reg = (x0 - hx0, y0 - hy0, 32 + hx0 + hx1, 32 + hy0 + hy1)
-        orec, _ = orc.trace(hd["osc"], AO, hd["pos"], hd["nrm"], radius=0.5, seed=1, sample=7,
-                            region=reg)
-        xs, ys = slice(reg[0], reg[0] + reg[2]), slice(reg[1], reg[1] + reg[3])
-        if np.any((orec[ys, xs, 7] != gtri[ys, xs]) & hd["valid"][ys, xs]):
-            continue                                   # a grazing flip in the neighbourhood
-        ref, mg = orc.reuse(None, AO, hd["pos"], hd["nrm"], orec, pat.as_tuple(), BIASED,
-                            radius=0.5, region=(x0, y0, 32, 32))
-        sl = (slice(y0, y0 + 32), slice(x0, x0 + 32))
-        v = hd["valid"][sl]
-        assert np.all(g[sl][~v] == 1.0)
-        errs.append(np.abs(g[sl].astype(np.float64) - ref[sl])[v])
-        checked += 1
-    assert checked >= 12
-    e = np.concatenate(errs)
-    print(f"sampled blocks: {checked}, max err {e.max():.2e}, over 1e-5: {(e > 1e-5).mean():.2e}")
-    assert (e > P.OUT_ATOL).mean() <= 2e-3 and np.quantile(e, 0.999) <= 1e-4
+    orec, omg = orc.trace(hd["osc"], effect, hd["pos"], hd["nrm"], radius=0.5, light=light,
+                          seed=1, sample=7)
+    tr = P.compare_trace(o, orec, omg, hd["valid"], hd["pos"], f"1080p trace {effect} sample 7")
+    r0, r1, _ = P.gpu_records(o)
+    grec = P.widen_records(r0, r1)
+    fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
+    for pname in ("disk8", "group4x2"):
+        pat = _pats(occ)[pname]
+        g = fn(ctx, hd["gb"], o, pat, 8, BIASED)
+        ctx.sync()
+        pt = pat.as_tuple()
+        rmin, flip_nb = P.neighbourhood_stats(hd["pos"], orec, pt, tr["flip_mask"])
+        ref, mg = orc.reuse(None, effect, hd["pos"], hd["nrm"], orec, pt, BIASED, radius=0.5,
+                            light=light)
+        on_g, mg_g = orc.reuse(None, effect, hd["pos"], hd["nrm"], grec, pt, BIASED, radius=0.5,
+                               light=light)
+        kappa = P.conditioning(orc, None, effect, hd["pos"], hd["nrm"], orec, pt, BIASED,
+                               radius=0.5, light=light)
+        res = P.compare_end_to_end(g.cpu().numpy(), ref, on_g, np.minimum(mg, mg_g), kappa, rmin,
+                                   flip_nb, hd["valid"], f"1080p e2e {pname} effect {effect}")
+        print(f"1080p end-to-end effect {effect} {pname}: max {res['max_err']:.2e}, p99.99 "
+              f"{res['p9999']:.2e}, over 1e-5 {res['over']} ({res['over_frac']:.2e}; r_min median "
+              f"{res.get('rmin_listed_q50_q90')} vs {res.get('rmin_all_q50')} overall), unexplained "
+              f"{res['unexplained']}, excluded {res['excluded_flip_nb']} next to {tr['mismatch']} "
+              f"trace flips; trace: {tr['grazing']} grazing-term hits, z error p99.9 "
+              f"{tr['z_err_ulps_p999']:.2f} ulp")

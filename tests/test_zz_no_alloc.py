@@ -49,15 +49,20 @@ def _noalloc(occ, gb, bvh, effect, radius, light, seed, sample, pat, est, out):
     return st, flags.value, msg.value.decode()
 
 
-@pytest.mark.parametrize("effect,est,pname", [(0, 1, "disk"), (0, 2, "box"), (1, 1, "group"),
-                                              (1, 3, "box")])
-def test_noalloc_matches_allocating_path_twice(setup, effect, est, pname):
+@pytest.mark.parametrize("effect,est,pname,packed", [(0, 1, "disk", False), (0, 2, "box", False),
+                                                     (1, 1, "group", False), (1, 3, "box", False),
+                                                     (0, 1, "group", True)])
+def test_noalloc_matches_allocating_path_twice(setup, effect, est, pname, packed):
     import torch
     occ, ctx, bvh, gb = setup
+    if packed:                 # packed G-buffer; the scratch records stay FP32
+        gb = occ.occ_pack_gbuffer(ctx, gb)
+        ctx.sync()
     pat = {"disk": occ.Pattern.offsets_of(synth.disk_offsets(8, 6.0, seed=3)),
            "box": occ.Pattern.box(3, 3), "group": occ.Pattern.group(4, 2)}[pname]
     light = np.array([0.0, 0.5, 3.0, 3.0, 0, 0, 0, -3.0, 0], dtype=np.float32)
     radius = 1.0
+    outs = []
     for sample in (0, 1):      # two calls in a row share the static scratch
         out = torch.full((gb.H, gb.W), -7.0, device="cuda")
         st, flags, msg = _noalloc(occ, gb, bvh, effect, radius, light, 11, sample, pat, est, out)
@@ -68,6 +73,10 @@ def test_noalloc_matches_allocating_path_twice(setup, effect, est, pname):
         ref = fn(ctx, gb, rec, pat, pat.K, est, bvh=bvh if est == 2 else None)
         ctx.sync()
         assert torch.allclose(out, ref, rtol=0.0, atol=TOL), (out - ref).abs().max().item()
+        outs.append(out)
+    # the second call's records replaced the first call's in the shared scratch: the two
+    # samples' estimates differ
+    assert (outs[0] != outs[1]).sum().item() >= 10
 
 
 def test_noalloc_rejects_frames_over_the_limit(setup):
