@@ -730,9 +730,22 @@ def run_ours(args):
     # the paper's own layout: 4x2 shared groups (K = 8) on warp lanes, HBM bound
     extra = {}
     if rank == 0:
+        g42 = occ.Pattern.group(4, 2)
         extra["reuse_group4x2"] = time_kernel(
-            lambda st: occ.occ_reuse_ao(ctx, gb, rec, occ.Pattern.group(4, 2), 8, occ.OCC_EST_BIASED,
-                                        out=out, stream=st), flush, stream, 200)
+            lambda st: occ.occ_reuse_ao(ctx, gb, rec, g42, 8, occ.OCC_EST_BIASED, out=out,
+                                        stream=st), flush, stream, 200)
+        # the group kernel's L2 prefetch choices (tuning group_prefetch 1 / 2 / 3)
+        pf = {}
+        try:
+            for c in (1, 2, 3):
+                occ.occ_set_tuning(ctx, group_prefetch=c)
+                pf[c] = time_kernel(lambda st: occ.occ_reuse_ao(ctx, gb, rec, g42, 8,
+                                                                occ.OCC_EST_BIASED, out=out,
+                                                                stream=st), flush, stream, 200)
+        finally:
+            occ.occ_set_tuning(ctx)
+        extra["reuse_group4x2"]["prefetch_choices_ms"] = {
+            {1: "none", 2: "gbuffer+rec0", 3: "gbuffer+rec0+rec1"}[c]: v["ms"] for c, v in pf.items()}
         extra["shadow"] = shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream)
         extra["packed"] = packed_frame(occ, ctx, gb, bvh, pat, out, flush, stream)
         extra["fused"] = fused_frame(occ, ctx, gb, bvh, rec, out, flush, stream)

@@ -75,8 +75,16 @@ enum { OCC_EST_NOREUSE = 0, OCC_EST_BIASED = 1, OCC_EST_UNBIASED = 2, OCC_EST_BO
  *  GROUP:   the screen is partitioned into gw x gh blocks; N_i is i's block.
  *  BOX:     the gw x gh window centred on i (dx in [-(gw-1)/2, gw/2]).
  *  OFFSETS: i plus i + (dx, dy) for each of n_offsets shared offsets.
+ *  RANDOM:  i plus n_offsets offsets drawn for each receiver and sample (the per-receiver
+ *           form of Eq. 8): slot s (1 .. n_offsets) of receiver pixel p takes the first
+ *           attempt a (0 .. 31) of Philox4x32-10 with counter (p, sample, 2, 32 s + a), key
+ *           (seed low 32 bits, seed high 32 bits), whose words w0, w1 give
+ *           dx = floor(w0 (2R + 1) / 2^32) - R, dy = floor(w1 (2R + 1) / 2^32) - R with
+ *           dx^2 + dy^2 <= R^2, (dx, dy) != (0, 0) and not drawn by an earlier slot of p
+ *           (R = radius_px; `sample` is the occluder records' sample); a slot without such
+ *           an attempt stays empty.
  * Members outside the image or with an invalid G-buffer entry are dropped. */
-enum { OCC_PAT_GROUP = 0, OCC_PAT_BOX = 1, OCC_PAT_OFFSETS = 2 };
+enum { OCC_PAT_GROUP = 0, OCC_PAT_BOX = 1, OCC_PAT_OFFSETS = 2, OCC_PAT_RANDOM = 3 };
 
 /* Storage formats.  FP32: as described at occ_gbuffer / occ_occluders.  PACKED (16 bytes
  * per pixel each, FP32 arithmetic on the unpacked values):
@@ -134,8 +142,10 @@ typedef struct {
 typedef struct {
     int32_t kind;              /* OCC_PAT_* */
     int32_t gw, gh;            /* GROUP / BOX extent */
-    int32_t n_offsets;         /* OFFSETS: number of (dx, dy) pairs, K - 1 */
+    int32_t n_offsets;         /* OFFSETS / RANDOM: number of offsets, K - 1 */
     const int32_t* offsets_host;   /* OFFSETS: 2 * n_offsets ints, copied at call time */
+    int32_t radius_px;         /* RANDOM: disk radius R in pixels, 1 .. 64 */
+    uint64_t seed;             /* RANDOM: key of the offset draws */
 } occ_pattern;
 
 typedef struct {
@@ -319,6 +329,9 @@ typedef struct {
     int32_t batch_ctas_per_sm;   /* persistent batched kernels: CTAs per SM (1 .. 16) */
     int32_t fused_ao_path;       /* occ_trace_reuse_ao: 1 one CTA per 16 x 8 tile, 2 persistent
                                     CTAs refilling whole groups from the context's counter */
+    int32_t group_prefetch;      /* GROUP reuse kernel: 1 no prefetch, 2 each CTA prefetches into
+                                    L2 the G-buffer and record plane 0 of the CTA one wave of
+                                    resident CTAs later, 3 also its hit-normal plane */
 } occ_tuning;
 occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t);
 occ_status occ_get_tuning(const occ_ctx* ctx, occ_tuning* t);

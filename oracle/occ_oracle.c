@@ -19,6 +19,8 @@
  *                          step 1); watertight test of Woop, Benthin, Wald,
  *                          JCGT 2013, evaluated in FP64; a median-split binary
  *                          BVH or brute force over all triangles.
+ *   Neighbour sets ....... Eq. 8: group blocks, centred box, shared offsets, and
+ *                          per-receiver random offsets in a disk (drawn with Philox).
  *   Densities ............ Eq. 15 (AO) and Eqs. 20-21 (shadow); with the
  *                          first-hit predicate (unbiased) or without it
  *                          (biased, Eqs. 18 and 24).
@@ -576,9 +578,63 @@ ORC_API void orc_trace(const void* sc, int effect, int W, int H, const float* po
  * -------------------------------------------------------------------------------- */
 #define MAX_MEMBERS 64
 
+/* Kind 3 (RANDOM): a neighbour set drawn per receiver, the per-pixel form of N_i in
+ * Eq. 8 (the paper's neighbourhoods are per receiver; its random disk sets are not
+ * specified further).  Reading: slot s (1 .. n_off) of receiver pixel p takes the first
+ * attempt a (0 .. 31) of Philox4x32-10 with counter (p, sample, 2, 32 s + a) and key
+ * (seed low, seed high) whose first two words w0, w1 give
+ *   dx = floor(w0 (2R + 1) / 2^32) - R,  dy = floor(w1 (2R + 1) / 2^32) - R
+ * with dx^2 + dy^2 <= R^2, (dx, dy) != (0, 0) and (dx, dy) not taken by an earlier slot
+ * of p; a slot with no such attempt stays empty.  Integer arithmetic only. */
+static int random_offset(uint64_t seed, uint32_t pix, uint32_t sample, int slot, int R,
+                         const int* acc, int nacc, int* dx, int* dy) {
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    for (int a = 0; a < 32; ++a) {
+        uint32_t ctr[4] = {pix, sample, 2u, (uint32_t)(32 * slot + a)}, o[4];
+        orc_philox4x32_10(ctr, key, o);
+        int x = (int)(((uint64_t)o[0] * (uint64_t)(2 * R + 1)) >> 32) - R;
+        int y = (int)(((uint64_t)o[1] * (uint64_t)(2 * R + 1)) >> 32) - R;
+        if (x * x + y * y > R * R || (x == 0 && y == 0)) continue;
+        int dup = 0;
+        for (int q = 0; q < nacc; ++q)
+            if (acc[2 * q] == x && acc[2 * q + 1] == y) dup = 1;
+        if (dup) continue;
+        *dx = x;
+        *dy = y;
+        return 1;
+    }
+    return 0;
+}
+
+/* The offsets drawn for receiver pixel p (kind 3), in slot order; returns their count. */
+ORC_API int orc_random_offsets(uint64_t seed, uint32_t pix, uint32_t sample, int R, int n_off,
+                               int32_t* out) {
+    int acc[2 * MAX_MEMBERS], nacc = 0;
+    for (int s = 1; s <= n_off && s < MAX_MEMBERS; ++s) {
+        int dx, dy;
+        if (!random_offset(seed, pix, sample, s, R, acc, nacc, &dx, &dy)) continue;
+        acc[2 * nacc] = dx;
+        acc[2 * nacc + 1] = dy;
+        ++nacc;
+    }
+    for (int q = 0; q < 2 * nacc; ++q) out[q] = acc[q];
+    return nacc;
+}
+
 static int members(int W, int H, const float* pos4, int px, int py, int kind, int gw, int gh,
-                   const int32_t* off, int n_off, int64_t* out) {
+                   const int32_t* off, int n_off, uint64_t pseed, uint32_t psample, int64_t* out) {
     int n = 0;
+    if (kind == 3) {
+        int32_t ro[2 * MAX_MEMBERS];
+        int nr = orc_random_offsets(pseed, (uint32_t)((int64_t)py * W + px), psample, gw, n_off, ro);
+        for (int a = -1; a < nr; ++a) {
+            int x = px + (a < 0 ? 0 : ro[2 * a]), y = py + (a < 0 ? 0 : ro[2 * a + 1]);
+            if (x < 0 || y < 0 || x >= W || y >= H) continue;
+            int64_t q = (int64_t)y * W + x;
+            if (pos4[4 * q + 3] != 0.0f && n < MAX_MEMBERS) out[n++] = q;
+        }
+        return n;
+    }
     if (kind == 0) {
         int bx = (px / gw) * gw, by = (py / gh) * gh;
         for (int y = by; y < by + gh; ++y)
@@ -677,6 +733,8 @@ typedef struct {
     const double* rec;
     int kind, gw, gh, n_off;
     const int32_t* off;
+    uint64_t pseed;     /* kind 3: offset-draw key and sample */
+    uint32_t psample;
     int estimator;
     double R2s;
     light_t L;
@@ -700,7 +758,8 @@ static double reuse_px(const reuse_args* a, int px, int py, double* margin) {
     if (a->pos4[4 * i + 3] == 0.0f) return 1.0;
     if (a->estimator == EST_NOREUSE) return a->rec[8 * i + 7] < 0.0 ? 1.0 : 0.0;
     int64_t m[MAX_MEMBERS];
-    int n = members(a->W, a->H, a->pos4, px, py, a->kind, a->gw, a->gh, a->off, a->n_off, m);
+    int n = members(a->W, a->H, a->pos4, px, py, a->kind, a->gw, a->gh, a->off, a->n_off,
+                    a->pseed, a->psample, m);
     if (a->estimator == EST_BOXMEAN) {
         double v = 0.0;
         for (int q = 0; q < n; ++q) v += a->rec[8 * m[q] + 7] < 0.0 ? 1.0 : 0.0;
@@ -724,13 +783,14 @@ static double reuse_px(const reuse_args* a, int px, int py, double* margin) {
 
 static reuse_args mk_args(const void* sc, int effect, int W, int H, const float* pos4,
                           const float* nrm4, const double* rec, int kind, int gw, int gh,
-                          const int32_t* off, int n_off, int estimator, float radius,
-                          const float* light) {
+                          const int32_t* off, int n_off, uint64_t pseed, uint32_t psample,
+                          int estimator, float radius, const float* light) {
     reuse_args a;
     memset(&a, 0, sizeof(a));
     a.s = (const scene_t*)sc;
     a.effect = effect; a.W = W; a.H = H; a.pos4 = pos4; a.nrm4 = nrm4; a.rec = rec;
     a.kind = kind; a.gw = gw; a.gh = gh; a.off = off; a.n_off = n_off;
+    a.pseed = pseed; a.psample = psample;
     a.estimator = estimator;
     a.R2s = (double)radius * (double)radius * SUPPORT_SLACK;
     if (effect == 1) a.L = mk_light(light);
@@ -739,11 +799,11 @@ static reuse_args mk_args(const void* sc, int effect, int W, int H, const float*
 
 ORC_API void orc_reuse(const void* sc, int effect, int W, int H, const float* pos4,
                        const float* nrm4, const double* rec, int kind, int gw, int gh,
-                       const int32_t* off, int n_off, int estimator, float radius,
-                       const float* light, int x0, int y0, int w, int h, double* out,
-                       double* margin) {
-    reuse_args a = mk_args(sc, effect, W, H, pos4, nrm4, rec, kind, gw, gh, off, n_off, estimator,
-                           radius, light);
+                       const int32_t* off, int n_off, uint64_t pseed, uint32_t psample,
+                       int estimator, float radius, const float* light, int x0, int y0, int w,
+                       int h, double* out, double* margin) {
+    reuse_args a = mk_args(sc, effect, W, H, pos4, nrm4, rec, kind, gw, gh, off, n_off, pseed,
+                           psample, estimator, radius, light);
     int64_t n = (int64_t)w * h;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t q = 0; q < n; ++q) {
@@ -766,12 +826,13 @@ ORC_API void orc_reuse(const void* sc, int effect, int W, int H, const float* po
  * -------------------------------------------------------------------------------- */
 static double light_reuse_px(const scene_t* s, int W, int H, const float* pos4, int px, int py,
                              int kind, int gw, int gh, const int32_t* off, int n_off,
-                             const light_t* L, uint64_t seed, uint32_t sample, double* margin) {
+                             uint64_t pseed, const light_t* L, uint64_t seed, uint32_t sample,
+                             double* margin) {
     int64_t i = (int64_t)py * W + px;
     *margin = INFINITY;
     if (pos4[4 * i + 3] == 0.0f) return 1.0;
     int64_t m[MAX_MEMBERS];
-    int n = members(W, H, pos4, px, py, kind, gw, gh, off, n_off, m);
+    int n = members(W, H, pos4, px, py, kind, gw, gh, off, n_off, pseed, sample, m);
     v3 xh = ldf(pos4 + 4 * i);
     double vis = 0.0;
     for (int q = 0; q < n; ++q) {
@@ -788,9 +849,9 @@ static double light_reuse_px(const scene_t* s, int W, int H, const float* pos4, 
 }
 
 ORC_API void orc_reuse_light(const void* sc, int W, int H, const float* pos4, int kind, int gw,
-                             int gh, const int32_t* off, int n_off, const float* light,
-                             uint64_t seed, uint32_t sample, int x0, int y0, int w, int h,
-                             double* out, double* margin) {
+                             int gh, const int32_t* off, int n_off, uint64_t pseed,
+                             const float* light, uint64_t seed, uint32_t sample, int x0, int y0,
+                             int w, int h, double* out, double* margin) {
     const scene_t* s = (const scene_t*)sc;
     light_t L = mk_light(light);
     int64_t n = (int64_t)w * h;
@@ -800,8 +861,8 @@ ORC_API void orc_reuse_light(const void* sc, int W, int H, const float* pos4, in
         if (px < 0 || py < 0 || px >= W || py >= H) continue;
         int64_t i = (int64_t)py * W + px;
         double mg;
-        out[i] = light_reuse_px(s, W, H, pos4, px, py, kind, gw, gh, off, n_off, &L, seed, sample,
-                                &mg);
+        out[i] = light_reuse_px(s, W, H, pos4, px, py, kind, gw, gh, off, n_off, pseed, &L, seed,
+                                sample, &mg);
         if (margin) margin[i] = mg;
     }
 }
@@ -811,11 +872,12 @@ ORC_API void orc_reuse_light(const void* sc, int W, int H, const float* pos4, in
  * (0 when the sum is 0).  Returns the member count; ids go to members_out. */
 ORC_API int orc_mis_weights(const void* sc, int effect, int W, int H, const float* pos4,
                             const float* nrm4, const double* rec, int kind, int gw, int gh,
-                            const int32_t* off, int n_off, int estimator, float radius,
-                            const float* light, int px, int py, int64_t* members_out, double* w) {
-    reuse_args a = mk_args(sc, effect, W, H, pos4, nrm4, rec, kind, gw, gh, off, n_off, estimator,
-                           radius, light);
-    int n = members(W, H, pos4, px, py, kind, gw, gh, off, n_off, members_out);
+                            const int32_t* off, int n_off, uint64_t pseed, uint32_t psample,
+                            int estimator, float radius, const float* light, int px, int py,
+                            int64_t* members_out, double* w) {
+    reuse_args a = mk_args(sc, effect, W, H, pos4, nrm4, rec, kind, gw, gh, off, n_off, pseed,
+                           psample, estimator, radius, light);
+    int n = members(W, H, pos4, px, py, kind, gw, gh, off, n_off, pseed, psample, members_out);
     for (int q = 0; q < n; ++q) {
         int64_t j = members_out[q];
         double P = 0.0, p[MAX_MEMBERS];
@@ -836,11 +898,13 @@ ORC_API int orc_mis_weights(const void* sc, int effect, int W, int H, const floa
  * -------------------------------------------------------------------------------- */
 ORC_API void orc_accumulate(const void* sc, int effect, int W, int H, const float* pos4,
                             const float* nrm4, int kind, int gw, int gh, const int32_t* off,
-                            int n_off, int estimator, float radius, const float* light,
-                            uint64_t seed, uint32_t sample0, int M, int x0, int y0, int w, int h,
-                            double* mean, double* var) {
+                            int n_off, uint64_t pseed, int estimator, float radius,
+                            const float* light, uint64_t seed, uint32_t sample0, int M, int x0,
+                            int y0, int w, int h, double* mean, double* var) {
     int hx0 = x0, hy0 = y0, hx1 = x0 + w, hy1 = y0 + h;
-    if (kind == 0) {
+    if (kind == 3) {
+        hx0 -= gw; hx1 += gw; hy0 -= gw; hy1 += gw;
+    } else if (kind == 0) {
         hx0 = (x0 / gw) * gw; hy0 = (y0 / gh) * gh;
         hx1 = ((x0 + w + gw - 1) / gw) * gw; hy1 = ((y0 + h + gh - 1) / gh) * gh;
     } else if (kind == 1) {
@@ -863,13 +927,13 @@ ORC_API void orc_accumulate(const void* sc, int effect, int W, int H, const floa
     for (int64_t i = 0; i < (int64_t)w * h; ++i) { mean[i] = 0.0; var[i] = 0.0; }
     for (int m = 0; m < M; ++m) {
         if (estimator == EST_LIGHT_UNBIASED) {
-            orc_reuse_light(sc, W, H, pos4, kind, gw, gh, off, n_off, light, seed,
+            orc_reuse_light(sc, W, H, pos4, kind, gw, gh, off, n_off, pseed, light, seed,
                             sample0 + (uint32_t)m, x0, y0, w, h, out, NULL);
         } else {
             orc_trace(sc, effect, W, H, pos4, nrm4, radius, light, seed, sample0 + (uint32_t)m,
                       hx0, hy0, hx1 - hx0, hy1 - hy0, rec, NULL);
-            orc_reuse(sc, effect, W, H, pos4, nrm4, rec, kind, gw, gh, off, n_off, estimator,
-                      radius, light, x0, y0, w, h, out, NULL);
+            orc_reuse(sc, effect, W, H, pos4, nrm4, rec, kind, gw, gh, off, n_off, pseed,
+                      sample0 + (uint32_t)m, estimator, radius, light, x0, y0, w, h, out, NULL);
         }
         for (int64_t q = 0; q < (int64_t)w * h; ++q) {
             int px = x0 + (int)(q % w), py = y0 + (int)(q / w);

@@ -26,7 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 EFFECT_AO, EFFECT_SHADOW = 0, 1
-PAT_GROUP, PAT_BOX, PAT_OFFSETS = 0, 1, 2
+PAT_GROUP, PAT_BOX, PAT_OFFSETS, PAT_RANDOM = 0, 1, 2, 3
 EST_NOREUSE, EST_BIASED, EST_UNBIASED, EST_BOXMEAN = 0, 1, 2, 3
 EST_LIGHT_UNBIASED = 4       # shadows: unbiased light-sample reuse (Light(N U), Sec. 6.2)
 STREAM_AO, STREAM_SHADOW = 0, 1
@@ -73,19 +73,21 @@ def lib():
                                 C.c_uint64, C.c_uint32, C.c_int, C.c_int, C.c_int, C.c_int,
                                 f64, f64]
         L.orc_reuse.argtypes = [vp, C.c_int, C.c_int, C.c_int, f32, f32, f64, C.c_int, C.c_int,
-                                C.c_int, i32, C.c_int, C.c_int, C.c_float, f32, C.c_int, C.c_int,
-                                C.c_int, C.c_int, f64, f64]
+                                C.c_int, i32, C.c_int, C.c_uint64, C.c_uint32, C.c_int,
+                                C.c_float, f32, C.c_int, C.c_int, C.c_int, C.c_int, f64, f64]
         L.orc_reuse_light.argtypes = [vp, C.c_int, C.c_int, f32, C.c_int, C.c_int, C.c_int, i32,
-                                      C.c_int, f32, C.c_uint64, C.c_uint32, C.c_int, C.c_int,
-                                      C.c_int, C.c_int, f64, f64]
+                                      C.c_int, C.c_uint64, f32, C.c_uint64, C.c_uint32, C.c_int,
+                                      C.c_int, C.c_int, C.c_int, f64, f64]
         L.orc_mis_weights.argtypes = [vp, C.c_int, C.c_int, C.c_int, f32, f32, f64, C.c_int,
-                                      C.c_int, C.c_int, i32, C.c_int, C.c_int, C.c_float, f32,
-                                      C.c_int, C.c_int, i64, f64]
+                                      C.c_int, C.c_int, i32, C.c_int, C.c_uint64, C.c_uint32,
+                                      C.c_int, C.c_float, f32, C.c_int, C.c_int, i64, f64]
         L.orc_mis_weights.restype = C.c_int
         L.orc_accumulate.argtypes = [vp, C.c_int, C.c_int, C.c_int, f32, f32, C.c_int, C.c_int,
-                                     C.c_int, i32, C.c_int, C.c_int, C.c_float, f32, C.c_uint64,
-                                     C.c_uint32, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
-                                     f64, f64]
+                                     C.c_int, i32, C.c_int, C.c_uint64, C.c_int, C.c_float, f32,
+                                     C.c_uint64, C.c_uint32, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.c_int, f64, f64]
+        L.orc_random_offsets.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_int, i32]
+        L.orc_random_offsets.restype = C.c_int
         L.orc_num_threads.restype = C.c_int
         L.orc_set_num_threads.argtypes = [C.c_int]
         L.orc_density.argtypes = [C.c_int, f64, f64, f64, f64, C.c_float, f32]
@@ -201,23 +203,36 @@ def trace(scene: OracleScene, effect: int, pos4: np.ndarray, nrm4: np.ndarray, r
 
 
 def _pattern(pattern):
+    """(kind, gw, gh, flat offsets, n_offsets, pattern seed).  ``pattern`` = (kind, gw, gh,
+    offsets) for groups, boxes and shared offsets, or (PAT_RANDOM, radius_px, n_offsets,
+    seed) for per-receiver random offsets in a disk."""
     kind, gw, gh, off = pattern
+    if kind == PAT_RANDOM:
+        return kind, int(gw), 0, np.zeros(0, dtype=np.int32), int(gh), int(off)
     off = np.zeros((0, 2), dtype=np.int32) if off is None else np.asarray(off, dtype=np.int32)
-    return kind, gw, gh, np.ascontiguousarray(off.reshape(-1)), off.shape[0]
+    return kind, gw, gh, np.ascontiguousarray(off.reshape(-1)), off.shape[0], 0
+
+
+def random_offsets(seed: int, pix: int, sample: int, radius: int, n_offsets: int) -> np.ndarray:
+    """Per-receiver random offsets (pattern kind PAT_RANDOM) of pixel ``pix``: [n, 2] int32."""
+    out = np.zeros(2 * 64, dtype=np.int32)
+    n = lib().orc_random_offsets(seed, pix, sample, radius, n_offsets, out)
+    return out[:2 * n].reshape(n, 2).copy()
 
 
 def reuse(scene, effect: int, pos4, nrm4, rec, pattern, estimator: int, radius: float = 0.0,
-          light=None, region=None, out=None):
+          light=None, region=None, out=None, sample: int = 0):
     """Estimator of Eqs. 17/18/23/24 (or a baseline) for every pixel of ``region``.
 
     ``pattern`` = (kind, gw, gh, offsets): kind 0 group blocks, 1 centred box,
-    2 receiver plus shared offsets [n, 2].  ``scene`` is needed only for the
-    unbiased estimator.  Returns (out float64 [H, W], margin [H, W]); ``out`` = (values,
-    margins) reuses caller buffers.
+    2 receiver plus shared offsets [n, 2]; or (3, radius_px, n_offsets, seed): per-receiver
+    random offsets drawn for ``sample`` (the records' sample index).  ``scene`` is needed
+    only for the unbiased estimator.  Returns (out float64 [H, W], margin [H, W]); ``out``
+    = (values, margins) reuses caller buffers.
     """
     H, W = pos4.shape[:2]
     x0, y0, w, h = region if region is not None else (0, 0, W, H)
-    kind, gw, gh, off, n_off = _pattern(pattern)
+    kind, gw, gh, off, n_off, pseed = _pattern(pattern)
     if out is not None:
         out, mg = out
     else:
@@ -226,8 +241,8 @@ def reuse(scene, effect: int, pos4, nrm4, rec, pattern, estimator: int, radius: 
     lib().orc_reuse(scene.handle if scene is not None else None, effect, W, H,
                     np.ascontiguousarray(pos4, dtype=np.float32),
                     np.ascontiguousarray(nrm4, dtype=np.float32),
-                    np.ascontiguousarray(rec, dtype=np.float64), kind, gw, gh, off, n_off,
-                    estimator, radius, _light(light), x0, y0, w, h, out, mg)
+                    np.ascontiguousarray(rec, dtype=np.float64), kind, gw, gh, off, n_off, pseed,
+                    sample, estimator, radius, _light(light), x0, y0, w, h, out, mg)
     return out, mg
 
 
@@ -237,14 +252,15 @@ def reuse_light(scene, pos4, pattern, light, seed: int, sample: int, region=None
     `seed`).  Returns (out float64 [H, W], margin [H, W])."""
     H, W = pos4.shape[:2]
     x0, y0, w, h = region if region is not None else (0, 0, W, H)
-    kind, gw, gh, off, n_off = _pattern(pattern)
+    kind, gw, gh, off, n_off, pseed = _pattern(pattern)
     if out is not None:
         out, mg = out
     else:
         out = np.full((H, W), np.nan)
         mg = np.full((H, W), np.inf)
     lib().orc_reuse_light(scene.handle, W, H, np.ascontiguousarray(pos4, dtype=np.float32), kind,
-                          gw, gh, off, n_off, _light(light), seed, sample, x0, y0, w, h, out, mg)
+                          gw, gh, off, n_off, pseed, _light(light), seed, sample, x0, y0, w, h,
+                          out, mg)
     return out, mg
 
 
@@ -255,17 +271,18 @@ def density(effect: int, z, nz, x, nx, radius: float = 0.0, light=None) -> float
 
 
 def mis_weights(scene, effect: int, pos4, nrm4, rec, pattern, estimator: int, px: int, py: int,
-                radius: float = 0.0, light=None):
+                radius: float = 0.0, light=None, sample: int = 0):
     """(member pixel ids, weight matrix w[j][k]) seen by receiver (px, py)."""
     H, W = pos4.shape[:2]
-    kind, gw, gh, off, n_off = _pattern(pattern)
+    kind, gw, gh, off, n_off, pseed = _pattern(pattern)
     mem = np.zeros(64, dtype=np.int64)
     w = np.zeros(64 * 64, dtype=np.float64)
     n = lib().orc_mis_weights(scene.handle if scene is not None else None, effect, W, H,
                               np.ascontiguousarray(pos4, dtype=np.float32),
                               np.ascontiguousarray(nrm4, dtype=np.float32),
                               np.ascontiguousarray(rec, dtype=np.float64), kind, gw, gh, off,
-                              n_off, estimator, radius, _light(light), px, py, mem, w)
+                              n_off, pseed, sample, estimator, radius, _light(light), px, py, mem,
+                              w)
     return mem[:n].copy(), w[:n * n].reshape(n, n).copy()
 
 
@@ -275,11 +292,11 @@ def accumulate(scene, effect: int, pos4, nrm4, pattern, estimator: int, radius: 
     sample0 .. sample0 + M - 1, for the pixels of ``region`` -> ([h, w], [h, w])."""
     H, W = pos4.shape[:2]
     x0, y0, w, h = region if region is not None else (0, 0, W, H)
-    kind, gw, gh, off, n_off = _pattern(pattern)
+    kind, gw, gh, off, n_off, pseed = _pattern(pattern)
     mean = np.zeros(w * h, dtype=np.float64)
     var = np.zeros(w * h, dtype=np.float64)
     lib().orc_accumulate(scene.handle, effect, W, H, np.ascontiguousarray(pos4, dtype=np.float32),
                          np.ascontiguousarray(nrm4, dtype=np.float32), kind, gw, gh, off, n_off,
-                         estimator, radius, _light(light), seed, sample0, M, x0, y0, w, h, mean,
-                         var)
+                         pseed, estimator, radius, _light(light), seed, sample0, M, x0, y0, w, h,
+                         mean, var)
     return mean.reshape(h, w), var.reshape(h, w)

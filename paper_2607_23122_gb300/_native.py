@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "OCC_OK", 1: "OCC_ERR_INVALID_ARG", 2: "OCC_ERR_CUDA", 3: "OC
 OCC_EFFECT_AO, OCC_EFFECT_SHADOW = 0, 1
 OCC_EST_NOREUSE, OCC_EST_BIASED, OCC_EST_UNBIASED, OCC_EST_BOXMEAN = 0, 1, 2, 3
 OCC_EST_LIGHT_UNBIASED = 4
-OCC_PAT_GROUP, OCC_PAT_BOX, OCC_PAT_OFFSETS = 0, 1, 2
+OCC_PAT_GROUP, OCC_PAT_BOX, OCC_PAT_OFFSETS, OCC_PAT_RANDOM = 0, 1, 2, 3
 OCC_REC_FP32, OCC_REC_PACKED = 0, 1
 OCC_GB_FP32, OCC_GB_PACKED = 0, 1
 MAX_MEMBERS = 64
@@ -46,7 +46,7 @@ class occ_occluders(C.Structure):
 
 class occ_pattern(C.Structure):
     _fields_ = [("kind", c_int32), ("gw", c_int32), ("gh", c_int32), ("n_offsets", c_int32),
-                ("offsets_host", C.POINTER(c_int32))]
+                ("offsets_host", C.POINTER(c_int32)), ("radius_px", c_int32), ("seed", c_uint64)]
 
 
 class occ_view(C.Structure):
@@ -58,7 +58,8 @@ class occ_view(C.Structure):
 
 class occ_tuning(C.Structure):
     _fields_ = [("reuse_tile_rows", c_int32), ("reuse_window_path", c_int32),
-                ("batch_ctas_per_sm", c_int32), ("fused_ao_path", c_int32)]
+                ("batch_ctas_per_sm", c_int32), ("fused_ao_path", c_int32),
+                ("group_prefetch", c_int32)]
 
 
 class occ_bvh_stats(C.Structure):

@@ -38,6 +38,24 @@ __device__ __forceinline__ int gather_members(const PatternParams& pat, const GB
                                               int y, int* mem, int* self) {
     int n = 0;
     *self = 0;
+    if (pat.kind == 3) {
+        // per-receiver random offsets: the receiver, then each drawn offset in slot order
+        int2 acc[MAXK];
+        int nacc = 0;
+        const uint32_t pix = (uint32_t)y * (uint32_t)gb.W + (uint32_t)x;
+        mem[n++] = (int)pix;   // reuse_pixel calls this for valid receivers only
+        for (int s = 1; s < pat.K && s < MAXK; ++s) {
+            int2 o;
+            if (!random_offset(pat.seed, pix, pat.sample, s, pat.radius, acc, nacc, &o)) continue;
+            acc[nacc++] = o;
+            const int px = x + o.x, py = y + o.y;
+            if (px < 0 || py < 0 || px >= gb.W || py >= gb.H) continue;
+            const int q = py * gb.W + px;
+            if (!gb_valid(gb.pos, gb.packed != 0, q)) continue;
+            mem[n++] = q;
+        }
+        return n;
+    }
     for (int a = 0; a < pat.K; ++a) {
         int px, py;
         if (pat.kind == 0) {
@@ -194,8 +212,9 @@ __global__ void __launch_bounds__(128) k_reuse_light(ReuseArgs a, uint64_t seed,
 // runs the per-receiver evaluation of its view.
 // ---------------------------------------------------------------------------------------
 template <int MAXK>
-__global__ void __launch_bounds__(128) k_reuse_batch(const BatchView* views, int n_views,
-                                                     int n_tiles, DevBVH bvh, unsigned* status) {
+__global__ void __launch_bounds__(128) k_reuse_batch(const BatchView* views, const BatchDyn* dyn,
+                                                     int n_views, int n_tiles, DevBVH bvh,
+                                                     unsigned* status) {
     __shared__ int s_first[kMaxBatchViews + 1];
     for (int v = threadIdx.x; v <= n_views; v += blockDim.x)
         s_first[v] = v < n_views ? views[v].first_tile : n_tiles;
@@ -215,6 +234,7 @@ __global__ void __launch_bounds__(128) k_reuse_batch(const BatchView* views, int
         a.gb = v->gb;
         a.rec = v->rec;
         a.pat = v->pat;
+        a.pat.sample = dyn[lo].sample;   // random patterns draw per sample
         a.R2s = v->R2s;
         a.lp = v->light;
         a.bvh = bvh;
@@ -298,8 +318,20 @@ bool window_pairs(int effect, int K, const Tuning& tune) {
     return tune.window_path == 0 && effect == kAO && K > 9;
 }
 
+// Planes the group kernel prefetches into L2 (tuning choice group_prefetch: 1 none, 2 the
+// G-buffer and record plane 0, 3 also the hit-normal plane; 0 the built-in default).
+#ifndef OCC_GROUP_PREFETCH_DEFAULT
+#define OCC_GROUP_PREFETCH_DEFAULT 2
+#endif
+int group_prefetch_planes(const Tuning& tune) {
+    const int c = tune.group_prefetch ? tune.group_prefetch : OCC_GROUP_PREFETCH_DEFAULT;
+    return c == 2 ? 3 : c == 3 ? 4 : 0;
+}
+
 template <int EFFECT>
-cudaError_t launch_effect(int est, const ReuseArgs& a, cudaStream_t s, const Tuning& tune) {
+cudaError_t launch_effect(int est, const ReuseArgs& a_in, cudaStream_t s, const Tuning& tune) {
+    ReuseArgs a = a_in;
+    a.pf_planes = group_prefetch_planes(tune);
     const dim3 grid((unsigned)((a.gb.W + 15) / 16), (unsigned)((a.gb.H + 7) / 8));
     if (est == kNoReuse) {
         k_reuse_simple<kNoReuse><<<grid, 128, 0, s>>>(a);
@@ -343,6 +375,8 @@ ReuseArgs make_args(const GBufView& gb, const RecView& rec, const PatternParams&
     a.vq = nullptr;
     a.vcount = nullptr;
     a.vbits = nullptr;
+    a.pf_planes = 0;
+    a.pf_ahead = 0;
     return a;
 }
 
@@ -379,7 +413,8 @@ cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const Re
     return e != cudaSuccess ? e : l;
 }
 
-cudaError_t launch_reuse_batch(const BatchView* views, int n_views, int n_tiles, int max_k,
+cudaError_t launch_reuse_batch(const BatchView* views, const BatchDyn* dyn, int n_views,
+                               int n_tiles, int max_k,
                                const DevBVH& bvh, int per_sm_wanted, unsigned* status,
                                cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
@@ -389,7 +424,7 @@ cudaError_t launch_reuse_batch(const BatchView* views, int n_views, int n_tiles,
         per_sm = 1;
     if (per_sm_wanted > 0 && per_sm_wanted < per_sm) per_sm = per_sm_wanted;
     const int ctas = per_sm * sm_count();
-    k<<<ctas < n_tiles ? ctas : n_tiles, 128, 0, s>>>(views, n_views, n_tiles, bvh, status);
+    k<<<ctas < n_tiles ? ctas : n_tiles, 128, 0, s>>>(views, dyn, n_views, n_tiles, bvh, status);
     return cudaGetLastError();
 }
 

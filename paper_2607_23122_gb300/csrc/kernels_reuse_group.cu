@@ -30,6 +30,11 @@ namespace {
 #ifndef OCC_GROUP_STREAM_LOADS
 #define OCC_GROUP_STREAM_LOADS 0
 #endif
+// Fire-and-forget bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ T group_load(const T* p) {
     if (OCC_GROUP_STREAM_LOADS) return __ldcs(p);
@@ -120,6 +125,24 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
     const int i = inside ? y * a.gb.W + x : 0;
     RectLight L;
     if (EFFECT == kShadow) L = make_light(a.lp);
+    // Prefetch into L2 the rows of the CTA one wave of resident CTAs later (CTAs start in
+    // launch order, so its loads then hit L2 instead of waiting for DRAM): one thread per
+    // row and plane, one bulk prefetch each.
+    if (a.pf_planes > 0 && threadIdx.x < (unsigned)(GH * a.pf_planes)) {
+        constexpr int CW = OCC_GROUP_WARPS * BW;
+        const unsigned t = blockIdx.y * gridDim.x + blockIdx.x + (unsigned)a.pf_ahead;
+        if (t < gridDim.x * gridDim.y) {
+            const int px = (int)(t % gridDim.x) * CW, py = (int)(t / gridDim.x) * GH + (int)threadIdx.x % GH;
+            if (py < a.gb.H) {
+                const int n = min(CW, a.gb.W - px);
+                const size_t q = (size_t)py * a.gb.W + px;
+                const int plane = (int)threadIdx.x / GH;
+                const float4* base = plane == 0 ? a.gb.pos : plane == 1 ? (PACKED ? a.rec.r0 : a.gb.nrm)
+                                   : plane == 2 ? a.rec.r0 : a.rec.r1;
+                if (base && !(PACKED && plane >= 2)) prefetch_l2(base + q, (uint32_t)n * 16u);
+            }
+        }
+    }
 
     float4 P = make_float4(0.0f, 0.0f, 0.0f, 0.0f), N = P;
     float4 R0 = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1)), R1 = P;
@@ -356,16 +379,40 @@ __global__ void __launch_bounds__(128, 8)
     if (OCC_CHECKS && bad && a.status) atomicOr(a.status, kStatusBadIndexBit);
 }
 
+// Resident CTAs of a kernel on this device (computed once per kernel; racing threads
+// compute the same value).
+template <typename Kern>
+int resident_ctas(Kern k, std::atomic<int>& cache) {
+    int n = cache.load(std::memory_order_relaxed);
+    if (!n) {
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * OCC_GROUP_WARPS, 0) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        n = per_sm * sm_count();
+        cache.store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 template <int EFFECT, int EST, int GW, int GH>
-void launch_group_t(const ReuseArgs& a, cudaStream_t s) {
+void launch_group_t(const ReuseArgs& a_in, cudaStream_t s) {
     constexpr int K = GW * GH;
     constexpr int BW = (32 / K) * GW;
     constexpr int CW = OCC_GROUP_WARPS * BW;
-    const dim3 grid((unsigned)((a.gb.W + CW - 1) / CW), (unsigned)((a.gb.H + GH - 1) / GH));
-    if (a.gb.packed && a.rec.packed)
-        k_reuse_group<EFFECT, EST, GW, GH, true><<<grid, 32 * OCC_GROUP_WARPS, 0, s>>>(a);
-    else if (!a.gb.packed && !a.rec.packed)
-        k_reuse_group<EFFECT, EST, GW, GH, false><<<grid, 32 * OCC_GROUP_WARPS, 0, s>>>(a);
+    const dim3 grid((unsigned)((a_in.gb.W + CW - 1) / CW), (unsigned)((a_in.gb.H + GH - 1) / GH));
+    ReuseArgs a = a_in;
+    static std::atomic<int> cache[2];
+    if (a.gb.packed && a.rec.packed) {
+        auto k = k_reuse_group<EFFECT, EST, GW, GH, true>;
+        if (a.pf_planes) a.pf_ahead = resident_ctas(k, cache[1]);
+        k<<<grid, 32 * OCC_GROUP_WARPS, 0, s>>>(a);
+    } else if (!a.gb.packed && !a.rec.packed) {
+        auto k = k_reuse_group<EFFECT, EST, GW, GH, false>;
+        if (a.pf_planes) a.pf_ahead = resident_ctas(k, cache[0]);
+        k<<<grid, 32 * OCC_GROUP_WARPS, 0, s>>>(a);
+    }
 }
 
 

@@ -21,12 +21,19 @@
 #include <mutex>
 
 #include "occ_device.cuh"
+#include "occ_f32x2.cuh"
 #include "occ_kernels.h"
 
 namespace occ {
 namespace {
 
 constexpr float kSupportSlackT = 1.0f + 1.0f / 65536.0f;
+
+// AO windows of 4 or 8 member slots evaluate their density columns on paired FP32
+// instructions (OCC_TILE_PAIRED=1; 0 keeps the scalar column).
+#ifndef OCC_TILE_PAIRED
+#define OCC_TILE_PAIRED 1
+#endif
 constexpr int kTileW = 32;
 constexpr uint32_t kWaitSpins = 1u << 24;
 
@@ -213,11 +220,89 @@ __device__ __forceinline__ void staged_cand(const Staged& st, int q, float4 r0, 
     }
 }
 
+// AO densities of candidate (z, n_z) at members s and s + 1 held as lane pairs (receiver
+// point and normal per axis): pair_density<kAO>'s operation order on each lane, so each
+// lane equals it bit for bit.
+__device__ __forceinline__ float2 pair_density_ao_x2(f32x2 zx, f32x2 zy, f32x2 zz, f32x2 mnx,
+                                                     f32x2 mny, f32x2 mnz, const f32x2* px,
+                                                     const f32x2* pn, float R2s) {
+    const f32x2 dx = sub2(zx, px[0]), dy = sub2(zy, px[1]), dz = sub2(zz, px[2]);
+    const f32x2 r2 = dot3x2(dx, dy, dz, dx, dy, dz);
+    const f32x2 a = dot3x2(pn[0], pn[1], pn[2], dx, dy, dz);
+    const f32x2 b = dot3x2(mnx, mny, mnz, dx, dy, dz);   // -(n_z . d), exactly
+    const float2 A = up2(a), B = up2(b), R = up2(r2), AB = up2(mul2(a, b)), R4 = up2(mul2(r2, r2));
+    const bool ok0 = (A.x > 0.0f) & (B.x > 0.0f) & (R.x > 0.0f) & (R.x <= R2s);
+    const bool ok1 = (A.y > 0.0f) & (B.y > 0.0f) & (R.y > 0.0f) & (R.y <= R2s);
+    return make_float2(ok0 ? __fdividef(AB.x, R4.x) : 0.0f, ok1 ? __fdividef(AB.y, R4.y) : 0.0f);
+}
+
+// One thread per receiver, AO, 4 or 8 member slots: the K receivers are held as lane
+// pairs (slots 2j, 2j + 1) and every candidate's column of densities runs on paired FP32
+// instructions (half the issue slots of the scalar column, the same results).
+template <int MAXK, bool PACKED>
+__device__ __forceinline__ void tile_single_ao_x2(const TileArgs& a, const RectLight& L,
+                                                  const Staged& st, int x0, int y0) {
+    constexpr int NP = MAXK / 2;
+    const int lx = threadIdx.x % a.TW, ly = threadIdx.x / a.TW;
+    const int x = x0 + lx, y = y0 + ly;
+    if (ly >= a.TH || x >= a.W || y >= a.H) return;
+    const int sc = (ly + a.hy0) * a.SW + (lx + a.hx0);
+    float res = 1.0f;
+    if (staged_valid<PACKED>(st.pos[sc])) {
+        int sidx[MAXK];
+        const uint32_t vmask = member_mask<MAXK, PACKED>(a, st.pos, x, y, sc, sidx);
+        f32x2 px[NP][3], pn[NP][3];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            float3 x0r, t0, x1r, t1;
+            staged_recv<kAO, PACKED>(st, sidx[2 * j], L, &x0r, &t0);
+            staged_recv<kAO, PACKED>(st, sidx[2 * j + 1], L, &x1r, &t1);
+            if (!((vmask >> (2 * j)) & 1u)) t0 = make_float3(0.0f, 0.0f, 0.0f);
+            if (!((vmask >> (2 * j + 1)) & 1u)) t1 = make_float3(0.0f, 0.0f, 0.0f);
+            px[j][0] = pk2(x0r.x, x1r.x);
+            px[j][1] = pk2(x0r.y, x1r.y);
+            px[j][2] = pk2(x0r.z, x1r.z);
+            pn[j][0] = pk2(t0.x, t1.x);
+            pn[j][1] = pk2(t0.y, t1.y);
+            pn[j][2] = pk2(t0.z, t1.z);
+        }
+        float B = 0.0f;
+#pragma unroll
+        for (int c = 0; c < MAXK; ++c) {
+            if (c >= a.K || !((vmask >> c) & 1u)) continue;
+            const int q = sidx[c];
+            const float4 r0 = st.r0[q];
+            if (__float_as_int(r0.w) < 0) continue;
+            float3 z, nz;
+            staged_cand<PACKED>(st, q, r0, &z, &nz);
+            const f32x2 zx = bc2(z.x), zy = bc2(z.y), zz = bc2(z.z);
+            const f32x2 mnx = bc2(-nz.x), mny = bc2(-nz.y), mnz = bc2(-nz.z);
+            float2 d[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j)
+                d[j] = pair_density_ao_x2(zx, zy, zz, mnx, mny, mnz, px[j], pn[j], a.R2s);
+            // slot 0 is the receiver: its density is the numerator; P_j sums in slot order
+            const float pi = d[0].x;
+            float Psum = pi + d[0].y;
+#pragma unroll
+            for (int j = 1; j < NP; ++j) Psum = (Psum + d[j].x) + d[j].y;
+            if (pi > 0.0f) B += pi / Psum;
+        }
+        res = 1.0f - B;
+    }
+    a.out[y * a.W + x] = res;
+}
+
 // One thread per receiver: its K receivers in registers (missing members carry zero
 // receiver terms, whose densities are 0, so the pair loop has no per-member test).
 template <int EFFECT, int MAXK, bool PACKED>
 __device__ __forceinline__ void tile_single(const TileArgs& a, const RectLight& L, const Staged& st,
                                             int x0, int y0) {
+    // (16 slots held as pairs spill: they keep the scalar column)
+    if (EFFECT == kAO && (MAXK == 4 || MAXK == 8) && OCC_TILE_PAIRED) {
+        tile_single_ao_x2<MAXK, PACKED>(a, L, st, x0, y0);
+        return;
+    }
     const int lx = threadIdx.x % a.TW, ly = threadIdx.x / a.TW;
     const int x = x0 + lx, y = y0 + ly;
     if (ly >= a.TH || x >= a.W || y >= a.H) return;

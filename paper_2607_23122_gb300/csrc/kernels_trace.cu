@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
         }
         if (!__any_sync(0xFFFFFFFFu, have)) break;
         if (have) {
-            trav_round(t, bvh, stack);
+            trav_round<false, EFFECT != kAO>(t, bvh, stack);
             if (trav_done(t)) {
                 overflow |= t.overflow;
                 bad |= t.bad;

@@ -139,6 +139,16 @@ occ_status make_pattern(occ_ctx* ctx, const occ_pattern* pat, int32_t K, occ::Pa
             out->halo[2] = std::max(out->halo[2], -dy);
             out->halo[3] = std::max(out->halo[3], dy);
         }
+    } else if (pat->kind == OCC_PAT_RANDOM) {
+        if (pat->n_offsets != K - 1)
+            return fail(ctx, OCC_ERR_INVALID_ARG, "K = %d != n_offsets + 1 = %d", K, pat->n_offsets + 1);
+        if (pat->radius_px < 1 || pat->radius_px > 64)
+            return fail(ctx, OCC_ERR_INVALID_ARG, "radius_px = %d must be in [1, 64]", pat->radius_px);
+        out->gw = out->gh = 1;
+        out->n_off = pat->n_offsets;
+        out->radius = pat->radius_px;
+        out->seed = pat->seed;
+        for (int i = 0; i < 4; ++i) out->halo[i] = pat->radius_px;
     } else {
         return fail(ctx, OCC_ERR_INVALID_ARG, "pattern kind %d invalid", pat->kind);
     }
@@ -212,6 +222,7 @@ occ_status reuse_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
         return fail(ctx, OCC_ERR_INVALID_ARG, "AO radius must be positive and finite");
     occ::PatternParams pat;
     if ((st = make_pattern(ctx, pattern, K, &pat)) != OCC_OK) return st;
+    pat.sample = occ->sample;
     const occ::DevBVH b = bvh ? dev_bvh(bvh) : occ::DevBVH{nullptr, nullptr};
     const occ::LightParams lp = to_params(&occ->light);
     occ::ValidateWs vws{nullptr, 0, nullptr, 0, nullptr};
@@ -758,6 +769,7 @@ OCC_EXPORT occ_status occ_debug_mis(occ_ctx* ctx, const occ_gbuffer* gb, const o
             return fail(ctx, OCC_ERR_INVALID_ARG, "pixel %d out of range", pix_host[i]);
     occ::PatternParams pat;
     if ((st = make_pattern(ctx, pattern, K, &pat)) != OCC_OK) return st;
+    pat.sample = occ->sample;
     if (n == 0) return OCC_OK;
     const size_t wn = (size_t)n * occ::kMaxMembers * occ::kMaxMembers;
     int32_t *d_pix = nullptr, *d_mem = nullptr;
@@ -851,7 +863,8 @@ cudaError_t launch_batch(occ_ctx* ctx, const occ_bvh* bvh, const occ::BatchView*
     cudaError_t e = occ::launch_trace_batch(views, dyn, n, n_tiles, b,
                                             occ::trace_batch_ctas(ctx->tune.batch_per_sm), ctx->status, s);
     if (e == cudaSuccess)
-        e = occ::launch_reuse_batch(views, n, n_tiles, max_k, b, ctx->tune.batch_per_sm, ctx->status, s);
+        e = occ::launch_reuse_batch(views, dyn, n, n_tiles, max_k, b, ctx->tune.batch_per_sm,
+                                    ctx->status, s);
     return e;
 }
 
@@ -980,10 +993,13 @@ OCC_EXPORT occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t) {
         return fail(ctx, OCC_ERR_INVALID_ARG, "batch_ctas_per_sm must be in [0, 16]");
     if (t->fused_ao_path < 0 || t->fused_ao_path > 2)
         return fail(ctx, OCC_ERR_INVALID_ARG, "fused_ao_path must be 0, 1 or 2");
+    if (t->group_prefetch < 0 || t->group_prefetch > 3)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "group_prefetch must be 0, 1, 2 or 3");
     ctx->tune.tile_rows = t->reuse_tile_rows;
     ctx->tune.window_path = t->reuse_window_path;
     ctx->tune.batch_per_sm = t->batch_ctas_per_sm;
     ctx->tune.fused_ao_path = t->fused_ao_path;
+    ctx->tune.group_prefetch = t->group_prefetch;
     return OCC_OK;
 }
 
@@ -993,6 +1009,7 @@ OCC_EXPORT occ_status occ_get_tuning(const occ_ctx* ctx, occ_tuning* t) {
     t->reuse_window_path = ctx->tune.window_path;
     t->batch_ctas_per_sm = ctx->tune.batch_per_sm;
     t->fused_ao_path = ctx->tune.fused_ao_path;
+    t->group_prefetch = ctx->tune.group_prefetch;
     return OCC_OK;
 }
 
@@ -1061,6 +1078,7 @@ OCC_EXPORT occ_status occ_frame_noalloc(const occ_gbuffer* gb, const occ_bvh* bv
     if (!out) return finish(fail(&local, OCC_ERR_INVALID_ARG, "out is NULL"));
     occ::PatternParams pat;
     if ((st = make_pattern(&local, pattern, K, &pat)) != OCC_OK) return finish(st);
+    pat.sample = sample;
 
     float4* base = nullptr;
     {

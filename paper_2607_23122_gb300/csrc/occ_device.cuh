@@ -14,6 +14,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "occ_f32x2.cuh"
 #include "occ_layout.h"
 
 namespace occ {
@@ -219,10 +220,23 @@ __device__ __forceinline__ float3 light_direction(const RectLight& L, float3 x, 
 // projection of a vertex is a fixed function of the vertex, so edges shared by two
 // triangles get identical edge functions (watertightness).
 // ---------------------------------------------------------------------------------------
+// 4-wide node visits evaluate the slab distances of two children per instruction (paired
+// FP32), take 3-input min / max, and sort packed (distance, slot) keys (OCC_VISIT_PAIRED=1);
+// 0 selects the scalar visit (also used by 8-wide trees).  The paired visit issues ~10 %
+// fewer instructions; measured at 1080p it is faster for the shadow trace (0.268 against
+// 0.275 ms) and slower for the persistent AO trace (0.378 against 0.371 ms), which keeps
+// the scalar visit (trav_round's PAIRED argument).
+#ifndef OCC_VISIT_PAIRED
+#define OCC_VISIT_PAIRED 1
+#endif
+constexpr bool kVisitPaired = OCC_VISIT_PAIRED && kWidth == 4;
+
 struct TraceRay {
     float3 o;
     float3 idir;            // 1 / d with zero components replaced by a tiny value
     float3 oidir;           // o * idir: slab distances are lo * idir - oidir (one FMA)
+    f32x2 idir2[3];         // paired visits: (idir.a, idir.a) and (-oidir.a, -oidir.a)
+    f32x2 noidir2[3];
     uint32_t nsel;          // bit a set: the high plane of axis a is entered first
     float3 rx, ry, rz;      // shear rows
     float3 d;
@@ -257,6 +271,14 @@ __device__ __forceinline__ TraceRay make_trace_ray(float3 o, float3 d) {
                          __frcp_rn(fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y)),
                          __frcp_rn(fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z)));
     r.oidir = make_float3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
+    if (kVisitPaired) {
+        r.idir2[0] = bc2(r.idir.x);
+        r.idir2[1] = bc2(r.idir.y);
+        r.idir2[2] = bc2(r.idir.z);
+        r.noidir2[0] = bc2(-r.oidir.x);
+        r.noidir2[1] = bc2(-r.oidir.y);
+        r.noidir2[2] = bc2(-r.oidir.z);
+    }
     // a node holds planes lox, hix, loy, hiy, loz, hiz in that order: for a positive
     // direction component the low plane is entered first.
     r.nsel = (r.idir.x >= 0.0f ? 0u : 1u) | (r.idir.y >= 0.0f ? 0u : 2u) | (r.idir.z >= 0.0f ? 0u : 4u);
@@ -326,6 +348,85 @@ __device__ __forceinline__ StackEntry stack_entry(uint32_t ref, float) { return 
 __device__ __forceinline__ uint32_t entry_ref(StackEntry e) { return e; }
 __device__ __forceinline__ bool entry_live(StackEntry, float) { return true; }
 #endif
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Child reference of slot s (0..3) of a node's reference quad.
+__device__ __forceinline__ uint32_t child_of(uint4 ch, uint32_t s) {
+    const uint32_t lo = (s & 1u) ? ch.y : ch.x, hi = (s & 1u) ? ch.w : ch.z;
+    return (s & 2u) ? hi : lo;
+}
+
+// Children of a 4-wide node hit by the ray before tbest, nearest first (see visit_node).
+// Slab distances of children (0, 1) and (2, 3) come from paired FMAs (each lane rounds as
+// fmaf); entry and exit distances take 3-input max / min.  A hit child's key is its entry
+// distance (>= 0, so its bits order like the float) with the slot in the two low bits; a
+// missed child's key is +inf with its slot.  The keys are sorted as integers: the order of
+// children whose entry distances agree to 3 ulps may differ from a float sort, which moves
+// no result (the closest hit and its tie rule do not depend on the visit order).  Empty
+// slots hold inverted infinite boxes, which no ray enters.
+__device__ __forceinline__ void visit_node4(const DevBVH& bvh, uint32_t cur, const TraceRay& r,
+                                            float tbest, StackEntry* stack, int& sp,
+                                            bool& overflow, uint32_t* next) {
+    const float4* nb = reinterpret_cast<const float4*>(bvh.nodes + cur);
+    const uint32_t ix = r.nsel & 1u, iy = 2u + ((r.nsel >> 1) & 1u), iz = 4u + ((r.nsel >> 2) & 1u);
+    const float4 nx = __ldg(nb + ix), fx = __ldg(nb + (ix ^ 1u));
+    const float4 ny = __ldg(nb + iy), fy = __ldg(nb + (iy ^ 1u));
+    const float4 nz = __ldg(nb + iz), fz = __ldg(nb + (iz ^ 1u));
+    const uint4 ch = __ldg(reinterpret_cast<const uint4*>(nb + 6));
+    const float2 nx01 = up2(fma2(pk2(nx.x, nx.y), r.idir2[0], r.noidir2[0]));
+    const float2 nx23 = up2(fma2(pk2(nx.z, nx.w), r.idir2[0], r.noidir2[0]));
+    const float2 ny01 = up2(fma2(pk2(ny.x, ny.y), r.idir2[1], r.noidir2[1]));
+    const float2 ny23 = up2(fma2(pk2(ny.z, ny.w), r.idir2[1], r.noidir2[1]));
+    const float2 nz01 = up2(fma2(pk2(nz.x, nz.y), r.idir2[2], r.noidir2[2]));
+    const float2 nz23 = up2(fma2(pk2(nz.z, nz.w), r.idir2[2], r.noidir2[2]));
+    const float2 fx01 = up2(fma2(pk2(fx.x, fx.y), r.idir2[0], r.noidir2[0]));
+    const float2 fx23 = up2(fma2(pk2(fx.z, fx.w), r.idir2[0], r.noidir2[0]));
+    const float2 fy01 = up2(fma2(pk2(fy.x, fy.y), r.idir2[1], r.noidir2[1]));
+    const float2 fy23 = up2(fma2(pk2(fy.z, fy.w), r.idir2[1], r.noidir2[1]));
+    const float2 fz01 = up2(fma2(pk2(fz.x, fz.y), r.idir2[2], r.noidir2[2]));
+    const float2 fz23 = up2(fma2(pk2(fz.z, fz.w), r.idir2[2], r.noidir2[2]));
+    const float tn[4] = {max3f(nx01.x, ny01.x, fmaxf(nz01.x, 0.0f)),
+                         max3f(nx01.y, ny01.y, fmaxf(nz01.y, 0.0f)),
+                         max3f(nx23.x, ny23.x, fmaxf(nz23.x, 0.0f)),
+                         max3f(nx23.y, ny23.y, fmaxf(nz23.y, 0.0f))};
+    const float tf[4] = {min3f(fx01.x, fy01.x, fminf(fz01.x, tbest)),
+                         min3f(fx01.y, fy01.y, fminf(fz01.y, tbest)),
+                         min3f(fx23.x, fy23.x, fminf(fz23.x, tbest)),
+                         min3f(fx23.y, fy23.y, fminf(fz23.y, tbest))};
+    constexpr uint32_t kMissKey = 0x7F800000u;
+    uint32_t k[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        k[c] = (tn[c] <= tf[c] ? (__float_as_uint(tn[c]) & ~3u) : kMissKey) | (uint32_t)c;
+    // ascending sorting network (0,1)(2,3)(0,2)(1,3)(1,2) on the integer keys
+#define OCC_USWAP(a, b)                                  \
+    {                                                    \
+        const uint32_t lo = min(k[a], k[b]), hi = max(k[a], k[b]); \
+        k[a] = lo;                                       \
+        k[b] = hi;                                       \
+    }
+    OCC_USWAP(0, 1) OCC_USWAP(2, 3) OCC_USWAP(0, 2) OCC_USWAP(1, 3) OCC_USWAP(1, 2)
+#undef OCC_USWAP
+#pragma unroll
+    for (int c = 3; c >= 1; --c) {
+        if (k[c] < kMissKey) {
+            if (sp < kStackSize) stack[sp++] = stack_entry(child_of(ch, k[c] & 3u), __uint_as_float(k[c] & ~3u));
+            else overflow = true;
+        }
+    }
+    *next = k[0] < kMissKey ? child_of(ch, k[0] & 3u) : kEmptyRef;
+}
 
 // Children of node `cur` hit by the ray before tbest, nearest first: the nearest goes to
 // *next, the others are pushed far-to-near.  *next = kEmptyRef if none is hit.
@@ -461,7 +562,7 @@ __device__ __forceinline__ bool trav_done(const Traversal& t) {
 // then the leaves.  Call only while !trav_done.  ANY: stop at the first triangle accepted
 // on (0, tmax] (visibility queries need only whether one exists; the acceptance test is
 // the closest-hit one, so the answer is the same).
-template <bool ANY = false>
+template <bool ANY = false, bool PAIRED = kVisitPaired>
 __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, StackEntry* stack) {
     while (t.cur != kEmptyRef && !is_leaf_ref(t.cur)) {
 #if OCC_CHECKS
@@ -473,7 +574,10 @@ __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, Stac
 #endif
         uint32_t next;
         count_node(bvh, t.cur);
-        visit_node(bvh, t.cur, t.r, t.tbest, stack, t.sp, t.overflow, &next);
+        if (PAIRED && kVisitPaired)
+            visit_node4(bvh, t.cur, t.r, t.tbest, stack, t.sp, t.overflow, &next);
+        else
+            visit_node(bvh, t.cur, t.r, t.tbest, stack, t.sp, t.overflow, &next);
         t.cur = next != kEmptyRef ? next : pop_next(stack, t.sp, t.tbest);
         if (t.cur != kEmptyRef && is_leaf_ref(t.cur) && t.leaf == kEmptyRef) {
             t.leaf = t.cur;   // postpone the leaf and keep walking internal nodes

@@ -32,12 +32,15 @@ struct LightParams {
 constexpr int kMaxMembers = 64;
 
 struct PatternParams {
-    int32_t kind;       // 0 group, 1 box, 2 offsets
+    int32_t kind;       // 0 group, 1 box, 2 offsets, 3 random per receiver
     int32_t gw, gh;
-    int32_t n_off;      // offsets: count
+    int32_t n_off;      // offsets / random: count
     int32_t K;          // members incl. the receiver
     int2 off[kMaxMembers - 1];
     int32_t halo[4];    // offsets: max extent left, right, up, down
+    int32_t radius;     // random: disk radius in pixels
+    uint32_t sample;    // random: the records' sample (counter word 1 of the draws)
+    uint64_t seed;      // random: key of the draws
 };
 
 enum Effect { kAO = 0, kShadow = 1 };
@@ -96,6 +99,7 @@ struct Tuning {
     int window_path = 0;
     int batch_per_sm = 0;
     int fused_ao_path = 0;
+    int group_prefetch = 0;   // group kernel L2 prefetch: 0 default, 1 none, 2 / 3 planes
 };
 
 // Workspace of the queued first-hit validation (unbiased group reuse): up to (K - 1) W H
@@ -118,7 +122,8 @@ cudaError_t launch_reuse(int effect, int estimator, const GBufView& gb, const Re
 cudaError_t launch_trace_batch(const BatchView* views, const BatchDyn* dyn, int n_views, int n_tiles,
                                const DevBVH& bvh, int ctas, unsigned* status, cudaStream_t s);
 int trace_batch_ctas(int per_sm_wanted);
-cudaError_t launch_reuse_batch(const BatchView* views, int n_views, int n_tiles, int max_k,
+cudaError_t launch_reuse_batch(const BatchView* views, const BatchDyn* dyn, int n_views,
+                               int n_tiles, int max_k,
                                const DevBVH& bvh, int per_sm_wanted, unsigned* status,
                                cudaStream_t s);
 

@@ -74,6 +74,28 @@ __device__ __forceinline__ uint32_t warp_start_node(const DevBVH& bvh, bool vali
                       make_float3(hi[0] + pad, hi[1] + pad, hi[2] + pad));
 }
 
+// Offset of slot s (>= 1) of receiver pixel `pix` in a random pattern (OCC_PAT_RANDOM,
+// the per-receiver form of Eq. 8): the first of 32 Philox4x32-10 draws (counter (pix,
+// sample, 2, 32 s + a), key = seed) that maps to a lattice point of the disk of radius R
+// other than (0, 0) and the slot's earlier offsets acc[0 .. nacc).  Integer arithmetic only;
+// false when no attempt qualifies (the slot stays empty).
+__device__ __forceinline__ bool random_offset(uint64_t seed, uint32_t pix, uint32_t sample, int s,
+                                              int R, const int2* acc, int nacc, int2* out) {
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint32_t span = 2u * (uint32_t)R + 1u;
+    for (int a = 0; a < 32; ++a) {
+        const uint4 w = philox4x32_10(make_uint4(pix, sample, 2u, 32u * (uint32_t)s + (uint32_t)a), key);
+        const int dx = (int)__umulhi(w.x, span) - R, dy = (int)__umulhi(w.y, span) - R;
+        if (dx * dx + dy * dy > R * R || (dx == 0 && dy == 0)) continue;
+        bool dup = false;
+        for (int q = 0; q < nacc; ++q) dup |= acc[q].x == dx && acc[q].y == dy;
+        if (dup) continue;
+        *out = make_int2(dx, dy);
+        return true;
+    }
+    return false;
+}
+
 // Receiver data needed by the density of each effect.
 struct Recv {
     float3 x;

@@ -25,6 +25,10 @@ struct ReuseArgs {
     uint32_t* vq;
     unsigned* vcount;
     uint32_t* vbits;
+    // group kernel: planes prefetched into L2 for the CTA `pf_ahead` launches later (0 none,
+    // 3: G-buffer position and normal and record plane 0, 4: also record plane 1)
+    int32_t pf_planes;
+    int32_t pf_ahead;
 };
 
 // Passes of the queued unbiased group reuse (internal estimator codes): collect the

@@ -15,6 +15,7 @@ from . import _native as N
 from ._native import (  # noqa: F401
     OCC_EFFECT_AO, OCC_EFFECT_SHADOW, OCC_EST_BIASED, OCC_EST_BOXMEAN, OCC_EST_LIGHT_UNBIASED,
     OCC_EST_NOREUSE, OCC_EST_UNBIASED, OCC_GB_FP32, OCC_GB_PACKED, OCC_PAT_BOX, OCC_PAT_GROUP, OCC_PAT_OFFSETS,
+    OCC_PAT_RANDOM,
     OCC_REC_FP32, OCC_REC_PACKED, MAX_MEMBERS)
 
 
@@ -159,13 +160,14 @@ class Occluders:
 
     @staticmethod
     def from_packed(plane: np.ndarray, effect: int, radius: float = 0.0, light=None,
-                    device="cuda") -> "Occluders":
+                    device="cuda", sample: int = 0) -> "Occluders":
         """Packed records prepared elsewhere: [H, W, 4] float32 view of the 16-byte records."""
         H, W = plane.shape[:2]
         o = Occluders.empty(H, W, device, packed=True)
         o.data[0].copy_(torch.from_numpy(np.ascontiguousarray(plane, dtype=np.float32)))
         o.meta.effect = effect
         o.meta.radius = radius
+        o.meta.sample = sample
         if light is not None:
             o.meta.light = _light(light)
         return o
@@ -176,14 +178,16 @@ class Occluders:
 
     @staticmethod
     def from_numpy(rec0: np.ndarray, rec1: np.ndarray, effect: int, radius: float = 0.0,
-                   light=None, device="cuda") -> "Occluders":
-        """Records prepared elsewhere (e.g. test inputs): planes [H, W, 4] float32."""
+                   light=None, device="cuda", sample: int = 0) -> "Occluders":
+        """Records prepared elsewhere (e.g. test inputs): planes [H, W, 4] float32; `sample`
+        is the records' sample index (random patterns draw their offsets with it)."""
         H, W = rec0.shape[:2]
         o = Occluders.empty(H, W, device)
         o.data[0].copy_(torch.from_numpy(np.ascontiguousarray(rec0, dtype=np.float32)))
         o.data[1].copy_(torch.from_numpy(np.ascontiguousarray(rec1, dtype=np.float32)))
         o.meta.effect = effect
         o.meta.radius = radius
+        o.meta.sample = sample
         if light is not None:
             o.meta.light = _light(light)
         return o
@@ -207,14 +211,19 @@ def _light(light) -> N.occ_rect_light:
 
 
 class Pattern:
-    """Neighbour pattern N_i: group blocks, a centred box, or shared offsets."""
+    """Neighbour pattern N_i: group blocks, a centred box, shared offsets, or offsets drawn
+    per receiver and sample in a disk (random)."""
 
-    def __init__(self, kind: int, gw: int = 1, gh: int = 1, offsets=None):
+    def __init__(self, kind: int, gw: int = 1, gh: int = 1, offsets=None, n_random: int = 0,
+                 radius_px: int = 0, seed: int = 0):
         self.kind, self.gw, self.gh = int(kind), int(gw), int(gh)
         off = np.zeros((0, 2), dtype=np.int32) if offsets is None else offsets
         self.offsets = np.ascontiguousarray(np.asarray(off, dtype=np.int32).reshape(-1, 2))
-        self._c = N.occ_pattern(self.kind, self.gw, self.gh, self.offsets.shape[0],
-                                self.offsets.ctypes.data_as(C.POINTER(C.c_int32)))
+        self.n_random, self.radius_px, self.seed = int(n_random), int(radius_px), int(seed)
+        n_off = self.n_random if self.kind == N.OCC_PAT_RANDOM else self.offsets.shape[0]
+        self._c = N.occ_pattern(self.kind, self.gw, self.gh, n_off,
+                                self.offsets.ctypes.data_as(C.POINTER(C.c_int32)),
+                                self.radius_px, self.seed)
 
     @staticmethod
     def group(gw: int, gh: int) -> "Pattern":
@@ -228,14 +237,24 @@ class Pattern:
     def offsets_of(off) -> "Pattern":
         return Pattern(N.OCC_PAT_OFFSETS, 1, 1, off)
 
+    @staticmethod
+    def random(K: int, radius_px: int, seed: int) -> "Pattern":
+        """The receiver plus K - 1 offsets drawn per receiver and sample in a disk."""
+        return Pattern(N.OCC_PAT_RANDOM, n_random=K - 1, radius_px=radius_px, seed=seed)
+
     @property
     def K(self) -> int:
         if self.kind == N.OCC_PAT_OFFSETS:
             return self.offsets.shape[0] + 1
+        if self.kind == N.OCC_PAT_RANDOM:
+            return self.n_random + 1
         return self.gw * self.gh
 
     def as_tuple(self):
-        """(kind, gw, gh, offsets) -- the form the oracle takes."""
+        """(kind, gw, gh, offsets), or (random kind, radius, n_offsets, seed) -- the form the
+        oracle takes."""
+        if self.kind == N.OCC_PAT_RANDOM:
+            return (self.kind, self.radius_px, self.n_random, self.seed)
         return (self.kind, self.gw, self.gh, self.offsets if self.offsets.size else None)
 
     def c(self) -> N.occ_pattern:
@@ -580,8 +599,9 @@ class Batch:
 
 
 def occ_set_tuning(ctx: Context, reuse_tile_rows: int = 0, reuse_window_path: int = 0,
-                   batch_ctas_per_sm: int = 0, fused_ao_path: int = 0):
-    t = N.occ_tuning(reuse_tile_rows, reuse_window_path, batch_ctas_per_sm, fused_ao_path)
+                   batch_ctas_per_sm: int = 0, fused_ao_path: int = 0, group_prefetch: int = 0):
+    t = N.occ_tuning(reuse_tile_rows, reuse_window_path, batch_ctas_per_sm, fused_ao_path,
+                     group_prefetch)
     ctx.check(ctx.lib.occ_set_tuning(ctx.handle, C.byref(t)))
 
 

@@ -59,6 +59,7 @@ def _patterns(occ):
         "group3x2": occ.Pattern.group(3, 2), "box3x3": occ.Pattern.box(3, 3),
         "disk8": occ.Pattern.offsets_of(synth.disk_offsets(8, 15.0, seed=3)),
         "disk16": occ.Pattern.offsets_of(synth.disk_offsets(16, 6.0, seed=4)),
+        "random8": occ.Pattern.random(8, 6, seed=21),
     }
 
 
@@ -140,7 +141,7 @@ def test_trace_matches_oracle(orc, occ, ctx, which, effect, request):
 # --------------------------------------------------------------------------------------
 
 PATTERN_NAMES = ["group2x1", "group2x2", "group4x2", "group4x4", "group3x2", "box3x3", "disk8",
-                 "disk16"]
+                 "disk16", "random8"]
 
 
 @pytest.mark.parametrize("est", [NOREUSE, BIASED, UNBIASED, BOXMEAN])
@@ -155,13 +156,13 @@ def test_reuse_record_conditioned(orc, occ, ctx, c1, effect, pname, est):
                             seed=99, sample=sample)
         r0, r1 = P.to_f32_records(orec)
         rec32 = P.widen_records(r0, r1)
-        o = occ.Occluders.from_numpy(r0, r1, effect, radius=R_C1, light=light)
+        o = occ.Occluders.from_numpy(r0, r1, effect, radius=R_C1, light=light, sample=sample)
         bvh = c1["bvh"] if est == UNBIASED else None
         fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
         g = fn(ctx, c1["gb"], o, pat, pat.K, est, bvh=bvh)
         ctx.sync()
         ref, mg = orc.reuse(c1["osc"], effect, c1["pos"], c1["nrm"], rec32, pat.as_tuple(), est,
-                            radius=R_C1, light=light)
+                            radius=R_C1, light=light, sample=sample)
         P.compare_out(g.cpu().numpy(), ref, mg, valid, f"{pname} est {est} effect {effect}")
 
 
@@ -205,6 +206,34 @@ def test_reuse_end_to_end(orc, occ, ctx, terrain_small, effect, pname):
               f"{tr['mismatch']}, listed {res['listed'][:4]}")
 
 
+def test_random_pattern_members_match_the_oracle_draw(orc, occ, ctx, c1):
+    """Per-receiver random neighbour sets: the GPU's members of sampled receivers (from
+    occ_debug_mis) are the receiver plus the offsets the oracle draws for that pixel and
+    sample, dropped where outside the image or background; K = 1 is no reuse."""
+    orec, _ = orc.trace(c1["osc"], AO, c1["pos"], c1["nrm"], radius=R_C1, seed=3, sample=5)
+    r0, r1 = P.to_f32_records(orec)
+    o = occ.Occluders.from_numpy(r0, r1, AO, radius=R_C1, sample=5)
+    valid = c1["pos"][..., 3] > 0
+    pix = np.flatnonzero(valid.reshape(-1))[::37]
+    for K, radius, seed in ((8, 6, 21), (16, 15, 2**40 + 7), (4, 1, 3)):
+        pat = occ.Pattern.random(K, radius, seed)
+        mem, _ = occ.occ_debug_mis(ctx, c1["gb"], o, pat, K, BIASED, pix)
+        for t, p in enumerate(pix):
+            y, x = divmod(int(p), 64)
+            offs = orc.random_offsets(seed, int(p), 5, radius, K - 1)
+            assert len(offs) == K - 1 or radius == 1   # radius 1 has only 4 lattice points
+            want = [int(p)] + [int((y + dy) * 64 + x + dx) for dx, dy in offs
+                               if 0 <= x + dx < 64 and 0 <= y + dy < 64 and valid[y + dy, x + dx]]
+            got = [int(m) for m in mem[t] if m >= 0]
+            assert got == want, (p, got, want)
+    pat = occ.Pattern.random(1, 6, 9)
+    g = occ.occ_reuse_ao(ctx, c1["gb"], o, pat, 1, BIASED)
+    nr = occ.occ_reuse_ao(ctx, c1["gb"], o, pat, 1, NOREUSE)
+    ctx.sync()
+    same = (g == nr).cpu().numpy()
+    assert same[valid].mean() > 0.999
+
+
 def test_mis_weights_sum_to_one(orc, occ, ctx, c1):
     orec, _ = orc.trace(c1["osc"], AO, c1["pos"], c1["nrm"], radius=R_C1, seed=3, sample=0)
     r0, r1 = P.to_f32_records(orec)
@@ -213,7 +242,7 @@ def test_mis_weights_sum_to_one(orc, occ, ctx, c1):
     valid_idx = np.flatnonzero(c1["pos"][..., 3].reshape(-1) > 0)
     pix = rng.choice(valid_idx, size=200, replace=False)
     rows = 0
-    for pname in ("group4x2", "box3x3", "disk8"):
+    for pname in ("group4x2", "box3x3", "disk8", "random8"):
         pat = _patterns(occ)[pname]
         for est, bvh in ((BIASED, None), (UNBIASED, c1["bvh"])):
             mem, w = occ.occ_debug_mis(ctx, c1["gb"], o, pat, pat.K, est, pix, bvh=bvh)
@@ -266,7 +295,7 @@ def test_ragged_and_tiny_images(orc, occ, ctx, c1, shape):
     nrm = np.ascontiguousarray(c1["nrm"][20:20 + H, 10:10 + W])
     gb = occ.GBuffer.from_numpy(pos, nrm)
     valid = pos[..., 3] > 0
-    for pname in ("group4x2", "box3x3", "disk8", "group3x2"):
+    for pname in ("group4x2", "box3x3", "disk8", "group3x2", "random8"):
         pat = _patterns(occ)[pname]
         o = occ.occ_trace_ao(ctx, gb, c1["bvh"], R_C1, 8, 1)
         r0, r1, _ = P.gpu_records(o)
@@ -275,7 +304,7 @@ def test_ragged_and_tiny_images(orc, occ, ctx, c1, shape):
                                  bvh=c1["bvh"] if est == UNBIASED else None)
             ctx.sync()
             ref, mg = orc.reuse(c1["osc"], AO, pos, nrm, P.widen_records(r0, r1), pat.as_tuple(),
-                                est, radius=R_C1)
+                                est, radius=R_C1, sample=1)
             P.compare_out(g.cpu().numpy(), ref, mg, valid, f"{shape} {pname} {est}")
 
 

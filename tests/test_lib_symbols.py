@@ -51,16 +51,16 @@ def test_struct_layouts_match_the_header():
     from paper_2607_23122_gb300 import _native as N
     assert ctypes.sizeof(N.occ_gbuffer) == 32
     assert ctypes.sizeof(N.occ_rect_light) == 36
-    assert ctypes.sizeof(N.occ_pattern) == 24
+    assert ctypes.sizeof(N.occ_pattern) == 40
     assert ctypes.sizeof(N.occ_bvh_stats) == 48
     # W H format (pad) data effect radius light(36) (pad) seed sample (pad)
     assert ctypes.sizeof(N.occ_occluders) == 88
     assert ctypes.sizeof(N.occ_sched_config) == 24
     assert ctypes.sizeof(N.occ_sched_stats) == 72
     assert ctypes.sizeof(N.occ_server_config) == 48
-    assert ctypes.sizeof(N.occ_tuning) == 16
-    # W H effect radius light(36) (pad) seed sample (pad) pattern(24) K estimator packed
+    assert ctypes.sizeof(N.occ_tuning) == 20
+    # W H effect radius light(36) (pad) seed sample (pad) pattern(40) K estimator packed
     # camera(40) eps 4 pointers deadline
-    assert ctypes.sizeof(N.occ_request) == 192
+    assert ctypes.sizeof(N.occ_request) == 208
     assert ctypes.sizeof(N.occ_result) == 40
     assert ctypes.sizeof(N.occ_server_stats) == 112

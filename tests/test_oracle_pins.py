@@ -22,7 +22,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 AO, SH = 0, 1
 NOREUSE, BIASED, UNBIASED, BOXMEAN = 0, 1, 2, 3
-GROUP, BOX, OFFS = 0, 1, 2
+GROUP, BOX, OFFS, RAND = 0, 1, 2, 3
 
 
 # --------------------------------------------------------------------------------------
@@ -324,7 +324,35 @@ def test_shadow_density_integrates_to_one_under_full_blocker(orc):
 # --------------------------------------------------------------------------------------
 
 PATTERNS = [(GROUP, 2, 2, None), (GROUP, 4, 2, None), (BOX, 3, 3, None),
-            (OFFS, 0, 0, synth.disk_offsets(8, 6.0, seed=3))]
+            (OFFS, 0, 0, synth.disk_offsets(8, 6.0, seed=3)), (RAND, 6, 7, 1234)]
+
+
+def test_random_offsets_uniform_on_the_disk_lattice(orc):
+    """Per-receiver random neighbour sets (the per-receiver form of N_i, Eq. 8): every offset
+    is a lattice point of the disk other than (0, 0), a receiver's offsets are distinct, and
+    each slot is uniform over the lattice points (chi^2); sets change with the sample and
+    the seed, and a seed above 32 bits uses its high word."""
+    R = 6
+    pts = [(x, y) for y in range(-R, R + 1) for x in range(-R, R + 1)
+           if x * x + y * y <= R * R and (x, y) != (0, 0)]
+    index = {p: i for i, p in enumerate(pts)}
+    n = 12000
+    counts = np.zeros((2, len(pts)))
+    for p in range(n):
+        offs = orc.random_offsets(77, p, p % 5, R, 7)
+        assert len(offs) == 7 and len({tuple(o) for o in offs}) == 7
+        assert all(tuple(o) in index for o in offs)
+        counts[0, index[tuple(offs[0])]] += 1
+        counts[1, index[tuple(offs[6])]] += 1
+    exp, dof = n / len(pts), len(pts) - 1
+    for c in counts:
+        assert ((c - exp) ** 2 / exp).sum() < dof + 5 * math.sqrt(2 * dof)
+    assert not np.array_equal(orc.random_offsets(77, 5, 0, R, 7), orc.random_offsets(77, 5, 1, R, 7))
+    assert not np.array_equal(orc.random_offsets(77, 5, 0, R, 7), orc.random_offsets(78, 5, 0, R, 7))
+    assert not np.array_equal(orc.random_offsets(77, 5, 0, R, 7),
+                              orc.random_offsets(77 + 2**32, 5, 0, R, 7))
+    # a disk of radius 1 has four lattice points besides the origin: four slots take all
+    assert sorted(map(tuple, orc.random_offsets(3, 9, 0, 1, 4))) == [(-1, 0), (0, -1), (0, 1), (1, 0)]
 
 
 def _grid_case(scene, W=24, H=16, spacing=0.05):
@@ -350,7 +378,8 @@ def _image_mean_over_samples(orc, sc, effect, pos, nrm, pattern, est, M, seed, r
     means = []
     for s in range(M):
         rec, _ = orc.trace(sc, effect, pos, nrm, radius=radius, light=light, seed=seed, sample=s)
-        out, _ = orc.reuse(sc, effect, pos, nrm, rec, pattern, est, radius=radius, light=light)
+        out, _ = orc.reuse(sc, effect, pos, nrm, rec, pattern, est, radius=radius, light=light,
+                           sample=s)
         means.append(out.mean())
     means = np.array(means)
     return means.mean(), means.std(ddof=1) / math.sqrt(M)
@@ -452,9 +481,10 @@ def test_k1_equals_noreuse(orc, effect):
         ref, _ = orc.reuse(sc, effect, pos, nrm, rec, (OFFS, 0, 0, None), NOREUSE, radius=R,
                            light=light)
         assert set(np.unique(ref).tolist()) <= {0.0, 1.0}
-        for pat in [(OFFS, 0, 0, None), (BOX, 1, 1, None), (GROUP, 1, 1, None)]:
+        for pat in [(OFFS, 0, 0, None), (BOX, 1, 1, None), (GROUP, 1, 1, None), (RAND, 6, 0, 5)]:
             for est in (BIASED, UNBIASED, BOXMEAN):
-                out, _ = orc.reuse(sc, effect, pos, nrm, rec, pat, est, radius=R, light=light)
+                out, _ = orc.reuse(sc, effect, pos, nrm, rec, pat, est, radius=R, light=light,
+                                   sample=s)
                 diff = np.argwhere(out != ref)
                 for py, px in diff:
                     # only a hit whose own density vanishes exactly may differ
@@ -556,7 +586,8 @@ def _convergence(orc, effect, pattern, M, region, light=None, R=1.0):
 
 @pytest.mark.slow
 @pytest.mark.parametrize("pattern", [(GROUP, 2, 2, None), (BOX, 3, 3, None),
-                                     (OFFS, 0, 0, synth.disk_offsets(8, 4.0, seed=9))])
+                                     (OFFS, 0, 0, synth.disk_offsets(8, 4.0, seed=9)),
+                                     (RAND, 4, 7, 99)])
 def test_unbiased_ao_converges_to_reference(orc, pattern):
     _convergence(orc, AO, pattern, 4096, (2, 44, 8, 8))
 
