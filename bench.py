@@ -276,6 +276,10 @@ NCU_TRAFFIC = {"k_trace_dyn<AO>": 72.457472e6 + 28.906496e6,
                "k_reuse_group<AO,biased,4,2>": 114.168832e6 + 4.530688e6}
 NCU_TRACE_ISSUE_ACTIVE = 0.6923   # smsp__issue_active of k_trace_dyn<AO> in its capture
 NCU_TRACE_WARP_INSTR = 300.359031e6   # smsp__inst_executed.sum of k_trace_dyn<AO>, same capture
+# What the 1080p AO trace (seed 1, sample 0) traverses, from the instrumented library:
+# OCC_LIB_VARIANT=counters python bench.py --count-touch
+TRACE_TOUCH = {"rays": 1409214, "node_visits": 22464463, "triangle_tests": 6760549,
+               "distinct_nodes": 49321, "distinct_triangles": 121469, "distinct_bytes": 12143600}
 
 
 def fp32_peak(occ, ctx, dev, stream) -> dict:
@@ -746,6 +750,9 @@ def run_ours(args):
             occ.occ_set_tuning(ctx)
         extra["reuse_group4x2"]["prefetch_choices_ms"] = {
             {1: "none", 2: "gbuffer+rec0", 3: "gbuffer+rec0+rec1"}[c]: v["ms"] for c, v in pf.items()}
+        # the same loads and stores with no arithmetic: what the kernel's bytes cost alone
+        extra["reuse_group4x2"]["stream_ceiling"] = time_kernel(
+            lambda st: occ.occ_debug_stream_ceiling(ctx, gb, rec, out, stream=st), flush, stream, 200)
         extra["shadow"] = shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream)
         extra["packed"] = packed_frame(occ, ctx, gb, bvh, pat, out, flush, stream)
         extra["fused"] = fused_frame(occ, ctx, gb, bvh, rec, out, flush, stream)
@@ -764,26 +771,35 @@ def run_ours(args):
         st = bvh.stats
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         tr, ru = float(t_trace.mean()), float(t_reuse.mean())
-        # trace: compulsory bytes = G-buffer read + record write + the BVH read once
-        trace_bytes = P * (32 + 32) + st["bytes"]
+        # trace: compulsory bytes = G-buffer read + record write + the distinct BVH nodes and
+        # triangles the traversal touches (instrumented-library count)
+        trace_bytes = P * (32 + 32) + TRACE_TOUCH["distinct_bytes"]
         # reuse (offset window, K^2 pair densities): FP32 ALU bound
         pairs = P * K * K
         issue_mhz = clk["sm_max_mhz"] or peaks.get("sm_max_mhz", 2070.0)
         alu_peak = fp32["peak"] * 1e12
-        trace_roof = {"kernel": "k_trace_dyn<AO>", "bound": "hbm",
-                      "achieved": trace_bytes / tr / 1e9, "peak": hbm, "unit": "GB/s",
-                      "frac": trace_bytes / tr / 1e9 / hbm,
+        # the trace is bound by instruction issue and dependent-fetch latency, not by bytes:
+        # its roofline is the warp-instruction issue rate (4 schedulers per SM, one warp
+        # instruction per cycle each, at the max SM clock), with the byte roofline beside it
+        issue_peak = sms * 4 * issue_mhz * 1e6
+        trace_roof = {"kernel": "k_trace_dyn<AO>", "bound": "alu",
+                      "achieved": NCU_TRACE_WARP_INSTR / tr / 1e9, "peak": issue_peak / 1e9,
+                      "unit": "G warp-instructions/s",
+                      "frac": NCU_TRACE_WARP_INSTR / tr / issue_peak,
                       "traffic": NCU_TRAFFIC["k_trace_dyn<AO>"],
-                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                      "algorithmic_bytes": trace_bytes,
-                      "note": "software traversal is issue/latency bound: issue slots "
-                              f"{NCU_TRACE_ISSUE_ACTIVE:.0%} busy under ncu",
-                      # the resource that binds it: warp-instruction issue (4 schedulers per
-                      # SM, one instruction per cycle each, at the max SM clock)
-                      "issue": {"warp_instructions": NCU_TRACE_WARP_INSTR,
-                                "achieved": NCU_TRACE_WARP_INSTR / tr,
-                                "peak": sms * 4 * issue_mhz * 1e6, "unit": "warp-instr/s",
-                                "frac": NCU_TRACE_WARP_INSTR / tr / (sms * 4 * issue_mhz * 1e6)}}
+                      "peak_source": f"{sms} SMs x 4 schedulers x 1 warp-instruction per cycle x "
+                                     f"{issue_mhz:.0f} MHz max SM clock",
+                      "algorithmic": "warp instructions per launch (ncu smsp__inst_executed.sum "
+                                     f"{NCU_TRACE_WARP_INSTR:.4g}); issue slots "
+                                     f"{NCU_TRACE_ISSUE_ACTIVE:.0%} busy under ncu",
+                      "hbm": {"algorithmic_bytes": trace_bytes, "achieved": trace_bytes / tr / 1e9,
+                              "peak": hbm, "unit": "GB/s", "frac": trace_bytes / tr / 1e9 / hbm,
+                              "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                              "bytes": "G-buffer 32 B/px + records 32 B/px + distinct BVH bytes "
+                                       f"touched {TRACE_TOUCH['distinct_bytes']} (of "
+                                       f"{st['bytes']})"},
+                      "traversal": {k: TRACE_TOUCH[k] / TRACE_TOUCH["rays"]
+                                    for k in ("node_visits", "triangle_tests")}}
         reuse_roof = {"kernel": "k_reuse_tile<AO,8> (TMA-staged window)", "bound": "alu",
                       "achieved": pairs * FLOPS_PER_PAIR_AO / ru / 1e12,
                       "peak": alu_peak / 1e12, "unit": "TFLOP/s",

@@ -106,15 +106,18 @@ enum { OCC_REC_FP32 = 0, OCC_REC_PACKED = 1 };
 typedef struct occ_ctx occ_ctx;   /* opaque: device, status word, workspace */
 typedef struct occ_bvh occ_bvh;   /* opaque: device-resident wide BVH */
 
-/* G-buffer of receivers.  pos4[p] = (x.xyz, valid): x is the receiver point
+/* G-buffer of receivers.  pos4[q] = (x.xyz, valid): x is the receiver point
  * (the visible surface point already offset along its normal), valid is 1
- * for a receiver and 0 for background.  nrm4[p] = (n.xyz, unused): the unit
- * geometric normal facing the viewer.  Both W*H float4, row-major. */
+ * for a receiver and 0 for background.  nrm4[q] = (n.xyz, unused): the unit
+ * geometric normal facing the viewer.  Row-major float4 planes: pixel (x, y) sits at
+ * q = y * pitch_px + x, pitch_px >= W (0 means W), so a G-buffer may be a window of a
+ * wider render target.  Records and outputs stay dense (W per row) whatever the pitch. */
 typedef struct {
     int32_t W, H;
     const float* pos4;         /* FP32: pos4 plane; PACKED: the packed plane */
     const float* nrm4;         /* FP32: nrm4 plane; PACKED: unused (NULL) */
     int32_t format;            /* OCC_GB_FP32 (0) or OCC_GB_PACKED */
+    int64_t pitch_px;          /* row pitch of the planes in pixels (0: W) */
 } occ_gbuffer;
 
 /* Rectangle light c + a eu + b ev, a, b in [-1/2, 1/2], eu orthogonal to ev.
@@ -332,6 +335,12 @@ typedef struct {
     int32_t group_prefetch;      /* GROUP reuse kernel: 1 no prefetch, 2 each CTA prefetches into
                                     L2 the G-buffer and record plane 0 of the CTA one wave of
                                     resident CTAs later, 3 also its hit-normal plane */
+    int32_t trace_path;          /* step-1 trace: 1 one CTA per 16 x 8 tile, 2 persistent CTAs
+                                    taking rays from the context's counter; 0: persistent for AO,
+                                    per tile for shadows */
+    int32_t trace_ctas_per_sm;   /* persistent trace: CTAs per SM (1 .. 16; 0 all that fit) */
+    int32_t trace_refill;        /* persistent trace: a warp takes new rays once this many of its
+                                    lanes are idle (1 .. 32; 0: 16) */
 } occ_tuning;
 occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t);
 occ_status occ_get_tuning(const occ_ctx* ctx, occ_tuning* t);
@@ -394,6 +403,15 @@ occ_status occ_debug_wait_timeout(occ_ctx* ctx, uint32_t spins, void* stream);
  * (2 per FMA).  Asynchronous on `stream`: time it with events there. */
 occ_status occ_debug_fp32_peak(occ_ctx* ctx, int32_t paired, int32_t iters, int32_t blocks,
                                float* sink_dev, double* flop_host, void* stream);
+
+/* Measurement aid (not part of the method): the streaming ceiling of the GROUP reuse
+ * kernel's memory pattern at 4 x 2 groups.  Reads what that kernel reads from gb and occ
+ * (FP32 formats only: G-buffer position and normal and record plane 0 of every pixel,
+ * record plane 1 of the pixels whose ray hit) with the same CTA shape, and writes one float
+ * per pixel into out (device float[H][W]) that is a checksum, not an estimate.
+ * Asynchronous on `stream`. */
+occ_status occ_debug_stream_ceiling(occ_ctx* ctx, const occ_gbuffer* gb, const occ_occluders* occ,
+                                    float* out, void* stream);
 
 /* Measurement aid for the instrumented library only (built with OCC_COUNTERS=1; the product
  * library returns OCC_ERR_UNSUPPORTED): what the traversal of every launch since the last

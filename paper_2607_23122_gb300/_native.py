@@ -31,7 +31,7 @@ MAX_MEMBERS = 64
 
 class occ_gbuffer(C.Structure):
     _fields_ = [("W", c_int32), ("H", c_int32), ("pos4", c_void_p), ("nrm4", c_void_p),
-                ("format", c_int32)]
+                ("format", c_int32), ("pitch_px", c_int64)]
 
 
 class occ_rect_light(C.Structure):
@@ -59,7 +59,8 @@ class occ_view(C.Structure):
 class occ_tuning(C.Structure):
     _fields_ = [("reuse_tile_rows", c_int32), ("reuse_window_path", c_int32),
                 ("batch_ctas_per_sm", c_int32), ("fused_ao_path", c_int32),
-                ("group_prefetch", c_int32)]
+                ("group_prefetch", c_int32), ("trace_path", c_int32),
+                ("trace_ctas_per_sm", c_int32), ("trace_refill", c_int32)]
 
 
 class occ_bvh_stats(C.Structure):
@@ -181,6 +182,8 @@ SIGNATURES = {
     "occ_debug_fp32_peak": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p,
                                       C.POINTER(c_double), c_void_p]),
     "occ_debug_bvh_counters": (c_int32, [c_void_p, c_void_p, c_int32, C.POINTER(c_uint64)]),
+    "occ_debug_stream_ceiling": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), C.POINTER(occ_occluders),
+                                           c_void_p, c_void_p]),
     "occ_debug_closest_hit": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p,
                                         c_void_p, c_void_p]),
     "occ_debug_philox": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),

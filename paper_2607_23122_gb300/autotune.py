@@ -6,6 +6,10 @@ and stores it in a JSON cache so later runs apply it without measuring:
 
   * reuse of window patterns (box / offsets): TMA-staged tile kernel with 4, 8 or 16
     receiver rows per tile, or the per-receiver kernel;
+  * reuse of group patterns: the group kernel's L2 prefetch (none, G-buffer and records);
+  * the step-1 trace: one CTA per 16 x 8 tile, or persistent CTAs taking rays from a
+    counter with a refill threshold of 8, 16 or 24 idle lanes and all or half of the CTAs
+    that fit;
   * persistent batched kernels: CTAs per SM (1, 2, 4, 8 or all that fit).
 
 Cache: $OCC_TUNE_CACHE, else ~/.cache/occreuse/tuning.json.
@@ -27,6 +31,9 @@ REUSE_CANDIDATES = [
     {"reuse_tile_rows": 4, "reuse_window_path": 1},
     {"reuse_tile_rows": 0, "reuse_window_path": 2},
 ]
+GROUP_CANDIDATES = [{"group_prefetch": c} for c in (1, 2, 3)]
+TRACE_CANDIDATES = [{"trace_path": 1}] + [
+    {"trace_path": 2, "trace_refill": r, "trace_ctas_per_sm": c} for r in (8, 16, 24) for c in (0, 4)]
 BATCH_CANDIDATES = [{"batch_ctas_per_sm": n} for n in (0, 1, 2, 4, 8)]
 
 
@@ -58,6 +65,11 @@ def reuse_key(gb: O.GBuffer, rec: O.Occluders, pattern: O.Pattern, estimator: in
               effect: int) -> str:
     return (f"reuse/{gb.W}x{gb.H}/pat{pattern.kind}:{pattern.gw}x{pattern.gh}/K{pattern.K}/"
             f"gb{int(gb.packed)}/rec{int(rec.packed)}/eff{effect}/est{estimator}")
+
+
+def trace_key(gb: O.GBuffer, rec: O.Occluders, bvh: O.BVH, effect: int) -> str:
+    return (f"trace/{gb.W}x{gb.H}/gb{int(gb.packed)}/rec{int(rec.packed)}/eff{effect}/"
+            f"tris{bvh.stats['num_tris']}")
 
 
 def batch_key(views: list) -> str:
@@ -99,11 +111,44 @@ def tune_reuse(ctx: O.Context, gb: O.GBuffer, rec: O.Occluders, pattern: O.Patte
         return cache[key]
     fn = O.occ_reuse_ao if rec.meta.effect == O.OCC_EFFECT_AO else O.occ_reuse_shadow
     timings = []
-    cands = REUSE_CANDIDATES if pattern.kind != O.OCC_PAT_GROUP else [{}]
+    cands = REUSE_CANDIDATES if pattern.kind != O.OCC_PAT_GROUP else GROUP_CANDIDATES
     for cfg in cands:
         _apply(ctx, cfg)
         ms = _time(lambda: fn(ctx, gb, rec, pattern, pattern.K, estimator, bvh=bvh, out=out), iters)
         timings.append({"config": cfg, "ms": ms})
+    best = min(timings, key=lambda t: t["ms"])
+    entry = {"best": best["config"], "timings": timings}
+    _apply(ctx, best["config"])
+    with _LOCK:
+        cache = load_cache()
+        cache[key] = entry
+        save_cache(cache)
+    return entry
+
+
+def tune_trace(ctx: O.Context, gb: O.GBuffer, bvh: O.BVH, effect: int, rec: O.Occluders,
+               radius: float = 0.0, light=None, iters: int = 15, use_cache: bool = True) -> dict:
+    """Picks the step-1 trace launch (kernel, refill threshold, CTAs per SM) for this
+    workload, timing it into the caller's record buffer, and applies it to ctx."""
+    key = trace_key(gb, rec, bvh, effect)
+    with _LOCK:
+        cache = load_cache() if use_cache else {}
+    if key in cache:
+        _apply(ctx, cache[key]["best"])
+        return cache[key]
+
+    def run():
+        if effect == O.OCC_EFFECT_AO:
+            O.occ_trace_ao(ctx, gb, bvh, radius, 1, 0, out=rec)
+        else:
+            O.occ_trace_shadow(ctx, gb, bvh, light, 1, 0, out=rec)
+
+    timings = []
+    for cfg in TRACE_CANDIDATES:
+        full = {"trace_path": 0, "trace_refill": 0, "trace_ctas_per_sm": 0}
+        full.update(cfg)
+        _apply(ctx, full)
+        timings.append({"config": full, "ms": _time(run, iters)})
     best = min(timings, key=lambda t: t["ms"])
     entry = {"best": best["config"], "timings": timings}
     _apply(ctx, best["config"])

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS) k_frame_group(Frame
     const bool inside = x < a.gb.W && y < a.gb.H;
     const uint32_t p = inside ? (uint32_t)y * (uint32_t)a.gb.W + (uint32_t)x : 0u;
     float3 xo = make_float3(0.0f, 0.0f, 0.0f), n = xo;
-    const bool valid = inside && gb_fetch(a.gb.pos, a.gb.nrm, a.gb.packed != 0, (int)p, &xo, &n);
+    const bool valid = inside && gb_fetch(a.gb, (int)p, &xo, &n);
     RectLight L;
     if (EFFECT == kShadow) L = make_light(a.lp);
     // AO segments are short: start below the part of the tree they cannot leave
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS)
                     const bool inside = x < a.gb.W && y < a.gb.H;
                     p = inside ? y * a.gb.W + x : -1;
                     float3 xo = make_float3(0.0f, 0.0f, 0.0f), n = xo;
-                    const bool valid = inside && gb_fetch(a.gb.pos, a.gb.nrm, a.gb.packed != 0, p, &xo, &n);
+                    const bool valid = inside && gb_fetch(a.gb, p, &xo, &n);
                     put_receiver<kAO>(s, me, xo, n, valid, L);
                     if (valid) {
                         float tmax;

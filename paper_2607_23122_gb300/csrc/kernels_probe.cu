@@ -67,7 +67,33 @@ __global__ void __launch_bounds__(kProbeThreads) k_fp32_peak(int iters, float* s
     sink[(size_t)blockIdx.x * kProbeThreads + threadIdx.x] = acc;
 }
 
+// Streaming ceiling of the group reuse kernel's memory pattern (4 x 2 groups, FP32): the
+// same CTA shape (4 warps side by side, each warp 16 x 2 pixels), the same loads (G-buffer
+// position and normal and record plane 0 for every pixel, record plane 1 for pixels whose
+// ray hit) and the same 4-byte store per pixel, with no arithmetic beyond a sum that keeps
+// the loads alive.  Its time is what the group kernel's bytes cost on their own.
+__global__ void __launch_bounds__(128) k_stream_ceiling(GBufView gb, RecView rec, float* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 3, m = lane & 7;
+    const int x = (blockIdx.x * 4 + warp) * 16 + g * 4 + (m & 3);
+    const int y = blockIdx.y * 2 + (m >> 2);
+    if (x >= gb.W || y >= gb.H) return;
+    const int i = y * gb.W + x, gi = y * gb.pitch + x;
+    const float4 P = __ldg(gb.pos + gi), N = __ldg(gb.nrm + gi), R0 = __ldg(rec.r0 + i);
+    float4 R1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (P.w != 0.0f && __float_as_int(R0.w) >= 0) R1 = __ldg(rec.r1 + i);
+    out[i] = P.x + N.y + R0.z + R1.x;
+}
+
 }  // namespace
+
+cudaError_t launch_stream_ceiling(const GBufView& gb, const RecView& rec, float* out,
+                                  cudaStream_t s) {
+    if (gb.W <= 0 || gb.H <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((gb.W + 63) / 64), (unsigned)((gb.H + 1) / 2));
+    k_stream_ceiling<<<grid, 128, 0, s>>>(gb, rec, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_fp32_peak(int paired, int iters, int blocks, float* sink, double* flop,
                              cudaStream_t s) {

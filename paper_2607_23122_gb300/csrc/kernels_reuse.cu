@@ -51,7 +51,7 @@ __device__ __forceinline__ int gather_members(const PatternParams& pat, const GB
             const int px = x + o.x, py = y + o.y;
             if (px < 0 || py < 0 || px >= gb.W || py >= gb.H) continue;
             const int q = py * gb.W + px;
-            if (!gb_valid(gb.pos, gb.packed != 0, q)) continue;
+            if (!gb_valid(gb, q)) continue;
             mem[n++] = q;
         }
         return n;
@@ -70,7 +70,7 @@ __device__ __forceinline__ int gather_members(const PatternParams& pat, const GB
         }
         if (px < 0 || py < 0 || px >= gb.W || py >= gb.H) continue;
         const int q = py * gb.W + px;
-        if (!gb_valid(gb.pos, gb.packed != 0, q)) continue;
+        if (!gb_valid(gb, q)) continue;
         if (px == x && py == y) *self = n;
         if (n < MAXK) mem[n++] = q;
     }
@@ -84,7 +84,7 @@ template <int EFFECT, int EST, int MAXK>
 __device__ __forceinline__ void reuse_pixel(const ReuseArgs& a, int x, int y) {
     if (x >= a.gb.W || y >= a.gb.H) return;
     const int i = y * a.gb.W + x;
-    if (!gb_valid(a.gb.pos, a.gb.packed != 0, i)) {
+    if (!gb_valid(a.gb, i)) {
         a.out[i] = 1.0f;
         return;
     }
@@ -117,7 +117,7 @@ __device__ __forceinline__ void reuse_pixel(const ReuseArgs& a, int x, int y) {
 #pragma unroll 1
     for (int c = 0; c < n; ++c) {
         float3 z, nz;
-        const int tri = fetch_cand(a.rec, mem[c], f3(__ldg(a.gb.pos + mem[c])), &z, &nz);
+        const int tri = fetch_cand(a.rec, mem[c], gb_point(a.gb, mem[c]), &z, &nz);
         if (tri < 0) continue;
         ++blocked;
         float Psum = 0.0f, pi = 0.0f;
@@ -152,7 +152,7 @@ template <int EST>
 __device__ __forceinline__ void reuse_simple_pixel(const ReuseArgs& a, int x, int y) {
     if (x >= a.gb.W || y >= a.gb.H) return;
     const int i = y * a.gb.W + x;
-    if (!gb_valid(a.gb.pos, a.gb.packed != 0, i)) {
+    if (!gb_valid(a.gb, i)) {
         a.out[i] = 1.0f;
         return;
     }
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(128) k_reuse_light(ReuseArgs a, uint64_t seed,
     tile_pixel(&x, &y);
     if (x >= a.gb.W || y >= a.gb.H) return;
     const int i = y * a.gb.W + x;
-    if (!gb_valid(a.gb.pos, a.gb.packed != 0, i)) {
+    if (!gb_valid(a.gb, i)) {
         a.out[i] = 1.0f;
         return;
     }
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(128) k_reuse_light(ReuseArgs a, uint64_t seed,
     int mem[MAXK];
     int self;
     const int n = gather_members<MAXK>(a.pat, a.gb, x, y, mem, &self);
-    const float3 xi = f3(__ldg(a.gb.pos + i));
+    const float3 xi = gb_point(a.gb, i);
     int vis = 0;
     for (int c = 0; c < n; ++c) {
         float tmax;
@@ -268,7 +268,7 @@ __global__ void k_debug_mis(ReuseArgs a, const int32_t* pix, int32_t npix, int32
     int mem[kMaxMembers];
     int self;
     int n = 0;
-    if (gb_valid(a.gb.pos, a.gb.packed != 0, i))
+    if (gb_valid(a.gb, i))
         n = gather_members<kMaxMembers>(a.pat, a.gb, x, y, mem, &self);
     for (int c = 0; c < kMaxMembers; ++c) members[t * kMaxMembers + c] = c < n ? mem[c] : -1;
     float* wt = w + (size_t)t * kMaxMembers * kMaxMembers;

@@ -5,7 +5,7 @@
 
 #include <atomic>
 
-#include "occ_f32x2.cuh"
+#include "occ_dens_x2.cuh"
 #include "occ_reuse.cuh"
 
 namespace occ {
@@ -13,7 +13,8 @@ namespace {
 
 // ---------------------------------------------------------------------------------------
 // Warp-cooperative GROUP kernel.  K = GW * GH lanes per group, 32 / K groups per warp
-// laid side by side (warp block = (32/K * GW) x GH pixels), 8 warps side by side per CTA.
+// laid side by side (warp block = (32/K * GW) x GH pixels), OCC_GROUP_WARPS warps side by side
+// per CTA.
 // ---------------------------------------------------------------------------------------
 // Loading the hit-normal plane only for rays that hit saves bytes but adds a dependent
 // round trip; OCC_GROUP_EAGER_R1=1 loads it together with the other planes (measured
@@ -24,8 +25,19 @@ namespace {
 // warps per CTA of the group kernel (side by side) and the load flavour: every byte of
 // the G-buffer and records is read exactly once, so streaming loads (evict-first) can be
 // used instead of read-only cached loads.
+// 4 warps per CTA measured faster than 8 at 1080p (4x2 AO 27.5 against 29.1 us; shadows
+// 32.8 against 34.8 us): the finer CTAs fill the SMs' slots left by finished ones sooner.
 #ifndef OCC_GROUP_WARPS
-#define OCC_GROUP_WARPS 8
+#define OCC_GROUP_WARPS 4
+#endif
+// resident CTAs per SM requested from the register allocator (0: no request)
+#ifndef OCC_GROUP_MIN_BLOCKS
+#define OCC_GROUP_MIN_BLOCKS 0
+#endif
+#if OCC_GROUP_MIN_BLOCKS > 0
+#define OCC_GROUP_BOUNDS __launch_bounds__(32 * OCC_GROUP_WARPS, OCC_GROUP_MIN_BLOCKS)
+#else
+#define OCC_GROUP_BOUNDS __launch_bounds__(32 * OCC_GROUP_WARPS)
 #endif
 #ifndef OCC_GROUP_STREAM_LOADS
 #define OCC_GROUP_STREAM_LOADS 0
@@ -41,65 +53,18 @@ __device__ __forceinline__ T group_load(const T* p) {
     return __ldg(p);
 }
 
-// AO column of candidate (z, n_z) against two receivers at once with paired FP32
-// instructions: the densities of Eq. 15 (without Occ and 1/pi) of members k, k + 1 given
-// their coordinates (xs, ys, zs) and normals (nxs, nys, nzs) as lane pairs.  The operation
-// order is dens_ao's, so each lane equals dens_ao bit for bit; an invalid member carries a
-// zero normal (n_x.d = 0 fails the support test).
-__device__ __forceinline__ float2 dens_ao_x2(f32x2 zx, f32x2 zy, f32x2 zz, f32x2 mnx, f32x2 mny,
-                                             f32x2 mnz, float2 xs, float2 ys, float2 zs,
-                                             float2 nxs, float2 nys, float2 nzs, float R2s) {
-    const f32x2 dx = sub2(zx, pk2(xs.x, xs.y));
-    const f32x2 dy = sub2(zy, pk2(ys.x, ys.y));
-    const f32x2 dz = sub2(zz, pk2(zs.x, zs.y));
-    const f32x2 r2 = dot3x2(dx, dy, dz, dx, dy, dz);
-    const f32x2 a = dot3x2(pk2(nxs.x, nxs.y), pk2(nys.x, nys.y), pk2(nzs.x, nzs.y), dx, dy, dz);
-    const f32x2 b = dot3x2(mnx, mny, mnz, dx, dy, dz);   // -(n_z . d), exactly
-    const float2 A = up2(a), B = up2(b), R = up2(r2), AB = up2(mul2(a, b)), R4 = up2(mul2(r2, r2));
-    const bool ok0 = (A.x > 0.0f) & (B.x > 0.0f) & (R.x > 0.0f) & (R.x <= R2s);
-    const bool ok1 = (A.y > 0.0f) & (B.y > 0.0f) & (R.y > 0.0f) & (R.y <= R2s);
-    return make_float2(ok0 ? __fdividef(AB.x, R4.x) : 0.0f, ok1 ? __fdividef(AB.y, R4.y) : 0.0f);
-}
-
-// Shadow counterpart (Eqs. 20-21 without Occ and 1/Area, dens_sh's operation order): the
-// receivers' precomputed plane terms (n_L.(c - x), (x - c).e_u, (x - c).e_v) come in
-// (nxs, nys, nzs); an invalid member carries zero terms (s_L = 0 fails s_L > 1).  Every
-// term is evaluated for both lanes and the support tests are combined at the end.
-__device__ __forceinline__ float2 dens_sh_x2(f32x2 zx, f32x2 zy, f32x2 zz, f32x2 mnx, f32x2 mny,
-                                             f32x2 mnz, float2 xs, float2 ys, float2 zs,
-                                             float2 hs, float2 us, float2 vs, const RectLight& L) {
-    const f32x2 dx = sub2(zx, pk2(xs.x, xs.y));
-    const f32x2 dy = sub2(zy, pk2(ys.x, ys.y));
-    const f32x2 dz = sub2(zz, pk2(zs.x, zs.y));
-    const float2 nd = up2(dot3x2(bc2(L.n.x), bc2(L.n.y), bc2(L.n.z), dx, dy, dz));
-    const float2 cz = up2(dot3x2(mnx, mny, mnz, dx, dy, dz));   // -(n_z . d), exactly
-    const float2 inv = make_float2(__fdividef(1.0f, nd.x), __fdividef(1.0f, nd.y));
-    const f32x2 inv2 = pk2(inv.x, inv.y);
-    const f32x2 sL = mul2(pk2(hs.x, hs.y), inv2);
-    const f32x2 du = dot3x2(dx, dy, dz, bc2(L.eu.x), bc2(L.eu.y), bc2(L.eu.z));
-    const f32x2 dv = dot3x2(dx, dy, dz, bc2(L.ev.x), bc2(L.ev.y), bc2(L.ev.z));
-    const float2 A = up2(mul2(fma2(sL, du, pk2(us.x, us.y)), bc2(L.inv_eu2)));
-    const float2 B = up2(mul2(fma2(sL, dv, pk2(vs.x, vs.y)), bc2(L.inv_ev2)));
-    const f32x2 neg_inv = pk2(-inv.x, -inv.y);
-    const float2 J = up2(mul2(mul2(mul2(sL, sL), pk2(cz.x, cz.y)), neg_inv));
-    const float2 S = up2(sL);
-    const bool ok0 = (nd.x < 0.0f) & (cz.x > 0.0f) & (S.x > 1.0f) & (fabsf(A.x) <= L.lim) &
-                     (fabsf(B.x) <= L.lim);
-    const bool ok1 = (nd.y < 0.0f) & (cz.y > 0.0f) & (S.y > 1.0f) & (fabsf(A.y) <= L.lim) &
-                     (fabsf(B.y) <= L.lim);
-    return make_float2(ok0 ? J.x : 0.0f, ok1 ? J.y : 0.0f);
-}
-
+// Densities of candidate (z, n_z) at two members given as float pairs (see occ_dens_x2.cuh).
 template <int EFFECT>
 __device__ __forceinline__ float2 dens_x2(f32x2 zx, f32x2 zy, f32x2 zz, f32x2 mnx, f32x2 mny,
                                           f32x2 mnz, float2 xs, float2 ys, float2 zs, float2 ns0,
                                           float2 ns1, float2 ns2, float R2s, const RectLight& L) {
-    if (EFFECT == kAO) return dens_ao_x2(zx, zy, zz, mnx, mny, mnz, xs, ys, zs, ns0, ns1, ns2, R2s);
-    return dens_sh_x2(zx, zy, zz, mnx, mny, mnz, xs, ys, zs, ns0, ns1, ns2, L);
+    return dens_x2_pairs<EFFECT>(zx, zy, zz, mnx, mny, mnz, pk2(xs.x, xs.y), pk2(ys.x, ys.y),
+                                 pk2(zs.x, zs.y), pk2(ns0.x, ns0.y), pk2(ns1.x, ns1.y),
+                                 pk2(ns2.x, ns2.y), R2s, L);
 }
 
 template <int EFFECT, int EST, int GW, int GH, bool PACKED>
-__global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs a) {
+__global__ void OCC_GROUP_BOUNDS k_reuse_group(ReuseArgs a) {
     constexpr int K = GW * GH;
     constexpr int GPW = 32 / K;
     constexpr int BW = GPW * GW;
@@ -123,6 +88,7 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
     const int y = blockIdx.y * GH + m / GW;
     const bool inside = x < a.gb.W && y < a.gb.H;
     const int i = inside ? y * a.gb.W + x : 0;
+    const int gi = inside ? y * a.gb.pitch + x : 0;   // G-buffer index
     RectLight L;
     if (EFFECT == kShadow) L = make_light(a.lp);
     // Prefetch into L2 the rows of the CTA one wave of resident CTAs later (CTAs start in
@@ -135,8 +101,10 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
             const int px = (int)(t % gridDim.x) * CW, py = (int)(t / gridDim.x) * GH + (int)threadIdx.x % GH;
             if (py < a.gb.H) {
                 const int n = min(CW, a.gb.W - px);
-                const size_t q = (size_t)py * a.gb.W + px;
                 const int plane = (int)threadIdx.x / GH;
+                // G-buffer planes are pitched, record planes dense
+                const bool gplane = plane == 0 || (plane == 1 && !PACKED);
+                const size_t q = (size_t)py * (gplane ? a.gb.pitch : a.gb.W) + px;
                 const float4* base = plane == 0 ? a.gb.pos : plane == 1 ? (PACKED ? a.rec.r0 : a.gb.nrm)
                                    : plane == 2 ? a.rec.r0 : a.rec.r1;
                 if (base && !(PACKED && plane >= 2)) prefetch_l2(base + q, (uint32_t)n * 16u);
@@ -151,7 +119,7 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
     if (PACKED) {
         // 16 + 16 bytes per pixel: (x, octahedral normal) and the packed record
         if (inside) {
-            P = group_load(a.gb.pos + i);
+            P = group_load(a.gb.pos + gi);
             R0 = group_load(a.rec.r0 + i);
         }
         valid = inside && __float_as_uint(P.w) != kOctInvalid;
@@ -160,8 +128,8 @@ __global__ void __launch_bounds__(32 * OCC_GROUP_WARPS) k_reuse_group(ReuseArgs 
         if (hit) rec_unpack(R0, f3(P), &z, &nz);
     } else {
         if (inside) {
-            P = group_load(a.gb.pos + i);
-            N = group_load(a.gb.nrm + i);
+            P = group_load(a.gb.pos + gi);
+            N = group_load(a.gb.nrm + gi);
             R0 = group_load(a.rec.r0 + i);
             if (OCC_GROUP_EAGER_R1) R1 = group_load(a.rec.r1 + i);
         }
@@ -355,8 +323,8 @@ __global__ void __launch_bounds__(128, 8)
                     const int x = (int)(cand % (uint32_t)W), y = (int)(cand / (uint32_t)W);
                     const int qm = ((y / gh) * gh + k / gw) * W + (x / gw) * gw + k % gw;
                     float3 xk = make_float3(0.0f, 0.0f, 0.0f), xi = xk, nn = xk, z = xk, nz = xk;
-                    gb_fetch(a.gb.pos, a.gb.nrm, a.gb.packed != 0, qm, &xk, &nn);
-                    gb_fetch(a.gb.pos, a.gb.nrm, a.gb.packed != 0, (int)cand, &xi, &nn);
+                    gb_fetch(a.gb, qm, &xk, &nn);
+                    gb_fetch(a.gb, (int)cand, &xi, &nn);
                     tri = (uint32_t)fetch_cand(a.rec, (int)cand, xi, &z, &nz);
                     bit = 1u << k;
                     trav_init(t, xk, sub3(z, xk), kValidateTmax, 0u);

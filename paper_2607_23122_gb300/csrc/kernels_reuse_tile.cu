@@ -20,6 +20,7 @@
 
 #include <mutex>
 
+#include "occ_dens_x2.cuh"
 #include "occ_device.cuh"
 #include "occ_f32x2.cuh"
 #include "occ_kernels.h"
@@ -29,8 +30,9 @@ namespace {
 
 constexpr float kSupportSlackT = 1.0f + 1.0f / 65536.0f;
 
-// AO windows of 4 or 8 member slots evaluate their density columns on paired FP32
-// instructions (OCC_TILE_PAIRED=1; 0 keeps the scalar column).
+// Windows of 4 or 8 member slots evaluate their density columns on paired FP32 instructions
+// and walk each receiver's own list of candidates (OCC_TILE_PAIRED=1; 0 keeps the scalar
+// column over every slot).
 #ifndef OCC_TILE_PAIRED
 #define OCC_TILE_PAIRED 1
 #endif
@@ -220,28 +222,13 @@ __device__ __forceinline__ void staged_cand(const Staged& st, int q, float4 r0, 
     }
 }
 
-// AO densities of candidate (z, n_z) at members s and s + 1 held as lane pairs (receiver
-// point and normal per axis): pair_density<kAO>'s operation order on each lane, so each
-// lane equals it bit for bit.
-__device__ __forceinline__ float2 pair_density_ao_x2(f32x2 zx, f32x2 zy, f32x2 zz, f32x2 mnx,
-                                                     f32x2 mny, f32x2 mnz, const f32x2* px,
-                                                     const f32x2* pn, float R2s) {
-    const f32x2 dx = sub2(zx, px[0]), dy = sub2(zy, px[1]), dz = sub2(zz, px[2]);
-    const f32x2 r2 = dot3x2(dx, dy, dz, dx, dy, dz);
-    const f32x2 a = dot3x2(pn[0], pn[1], pn[2], dx, dy, dz);
-    const f32x2 b = dot3x2(mnx, mny, mnz, dx, dy, dz);   // -(n_z . d), exactly
-    const float2 A = up2(a), B = up2(b), R = up2(r2), AB = up2(mul2(a, b)), R4 = up2(mul2(r2, r2));
-    const bool ok0 = (A.x > 0.0f) & (B.x > 0.0f) & (R.x > 0.0f) & (R.x <= R2s);
-    const bool ok1 = (A.y > 0.0f) & (B.y > 0.0f) & (R.y > 0.0f) & (R.y <= R2s);
-    return make_float2(ok0 ? __fdividef(AB.x, R4.x) : 0.0f, ok1 ? __fdividef(AB.y, R4.y) : 0.0f);
-}
-
-// One thread per receiver, AO, 4 or 8 member slots: the K receivers are held as lane
-// pairs (slots 2j, 2j + 1) and every candidate's column of densities runs on paired FP32
+// One thread per receiver, 4 or 8 member slots: the K receivers are held as lane pairs
+// (slots 2j, 2j + 1) and every candidate's column of densities runs on paired FP32
 // instructions (half the issue slots of the scalar column, the same results).
-template <int MAXK, bool PACKED>
-__device__ __forceinline__ void tile_single_ao_x2(const TileArgs& a, const RectLight& L,
-                                                  const Staged& st, int x0, int y0) {
+template <int EFFECT, int MAXK, bool PACKED>
+__device__ __forceinline__ void tile_single_x2(const TileArgs& a, const RectLight& L,
+                                               const Staged& st, const int* s_qoff, int x0,
+                                               int y0) {
     constexpr int NP = MAXK / 2;
     const int lx = threadIdx.x % a.TW, ly = threadIdx.x / a.TW;
     const int x = x0 + lx, y = y0 + ly;
@@ -255,8 +242,8 @@ __device__ __forceinline__ void tile_single_ao_x2(const TileArgs& a, const RectL
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             float3 x0r, t0, x1r, t1;
-            staged_recv<kAO, PACKED>(st, sidx[2 * j], L, &x0r, &t0);
-            staged_recv<kAO, PACKED>(st, sidx[2 * j + 1], L, &x1r, &t1);
+            staged_recv<EFFECT, PACKED>(st, sidx[2 * j], L, &x0r, &t0);
+            staged_recv<EFFECT, PACKED>(st, sidx[2 * j + 1], L, &x1r, &t1);
             if (!((vmask >> (2 * j)) & 1u)) t0 = make_float3(0.0f, 0.0f, 0.0f);
             if (!((vmask >> (2 * j + 1)) & 1u)) t1 = make_float3(0.0f, 0.0f, 0.0f);
             px[j][0] = pk2(x0r.x, x1r.x);
@@ -266,13 +253,22 @@ __device__ __forceinline__ void tile_single_ao_x2(const TileArgs& a, const RectL
             pn[j][1] = pk2(t0.y, t1.y);
             pn[j][2] = pk2(t0.z, t1.z);
         }
-        float B = 0.0f;
+        // the member slots whose record holds an occluder: each lane walks its own list, so
+        // a warp takes as many candidate steps as its busiest lane (lanes whose candidate
+        // missed no longer idle through the other lanes' columns)
+        uint32_t hm = 0;
 #pragma unroll
-        for (int c = 0; c < MAXK; ++c) {
-            if (c >= a.K || !((vmask >> c) & 1u)) continue;
-            const int q = sidx[c];
+        for (int c = 0; c < MAXK; ++c)
+            if (c < a.K && ((vmask >> c) & 1u) &&
+                __float_as_int(reinterpret_cast<const float*>(st.r0 + sidx[c])[3]) >= 0)
+                hm |= 1u << c;
+        const uint32_t blocked = hm;   // valid members whose record holds an occluder
+        float B = 0.0f;
+        while (hm) {
+            const int c = __ffs(hm) - 1;
+            hm &= hm - 1u;
+            const int q = sc + s_qoff[c];
             const float4 r0 = st.r0[q];
-            if (__float_as_int(r0.w) < 0) continue;
             float3 z, nz;
             staged_cand<PACKED>(st, q, r0, &z, &nz);
             const f32x2 zx = bc2(z.x), zy = bc2(z.y), zz = bc2(z.z);
@@ -280,7 +276,8 @@ __device__ __forceinline__ void tile_single_ao_x2(const TileArgs& a, const RectL
             float2 d[NP];
 #pragma unroll
             for (int j = 0; j < NP; ++j)
-                d[j] = pair_density_ao_x2(zx, zy, zz, mnx, mny, mnz, px[j], pn[j], a.R2s);
+                d[j] = dens_x2_pairs<EFFECT>(zx, zy, zz, mnx, mny, mnz, px[j][0], px[j][1],
+                                             px[j][2], pn[j][0], pn[j][1], pn[j][2], a.R2s, L);
             // slot 0 is the receiver: its density is the numerator; P_j sums in slot order
             const float pi = d[0].x;
             float Psum = pi + d[0].y;
@@ -289,6 +286,7 @@ __device__ __forceinline__ void tile_single_ao_x2(const TileArgs& a, const RectL
             if (pi > 0.0f) B += pi / Psum;
         }
         res = 1.0f - B;
+        if (EFFECT == kShadow && blocked == vmask) res = 0.0f;   // all-blocked guard
     }
     a.out[y * a.W + x] = res;
 }
@@ -297,10 +295,10 @@ __device__ __forceinline__ void tile_single_ao_x2(const TileArgs& a, const RectL
 // receiver terms, whose densities are 0, so the pair loop has no per-member test).
 template <int EFFECT, int MAXK, bool PACKED>
 __device__ __forceinline__ void tile_single(const TileArgs& a, const RectLight& L, const Staged& st,
-                                            int x0, int y0) {
+                                            const int* s_qoff, int x0, int y0) {
     // (16 slots held as pairs spill: they keep the scalar column)
-    if (EFFECT == kAO && (MAXK == 4 || MAXK == 8) && OCC_TILE_PAIRED) {
-        tile_single_ao_x2<MAXK, PACKED>(a, L, st, x0, y0);
+    if ((MAXK == 4 || MAXK == 8) && OCC_TILE_PAIRED) {
+        tile_single_x2<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, x0, y0);
         return;
     }
     const int lx = threadIdx.x % a.TW, ly = threadIdx.x / a.TW;
@@ -454,6 +452,14 @@ __device__ __forceinline__ void reuse_tile_body(const CUtensorMap* tm_pos, const
             tma_load_2d(base + 3 * plane, tm_r1, gx, gy, &bar[b]);
         }
     };
+    // staged-index offset of every member slot (slot s of the receiver at staged index sc
+    // sits at sc + s_qoff[s])
+    __shared__ int s_qoff[kMaxMembers];
+    if (threadIdx.x < (unsigned)a.K) {
+        const int2 o = member_offset(a, (int)threadIdx.x);
+        s_qoff[threadIdx.x] = o.y * a.SW + o.x;
+    }
+    __syncthreads();
     uint32_t parity[2] = {0u, 0u};
     if (threadIdx.x == 0 && (int)blockIdx.x < a.n_tiles) issue(blockIdx.x, 0);
     int it = 0;
@@ -483,7 +489,7 @@ __device__ __forceinline__ void reuse_tile_body(const CUtensorMap* tm_pos, const
         if (PAIRS)
             tile_pairs<EFFECT, MAXK, PACKED>(a, L, st, x0, y0);
         else
-            tile_single<EFFECT, MAXK, PACKED>(a, L, st, x0, y0);
+            tile_single<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, x0, y0);
         __syncthreads();   // buffer b is free for the copies issued next
         if (a.stages == 1 && threadIdx.x == 0 && tile + (int)gridDim.x < a.n_tiles)
             issue(tile + gridDim.x, 0);
@@ -538,11 +544,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 2D view of a W x H float4 plane as float32 [H][4W]; box = (4 SW, SH).
-bool make_map(CUtensorMap* m, const void* base, int W, int H, int SW, int SH) {
+// 2D map of a float4 plane of W x H pixels with rows `pitch` pixels apart.
+bool make_map(CUtensorMap* m, const void* base, int W, int H, int pitch, int SW, int SH) {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)4 * W, (cuuint64_t)H};
-    const cuuint64_t strides[1] = {(cuuint64_t)W * 16};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * 16};
     const cuuint32_t box[2] = {(cuuint32_t)(4 * SW), (cuuint32_t)SH};
     const cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box,
@@ -631,15 +638,15 @@ bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const
     CUtensorMap maps[4];
     if (packed) {
         // the kernel reads the packed G-buffer and record planes only
-        if (!make_map(&maps[0], gb.pos, gb.W, gb.H, a.SW, a.SH) ||
-            !make_map(&maps[2], rec.r0, gb.W, gb.H, a.SW, a.SH))
+        if (!make_map(&maps[0], gb.pos, gb.W, gb.H, gb.pitch, a.SW, a.SH) ||
+            !make_map(&maps[2], rec.r0, gb.W, gb.H, gb.W, a.SW, a.SH))
             return false;
         maps[1] = maps[0];
         maps[3] = maps[2];
-    } else if (!make_map(&maps[0], gb.pos, gb.W, gb.H, a.SW, a.SH) ||
-               !make_map(&maps[1], gb.nrm, gb.W, gb.H, a.SW, a.SH) ||
-               !make_map(&maps[2], rec.r0, gb.W, gb.H, a.SW, a.SH) ||
-               !make_map(&maps[3], rec.r1, gb.W, gb.H, a.SW, a.SH)) {
+    } else if (!make_map(&maps[0], gb.pos, gb.W, gb.H, gb.pitch, a.SW, a.SH) ||
+               !make_map(&maps[1], gb.nrm, gb.W, gb.H, gb.pitch, a.SW, a.SH) ||
+               !make_map(&maps[2], rec.r0, gb.W, gb.H, gb.W, a.SW, a.SH) ||
+               !make_map(&maps[3], rec.r1, gb.W, gb.H, gb.W, a.SW, a.SH)) {
         return false;
     }
     // slot counts: every slot beyond K costs a density, so the common sizes get their own

@@ -6,6 +6,7 @@
 // receivers and touch the same BVH nodes (short AO rays stay local).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "occ_device.cuh"
@@ -38,7 +39,7 @@ __device__ __forceinline__ void trace_pixel(const GBufView& gb, const DevBVH& bv
     const bool inside = x < gb.W && y < gb.H;
     const uint32_t p = inside ? (uint32_t)y * (uint32_t)gb.W + (uint32_t)x : 0u;
     float3 xo = make_float3(0.0f, 0.0f, 0.0f), n = xo;
-    const bool valid = inside && gb_fetch(gb.pos, gb.nrm, gb.packed != 0, (int)p, &xo, &n);
+    const bool valid = inside && gb_fetch(gb, (int)p, &xo, &n);
     // AO segments are short: start below the part of the tree they cannot leave
     const uint32_t start = EFFECT == kAO ? warp_start_node(bvh, valid, xo, radius) : 0u;
     if (!inside) return;
@@ -102,7 +103,7 @@ template <int EFFECT>
 __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
     k_trace_dyn(GBufView gb, DevBVH bvh, float radius, LightParams lp, uint64_t seed,
                 uint32_t sample, RecView rec, unsigned* status, unsigned* counter, int tiles_x,
-                uint32_t n_idx) {
+                uint32_t n_idx, int min_idle) {
     RectLight L;
     if (EFFECT == kShadow) L = make_light(lp);
     const int lane = threadIdx.x & 31;
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
         while (!exhausted) {
             const unsigned need = __ballot_sync(0xFFFFFFFFu, !have);
             if (!need) break;
-            if (__popc(need) < OCC_TRACE_DYN_MIN_IDLE && need != 0xFFFFFFFFu) break;
+            if (__popc(need) < min_idle && need != 0xFFFFFFFFu) break;
             uint32_t base = 0;
             if (lane == 0) base = atomicAdd(counter, (unsigned)__popc(need));
             base = __shfl_sync(0xFFFFFFFFu, base, 0);
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
                 if (idx < n_idx && x < gb.W && y < gb.H) {
                     p = (uint32_t)y * (uint32_t)gb.W + (uint32_t)x;
                     float3 xo = make_float3(0.0f, 0.0f, 0.0f), n = xo;
-                    if (gb_fetch(gb.pos, gb.nrm, gb.packed != 0, (int)p, &xo, &n)) {
+                    if (gb_fetch(gb, (int)p, &xo, &n)) {
                         float tmax;
                         const float3 d = step1_ray<EFFECT>(xo, n, p, radius, L, seed, sample, &tmax);
                         trav_init(t, xo, d, tmax, 0u);
@@ -269,7 +270,7 @@ __global__ void k_debug_rays(GBufView gb, float radius, LightParams lp, uint64_t
     if (x >= gb.W || y >= gb.H) return;
     const uint32_t p = (uint32_t)y * (uint32_t)gb.W + (uint32_t)x;
     float3 xo, n;
-    if (!gb_fetch(gb.pos, gb.nrm, gb.packed != 0, (int)p, &xo, &n)) {
+    if (!gb_fetch(gb, (int)p, &xo, &n)) {
         out[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         return;
     }
@@ -284,8 +285,9 @@ __global__ void k_debug_rays(GBufView gb, float radius, LightParams lp, uint64_t
 __global__ void k_pack_gbuffer(GBufView gb, float4* out) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= (int64_t)gb.W * gb.H) return;
-    const float4 P = __ldg(gb.pos + p);
-    const uint32_t code = P.w != 0.0f ? oct_encode(f3(__ldg(gb.nrm + p))) : kOctInvalid;
+    const int g = gb_at(gb, (int)p);
+    const float4 P = __ldg(gb.pos + g);
+    const uint32_t code = P.w != 0.0f ? oct_encode(f3(__ldg(gb.nrm + g))) : kOctInvalid;
     out[p] = make_float4(P.x, P.y, P.z, __uint_as_float(code));
 }
 
@@ -297,10 +299,13 @@ dim3 tile_grid(int W, int H) {
 
 cudaError_t launch_trace(int effect, const GBufView& gb, const DevBVH& bvh, float radius,
                          const LightParams& light, uint64_t seed, uint32_t sample, RecView rec,
-                         unsigned* status, cudaStream_t s, unsigned* counter) {
+                         unsigned* status, cudaStream_t s, unsigned* counter, const Tuning* tune) {
     if (gb.W <= 0 || gb.H <= 0) return cudaSuccess;
     const dim3 grid = tile_grid(gb.W, gb.H);
-    if (OCC_TRACE_DYN && counter && effect == kAO) {
+    // persistent kernel by default for AO; the tuning may pick either kernel for either effect
+    const int path = tune ? tune->trace_path : 0;
+    const bool persistent = path == 2 || (path == 0 && effect == kAO);
+    if (OCC_TRACE_DYN && counter && persistent) {
         const uint32_t n_idx = grid.x * grid.y * 128u;
         // persistent grid: resident CTAs per SM x SMs (computed once; threads that race
         // here compute the same value)
@@ -316,15 +321,23 @@ cudaError_t launch_trace(int effect, const GBufView& gb, const DevBVH& bvh, floa
             n = (per_sm > 0 ? per_sm : 1) * sms;
             ctas[ei].store(n, std::memory_order_relaxed);
         }
-        const unsigned blocks = (unsigned)n < grid.x * grid.y ? (unsigned)n : grid.x * grid.y;
+        int want = n;
+        if (tune && tune->trace_ctas_per_sm > 0) {
+            int dev = 0, sms = 1;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            want = std::min(n, tune->trace_ctas_per_sm * sms);
+        }
+        const int min_idle = tune && tune->trace_refill > 0 ? tune->trace_refill : OCC_TRACE_DYN_MIN_IDLE;
+        const unsigned blocks = (unsigned)want < grid.x * grid.y ? (unsigned)want : grid.x * grid.y;
         cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) return e;
         if (effect == kAO)
             k_trace_dyn<kAO><<<blocks, 128, 0, s>>>(gb, bvh, radius, light, seed, sample, rec, status,
-                                                   counter, (int)grid.x, n_idx);
+                                                   counter, (int)grid.x, n_idx, min_idle);
         else
             k_trace_dyn<kShadow><<<blocks, 128, 0, s>>>(gb, bvh, radius, light, seed, sample, rec,
-                                                       status, counter, (int)grid.x, n_idx);
+                                                       status, counter, (int)grid.x, n_idx, min_idle);
         return cudaGetLastError();
     }
     if (effect == kAO)

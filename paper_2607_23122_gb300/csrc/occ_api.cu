@@ -53,6 +53,10 @@ occ_status check_gbuffer(occ_ctx* ctx, const occ_gbuffer* gb) {
         return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pointers are NULL");
     if (!aligned16(gb->pos4) || (gb->format == OCC_GB_FP32 && !aligned16(gb->nrm4)))
         return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pointers must be 16-byte aligned");
+    if (gb->pitch_px != 0 &&
+        (gb->pitch_px < gb->W || (int64_t)(gb->H - 1) * gb->pitch_px + gb->W > ((int64_t)1 << 31)))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pitch %lld invalid for width %d",
+                    (long long)gb->pitch_px, gb->W);
     return OCC_OK;
 }
 
@@ -165,7 +169,8 @@ using occ::to_params;
 
 occ::GBufView view(const occ_gbuffer* gb) {
     return occ::GBufView{gb->W, gb->H, reinterpret_cast<const float4*>(gb->pos4),
-                         reinterpret_cast<const float4*>(gb->nrm4), gb->format == OCC_GB_PACKED};
+                         reinterpret_cast<const float4*>(gb->nrm4), gb->format == OCC_GB_PACKED,
+                         gb->pitch_px ? (int32_t)gb->pitch_px : gb->W};
 }
 
 occ::RecView rec_view(const occ_occluders* o) {
@@ -283,7 +288,7 @@ occ_status trace_common(occ_ctx* ctx, int effect, const occ_gbuffer* gb, const o
     return launched(ctx,
                     occ::launch_trace(effect, view(gb), dev_bvh(bvh), radius, to_params(light), seed,
                                       sample, rec_view(out), ctx->status, (cudaStream_t)stream,
-                                      ctx->counter),
+                                      ctx->counter, &ctx->tune),
                     "trace launch");
 }
 
@@ -697,6 +702,19 @@ OCC_EXPORT occ_status occ_debug_fp32_peak(occ_ctx* ctx, int32_t paired, int32_t 
                     "fp32 probe launch");
 }
 
+OCC_EXPORT occ_status occ_debug_stream_ceiling(occ_ctx* ctx, const occ_gbuffer* gb,
+                                               const occ_occluders* occ, float* out, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if ((st = check_gbuffer(ctx, gb)) != OCC_OK) return st;
+    if ((st = check_occluders(ctx, gb, occ)) != OCC_OK) return st;
+    if (gb->format != OCC_GB_FP32 || occ->format != OCC_REC_FP32)
+        return fail(ctx, OCC_ERR_UNSUPPORTED, "the streaming probe reads FP32 G-buffers and records");
+    if (!out) return fail(ctx, OCC_ERR_INVALID_ARG, "out is NULL");
+    return launched(ctx, occ::launch_stream_ceiling(view(gb), rec_view(occ), out, (cudaStream_t)stream),
+                    "stream probe launch");
+}
+
 OCC_EXPORT occ_status occ_debug_bvh_counters(occ_ctx* ctx, const occ_bvh* bvh, int32_t reset,
                                              uint64_t* out_host) {
     occ_status st = check_ctx(ctx);
@@ -995,11 +1013,20 @@ OCC_EXPORT occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t) {
         return fail(ctx, OCC_ERR_INVALID_ARG, "fused_ao_path must be 0, 1 or 2");
     if (t->group_prefetch < 0 || t->group_prefetch > 3)
         return fail(ctx, OCC_ERR_INVALID_ARG, "group_prefetch must be 0, 1, 2 or 3");
+    if (t->trace_path < 0 || t->trace_path > 2)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "trace_path must be 0, 1 or 2");
+    if (t->trace_ctas_per_sm < 0 || t->trace_ctas_per_sm > 16)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "trace_ctas_per_sm must be in [0, 16]");
+    if (t->trace_refill < 0 || t->trace_refill > 32)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "trace_refill must be in [0, 32]");
     ctx->tune.tile_rows = t->reuse_tile_rows;
     ctx->tune.window_path = t->reuse_window_path;
     ctx->tune.batch_per_sm = t->batch_ctas_per_sm;
     ctx->tune.fused_ao_path = t->fused_ao_path;
     ctx->tune.group_prefetch = t->group_prefetch;
+    ctx->tune.trace_path = t->trace_path;
+    ctx->tune.trace_ctas_per_sm = t->trace_ctas_per_sm;
+    ctx->tune.trace_refill = t->trace_refill;
     return OCC_OK;
 }
 
@@ -1010,6 +1037,9 @@ OCC_EXPORT occ_status occ_get_tuning(const occ_ctx* ctx, occ_tuning* t) {
     t->batch_ctas_per_sm = ctx->tune.batch_per_sm;
     t->fused_ao_path = ctx->tune.fused_ao_path;
     t->group_prefetch = ctx->tune.group_prefetch;
+    t->trace_path = ctx->tune.trace_path;
+    t->trace_ctas_per_sm = ctx->tune.trace_ctas_per_sm;
+    t->trace_refill = ctx->tune.trace_refill;
     return OCC_OK;
 }
 

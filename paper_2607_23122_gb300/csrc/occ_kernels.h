@@ -13,6 +13,8 @@ struct GBufView {
     const float4* pos;   // FP32: (x.xyz, valid); packed: (x.xyz, octahedral normal code)
     const float4* nrm;   // FP32: (n.xyz, -); packed: unused
     int32_t packed;
+    int32_t pitch;       // row pitch of the planes in pixels (>= W); pixel p = y W + x sits at
+                         // y pitch + x
 };
 
 // Occluder records.  FP32: plane 0 (z.xyz, tri id bits), plane 1 (n_z.xyz, t).
@@ -69,11 +71,14 @@ enum Estimator { kNoReuse = 0, kBiased = 1, kUnbiased = 2, kBoxMean = 3, kLightU
 
 cudaError_t launch_gbuffer(const DevBVH& bvh, const float* cam, float eps, int W, int H,
                            float4* pos, float4* nrm, unsigned* status, cudaStream_t s);
+struct Tuning;
 // counter: a device word for the persistent dynamic-fetch kernel (reset on `s` before the
-// launch); nullptr selects the one-CTA-per-tile kernel.
+// launch); nullptr selects the one-CTA-per-tile kernel.  tune: trace launch choices
+// (nullptr: defaults).
 cudaError_t launch_trace(int effect, const GBufView& gb, const DevBVH& bvh, float radius,
                          const LightParams& light, uint64_t seed, uint32_t sample, RecView rec,
-                         unsigned* status, cudaStream_t s, unsigned* counter = nullptr);
+                         unsigned* status, cudaStream_t s, unsigned* counter = nullptr,
+                         const Tuning* tune = nullptr);
 cudaError_t launch_pack_gbuffer(const GBufView& gb, float4* out, cudaStream_t s);
 constexpr int kMaxLights = 16;
 struct LightWeights {
@@ -89,6 +94,9 @@ cudaError_t launch_debug_closest_hit(const DevBVH& bvh, const float4* rays, int6
 cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
                               const LightParams& light, uint64_t seed, uint32_t sample,
                               float4* out, cudaStream_t s);
+// Streaming ceiling of the group reuse kernel's memory pattern (kernels_probe.cu).
+cudaError_t launch_stream_ceiling(const GBufView& gb, const RecView& rec, float* out,
+                                  cudaStream_t s);
 // FP32 throughput probe (kernels_probe.cu): *flop = FLOPs of the launch.
 cudaError_t launch_fp32_peak(int paired, int iters, int blocks, float* sink, double* flop,
                              cudaStream_t s);
@@ -100,6 +108,9 @@ struct Tuning {
     int batch_per_sm = 0;
     int fused_ao_path = 0;
     int group_prefetch = 0;   // group kernel L2 prefetch: 0 default, 1 none, 2 / 3 planes
+    int trace_path = 0;       // 0 default (AO persistent, shadow per tile), 1 per tile, 2 persistent
+    int trace_ctas_per_sm = 0;   // persistent trace: CTAs per SM (0: all that fit)
+    int trace_refill = 0;     // persistent trace: idle lanes that trigger a refill (0: default)
 };
 
 // Workspace of the queued first-hit validation (unbiased group reuse): up to (K - 1) W H

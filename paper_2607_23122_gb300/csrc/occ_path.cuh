@@ -10,6 +10,26 @@
 namespace occ {
 
 constexpr float kSupportSlack = 1.0f + 1.0f / 65536.0f;
+
+// G-buffer index of pixel p = y W + x (records and outputs use p itself): y pitch + x.
+__device__ __forceinline__ int gb_at(const GBufView& gb, int p) {
+    if (gb.pitch == gb.W) return p;
+    const int y = p / gb.W;
+    return y * gb.pitch + (p - y * gb.W);
+}
+
+// G-buffer entry of pixel p: receiver point, normal, validity.
+__device__ __forceinline__ bool gb_fetch(const GBufView& gb, int p, float3* x, float3* n) {
+    return gb_fetch(gb.pos, gb.nrm, gb.packed != 0, gb_at(gb, p), x, n);
+}
+
+__device__ __forceinline__ bool gb_valid(const GBufView& gb, int p) {
+    return gb_valid(gb.pos, gb.packed != 0, gb_at(gb, p));
+}
+
+__device__ __forceinline__ float3 gb_point(const GBufView& gb, int p) {
+    return f3(__ldg(gb.pos + gb_at(gb, p)));
+}
 constexpr float kValidateTmax = 1.0f + 1.0f / 1024.0f;
 
 __device__ __forceinline__ RectLight make_light(const LightParams& p) {

@@ -40,7 +40,7 @@ constexpr int kUnbFinal = 101;
 template <int EFFECT>
 __device__ __forceinline__ Recv fetch_recv(const GBufView& gb, int q, const RectLight& L) {
     float3 x = make_float3(0.0f, 0.0f, 0.0f), n = x;
-    const bool v = gb_fetch(gb.pos, gb.nrm, gb.packed != 0, q, &x, &n);
+    const bool v = gb_fetch(gb, q, &x, &n);
     return make_recv<EFFECT>(x, n, v, L);
 }
 

@@ -127,14 +127,21 @@ class GBuffer:
     def packed(self) -> bool:
         return self.nrm4 is None
 
+    @property
+    def pitch(self) -> int:
+        """Row pitch of the planes in pixels (the tensors may be windows of wider ones)."""
+        return int(self.pos4.stride(0)) // 4
+
     def c(self) -> N.occ_gbuffer:
         for t in (self.pos4,) if self.packed else (self.pos4, self.nrm4):
-            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
-                    and tuple(t.shape) == (self.H, self.W, 4)):
-                raise ValueError("G-buffer tensors must be contiguous float32 CUDA [H, W, 4]")
+            if not (t.is_cuda and t.dtype == torch.float32 and tuple(t.shape) == (self.H, self.W, 4)
+                    and t.stride(2) == 1 and t.stride(1) == 4 and t.stride(0) % 4 == 0
+                    and t.stride(0) // 4 == self.pitch and self.pitch >= self.W):
+                raise ValueError("G-buffer tensors must be float32 CUDA [H, W, 4] with contiguous "
+                                 "rows and the same row pitch")
         return N.occ_gbuffer(self.W, self.H, self.pos4.data_ptr(),
                              None if self.packed else self.nrm4.data_ptr(),
-                             N.OCC_GB_PACKED if self.packed else N.OCC_GB_FP32)
+                             N.OCC_GB_PACKED if self.packed else N.OCC_GB_FP32, self.pitch)
 
     @staticmethod
     def from_numpy(pos4: np.ndarray, nrm4: np.ndarray, device="cuda") -> "GBuffer":
@@ -464,6 +471,14 @@ def occ_debug_fp32_peak(ctx: Context, paired: bool, iters: int, blocks: int, sin
     return float(flop.value)
 
 
+def occ_debug_stream_ceiling(ctx: Context, gb: GBuffer, occ: Occluders, out: torch.Tensor,
+                             stream=None):
+    """Launches the group kernel's streaming-ceiling probe (FP32 formats) on `stream`."""
+    g = gb.c()
+    ctx.check(ctx.lib.occ_debug_stream_ceiling(ctx.handle, C.byref(g), C.byref(occ.c()),
+                                               out.data_ptr(), _stream_handle(stream)))
+
+
 def occ_debug_bvh_counters(ctx: Context, bvh: BVH, reset: bool = True) -> dict:
     """Traversal counters of the instrumented library since the last reset."""
     out = (C.c_uint64 * 5)()
@@ -599,9 +614,10 @@ class Batch:
 
 
 def occ_set_tuning(ctx: Context, reuse_tile_rows: int = 0, reuse_window_path: int = 0,
-                   batch_ctas_per_sm: int = 0, fused_ao_path: int = 0, group_prefetch: int = 0):
+                   batch_ctas_per_sm: int = 0, fused_ao_path: int = 0, group_prefetch: int = 0,
+                   trace_path: int = 0, trace_ctas_per_sm: int = 0, trace_refill: int = 0):
     t = N.occ_tuning(reuse_tile_rows, reuse_window_path, batch_ctas_per_sm, fused_ao_path,
-                     group_prefetch)
+                     group_prefetch, trace_path, trace_ctas_per_sm, trace_refill)
     ctx.check(ctx.lib.occ_set_tuning(ctx.handle, C.byref(t)))
 
 

@@ -23,3 +23,7 @@ def test_candidates_are_valid_tuning_values():
     for c in autotune.REUSE_CANDIDATES:
         assert c["reuse_tile_rows"] in (0, 4, 8, 16) and c["reuse_window_path"] in (1, 2, 3)
     assert all(0 <= c["batch_ctas_per_sm"] <= 16 for c in autotune.BATCH_CANDIDATES)
+    assert all(c["group_prefetch"] in (1, 2, 3) for c in autotune.GROUP_CANDIDATES)
+    for c in autotune.TRACE_CANDIDATES:
+        assert c["trace_path"] in (1, 2)
+        assert 0 <= c.get("trace_refill", 0) <= 32 and 0 <= c.get("trace_ctas_per_sm", 0) <= 16

@@ -255,6 +255,35 @@ def test_tuning_choices_match_oracle(orc, occ, ctx, c1, cfg, pname, effect):
     P.compare_out(g.cpu().numpy(), ref, mg, c1["pos"][..., 3] > 0, f"tuning {cfg} {pname}")
 
 
+@pytest.mark.parametrize("cfg", [dict(trace_path=1), dict(trace_path=2),
+                                 dict(trace_path=2, trace_refill=1, trace_ctas_per_sm=1),
+                                 dict(trace_path=2, trace_refill=32, trace_ctas_per_sm=3),
+                                 dict(group_prefetch=1), dict(group_prefetch=3)])
+@pytest.mark.parametrize("effect", [AO, SH])
+def test_trace_and_group_tuning_choices_are_bit_identical(occ, ctx, c1, cfg, effect):
+    """Every trace launch choice (kernel, refill threshold, CTAs per SM) writes the same
+    records, and every group prefetch choice the same estimate, as the defaults."""
+    gb = occ.GBuffer.from_numpy(c1["pos"], c1["nrm"])
+
+    def run():
+        o = (occ.occ_trace_ao(ctx, gb, c1["bvh"], R_C1, 13, 2) if effect == AO else
+             occ.occ_trace_shadow(ctx, gb, c1["bvh"], LIGHT_C1, 13, 2))
+        fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
+        g = fn(ctx, gb, o, occ.Pattern.group(4, 2), 8, BIASED)
+        ctx.sync()
+        return o.data.clone(), g
+    rec0, out0 = run()
+    occ.occ_set_tuning(ctx, **cfg)
+    try:
+        assert {k: occ.occ_get_tuning(ctx)[k] for k in cfg} == cfg
+        rec1, out1 = run()
+    finally:
+        occ.occ_set_tuning(ctx)
+    # records compared as bits (a miss's triangle id -1 is a NaN pattern as a float)
+    i32 = occ.torch.int32
+    assert occ.torch.equal(rec0.view(i32), rec1.view(i32)) and occ.torch.equal(out0, out1)
+
+
 def test_autotuner_picks_caches_and_reapplies(occ, ctx, c1, tmp_path, monkeypatch):
     from paper_2607_23122_gb300 import autotune
     monkeypatch.setenv("OCC_TUNE_CACHE", str(tmp_path / "tune.json"))
@@ -279,5 +308,16 @@ def test_autotuner_picks_caches_and_reapplies(occ, ctx, c1, tmp_path, monkeypatc
     views, _ = _make_views(occ, c1, SPECS[:3])
     b = autotune.tune_batch(ctx, c1["bvh"], views, iters=2, use_cache=False)
     assert b["best"] in autotune.BATCH_CANDIDATES
+    occ.occ_set_tuning(ctx)
+    rec = occ.Occluders.empty(64, 64)
+    t = autotune.tune_trace(ctx, gb, c1["bvh"], AO, rec, radius=R_C1, iters=2)
+    assert len(t["timings"]) == len(autotune.TRACE_CANDIDATES)
+    assert all(occ.occ_get_tuning(ctx)[k] == v for k, v in t["best"].items())
+    key = autotune.trace_key(gb, rec, c1["bvh"], AO)
+    assert autotune.load_cache()[key]["best"] == t["best"]
+    occ.occ_set_tuning(ctx)
+    g = autotune.tune_reuse(ctx, gb, o, occ.Pattern.group(4, 2), BIASED, out, iters=2,
+                            use_cache=False)
+    assert g["best"] in autotune.GROUP_CANDIDATES
     occ.occ_set_tuning(ctx)
     ctx.sync()

@@ -308,6 +308,55 @@ def test_ragged_and_tiny_images(orc, occ, ctx, c1, shape):
             P.compare_out(g.cpu().numpy(), ref, mg, valid, f"{shape} {pname} {est}")
 
 
+def test_pitched_gbuffer_matches_its_dense_copy(occ, ctx, c1):
+    """A G-buffer that is a window of a wider render target (row pitch 64 > W = 40) gives the
+    same records and estimates, bit for bit, as the dense copy of the window: the AO trace
+    (persistent kernel), the shadow trace, the fused trace + group reuse, and the group,
+    window (TMA), per-receiver (unbiased, random pattern) and box-mean reuse kernels, in
+    both G-buffer formats."""
+    import torch
+    W, H, x0, y0 = 40, 30, 9, 17
+    big_pos = torch.from_numpy(c1["pos"]).cuda()
+    big_nrm = torch.from_numpy(c1["nrm"]).cuda()
+    win = occ.GBuffer(big_pos[y0:y0 + H, x0:x0 + W], big_nrm[y0:y0 + H, x0:x0 + W])
+    dense = occ.GBuffer(win.pos4.contiguous(), win.nrm4.contiguous())
+    assert win.pitch == 64 and dense.pitch == W
+    big_packed = occ.occ_pack_gbuffer(ctx, occ.GBuffer(big_pos, big_nrm))
+    pwin = occ.GBuffer(big_packed.pos4[y0:y0 + H, x0:x0 + W], None)
+    pdense = occ.occ_pack_gbuffer(ctx, win)
+    ctx.sync()
+    assert pwin.pitch == 64 and torch.equal(pwin.pos4.contiguous(), pdense.pos4)
+    pats = _patterns(occ)
+    for packed, (gw, gd) in ((False, (win, dense)), (True, (pwin, pdense))):
+        for effect in (AO, SH):
+            def trace(gb):
+                if effect == AO:
+                    return occ.occ_trace_ao(ctx, gb, c1["bvh"], R_C1, 4, 2, packed=packed)
+                return occ.occ_trace_shadow(ctx, gb, c1["bvh"], LIGHT_C1, 4, 2, packed=packed)
+            ow, od = trace(gw), trace(gd)
+            ctx.sync()
+            # compare bits: a miss stores triangle id -1, a NaN pattern as a float
+            assert torch.equal(ow.data.view(torch.int32), od.data.view(torch.int32)), (packed, effect)
+            fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
+            for pname in ("group4x2", "box3x3", "disk8", "random8"):
+                pat = pats[pname]
+                for est in (NOREUSE, BIASED, UNBIASED, BOXMEAN):
+                    bv = c1["bvh"] if est == UNBIASED else None
+                    a = fn(ctx, gw, ow, pat, pat.K, est, bvh=bv)
+                    b = fn(ctx, gd, od, pat, pat.K, est, bvh=bv)
+                    ctx.sync()
+                    assert torch.equal(a, b), (packed, effect, pname, est)
+            if not packed:
+                fused = occ.occ_trace_reuse_ao if effect == AO else occ.occ_trace_reuse_shadow
+                arg = R_C1 if effect == AO else LIGHT_C1
+                a = fused(ctx, gw, c1["bvh"], arg, 4, 2, pats["group4x2"], 8, BIASED)
+                b = fused(ctx, gd, c1["bvh"], arg, 4, 2, pats["group4x2"], 8, BIASED)
+                ctx.sync()
+                assert torch.equal(a, b), ("fused", effect)
+    with pytest.raises(ValueError):
+        occ.GBuffer(big_pos[:, :W].transpose(0, 1), big_nrm[:, :W].transpose(0, 1)).c()
+
+
 def test_all_invalid_gbuffer_and_max_k(orc, occ, ctx, c1):
     pos = np.zeros((20, 30, 4), dtype=np.float32)
     gb = occ.GBuffer.from_numpy(pos, pos)

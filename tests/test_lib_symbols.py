@@ -49,7 +49,7 @@ def test_version_and_no_gpu_errors_are_clean():
 def test_struct_layouts_match_the_header():
     """Sizes of the ctypes mirrors equal the C structs (LP64)."""
     from paper_2607_23122_gb300 import _native as N
-    assert ctypes.sizeof(N.occ_gbuffer) == 32
+    assert ctypes.sizeof(N.occ_gbuffer) == 40
     assert ctypes.sizeof(N.occ_rect_light) == 36
     assert ctypes.sizeof(N.occ_pattern) == 40
     assert ctypes.sizeof(N.occ_bvh_stats) == 48
@@ -58,7 +58,7 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(N.occ_sched_config) == 24
     assert ctypes.sizeof(N.occ_sched_stats) == 72
     assert ctypes.sizeof(N.occ_server_config) == 48
-    assert ctypes.sizeof(N.occ_tuning) == 20
+    assert ctypes.sizeof(N.occ_tuning) == 32
     # W H effect radius light(36) (pad) seed sample (pad) pattern(40) K estimator packed
     # camera(40) eps 4 pointers deadline
     assert ctypes.sizeof(N.occ_request) == 208
