@@ -76,6 +76,7 @@ struct Builder {
     const std::vector<AABB>& tb;           // triangle bounds
     const std::vector<std::array<float, 3>>& tc;   // centroids
     std::vector<uint32_t>& perm;
+    uint32_t leaf_max = kLeafMax;          // never keep a leaf bigger than this
 
     // Builds the subtree of perm[begin, end) into `out` (root at out[base]) and returns the
     // index of its root.
@@ -139,7 +140,7 @@ struct Builder {
             kTraverseCost + kIntersectCost * best_cost / (parea > 0.0f ? parea : 1.0f);
         const float leaf_cost = kIntersectCost * n;
         // small ranges become leaves when SAH does not favour a split; larger ones always split
-        if (n <= kLeafMax && (best_axis < 0 || split_cost >= leaf_cost)) return make_leaf();
+        if (n <= leaf_max && (best_axis < 0 || split_cost >= leaf_cost)) return make_leaf();
         uint32_t mid;
         if (best_axis < 0) {
             mid = begin + n / 2;   // all centroids coincide: split the range
@@ -187,6 +188,7 @@ struct Builder {
 };
 
 // Component c (child index) of plane p of a node.
+#if !OCC_BVH_CW8
 inline float& plane_at(BvhNode& n, int p, int c) {
     float4& v = n.plane[p * kPlaneVecs + c / 4];
     return (&v.x)[c % 4];
@@ -273,6 +275,171 @@ struct Collapser {
     }
 };
 
+#endif  // !OCC_BVH_CW8
+
+#if OCC_BVH_CW8
+// Collapse of the binary tree (leaves of at most 3 triangles) into compressed 8-wide nodes
+// (layout in occ_layout.h).  A node takes up to 8 children by opening its largest-area
+// internal children; the children are placed in slots so that slot s holds the child
+// nearest the corner of octant s (high on the axes whose bit is set), which the traversal
+// visits first for rays whose direction signs are the complement of s; internal children
+// go to consecutive node indices in slot order and the leaf children's triangles to
+// consecutive triangle slots.
+struct CwCollapser {
+    const std::vector<BNode>& bn;
+    const std::vector<uint32_t>& perm;
+    const float* tris;               // input triangles [T][3][3]
+    float pad;                       // absolute growth of every child box
+    std::vector<BvhNode>& nodes;
+    std::vector<float4>& otris;      // triangles in node order, 3 float4 each
+    int max_depth = 0;
+    int64_t leaves = 0;
+    uint32_t max_leaf = 0;
+
+    static void put_byte(float4& v, int word, int byte, uint32_t val) {
+        unsigned char* b = reinterpret_cast<unsigned char*>(&v);
+        b[4 * word + byte] = (unsigned char)(val & 0xFFu);   // little-endian word layout
+    }
+    static void put_word(float4& v, int word, uint32_t val) {
+        std::memcpy(reinterpret_cast<unsigned char*>(&v) + 4 * word, &val, 4);
+    }
+
+    void append_tri(uint32_t id) {
+        const float* v = tris + 9 * (int64_t)id;
+        float idf;
+        std::memcpy(&idf, &id, sizeof(idf));
+        otris.push_back(make_float4(v[0], v[1], v[2], idf));
+        otris.push_back(make_float4(v[3], v[4], v[5], 0.0f));
+        otris.push_back(make_float4(v[6], v[7], v[8], 0.0f));
+    }
+
+    // Fills node `me` for binary node b (internal; or a leaf standing alone as the root).
+    void fill(uint32_t me, int32_t b, int depth) {
+        max_depth = std::max(max_depth, depth);
+        std::vector<int32_t> kids;
+        if (bn[b].left < 0) {
+            kids.push_back(b);
+        } else {
+            kids = {bn[b].left, bn[b].right};
+            while ((int)kids.size() < 8) {
+                int pick = -1;
+                float best = -1.0f;
+                for (int i = 0; i < (int)kids.size(); ++i) {
+                    const BNode& c = bn[kids[i]];
+                    if (c.left < 0) continue;
+                    const float a = c.box.area();
+                    if (a > best) {
+                        best = a;
+                        pick = i;
+                    }
+                }
+                if (pick < 0) break;
+                const int32_t open = kids[pick];
+                kids[pick] = bn[open].left;
+                kids.push_back(bn[open].right);
+            }
+        }
+        // the node's grid covers the padded children, one step of margin on each side
+        AABB box;
+        for (int32_t k : kids) box.grow(bn[k].box);
+        float lo[3], hi[3], step[3];
+        uint32_t ebits[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = box.lo[a] - pad;
+            hi[a] = box.hi[a] + pad;
+            const double ext = (double)hi[a] - (double)lo[a];
+            int e = -126;
+            while (e < 126 && std::ldexp(1.0, e) * 252.0 < ext) ++e;   // ext + 3 steps <= 255 steps
+            step[a] = (float)std::ldexp(1.0, e);
+            ebits[a] = (uint32_t)(e + 127);
+            lo[a] = (float)((double)lo[a] - (double)step[a]);   // one step below the padded box
+        }
+        // slot assignment: greedy by distance into each octant's corner
+        const int n = (int)kids.size();
+        float pc[3];
+        for (int a = 0; a < 3; ++a) pc[a] = 0.5f * (box.lo[a] + box.hi[a]);
+        int slot_of[8], kid_in[8];
+        for (int s = 0; s < 8; ++s) kid_in[s] = -1;
+        std::vector<bool> placed(n, false);
+        for (int round = 0; round < n; ++round) {
+            float best = std::numeric_limits<float>::infinity();
+            int bk = -1, bs = -1;
+            for (int k = 0; k < n; ++k) {
+                if (placed[k]) continue;
+                const AABB& cb = bn[kids[k]].box;
+                for (int s = 0; s < 8; ++s) {
+                    if (kid_in[s] >= 0) continue;
+                    float cost = 0.0f;
+                    for (int a = 0; a < 3; ++a) {
+                        const float d = 0.5f * (cb.lo[a] + cb.hi[a]) - pc[a];
+                        cost += ((s >> a) & 1) ? -d : d;
+                    }
+                    if (cost < best) {
+                        best = cost;
+                        bk = k;
+                        bs = s;
+                    }
+                }
+            }
+            placed[bk] = true;
+            kid_in[bs] = bk;
+            slot_of[bk] = bs;
+        }
+        (void)slot_of;
+        // internal children in slot order, then the node's own fields
+        uint32_t imask = 0, n_int = 0;
+        for (int s = 0; s < 8; ++s)
+            if (kid_in[s] >= 0 && bn[kids[kid_in[s]]].left >= 0) {
+                imask |= 1u << s;
+                ++n_int;
+            }
+        const uint32_t child_base = (uint32_t)nodes.size();
+        nodes.resize(nodes.size() + n_int);
+        const uint32_t tri_base = (uint32_t)(otris.size() / 3);
+        BvhNode node;
+        std::memset(&node, 0, sizeof(node));
+        node.v[0] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+        put_word(node.v[0], 3, ebits[0] | (ebits[1] << 8) | (ebits[2] << 16) | (imask << 24));
+        put_word(node.v[1], 0, child_base);
+        put_word(node.v[1], 1, tri_base);
+        uint32_t tri_off = 0;
+        for (int s = 0; s < 8; ++s) {
+            uint32_t meta = 0, ql[3] = {255, 255, 255}, qh[3] = {0, 0, 0};
+            if (kid_in[s] >= 0) {
+                const BNode& c = bn[kids[kid_in[s]]];
+                if (c.left >= 0) {
+                    meta = 0x20u | (24u + (uint32_t)s);
+                } else {
+                    meta = (((1u << c.count) - 1u) << 5) | tri_off;
+                    for (uint32_t i = 0; i < c.count; ++i) append_tri(perm[c.first + i]);
+                    tri_off += c.count;
+                    ++leaves;
+                    max_leaf = std::max(max_leaf, c.count);
+                }
+                for (int a = 0; a < 3; ++a) {
+                    // conservative grid cells of the padded child box, widened by one more step
+                    const double l = ((double)c.box.lo[a] - pad - lo[a]) / step[a];
+                    const double h = ((double)c.box.hi[a] + pad - lo[a]) / step[a];
+                    ql[a] = (uint32_t)std::max(0.0, std::floor(l) - 1.0);
+                    qh[a] = (uint32_t)std::min(255.0, std::ceil(h) + 1.0);
+                }
+            }
+            put_byte(node.v[1], 2 + s / 4, s % 4, meta);
+            put_byte(node.v[2], s / 4, s % 4, ql[0]);
+            put_byte(node.v[2], 2 + s / 4, s % 4, ql[1]);
+            put_byte(node.v[3], s / 4, s % 4, ql[2]);
+            put_byte(node.v[3], 2 + s / 4, s % 4, qh[0]);
+            put_byte(node.v[4], s / 4, s % 4, qh[1]);
+            put_byte(node.v[4], 2 + s / 4, s % 4, qh[2]);
+        }
+        nodes[me] = node;
+        uint32_t next = child_base;
+        for (int s = 0; s < 8; ++s)
+            if ((imask >> s) & 1u) fill(next++, kids[kid_in[s]], depth + 1);
+    }
+};
+#endif  // OCC_BVH_CW8
+
 }  // namespace
 
 bool build_bvh4(const float* tris, int64_t T, HostBVH* out, std::string* err) {
@@ -300,6 +467,7 @@ bool build_bvh4(const float* tris, int64_t T, HostBVH* out, std::string* err) {
     std::vector<BNode> bn;
     bn.reserve((size_t)(2 * T));
     Builder b{tb, tc, perm};
+    if (OCC_BVH_CW8) b.leaf_max = kCwMaxLeafTris;
     const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
     int spawn = 0;
     while ((1u << spawn) < hw && spawn < 6) ++spawn;
@@ -312,6 +480,21 @@ bool build_bvh4(const float* tris, int64_t T, HostBVH* out, std::string* err) {
     float mag = 1.0f;
     for (int64_t i = 0; i < 9 * T; ++i) mag = std::max(mag, std::fabs(tris[i]));
     out->nodes.clear();
+#if OCC_BVH_CW8
+    out->tris.clear();
+    out->tris.reserve((size_t)(3 * T));
+    CwCollapser cw{bn, perm, tris, std::ldexp(mag, -17), out->nodes, out->tris};
+    out->nodes.resize(1);
+    cw.fill(0, 0, 0);
+    if (cw.max_depth + 1 > kStackSize) {
+        *err = "BVH too deep for the traversal stack";
+        return false;
+    }
+    out->num_leaves = cw.leaves;
+    out->depth = cw.max_depth + 1;
+    out->max_leaf_tris = (int)cw.max_leaf;
+    return true;
+#else
     Collapser col{bn, out->nodes, std::ldexp(mag, -17)};
     if (bn[0].left < 0) {
         // the whole scene is one leaf: a root node with that single child
@@ -347,6 +530,7 @@ bool build_bvh4(const float* tris, int64_t T, HostBVH* out, std::string* err) {
     out->depth = col.max_depth + 1;
     out->max_leaf_tris = (int)col.max_leaf;
     return true;
+#endif
 }
 
 }  // namespace occ

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS)
     const RectLight L{};
     Traversal t;
     StackEntry stack[kStackSize];
-    t.cur = t.leaf = kEmptyRef;
+    trav_clear(t);
     t.overflow = false;
     t.bad = false;
     bool active = false, tracing = false, exhausted = false, overflow = false, bad = false;

@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(128, 8)
     const int gw = a.pat.gw, gh = a.pat.gh, W = a.gb.W;
     Traversal t;
     StackEntry stack[kStackSize];
-    t.cur = t.leaf = kEmptyRef;
+    trav_clear(t);
     t.overflow = false;
     t.bad = false;
     bool have = false, exhausted = false, overflow = false, bad = false;

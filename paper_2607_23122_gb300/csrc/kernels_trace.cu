@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
     const unsigned below = (1u << lane) - 1u;
     Traversal t;
     StackEntry stack[kStackSize];
-    t.cur = t.leaf = kEmptyRef;
+    trav_clear(t);
     t.overflow = false;
     t.bad = false;
     bool have = false, exhausted = false, overflow = false, bad = false;

@@ -326,6 +326,37 @@ struct Hit {
     float t;
 };
 
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Instrumented build (OCC_COUNTERS): a visit of node n / a test of triangle slot s.
+__device__ __forceinline__ void count_node(const DevBVH& bvh, uint32_t n) {
+#if OCC_COUNTERS
+    if (bvh.ctr) {
+        atomicAdd(bvh.ctr + 0, 1ull);
+        atomicOr(bvh.node_bits + (n >> 5), 1u << (n & 31u));
+    }
+#endif
+}
+__device__ __forceinline__ void count_tri(const DevBVH& bvh, uint32_t s) {
+#if OCC_COUNTERS
+    if (bvh.ctr) {
+        atomicAdd(bvh.ctr + 1, 1ull);
+        atomicOr(bvh.tri_bits + (s >> 5), 1u << (s & 31u));
+    }
+#endif
+}
+
+#if !OCC_BVH_CW8
 // Traversal stack entries: the node reference alone (4 bytes; a popped node beyond the
 // current best hit is culled by its own box test), or with its entry distance so that it
 // is skipped without the fetch (OCC_STACK_KEYS=1, 8 bytes).  Measured at 1080p: equal for
@@ -348,18 +379,6 @@ __device__ __forceinline__ StackEntry stack_entry(uint32_t ref, float) { return 
 __device__ __forceinline__ uint32_t entry_ref(StackEntry e) { return e; }
 __device__ __forceinline__ bool entry_live(StackEntry, float) { return true; }
 #endif
-
-__device__ __forceinline__ float max3f(float a, float b, float c) {
-    float d;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-    return d;
-}
-
-__device__ __forceinline__ float min3f(float a, float b, float c) {
-    float d;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-    return d;
-}
 
 // Child reference of slot s (0..3) of a node's reference quad.
 __device__ __forceinline__ uint32_t child_of(uint4 ch, uint32_t s) {
@@ -503,24 +522,6 @@ __device__ __forceinline__ uint32_t pop_next(const StackEntry* stack, int& sp, f
 
 __device__ __forceinline__ bool is_leaf_ref(uint32_t ref) { return (ref & kLeafBit) != 0u; }
 
-// Instrumented build (OCC_COUNTERS): a visit of node n / a test of triangle slot s.
-__device__ __forceinline__ void count_node(const DevBVH& bvh, uint32_t n) {
-#if OCC_COUNTERS
-    if (bvh.ctr) {
-        atomicAdd(bvh.ctr + 0, 1ull);
-        atomicOr(bvh.node_bits + (n >> 5), 1u << (n & 31u));
-    }
-#endif
-}
-__device__ __forceinline__ void count_tri(const DevBVH& bvh, uint32_t s) {
-#if OCC_COUNTERS
-    if (bvh.ctr) {
-        atomicAdd(bvh.ctr + 1, 1ull);
-        atomicOr(bvh.tri_bits + (s >> 5), 1u << (s & 31u));
-    }
-#endif
-}
-
 // Resumable closest-hit traversal of one ray on (0, tmax] (t in units of |d|).  While-while
 // order: each round walks internal nodes until every active lane of the warp holds a
 // postponed leaf, then all lanes test their leaves together, which keeps the lanes on the
@@ -552,6 +553,14 @@ __device__ __forceinline__ void trav_init(Traversal& t, float3 o, float3 d, floa
         t.leaf = t.cur;
         t.cur = kEmptyRef;
     }
+}
+
+// A traversal with no ray (trav_done is true).
+__device__ __forceinline__ void trav_clear(Traversal& t) {
+    t.cur = t.leaf = kEmptyRef;
+    t.sp = 0;
+    t.overflow = false;
+    t.bad = false;
 }
 
 __device__ __forceinline__ bool trav_done(const Traversal& t) {
@@ -613,6 +622,190 @@ __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, Stac
     }
 }
 
+#else  // OCC_BVH_CW8
+// ---------------------------------------------------------------------------------------
+// Traversal of the compressed 8-wide layout (occ_layout.h).  Per ray the octant (bit a set
+// for a negative direction component) orders the children: a node's hit internal children
+// become bits 24 + (slot ^ octant) of a node group (child base index, bits | imask), visited
+// lowest bit first, and its hit leaf children's triangles bits of a triangle group (triangle
+// base index, bits 0..23).  The stack holds node groups, one entry per level at most.
+// While-while order: a lane walks nodes until it holds a triangle group (or ran out), then
+// the lanes test their triangles together.
+// ---------------------------------------------------------------------------------------
+using StackEntry = uint2;
+
+struct Traversal {
+    TraceRay r;
+    float tbest;
+    uint32_t best_id, best_slot;
+    uint2 ng;               // node group: (child base, hit bits 24..31 | imask bits 0..7)
+    uint2 tg;               // triangle group: (triangle base, hit bits 0..23)
+    uint32_t oct;           // ray octant
+    int sp;
+    bool overflow;
+    bool bad;               // OCC_CHECKS: an index outside the BVH was met
+};
+
+__device__ __forceinline__ void trav_clear(Traversal& t) {
+    t.ng = make_uint2(0u, 0u);
+    t.tg = make_uint2(0u, 0u);
+    t.sp = 0;
+    t.overflow = false;
+    t.bad = false;
+}
+
+// Starts at the root (`start` = kEmptyRef: no triangle can be met, nothing to do).
+__device__ __forceinline__ void trav_init(Traversal& t, float3 o, float3 d, float tmax,
+                                          uint32_t start) {
+    t.r = make_trace_ray(o, d);
+    t.tbest = tmax;
+    t.best_id = kNoHit;
+    t.best_slot = kNoHit;
+    trav_clear(t);
+    t.oct = t.r.nsel;
+    // the root as slot 0 of a one-child group based at node 0
+    if (start != kEmptyRef) t.ng = make_uint2(0u, (1u << (24u + t.oct)) | 1u);
+}
+
+__device__ __forceinline__ bool trav_done(const Traversal& t) {
+    return (t.ng.y >> 24) == 0u && t.tg.y == 0u && t.sp == 0;
+}
+
+// Byte b (0..3) of w as the float 2^23 + byte (one byte permutation).
+__device__ __forceinline__ float byte_f(uint32_t w, uint32_t b) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | b));
+}
+
+// Node visit: slab tests of the 8 children (two per paired FMA), then the groups of the hit
+// children.  Plane distance of grid value q on axis a: (p_a + q 2^e_a - o_a) / d_a, taken
+// as one FMA of the biased byte value f = 2^23 + q: f (2^e_a / d_a) + (p_a - o_a) / d_a
+// - 2^23 (2^e_a / d_a); the rounding of the last term is below half a grid step, which the
+// builder's extra step of margin on every side absorbs.
+__device__ __forceinline__ void visit_cw(const DevBVH& bvh, uint32_t node, const TraceRay& r,
+                                         float tbest, uint32_t oct, uint2* ng, uint2* tg) {
+    const float4* nb = reinterpret_cast<const float4*>(bvh.nodes) + 5ull * node;
+    const float4 v0 = __ldg(nb), v1 = __ldg(nb + 1), v2 = __ldg(nb + 2), v3 = __ldg(nb + 3),
+                 v4 = __ldg(nb + 4);
+    const uint32_t eb = __float_as_uint(v0.w);
+    const float sx = __uint_as_float((eb & 0xFFu) << 23) * r.idir.x;
+    const float sy = __uint_as_float(((eb >> 8) & 0xFFu) << 23) * r.idir.y;
+    const float sz = __uint_as_float(((eb >> 16) & 0xFFu) << 23) * r.idir.z;
+    const float cx = fmaf(-8388608.0f, sx, (v0.x - r.o.x) * r.idir.x);
+    const float cy = fmaf(-8388608.0f, sy, (v0.y - r.o.y) * r.idir.y);
+    const float cz = fmaf(-8388608.0f, sz, (v0.z - r.o.z) * r.idir.z);
+    // near / far plane words (children 0-3, 4-7) per axis: low planes for positive directions
+    const uint32_t lox0 = __float_as_uint(v2.x), lox1 = __float_as_uint(v2.y);
+    const uint32_t loy0 = __float_as_uint(v2.z), loy1 = __float_as_uint(v2.w);
+    const uint32_t loz0 = __float_as_uint(v3.x), loz1 = __float_as_uint(v3.y);
+    const uint32_t hix0 = __float_as_uint(v3.z), hix1 = __float_as_uint(v3.w);
+    const uint32_t hiy0 = __float_as_uint(v4.x), hiy1 = __float_as_uint(v4.y);
+    const uint32_t hiz0 = __float_as_uint(v4.z), hiz1 = __float_as_uint(v4.w);
+    const bool nx = oct & 1u, ny = oct & 2u, nz = oct & 4u;
+    const uint32_t nxw[2] = {nx ? hix0 : lox0, nx ? hix1 : lox1}, fxw[2] = {nx ? lox0 : hix0, nx ? lox1 : hix1};
+    const uint32_t nyw[2] = {ny ? hiy0 : loy0, ny ? hiy1 : loy1}, fyw[2] = {ny ? loy0 : hiy0, ny ? loy1 : hiy1};
+    const uint32_t nzw[2] = {nz ? hiz0 : loz0, nz ? hiz1 : loz1}, fzw[2] = {nz ? loz0 : hiz0, nz ? loz1 : hiz1};
+    const f32x2 sx2 = bc2(sx), sy2 = bc2(sy), sz2 = bc2(sz), cx2 = bc2(cx), cy2 = bc2(cy), cz2 = bc2(cz);
+    const uint32_t imask = eb >> 24;
+    const uint32_t meta[2] = {__float_as_uint(v1.z), __float_as_uint(v1.w)};
+    uint32_t bits = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c += 2) {
+        const int h = c >> 2;
+        const uint32_t b0 = (uint32_t)(c & 3), b1 = b0 + 1u;
+        const float2 tnx = up2(fma2(pk2(byte_f(nxw[h], b0), byte_f(nxw[h], b1)), sx2, cx2));
+        const float2 tny = up2(fma2(pk2(byte_f(nyw[h], b0), byte_f(nyw[h], b1)), sy2, cy2));
+        const float2 tnz = up2(fma2(pk2(byte_f(nzw[h], b0), byte_f(nzw[h], b1)), sz2, cz2));
+        const float2 tfx = up2(fma2(pk2(byte_f(fxw[h], b0), byte_f(fxw[h], b1)), sx2, cx2));
+        const float2 tfy = up2(fma2(pk2(byte_f(fyw[h], b0), byte_f(fyw[h], b1)), sy2, cy2));
+        const float2 tfz = up2(fma2(pk2(byte_f(fzw[h], b0), byte_f(fzw[h], b1)), sz2, cz2));
+        const float tn0 = max3f(tnx.x, tny.x, fmaxf(tnz.x, 0.0f));
+        const float tn1 = max3f(tnx.y, tny.y, fmaxf(tnz.y, 0.0f));
+        const float tf0 = min3f(tfx.x, tfy.x, fminf(tfz.x, tbest));
+        const float tf1 = min3f(tfx.y, tfy.y, fminf(tfz.y, tbest));
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int s = c + e;
+            const uint32_t m = (meta[h] >> (8 * (s & 3))) & 0xFFu;
+            // internal child: one bit at 24 + (slot ^ octant); leaf: its triangles' bits
+            const uint32_t idx = (m & 31u) ^ (((imask >> s) & 1u) ? oct : 0u);
+            const bool hit = (e == 0 ? tn0 <= tf0 : tn1 <= tf1);
+            if (hit) bits |= (m >> 5) << idx;
+        }
+    }
+    *ng = make_uint2(__float_as_uint(v1.x), (bits & 0xFF000000u) | imask);
+    *tg = make_uint2(__float_as_uint(v1.y), bits & 0x00FFFFFFu);
+}
+
+// One round: lanes walk node groups while some lane can; a lane that holds triangles waits
+// for the round's triangle phase, unless under a fifth of the active lanes hold triangles:
+// then it pushes its triangle group (a stack entry with no node bits) and walks on, so the
+// warp's triangle tests are batched (triangle postponing, after Ylitie et al.).  ANY: stop
+// at the first triangle accepted on (0, tmax].
+#ifndef OCC_CW_POSTPONE_FIFTHS
+#define OCC_CW_POSTPONE_FIFTHS 1
+#endif
+template <bool ANY = false, bool PAIRED = true>
+__device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, StackEntry* stack) {
+    for (;;) {
+        const unsigned act = __activemask();
+        const bool can_walk = (t.ng.y >> 24) != 0u || t.sp > 0;
+        const unsigned tri_lanes = __ballot_sync(act, t.tg.y != 0u);
+        if (t.tg.y != 0u && can_walk && __popc(tri_lanes) * 5 < __popc(act) * OCC_CW_POSTPONE_FIFTHS) {
+            if (t.sp < kStackSize) {
+                stack[t.sp++] = t.tg;      // (triangle base, bits 0..23): no node bits
+                t.tg.y = 0u;
+            }
+        }
+        const bool walk = t.tg.y == 0u && can_walk;
+        if (!__any_sync(act, walk)) break;
+        if (!walk) continue;
+        if ((t.ng.y >> 24) == 0u) {
+            const uint2 e = stack[--t.sp];
+            if (e.y >> 24) t.ng = e;       // a node group
+            else t.tg = e;                 // a postponed triangle group
+            continue;
+        }
+        const uint32_t b = (uint32_t)__ffs(t.ng.y >> 24) - 1u;
+        t.ng.y &= ~(1u << (24u + b));
+        const uint32_t slot = b ^ t.oct;
+        const uint32_t node = t.ng.x + (uint32_t)__popc(t.ng.y & 0xFFu & ((1u << slot) - 1u));
+        if (t.ng.y >> 24) {
+            if (t.sp < kStackSize) stack[t.sp++] = t.ng;
+            else t.overflow = true;
+        }
+#if OCC_CHECKS
+        if (node >= bvh.n_nodes) {
+            t.bad = true;
+            trav_clear(t);
+            return;
+        }
+#endif
+        count_node(bvh, node);
+        visit_cw(bvh, node, t.r, t.tbest, t.oct, &t.ng, &t.tg);
+    }
+    while (t.tg.y) {
+        const uint32_t i = t.tg.x + (uint32_t)__ffs(t.tg.y) - 1u;
+        t.tg.y &= t.tg.y - 1u;
+#if OCC_CHECKS
+        if (i >= bvh.n_tris) {
+            t.bad = true;
+            trav_clear(t);
+            return;
+        }
+#endif
+        count_tri(bvh, i);
+        const float4* tr = bvh.tris + 3ull * i;
+        triangle_test(t.r, __ldg(tr), __ldg(tr + 1), __ldg(tr + 2), i, t.tbest, t.best_id,
+                      t.best_slot);
+        if (ANY && t.best_id != kNoHit) {
+            trav_clear(t);
+            return;
+        }
+    }
+}
+
+#endif  // OCC_BVH_CW8
+
 // Closest hit on (0, tmax] from `start` (see trav_init).  Sets kStatusStackOverflowBit in
 // *status if the short stack would overflow (the builder bounds the tree depth so that it
 // cannot).
@@ -649,6 +842,9 @@ __device__ __forceinline__ bool any_hit(const DevBVH& bvh, float3 o, float3 d, f
 // do not reach the query box); kEmptyRef means no triangle can be met.  Uniform across
 // the calling threads when the query box is.
 __device__ __forceinline__ uint32_t start_node(const DevBVH& bvh, float3 qlo, float3 qhi) {
+#if OCC_BVH_CW8
+    return 0u;   // compressed nodes: every ray starts at the root
+#else
     uint32_t cur = 0;
     for (int level = 0; level < kStackSize; ++level) {
         count_node(bvh, cur);
@@ -680,6 +876,7 @@ __device__ __forceinline__ uint32_t start_node(const DevBVH& bvh, float3 qlo, fl
         cur = only;
     }
     return cur;
+#endif
 }
 
 // Unit geometric normal of BVH triangle `slot`, turned against direction d.

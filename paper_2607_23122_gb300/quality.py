@@ -31,6 +31,23 @@ def relmse(est: np.ndarray, ref: np.ndarray, valid: np.ndarray, eps: float = REL
     return float(np.mean(e * e / (ref.astype(np.float64)[valid] ** 2 + eps)))
 
 
+def region_errors(est: np.ndarray, ref: np.ndarray, valid: np.ndarray,
+                  eps: float = RELMSE_EPS) -> dict:
+    """Errors by region of the reference: umbra (reference 0: every reference sample blocked),
+    penumbra, lit (reference 1).  Per region: pixel count, MSE, share of the image's summed
+    relative squared error, and mean error."""
+    r = ref.astype(np.float64)[valid]
+    e = est.astype(np.float64)[valid] - r
+    rel = e * e / (r * r + eps)
+    out = {}
+    for name, m in (("umbra", r == 0.0), ("penumbra", (r > 0.0) & (r < 1.0)), ("lit", r == 1.0)):
+        n = int(m.sum())
+        out[name] = {"pixels": n, "mse": float(np.mean(e[m] * e[m])) if n else 0.0,
+                     "relmse_share": float(rel[m].sum() / max(rel.sum(), 1e-300)),
+                     "bias": float(np.mean(e[m])) if n else 0.0}
+    return out
+
+
 def _trace(ctx, gb, bvh, effect, radius, light, seed, sample, rec, stream=None):
     if effect == O.OCC_EFFECT_AO:
         return O.occ_trace_ao(ctx, gb, bvh, radius, seed, sample, out=rec, stream=stream)
@@ -116,7 +133,8 @@ def equal_time(ctx, gb, bvh, effect, budget_ms, ref, radius=0.5, light=None, ext
         img = estimate(ctx, gb, bvh, effect, pat, est, frames, radius, light)
         e = img[valid].astype(np.float64) - ref[valid]
         rows[name] = {"frame_ms": t, "frames": frames, "relmse": relmse(img, ref, valid),
-                      "mse": float(np.mean(e * e)), "bias": float(np.mean(e))}
+                      "mse": float(np.mean(e * e)), "bias": float(np.mean(e)),
+                      "bins": region_errors(img, ref, valid)}
     base = rows["NoReuse"]["relmse"]
     for r in rows.values():
         r["ratio_to_noreuse"] = r["relmse"] / base if base > 0 else float("nan")
