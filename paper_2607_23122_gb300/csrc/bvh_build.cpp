@@ -486,6 +486,7 @@ bool build_bvh4(const float* tris, int64_t T, HostBVH* out, std::string* err) {
     CwCollapser cw{bn, perm, tris, std::ldexp(mag, -17), out->nodes, out->tris};
     out->nodes.resize(1);
     cw.fill(0, 0, 0);
+    // one stack entry (node group) per level
     if (cw.max_depth + 1 > kStackSize) {
         *err = "BVH too deep for the traversal stack";
         return false;

@@ -736,52 +736,38 @@ __device__ __forceinline__ void visit_cw(const DevBVH& bvh, uint32_t node, const
     *tg = make_uint2(__float_as_uint(v1.y), bits & 0x00FFFFFFu);
 }
 
-// One round: lanes walk node groups while some lane can; a lane that holds triangles waits
-// for the round's triangle phase, unless under a fifth of the active lanes hold triangles:
-// then it pushes its triangle group (a stack entry with no node bits) and walks on, so the
-// warp's triangle tests are batched (triangle postponing, after Ylitie et al.).  ANY: stop
-// at the first triangle accepted on (0, tmax].
-#ifndef OCC_CW_POSTPONE_FIFTHS
-#define OCC_CW_POSTPONE_FIFTHS 1
-#endif
+// One round: node groups until this lane holds triangles (or ran out) while any active lane
+// still walks, then the triangles.  Every step of a walking lane consumes a child bit or a
+// stack entry, so the node loop ends.  (Postponing a lane's triangles onto the stack while
+// few lanes hold some, as Ylitie et al. do, did not raise lane use in a lockstep CPU
+// emulation of this loop: 24-26 % either way on incoherent rays.)  ANY: stop at the first
+// triangle accepted on (0, tmax].
 template <bool ANY = false, bool PAIRED = true>
 __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, StackEntry* stack) {
-    for (;;) {
-        const unsigned act = __activemask();
-        const bool can_walk = (t.ng.y >> 24) != 0u || t.sp > 0;
-        const unsigned tri_lanes = __ballot_sync(act, t.tg.y != 0u);
-        if (t.tg.y != 0u && can_walk && __popc(tri_lanes) * 5 < __popc(act) * OCC_CW_POSTPONE_FIFTHS) {
-            if (t.sp < kStackSize) {
-                stack[t.sp++] = t.tg;      // (triangle base, bits 0..23): no node bits
-                t.tg.y = 0u;
-            }
-        }
-        const bool walk = t.tg.y == 0u && can_walk;
-        if (!__any_sync(act, walk)) break;
-        if (!walk) continue;
+    while (t.tg.y == 0u) {
         if ((t.ng.y >> 24) == 0u) {
-            const uint2 e = stack[--t.sp];
-            if (e.y >> 24) t.ng = e;       // a node group
-            else t.tg = e;                 // a postponed triangle group
-            continue;
-        }
-        const uint32_t b = (uint32_t)__ffs(t.ng.y >> 24) - 1u;
-        t.ng.y &= ~(1u << (24u + b));
-        const uint32_t slot = b ^ t.oct;
-        const uint32_t node = t.ng.x + (uint32_t)__popc(t.ng.y & 0xFFu & ((1u << slot) - 1u));
-        if (t.ng.y >> 24) {
-            if (t.sp < kStackSize) stack[t.sp++] = t.ng;
-            else t.overflow = true;
-        }
+            if (t.sp == 0) break;
+            t.ng = stack[--t.sp];
+        } else {
+            const uint32_t b = (uint32_t)__ffs(t.ng.y >> 24) - 1u;
+            t.ng.y &= ~(1u << (24u + b));
+            const uint32_t slot = b ^ t.oct;
+            const uint32_t node = t.ng.x + (uint32_t)__popc(t.ng.y & 0xFFu & ((1u << slot) - 1u));
+            if (t.ng.y >> 24) {
+                if (t.sp < kStackSize) stack[t.sp++] = t.ng;
+                else t.overflow = true;
+            }
 #if OCC_CHECKS
-        if (node >= bvh.n_nodes) {
-            t.bad = true;
-            trav_clear(t);
-            return;
-        }
+            if (node >= bvh.n_nodes) {
+                t.bad = true;
+                trav_clear(t);
+                return;
+            }
 #endif
-        count_node(bvh, node);
-        visit_cw(bvh, node, t.r, t.tbest, t.oct, &t.ng, &t.tg);
+            count_node(bvh, node);
+            visit_cw(bvh, node, t.r, t.tbest, t.oct, &t.ng, &t.tg);
+        }
+        if (!__any_sync(__activemask(), t.tg.y == 0u && !trav_done(t))) break;
     }
     while (t.tg.y) {
         const uint32_t i = t.tg.x + (uint32_t)__ffs(t.tg.y) - 1u;
