@@ -753,6 +753,14 @@ def run_ours(args):
         # the same loads and stores with no arithmetic: what the kernel's bytes cost alone
         extra["reuse_group4x2"]["stream_ceiling"] = time_kernel(
             lambda st: occ.occ_debug_stream_ceiling(ctx, gb, rec, out, stream=st), flush, stream, 200)
+        # the trace's launch choices on this frame (autotuner candidates, bit-identical records)
+        from paper_2607_23122_gb300 import autotune
+        tt = autotune.tune_trace(ctx, gb, bvh, occ.OCC_EFFECT_AO, rec, radius=RADIUS, iters=10,
+                                 use_cache=False)
+        occ.occ_set_tuning(ctx)
+        extra["trace_tuning"] = {"best": tt["best"],
+                                 "ms": {json.dumps(t["config"], sort_keys=True): t["ms"]
+                                        for t in tt["timings"]}}
         extra["shadow"] = shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream)
         extra["packed"] = packed_frame(occ, ctx, gb, bvh, pat, out, flush, stream)
         extra["fused"] = fused_frame(occ, ctx, gb, bvh, rec, out, flush, stream)
@@ -834,6 +842,7 @@ def run_ours(args):
                                    achieved_gbs=P * GROUP_BYTES_PER_PX / extra["reuse_group4x2"]["s"] / 1e9,
                                    frac_hbm=P * GROUP_BYTES_PER_PX / extra["reuse_group4x2"]["s"] / 1e9 / hbm,
                                    neighbour_samples_per_s=P * 8 / extra["reuse_group4x2"]["s"]),
+            "trace_tuning_ao": extra["trace_tuning"],
             "shadow_frame": extra["shadow"],
             "packed_frame": dict(extra["packed"],
                                  group_frac_hbm=P * PACKED_GROUP_BYTES_PER_PX

@@ -341,6 +341,9 @@ typedef struct {
     int32_t trace_ctas_per_sm;   /* persistent trace: CTAs per SM (1 .. 16; 0 all that fit) */
     int32_t trace_refill;        /* persistent trace: a warp takes new rays once this many of its
                                     lanes are idle (1 .. 32; 0: 16) */
+    int32_t trace_order;         /* persistent trace: order in which rays are handed out by 16 x 8
+                                    tile: 1 tiles row-major, 2 blocks of 8 x 8 tiles row-major with
+                                    the tiles of a block in Morton order (0: row-major) */
 } occ_tuning;
 occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t);
 occ_status occ_get_tuning(const occ_ctx* ctx, occ_tuning* t);

@@ -60,7 +60,8 @@ class occ_tuning(C.Structure):
     _fields_ = [("reuse_tile_rows", c_int32), ("reuse_window_path", c_int32),
                 ("batch_ctas_per_sm", c_int32), ("fused_ao_path", c_int32),
                 ("group_prefetch", c_int32), ("trace_path", c_int32),
-                ("trace_ctas_per_sm", c_int32), ("trace_refill", c_int32)]
+                ("trace_ctas_per_sm", c_int32), ("trace_refill", c_int32),
+                ("trace_order", c_int32)]
 
 
 class occ_bvh_stats(C.Structure):

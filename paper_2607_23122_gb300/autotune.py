@@ -8,8 +8,8 @@ and stores it in a JSON cache so later runs apply it without measuring:
     receiver rows per tile, or the per-receiver kernel;
   * reuse of group patterns: the group kernel's L2 prefetch (none, G-buffer and records);
   * the step-1 trace: one CTA per 16 x 8 tile, or persistent CTAs taking rays from a
-    counter with a refill threshold of 8, 16 or 24 idle lanes and all or half of the CTAs
-    that fit;
+    counter with a refill threshold of 8, 16 or 24 idle lanes, all or half of the CTAs that
+    fit, and the rays handed out by tiles row-major or by 8 x 8-tile blocks in Morton order;
   * persistent batched kernels: CTAs per SM (1, 2, 4, 8 or all that fit).
 
 Cache: $OCC_TUNE_CACHE, else ~/.cache/occreuse/tuning.json.
@@ -33,7 +33,8 @@ REUSE_CANDIDATES = [
 ]
 GROUP_CANDIDATES = [{"group_prefetch": c} for c in (1, 2, 3)]
 TRACE_CANDIDATES = [{"trace_path": 1}] + [
-    {"trace_path": 2, "trace_refill": r, "trace_ctas_per_sm": c} for r in (8, 16, 24) for c in (0, 4)]
+    {"trace_path": 2, "trace_refill": r, "trace_ctas_per_sm": c, "trace_order": o}
+    for r in (8, 16, 24) for c in (0, 4) for o in (1, 2)]
 BATCH_CANDIDATES = [{"batch_ctas_per_sm": n} for n in (0, 1, 2, 4, 8)]
 
 
@@ -145,7 +146,7 @@ def tune_trace(ctx: O.Context, gb: O.GBuffer, bvh: O.BVH, effect: int, rec: O.Oc
 
     timings = []
     for cfg in TRACE_CANDIDATES:
-        full = {"trace_path": 0, "trace_refill": 0, "trace_ctas_per_sm": 0}
+        full = {"trace_path": 0, "trace_refill": 0, "trace_ctas_per_sm": 0, "trace_order": 0}
         full.update(cfg)
         _apply(ctx, full)
         timings.append({"config": full, "ms": _time(run, iters)})

@@ -92,18 +92,31 @@ __global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS) k_trace(GBufView gb
 #define OCC_TRACE_DYN_MIN_BLOCKS 7
 #endif
 
-__device__ __forceinline__ void index_pixel(uint32_t i, int tiles_x, int* x, int* y) {
+// Ray index i -> pixel: 128 rays per 16 x 8 tile (warp sub-tiles of 8 x 4).  order 0: tiles
+// row-major (tiles_x per row); order 1: blocks of 8 x 8 tiles row-major (tiles_x rounded up
+// to a multiple of 8), the tiles of a block in Morton order, so that the rays in flight cover
+// compact regions of the image.  Indices of tiles outside the image give x >= W or y >= H.
+__device__ __forceinline__ void index_pixel(uint32_t i, int tiles_x, int order, int* x, int* y) {
     const uint32_t tile = i >> 7, within = i & 127u;
     const uint32_t w = within >> 5, l = within & 31u;
-    *x = (int)(tile % (uint32_t)tiles_x) * kTileW + (int)(w & 1u) * 8 + (int)(l & 7u);
-    *y = (int)(tile / (uint32_t)tiles_x) * kTileH + (int)(w >> 1) * 4 + (int)(l >> 3);
+    uint32_t tx, ty;
+    if (order == 1) {
+        const uint32_t bx = ((uint32_t)tiles_x + 7u) >> 3, blk = tile >> 6, m = tile & 63u;
+        tx = (blk % bx) * 8u + ((m & 1u) | ((m >> 1) & 2u) | ((m >> 2) & 4u));
+        ty = (blk / bx) * 8u + (((m >> 1) & 1u) | ((m >> 2) & 2u) | ((m >> 3) & 4u));
+    } else {
+        tx = tile % (uint32_t)tiles_x;
+        ty = tile / (uint32_t)tiles_x;
+    }
+    *x = (int)tx * kTileW + (int)(w & 1u) * 8 + (int)(l & 7u);
+    *y = (int)ty * kTileH + (int)(w >> 1) * 4 + (int)(l >> 3);
 }
 
 template <int EFFECT>
 __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
     k_trace_dyn(GBufView gb, DevBVH bvh, float radius, LightParams lp, uint64_t seed,
                 uint32_t sample, RecView rec, unsigned* status, unsigned* counter, int tiles_x,
-                uint32_t n_idx, int min_idle) {
+                uint32_t n_idx, int min_idle, int order) {
     RectLight L;
     if (EFFECT == kShadow) L = make_light(lp);
     const int lane = threadIdx.x & 31;
@@ -132,7 +145,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
             if (!have) {
                 const uint32_t idx = base + (uint32_t)__popc(need & below);
                 int x, y;
-                index_pixel(idx, tiles_x, &x, &y);
+                index_pixel(idx, tiles_x, order, &x, &y);
                 if (idx < n_idx && x < gb.W && y < gb.H) {
                     p = (uint32_t)y * (uint32_t)gb.W + (uint32_t)x;
                     float3 xo = make_float3(0.0f, 0.0f, 0.0f), n = xo;
@@ -306,7 +319,9 @@ cudaError_t launch_trace(int effect, const GBufView& gb, const DevBVH& bvh, floa
     const int path = tune ? tune->trace_path : 0;
     const bool persistent = path == 2 || (path == 0 && effect == kAO);
     if (OCC_TRACE_DYN && counter && persistent) {
-        const uint32_t n_idx = grid.x * grid.y * 128u;
+        const int order = tune && tune->trace_order == 2 ? 1 : 0;
+        const uint32_t n_idx = order == 1 ? ((grid.x + 7u) / 8u) * ((grid.y + 7u) / 8u) * 64u * 128u
+                                          : grid.x * grid.y * 128u;
         // persistent grid: resident CTAs per SM x SMs (computed once; threads that race
         // here compute the same value)
         static std::atomic<int> ctas[2];
@@ -334,10 +349,11 @@ cudaError_t launch_trace(int effect, const GBufView& gb, const DevBVH& bvh, floa
         if (e != cudaSuccess) return e;
         if (effect == kAO)
             k_trace_dyn<kAO><<<blocks, 128, 0, s>>>(gb, bvh, radius, light, seed, sample, rec, status,
-                                                   counter, (int)grid.x, n_idx, min_idle);
+                                                   counter, (int)grid.x, n_idx, min_idle, order);
         else
             k_trace_dyn<kShadow><<<blocks, 128, 0, s>>>(gb, bvh, radius, light, seed, sample, rec,
-                                                       status, counter, (int)grid.x, n_idx, min_idle);
+                                                       status, counter, (int)grid.x, n_idx, min_idle,
+                                                       order);
         return cudaGetLastError();
     }
     if (effect == kAO)

@@ -1019,6 +1019,8 @@ OCC_EXPORT occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t) {
         return fail(ctx, OCC_ERR_INVALID_ARG, "trace_ctas_per_sm must be in [0, 16]");
     if (t->trace_refill < 0 || t->trace_refill > 32)
         return fail(ctx, OCC_ERR_INVALID_ARG, "trace_refill must be in [0, 32]");
+    if (t->trace_order < 0 || t->trace_order > 2)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "trace_order must be 0, 1 or 2");
     ctx->tune.tile_rows = t->reuse_tile_rows;
     ctx->tune.window_path = t->reuse_window_path;
     ctx->tune.batch_per_sm = t->batch_ctas_per_sm;
@@ -1027,6 +1029,7 @@ OCC_EXPORT occ_status occ_set_tuning(occ_ctx* ctx, const occ_tuning* t) {
     ctx->tune.trace_path = t->trace_path;
     ctx->tune.trace_ctas_per_sm = t->trace_ctas_per_sm;
     ctx->tune.trace_refill = t->trace_refill;
+    ctx->tune.trace_order = t->trace_order;
     return OCC_OK;
 }
 
@@ -1040,6 +1043,7 @@ OCC_EXPORT occ_status occ_get_tuning(const occ_ctx* ctx, occ_tuning* t) {
     t->trace_path = ctx->tune.trace_path;
     t->trace_ctas_per_sm = ctx->tune.trace_ctas_per_sm;
     t->trace_refill = ctx->tune.trace_refill;
+    t->trace_order = ctx->tune.trace_order;
     return OCC_OK;
 }
 

@@ -111,6 +111,7 @@ struct Tuning {
     int trace_path = 0;       // 0 default (AO persistent, shadow per tile), 1 per tile, 2 persistent
     int trace_ctas_per_sm = 0;   // persistent trace: CTAs per SM (0: all that fit)
     int trace_refill = 0;     // persistent trace: idle lanes that trigger a refill (0: default)
+    int trace_order = 0;      // persistent trace: 0 / 1 tiles row-major, 2 Morton blocks
 };
 
 // Workspace of the queued first-hit validation (unbiased group reuse): up to (K - 1) W H

@@ -615,9 +615,10 @@ class Batch:
 
 def occ_set_tuning(ctx: Context, reuse_tile_rows: int = 0, reuse_window_path: int = 0,
                    batch_ctas_per_sm: int = 0, fused_ao_path: int = 0, group_prefetch: int = 0,
-                   trace_path: int = 0, trace_ctas_per_sm: int = 0, trace_refill: int = 0):
+                   trace_path: int = 0, trace_ctas_per_sm: int = 0, trace_refill: int = 0,
+                   trace_order: int = 0):
     t = N.occ_tuning(reuse_tile_rows, reuse_window_path, batch_ctas_per_sm, fused_ao_path,
-                     group_prefetch, trace_path, trace_ctas_per_sm, trace_refill)
+                     group_prefetch, trace_path, trace_ctas_per_sm, trace_refill, trace_order)
     ctx.check(ctx.lib.occ_set_tuning(ctx.handle, C.byref(t)))
 
 

@@ -27,3 +27,4 @@ def test_candidates_are_valid_tuning_values():
     for c in autotune.TRACE_CANDIDATES:
         assert c["trace_path"] in (1, 2)
         assert 0 <= c.get("trace_refill", 0) <= 32 and 0 <= c.get("trace_ctas_per_sm", 0) <= 16
+        assert c.get("trace_order", 0) in (0, 1, 2)

@@ -258,6 +258,8 @@ def test_tuning_choices_match_oracle(orc, occ, ctx, c1, cfg, pname, effect):
 @pytest.mark.parametrize("cfg", [dict(trace_path=1), dict(trace_path=2),
                                  dict(trace_path=2, trace_refill=1, trace_ctas_per_sm=1),
                                  dict(trace_path=2, trace_refill=32, trace_ctas_per_sm=3),
+                                 dict(trace_path=2, trace_order=2),
+                                 dict(trace_path=2, trace_order=2, trace_refill=8),
                                  dict(group_prefetch=1), dict(group_prefetch=3)])
 @pytest.mark.parametrize("effect", [AO, SH])
 def test_trace_and_group_tuning_choices_are_bit_identical(occ, ctx, c1, cfg, effect):

@@ -58,7 +58,7 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(N.occ_sched_config) == 24
     assert ctypes.sizeof(N.occ_sched_stats) == 72
     assert ctypes.sizeof(N.occ_server_config) == 48
-    assert ctypes.sizeof(N.occ_tuning) == 32
+    assert ctypes.sizeof(N.occ_tuning) == 36
     # W H effect radius light(36) (pad) seed sample (pad) pattern(40) K estimator packed
     # camera(40) eps 4 pointers deadline
     assert ctypes.sizeof(N.occ_request) == 208
