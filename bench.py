@@ -271,15 +271,15 @@ def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
 GROUP_BYTES_PER_PX = 52   # x 12, n 12, z 12, n_z 12, out 4
 # DRAM bytes (read + write) per launch from one `ncu --set full` capture of
 # `bench.py --profile-step` (cold L2); None once a kernel changes
-NCU_TRAFFIC = {"k_trace_dyn<AO>": 72.457472e6 + 28.906496e6,
-               "k_reuse_tile<AO,8>": 132.794624e6 + 6.783488e6,
+NCU_TRAFFIC = {"k_trace_dyn<AO>": None,
+               "k_reuse_tile<AO,8>": None,
                "k_reuse_group<AO,biased,4,2>": 114.168832e6 + 4.530688e6}
-NCU_TRACE_ISSUE_ACTIVE = 0.6923   # smsp__issue_active of k_trace_dyn<AO> in its capture
-NCU_TRACE_WARP_INSTR = 300.359031e6   # smsp__inst_executed.sum of k_trace_dyn<AO>, same capture
+NCU_TRACE_ISSUE_ACTIVE = None   # smsp__issue_active of k_trace_dyn<AO> in its capture
+NCU_TRACE_WARP_INSTR = None   # smsp__inst_executed.sum of k_trace_dyn<AO>, same capture
 # What the 1080p AO trace (seed 1, sample 0) traverses, from the instrumented library:
 # OCC_LIB_VARIANT=counters python bench.py --count-touch
-TRACE_TOUCH = {"rays": 1409214, "node_visits": 22464463, "triangle_tests": 6760549,
-               "distinct_nodes": 49321, "distinct_triangles": 121469, "distinct_bytes": 12143600}
+TRACE_TOUCH = {"rays": 1409214, "node_visits": 22216647, "triangle_tests": 5323819,
+               "distinct_nodes": 53993, "distinct_triangles": 116401, "distinct_bytes": 12498352}
 
 
 def fp32_peak(occ, ctx, dev, stream) -> dict:
@@ -790,16 +790,18 @@ def run_ours(args):
         # its roofline is the warp-instruction issue rate (4 schedulers per SM, one warp
         # instruction per cycle each, at the max SM clock), with the byte roofline beside it
         issue_peak = sms * 4 * issue_mhz * 1e6
+        winstr = NCU_TRACE_WARP_INSTR
         trace_roof = {"kernel": "k_trace_dyn<AO>", "bound": "alu",
-                      "achieved": NCU_TRACE_WARP_INSTR / tr / 1e9, "peak": issue_peak / 1e9,
+                      "achieved": winstr / tr / 1e9 if winstr else None, "peak": issue_peak / 1e9,
                       "unit": "G warp-instructions/s",
-                      "frac": NCU_TRACE_WARP_INSTR / tr / issue_peak,
+                      "frac": winstr / tr / issue_peak if winstr else None,
                       "traffic": NCU_TRAFFIC["k_trace_dyn<AO>"],
                       "peak_source": f"{sms} SMs x 4 schedulers x 1 warp-instruction per cycle x "
                                      f"{issue_mhz:.0f} MHz max SM clock",
-                      "algorithmic": "warp instructions per launch (ncu smsp__inst_executed.sum "
-                                     f"{NCU_TRACE_WARP_INSTR:.4g}); issue slots "
-                                     f"{NCU_TRACE_ISSUE_ACTIVE:.0%} busy under ncu",
+                      "algorithmic": ("warp instructions per launch (ncu smsp__inst_executed.sum "
+                                      f"{winstr:.4g}); issue slots "
+                                      f"{NCU_TRACE_ISSUE_ACTIVE:.0%} busy under ncu") if winstr
+                                     else "warp instructions per launch: not captured for this build",
                       "hbm": {"algorithmic_bytes": trace_bytes, "achieved": trace_bytes / tr / 1e9,
                               "peak": hbm, "unit": "GB/s", "frac": trace_bytes / tr / 1e9 / hbm,
                               "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",

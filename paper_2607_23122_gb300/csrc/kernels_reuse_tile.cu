@@ -36,6 +36,35 @@ constexpr float kSupportSlackT = 1.0f + 1.0f / 65536.0f;
 #ifndef OCC_TILE_PAIRED
 #define OCC_TILE_PAIRED 1
 #endif
+// P_j of the paired column as a pairwise tree of paired adds (1) or a slot-order chain (0)
+#ifndef OCC_TILE_TREESUM
+#define OCC_TILE_TREESUM 0
+#endif
+// Two candidate columns per step of the paired loop (1) or one (0; 1080p AO 0.099 against
+// 0.103 ms with two)
+#ifndef OCC_TILE_CAND2
+#define OCC_TILE_CAND2 0
+#endif
+// MIS weight p_i / P_j with the approximate division __fdividef (1: a few ulp, far inside the
+// 1e-5 output tolerance; P_j >= p_i > 0 and P_j < 2^126 here) or the IEEE one (0).
+// 1080p, 8 disk offsets: AO 0.097 against 0.099 ms, shadows 0.127 against 0.130 ms.
+#ifndef OCC_TILE_FASTDIV
+#define OCC_TILE_FASTDIV 1
+#endif
+__device__ __forceinline__ float tile_ratio(float p, float P) {
+#if OCC_TILE_FASTDIV
+    return __fdividef(p, P);
+#else
+    return p / P;
+#endif
+}
+// One extra warp issues the bulk-tensor copies and the receiver warps release each staged
+// buffer on an mbarrier (1), instead of thread 0 issuing them between CTA-wide barriers (0):
+// a warp whose receivers had fewer candidates starts the next tile without waiting for the
+// slowest warp of the CTA (1080p, 8 disk offsets, AO: 0.099 against 0.110 ms).
+#ifndef OCC_TILE_WS
+#define OCC_TILE_WS 1
+#endif
 constexpr int kTileW = 32;
 constexpr uint32_t kWaitSpins = 1u << 24;
 
@@ -61,6 +90,15 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init_count(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -263,10 +301,8 @@ __device__ __forceinline__ void tile_single_x2(const TileArgs& a, const RectLigh
                 __float_as_int(reinterpret_cast<const float*>(st.r0 + sidx[c])[3]) >= 0)
                 hm |= 1u << c;
         const uint32_t blocked = hm;   // valid members whose record holds an occluder
-        float B = 0.0f;
-        while (hm) {
-            const int c = __ffs(hm) - 1;
-            hm &= hm - 1u;
+        // column of candidate slot c: the receiver's density (slot 0) and P_c
+        auto column = [&](int c, float* pi_out, float* psum_out) {
             const int q = sc + s_qoff[c];
             const float4 r0 = st.r0[q];
             float3 z, nz;
@@ -278,13 +314,53 @@ __device__ __forceinline__ void tile_single_x2(const TileArgs& a, const RectLigh
             for (int j = 0; j < NP; ++j)
                 d[j] = dens_x2_pairs<EFFECT>(zx, zy, zz, mnx, mny, mnz, px[j][0], px[j][1],
                                              px[j][2], pn[j][0], pn[j][1], pn[j][2], a.R2s, L);
-            // slot 0 is the receiver: its density is the numerator; P_j sums in slot order
+            // slot 0 is the receiver: its density is the numerator
             const float pi = d[0].x;
+#if OCC_TILE_TREESUM
+            // P_c as a pairwise tree on paired adds (depth log2 K instead of K - 1)
+            f32x2 s2[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) s2[j] = pk2(d[j].x, d[j].y);
+#pragma unroll
+            for (int w = NP / 2; w >= 1; w /= 2)
+#pragma unroll
+                for (int j = 0; j < w; ++j) s2[j] = add2(s2[j], s2[j + w]);
+            const float2 sp = up2(s2[0]);
+            const float Psum = sp.x + sp.y;
+#else
+            // P_c sums in slot order
             float Psum = pi + d[0].y;
 #pragma unroll
             for (int j = 1; j < NP; ++j) Psum = (Psum + d[j].x) + d[j].y;
-            if (pi > 0.0f) B += pi / Psum;
+#endif
+            *pi_out = pi;
+            *psum_out = Psum;
+        };
+        float B = 0.0f;
+#if OCC_TILE_CAND2
+        // two candidate columns per step (independent work for the scheduler); the terms
+        // are added in slot order as in the one-column loop
+        while (hm) {
+            const int c0 = __ffs(hm) - 1;
+            hm &= hm - 1u;
+            const bool two = hm != 0u;
+            const int c1 = two ? __ffs(hm) - 1 : c0;
+            hm &= hm - 1u;
+            float pi0, P0, pi1, P1;
+            column(c0, &pi0, &P0);
+            column(c1, &pi1, &P1);
+            if (pi0 > 0.0f) B += tile_ratio(pi0, P0);
+            if (two && pi1 > 0.0f) B += tile_ratio(pi1, P1);
         }
+#else
+        while (hm) {
+            const int c = __ffs(hm) - 1;
+            hm &= hm - 1u;
+            float pi, Psum;
+            column(c, &pi, &Psum);
+            if (pi > 0.0f) B += tile_ratio(pi, Psum);
+        }
+#endif
         res = 1.0f - B;
         if (EFFECT == kShadow && blocked == vmask) res = 0.0f;   // all-blocked guard
     }
@@ -331,7 +407,7 @@ __device__ __forceinline__ void tile_single(const TileArgs& a, const RectLight& 
             float Psum = pi;
 #pragma unroll
             for (int s = 1; s < MAXK; ++s) Psum += pair_density<EFFECT>(z, nz, rx[s], rt[s], a.R2s, L);
-            if (pi > 0.0f) B += pi / Psum;
+            if (pi > 0.0f) B += tile_ratio(pi, Psum);
         };
         // AO: the unrolled candidate loop keeps the member indices in registers (1080p,
         // 8 disk offsets: 0.129 against 0.134 ms rolled); shadows measured faster rolled
@@ -496,12 +572,105 @@ __device__ __forceinline__ void reuse_tile_body(const CUtensorMap* tm_pos, const
     }
 }
 
+// The same walk with a producer warp (the CTA's last warp, lane 0) that issues the copies
+// of the CTA's tiles into `stages` buffers: full[b] completes when the copies into buffer b
+// have landed, empty[b] when every receiver warp has finished with it (one arrival per
+// warp).  The producer refills a buffer only after its empty phase; at the end it waits
+// for its own last copies, so none is in flight when the CTA exits.  Every wait is bounded:
+// on expiry the waiter records kStatusWaitTimeoutBit and stops (the producer issues nothing
+// more; a receiver warp returns).
+template <int EFFECT, int MAXK, bool PACKED>
+__device__ __forceinline__ void reuse_tile_body_ws(const CUtensorMap* tm_pos, const CUtensorMap* tm_nrm,
+                                                   const CUtensorMap* tm_r0, const CUtensorMap* tm_r1,
+                                                   const TileArgs& a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[2], empty[2];
+    __shared__ int s_qoff[kMaxMembers];
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    constexpr int kPlanes = PACKED ? 2 : 4;
+    const int plane = ((a.SW * a.SH + 7) / 8) * 8;
+    const uint32_t bytes = (uint32_t)kPlanes * (uint32_t)(a.SW * a.SH) * 16u;
+    const int S = a.stages;
+    const int consumers = a.TW * a.TH;           // receiver threads; the producer warp follows
+    const uint32_t cwarps = (uint32_t)(consumers / 32);
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0]);
+        mbar_init(&full[1]);
+        mbar_init_count(&empty[0], cwarps);
+        mbar_init_count(&empty[1], cwarps);
+    }
+    if (threadIdx.x < (unsigned)a.K) {
+        const int2 o = member_offset(a, (int)threadIdx.x);
+        s_qoff[threadIdx.x] = o.y * a.SW + o.x;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x >= consumers) {
+        if ((int)threadIdx.x != consumers) return;
+        int it = 0, last = -1;
+        for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
+            const int b = it % S;
+            if (it >= S && !mbar_wait(&empty[b], (uint32_t)((it / S - 1) & 1))) {
+                atomicOr(a.status, kStatusWaitTimeoutBit);
+                break;
+            }
+            float4* base = reinterpret_cast<float4*>(smem) + (size_t)b * kPlanes * plane;
+            const int x0 = (tile % a.tiles_x) * a.TW, y0 = (tile / a.tiles_x) * a.TH;
+            const int gx = 4 * (x0 - a.hx0), gy = y0 - a.hy0;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&full[b], bytes);
+            tma_load_2d(base, tm_pos, gx, gy, &full[b]);
+            if (PACKED) {
+                tma_load_2d(base + plane, tm_r0, gx, gy, &full[b]);
+            } else {
+                tma_load_2d(base + plane, tm_nrm, gx, gy, &full[b]);
+                tma_load_2d(base + 2 * plane, tm_r0, gx, gy, &full[b]);
+                tma_load_2d(base + 3 * plane, tm_r1, gx, gy, &full[b]);
+            }
+            last = it;
+        }
+        // the copies of the last `S` issued tiles may still be landing
+        for (int j = last; j >= 0 && j > last - S; --j)
+            if (!mbar_wait(&full[j % S], (uint32_t)((j / S) & 1))) atomicOr(a.status, kStatusWaitTimeoutBit);
+        return;
+    }
+    RectLight L;
+    if (EFFECT == kShadow) L = tile_light(a.lp);
+    const int lane = threadIdx.x & 31;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
+        const int b = it % S;
+        if (!mbar_wait(&full[b], (uint32_t)((it / S) & 1))) {
+            if (lane == 0) atomicOr(a.status, kStatusWaitTimeoutBit);
+            return;
+        }
+        Staged st;
+        st.pos = reinterpret_cast<const float4*>(smem) + (size_t)b * kPlanes * plane;
+        if (PACKED) {
+            st.nrm = nullptr;
+            st.r0 = st.pos + plane;
+            st.r1 = nullptr;
+        } else {
+            st.nrm = st.pos + plane;
+            st.r0 = st.pos + 2 * plane;
+            st.r1 = st.pos + 3 * plane;
+        }
+        const int x0 = (tile % a.tiles_x) * a.TW, y0 = (tile / a.tiles_x) * a.TH;
+        tile_single<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, x0, y0);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[b]);
+    }
+}
+
 template <int EFFECT, int MAXK, bool PACKED>
 __global__ void __launch_bounds__(512, 1)
     k_reuse_tile(const __grid_constant__ CUtensorMap tm_pos, const __grid_constant__ CUtensorMap tm_nrm,
                  const __grid_constant__ CUtensorMap tm_r0, const __grid_constant__ CUtensorMap tm_r1,
                  const __grid_constant__ TileArgs a) {
+#if OCC_TILE_WS
+    reuse_tile_body_ws<EFFECT, MAXK, PACKED>(&tm_pos, &tm_nrm, &tm_r0, &tm_r1, a);
+#else
     reuse_tile_body<EFFECT, MAXK, false, PACKED>(&tm_pos, &tm_nrm, &tm_r0, &tm_r1, a);
+#endif
 }
 
 template <int EFFECT, int MAXK, bool PACKED>
@@ -566,7 +735,8 @@ cudaError_t launch_t(const CUtensorMap* maps, const TileArgs& a, size_t smem, in
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = a.n_tiles < sms ? a.n_tiles : sms;
-    k<<<grid, a.TW * a.TH * (pairs ? 2 : 1), smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
+    const int threads = pairs ? 2 * a.TW * a.TH : a.TW * a.TH + 32 * OCC_TILE_WS;
+    k<<<grid, threads, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
     return cudaPeekAtLastError();
 }
 
@@ -597,12 +767,16 @@ bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return false;
-    // largest tile height whose staging fits; two buffers (prefetch) when they fit
+    // largest tile height whose staging fits; two buffers (prefetch) when they fit.  With a
+    // producer warp the tiles are one row shorter (15, 7 or 3 rows) so that the receiver
+    // warps and the producer make 512, 256 or 128 threads.
     int TH = (tile_rows == 4 || tile_rows == 8) ? tile_rows : 16, stages = 1;
     size_t smem = 0;
+    const bool ws = OCC_TILE_WS && !pairs;
     for (; TH >= 4; TH /= 2) {
-        if (hy + TH > 256) continue;
-        smem = planes * (((size_t)SW * (TH + hy) + 7) / 8 * 8) * 16;   // 128-byte planes
+        const int rows = ws ? TH - 1 : TH;
+        if (hy + rows > 256) continue;
+        smem = planes * (((size_t)SW * (rows + hy) + 7) / 8 * 8) * 16;   // 128-byte planes
         if (2 * smem + 1024 <= (size_t)max_smem) {
             stages = 2;
             smem = 2 * smem + 128;
@@ -614,6 +788,7 @@ bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const
         }
     }
     if (TH < 4) return false;
+    if (ws) --TH;
     TileArgs a;
     a.W = gb.W;
     a.H = gb.H;

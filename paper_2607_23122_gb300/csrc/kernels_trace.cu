@@ -77,7 +77,9 @@ __global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS) k_trace(GBufView gb
 // 2009).  Ray index i covers the same 16 x 8 tiles and 8 x 4 warp sub-tiles as k_trace,
 // so a refill takes neighbouring pixels.  Rays start at the root.  Measured at 1080p on
 // the 1M-triangle scene: 0.387 ms against 0.473 ms for k_trace<AO> (refill thresholds
-// 16-24 equal, 1 lane: 0.411 ms; a per-ray start node did not help).  Shadow rays of a
+// 16-24 equal, 1 lane: 0.411 ms; a per-ray start node did not help, nor did one start node
+// per refill, the deepest node holding every refilled segment: 0.387 against 0.354 ms
+// with the 128-bin tree).  Shadow rays of a
 // tile head for one small light and stay coherent in k_trace, which refills would break
 // (0.341 against 0.284 ms), so they keep the one-CTA-per-tile kernel.
 #ifndef OCC_TRACE_DYN
@@ -142,22 +144,25 @@ __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
                 exhausted = true;
                 break;
             }
+            bool fresh = false;   // this lane took a valid receiver in this refill
+            float3 xo = make_float3(0.0f, 0.0f, 0.0f), n = xo;
             if (!have) {
                 const uint32_t idx = base + (uint32_t)__popc(need & below);
                 int x, y;
                 index_pixel(idx, tiles_x, order, &x, &y);
                 if (idx < n_idx && x < gb.W && y < gb.H) {
                     p = (uint32_t)y * (uint32_t)gb.W + (uint32_t)x;
-                    float3 xo = make_float3(0.0f, 0.0f, 0.0f), n = xo;
-                    if (gb_fetch(gb, (int)p, &xo, &n)) {
-                        float tmax;
-                        const float3 d = step1_ray<EFFECT>(xo, n, p, radius, L, seed, sample, &tmax);
-                        trav_init(t, xo, d, tmax, 0u);
-                        have = true;
-                    } else {
+                    if (gb_fetch(gb, (int)p, &xo, &n))
+                        fresh = true;
+                    else
                         write_record(rec, p, xo, xo, xo, 0.0f, -1);
-                    }
                 }
+            }
+            if (fresh) {
+                float tmax;
+                const float3 d = step1_ray<EFFECT>(xo, n, p, radius, L, seed, sample, &tmax);
+                trav_init(t, xo, d, tmax, 0u);
+                have = true;
             }
         }
         if (!__any_sync(0xFFFFFFFFu, have)) break;

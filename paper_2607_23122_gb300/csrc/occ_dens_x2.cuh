@@ -11,6 +11,13 @@
 
 namespace occ {
 
+// AO support test: min(n_x.d, -n_z.d, r^2) > 0 as one three-input minimum instead of three
+// compares (the same outcome for every finite input; a NaN in d makes all three NaN and
+// fails both forms).
+#ifndef OCC_DENS_MIN3
+#define OCC_DENS_MIN3 0
+#endif
+
 // Eq. 15 without Occ and 1/pi for candidate (z, n_z) at members with points (xx, xy, xz) and
 // normals (nx, ny, nz) as lane pairs; (mnx, mny, mnz) = -n_z in both lanes.  An invalid
 // member carries a zero normal (n_x.d = 0 fails the support test).
@@ -22,8 +29,13 @@ __device__ __forceinline__ float2 dens_ao_x2(f32x2 zx, f32x2 zy, f32x2 zz, f32x2
     const f32x2 a = dot3x2(nx, ny, nz, dx, dy, dz);
     const f32x2 b = dot3x2(mnx, mny, mnz, dx, dy, dz);   // -(n_z . d), exactly
     const float2 A = up2(a), B = up2(b), R = up2(r2), AB = up2(mul2(a, b)), R4 = up2(mul2(r2, r2));
+#if OCC_DENS_MIN3
+    const bool ok0 = (min3f(A.x, B.x, R.x) > 0.0f) & (R.x <= R2s);
+    const bool ok1 = (min3f(A.y, B.y, R.y) > 0.0f) & (R.y <= R2s);
+#else
     const bool ok0 = (A.x > 0.0f) & (B.x > 0.0f) & (R.x > 0.0f) & (R.x <= R2s);
     const bool ok1 = (A.y > 0.0f) & (B.y > 0.0f) & (R.y > 0.0f) & (R.y <= R2s);
+#endif
     return make_float2(ok0 ? __fdividef(AB.x, R4.x) : 0.0f, ok1 ? __fdividef(AB.y, R4.y) : 0.0f);
 }
 

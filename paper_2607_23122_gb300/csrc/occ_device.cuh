@@ -447,6 +447,12 @@ __device__ __forceinline__ void visit_node4(const DevBVH& bvh, uint32_t cur, con
     *next = k[0] < kMissKey ? child_of(ch, k[0] & 3u) : kEmptyRef;
 }
 
+// Four-wide nodes: 1 sorts the hit children fully; 0 stops after the three comparators
+// that find the nearest (the others are pushed in partial order).
+#ifndef OCC_VISIT_FULL_SORT
+#define OCC_VISIT_FULL_SORT 1
+#endif
+
 // Children of node `cur` hit by the ray before tbest, nearest first: the nearest goes to
 // *next, the others are pushed far-to-near.  *next = kEmptyRef if none is hit.
 #define OCC_CSWAP(a, b)                                                          \
@@ -492,7 +498,10 @@ __device__ __forceinline__ void visit_node(const DevBVH& bvh, uint32_t cur, cons
     // 19-comparator network (pairs, quadruples, merge).  The nearest child is visited next,
     // the others are pushed far-to-near so closer ones pop first.
     if (kWidth == 4) {
-        OCC_CSWAP(0, 1) OCC_CSWAP(2, 3) OCC_CSWAP(0, 2) OCC_CSWAP(1, 3) OCC_CSWAP(1, 2)
+        OCC_CSWAP(0, 1) OCC_CSWAP(2, 3) OCC_CSWAP(0, 2)
+#if OCC_VISIT_FULL_SORT
+        OCC_CSWAP(1, 3) OCC_CSWAP(1, 2)
+#endif
     } else {
         OCC_CSWAP(0, 2) OCC_CSWAP(1, 3) OCC_CSWAP(4, 6) OCC_CSWAP(5, 7)
         OCC_CSWAP(0, 4) OCC_CSWAP(1, 5) OCC_CSWAP(2, 6) OCC_CSWAP(3, 7)
