@@ -271,11 +271,11 @@ def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
 GROUP_BYTES_PER_PX = 52   # x 12, n 12, z 12, n_z 12, out 4
 # DRAM bytes (read + write) per launch from one `ncu --set full` capture of
 # `bench.py --profile-step` (cold L2); None once a kernel changes
-NCU_TRAFFIC = {"k_trace_dyn<AO>": None,
-               "k_reuse_tile<AO,8>": None,
-               "k_reuse_group<AO,biased,4,2>": 114.168832e6 + 4.530688e6}
-NCU_TRACE_ISSUE_ACTIVE = None   # smsp__issue_active of k_trace_dyn<AO> in its capture
-NCU_TRACE_WARP_INSTR = None   # smsp__inst_executed.sum of k_trace_dyn<AO>, same capture
+NCU_TRAFFIC = {"k_trace_dyn<AO>": 72.747008e6 + 28.316416e6,
+               "k_reuse_tile<AO,8>": 132.7616e6 + 7.310336e6,
+               "k_reuse_group<AO,biased,4,2>": 114.169088e6 + 5.264384e6}
+NCU_TRACE_ISSUE_ACTIVE = 0.6843   # smsp__issue_active of k_trace_dyn<AO> in its capture
+NCU_TRACE_WARP_INSTR = 285.521526e6   # smsp__inst_executed.sum of k_trace_dyn<AO>, same capture
 # What the 1080p AO trace (seed 1, sample 0) traverses, from the instrumented library:
 # OCC_LIB_VARIANT=counters python bench.py --count-touch
 TRACE_TOUCH = {"rays": 1409214, "node_visits": 22216647, "triangle_tests": 5323819,
