@@ -61,7 +61,12 @@ __device__ __forceinline__ float tile_ratio(float p, float P) {
 // One extra warp issues the bulk-tensor copies and the receiver warps release each staged
 // buffer on an mbarrier (1), instead of thread 0 issuing them between CTA-wide barriers (0):
 // a warp whose receivers had fewer candidates starts the next tile without waiting for the
-// slowest warp of the CTA (1080p, 8 disk offsets, AO: 0.099 against 0.110 ms).
+// slowest warp of the CTA (1080p, 8 disk offsets, AO: 0.099 against 0.110 ms).  Two ways of
+// also balancing the lanes' candidate lists were measured slower and dropped: the producer
+// ordering each landed tile's receivers by candidate count (0.18 ms: the ordering, a warp's
+// work, sat on the critical path), and a shared per-tile receiver queue refilling idle lanes
+// (0.117 ms: receivers then start in small groups, and setting up a receiver's members costs
+// about as much as its ~2 candidate columns).
 #ifndef OCC_TILE_WS
 #define OCC_TILE_WS 1
 #endif
@@ -260,15 +265,92 @@ __device__ __forceinline__ void staged_cand(const Staged& st, int q, float4 r0, 
     }
 }
 
+// Receiver terms of the member slots of a receiver as lane pairs (slots 2j, 2j + 1); a slot
+// outside vmask carries zero terms (its densities are 0).
+template <int EFFECT, int MAXK, bool PACKED>
+__device__ __forceinline__ void members_x2(const RectLight& L, const Staged& st, const int* sidx,
+                                           uint32_t vmask, f32x2 (&px)[MAXK / 2][3],
+                                           f32x2 (&pn)[MAXK / 2][3]) {
+#pragma unroll
+    for (int j = 0; j < MAXK / 2; ++j) {
+        float3 x0r, t0, x1r, t1;
+        staged_recv<EFFECT, PACKED>(st, sidx[2 * j], L, &x0r, &t0);
+        staged_recv<EFFECT, PACKED>(st, sidx[2 * j + 1], L, &x1r, &t1);
+        if (!((vmask >> (2 * j)) & 1u)) t0 = make_float3(0.0f, 0.0f, 0.0f);
+        if (!((vmask >> (2 * j + 1)) & 1u)) t1 = make_float3(0.0f, 0.0f, 0.0f);
+        px[j][0] = pk2(x0r.x, x1r.x);
+        px[j][1] = pk2(x0r.y, x1r.y);
+        px[j][2] = pk2(x0r.z, x1r.z);
+        pn[j][0] = pk2(t0.x, t1.x);
+        pn[j][1] = pk2(t0.y, t1.y);
+        pn[j][2] = pk2(t0.z, t1.z);
+    }
+}
+
+// Member slots of a receiver whose staged record holds an occluder.
+template <int MAXK>
+__device__ __forceinline__ uint32_t hit_slots(const TileArgs& a, const Staged& st, const int* sidx,
+                                              uint32_t vmask) {
+    uint32_t hm = 0;
+#pragma unroll
+    for (int c = 0; c < MAXK; ++c)
+        if (c < a.K && ((vmask >> c) & 1u) &&
+            __float_as_int(reinterpret_cast<const float*>(st.r0 + sidx[c])[3]) >= 0)
+            hm |= 1u << c;
+    return hm;
+}
+
+// Column of candidate slot c of the receiver at staged index sc on paired instructions: the
+// receiver's own density (slot 0) and P_c = sum over the slots.
+template <int EFFECT, int MAXK, bool PACKED>
+__device__ __forceinline__ void column_x2(const TileArgs& a, const RectLight& L, const Staged& st,
+                                          const int* s_qoff, int sc, int c,
+                                          const f32x2 (&px)[MAXK / 2][3],
+                                          const f32x2 (&pn)[MAXK / 2][3], float* pi_out,
+                                          float* psum_out) {
+    constexpr int NP = MAXK / 2;
+    const int q = sc + s_qoff[c];
+    const float4 r0 = st.r0[q];
+    float3 z, nz;
+    staged_cand<PACKED>(st, q, r0, &z, &nz);
+    const f32x2 zx = bc2(z.x), zy = bc2(z.y), zz = bc2(z.z);
+    const f32x2 mnx = bc2(-nz.x), mny = bc2(-nz.y), mnz = bc2(-nz.z);
+    float2 d[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+        d[j] = dens_x2_pairs<EFFECT>(zx, zy, zz, mnx, mny, mnz, px[j][0], px[j][1], px[j][2],
+                                     pn[j][0], pn[j][1], pn[j][2], a.R2s, L);
+    // slot 0 is the receiver: its density is the numerator
+    const float pi = d[0].x;
+#if OCC_TILE_TREESUM
+    // P_c as a pairwise tree on paired adds (depth log2 K instead of K - 1)
+    f32x2 s2[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) s2[j] = pk2(d[j].x, d[j].y);
+#pragma unroll
+    for (int w = NP / 2; w >= 1; w /= 2)
+#pragma unroll
+        for (int j = 0; j < w; ++j) s2[j] = add2(s2[j], s2[j + w]);
+    const float2 sp = up2(s2[0]);
+    const float Psum = sp.x + sp.y;
+#else
+    // P_c sums in slot order
+    float Psum = pi + d[0].y;
+#pragma unroll
+    for (int j = 1; j < NP; ++j) Psum = (Psum + d[j].x) + d[j].y;
+#endif
+    *pi_out = pi;
+    *psum_out = Psum;
+}
+
 // One thread per receiver, 4 or 8 member slots: the K receivers are held as lane pairs
 // (slots 2j, 2j + 1) and every candidate's column of densities runs on paired FP32
 // instructions (half the issue slots of the scalar column, the same results).
 template <int EFFECT, int MAXK, bool PACKED>
 __device__ __forceinline__ void tile_single_x2(const TileArgs& a, const RectLight& L,
                                                const Staged& st, const int* s_qoff, int x0,
-                                               int y0) {
+                                               int y0, int lx, int ly) {
     constexpr int NP = MAXK / 2;
-    const int lx = threadIdx.x % a.TW, ly = threadIdx.x / a.TW;
     const int x = x0 + lx, y = y0 + ly;
     if (ly >= a.TH || x >= a.W || y >= a.H) return;
     const int sc = (ly + a.hy0) * a.SW + (lx + a.hx0);
@@ -277,65 +359,12 @@ __device__ __forceinline__ void tile_single_x2(const TileArgs& a, const RectLigh
         int sidx[MAXK];
         const uint32_t vmask = member_mask<MAXK, PACKED>(a, st.pos, x, y, sc, sidx);
         f32x2 px[NP][3], pn[NP][3];
-#pragma unroll
-        for (int j = 0; j < NP; ++j) {
-            float3 x0r, t0, x1r, t1;
-            staged_recv<EFFECT, PACKED>(st, sidx[2 * j], L, &x0r, &t0);
-            staged_recv<EFFECT, PACKED>(st, sidx[2 * j + 1], L, &x1r, &t1);
-            if (!((vmask >> (2 * j)) & 1u)) t0 = make_float3(0.0f, 0.0f, 0.0f);
-            if (!((vmask >> (2 * j + 1)) & 1u)) t1 = make_float3(0.0f, 0.0f, 0.0f);
-            px[j][0] = pk2(x0r.x, x1r.x);
-            px[j][1] = pk2(x0r.y, x1r.y);
-            px[j][2] = pk2(x0r.z, x1r.z);
-            pn[j][0] = pk2(t0.x, t1.x);
-            pn[j][1] = pk2(t0.y, t1.y);
-            pn[j][2] = pk2(t0.z, t1.z);
-        }
+        members_x2<EFFECT, MAXK, PACKED>(L, st, sidx, vmask, px, pn);
         // the member slots whose record holds an occluder: each lane walks its own list, so
         // a warp takes as many candidate steps as its busiest lane (lanes whose candidate
         // missed no longer idle through the other lanes' columns)
-        uint32_t hm = 0;
-#pragma unroll
-        for (int c = 0; c < MAXK; ++c)
-            if (c < a.K && ((vmask >> c) & 1u) &&
-                __float_as_int(reinterpret_cast<const float*>(st.r0 + sidx[c])[3]) >= 0)
-                hm |= 1u << c;
+        uint32_t hm = hit_slots<MAXK>(a, st, sidx, vmask);
         const uint32_t blocked = hm;   // valid members whose record holds an occluder
-        // column of candidate slot c: the receiver's density (slot 0) and P_c
-        auto column = [&](int c, float* pi_out, float* psum_out) {
-            const int q = sc + s_qoff[c];
-            const float4 r0 = st.r0[q];
-            float3 z, nz;
-            staged_cand<PACKED>(st, q, r0, &z, &nz);
-            const f32x2 zx = bc2(z.x), zy = bc2(z.y), zz = bc2(z.z);
-            const f32x2 mnx = bc2(-nz.x), mny = bc2(-nz.y), mnz = bc2(-nz.z);
-            float2 d[NP];
-#pragma unroll
-            for (int j = 0; j < NP; ++j)
-                d[j] = dens_x2_pairs<EFFECT>(zx, zy, zz, mnx, mny, mnz, px[j][0], px[j][1],
-                                             px[j][2], pn[j][0], pn[j][1], pn[j][2], a.R2s, L);
-            // slot 0 is the receiver: its density is the numerator
-            const float pi = d[0].x;
-#if OCC_TILE_TREESUM
-            // P_c as a pairwise tree on paired adds (depth log2 K instead of K - 1)
-            f32x2 s2[NP];
-#pragma unroll
-            for (int j = 0; j < NP; ++j) s2[j] = pk2(d[j].x, d[j].y);
-#pragma unroll
-            for (int w = NP / 2; w >= 1; w /= 2)
-#pragma unroll
-                for (int j = 0; j < w; ++j) s2[j] = add2(s2[j], s2[j + w]);
-            const float2 sp = up2(s2[0]);
-            const float Psum = sp.x + sp.y;
-#else
-            // P_c sums in slot order
-            float Psum = pi + d[0].y;
-#pragma unroll
-            for (int j = 1; j < NP; ++j) Psum = (Psum + d[j].x) + d[j].y;
-#endif
-            *pi_out = pi;
-            *psum_out = Psum;
-        };
         float B = 0.0f;
 #if OCC_TILE_CAND2
         // two candidate columns per step (independent work for the scheduler); the terms
@@ -347,8 +376,8 @@ __device__ __forceinline__ void tile_single_x2(const TileArgs& a, const RectLigh
             const int c1 = two ? __ffs(hm) - 1 : c0;
             hm &= hm - 1u;
             float pi0, P0, pi1, P1;
-            column(c0, &pi0, &P0);
-            column(c1, &pi1, &P1);
+            column_x2<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, sc, c0, px, pn, &pi0, &P0);
+            column_x2<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, sc, c1, px, pn, &pi1, &P1);
             if (pi0 > 0.0f) B += tile_ratio(pi0, P0);
             if (two && pi1 > 0.0f) B += tile_ratio(pi1, P1);
         }
@@ -357,7 +386,7 @@ __device__ __forceinline__ void tile_single_x2(const TileArgs& a, const RectLigh
             const int c = __ffs(hm) - 1;
             hm &= hm - 1u;
             float pi, Psum;
-            column(c, &pi, &Psum);
+            column_x2<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, sc, c, px, pn, &pi, &Psum);
             if (pi > 0.0f) B += tile_ratio(pi, Psum);
         }
 #endif
@@ -371,13 +400,12 @@ __device__ __forceinline__ void tile_single_x2(const TileArgs& a, const RectLigh
 // receiver terms, whose densities are 0, so the pair loop has no per-member test).
 template <int EFFECT, int MAXK, bool PACKED>
 __device__ __forceinline__ void tile_single(const TileArgs& a, const RectLight& L, const Staged& st,
-                                            const int* s_qoff, int x0, int y0) {
+                                            const int* s_qoff, int x0, int y0, int lx, int ly) {
     // (16 slots held as pairs spill: they keep the scalar column)
     if ((MAXK == 4 || MAXK == 8) && OCC_TILE_PAIRED) {
-        tile_single_x2<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, x0, y0);
+        tile_single_x2<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, x0, y0, lx, ly);
         return;
     }
-    const int lx = threadIdx.x % a.TW, ly = threadIdx.x / a.TW;
     const int x = x0 + lx, y = y0 + ly;
     if (ly >= a.TH || x >= a.W || y >= a.H) return;
     const int sc = (ly + a.hy0) * a.SW + (lx + a.hx0);
@@ -565,7 +593,8 @@ __device__ __forceinline__ void reuse_tile_body(const CUtensorMap* tm_pos, const
         if (PAIRS)
             tile_pairs<EFFECT, MAXK, PACKED>(a, L, st, x0, y0);
         else
-            tile_single<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, x0, y0);
+            tile_single<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, x0, y0, (int)threadIdx.x % a.TW,
+                                              (int)threadIdx.x / a.TW);
         __syncthreads();   // buffer b is free for the copies issued next
         if (a.stages == 1 && threadIdx.x == 0 && tile + (int)gridDim.x < a.n_tiles)
             issue(tile + gridDim.x, 0);
@@ -575,10 +604,10 @@ __device__ __forceinline__ void reuse_tile_body(const CUtensorMap* tm_pos, const
 // The same walk with a producer warp (the CTA's last warp, lane 0) that issues the copies
 // of the CTA's tiles into `stages` buffers: full[b] completes when the copies into buffer b
 // have landed, empty[b] when every receiver warp has finished with it (one arrival per
-// warp).  The producer refills a buffer only after its empty phase; at the end it waits
-// for its own last copies, so none is in flight when the CTA exits.  Every wait is bounded:
-// on expiry the waiter records kStatusWaitTimeoutBit and stops (the producer issues nothing
-// more; a receiver warp returns).
+// warp).  The producer refills a buffer only after its empty phase; at the end it waits for
+// its own last copies, so none is in flight when the CTA exits.  Every wait is bounded: on expiry the waiter records
+// kStatusWaitTimeoutBit and stops (the producer issues nothing more; a receiver warp
+// returns).
 template <int EFFECT, int MAXK, bool PACKED>
 __device__ __forceinline__ void reuse_tile_body_ws(const CUtensorMap* tm_pos, const CUtensorMap* tm_nrm,
                                                    const CUtensorMap* tm_r0, const CUtensorMap* tm_r1,
@@ -655,7 +684,8 @@ __device__ __forceinline__ void reuse_tile_body_ws(const CUtensorMap* tm_pos, co
             st.r1 = st.pos + 3 * plane;
         }
         const int x0 = (tile % a.tiles_x) * a.TW, y0 = (tile / a.tiles_x) * a.TH;
-        tile_single<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, x0, y0);
+        tile_single<EFFECT, MAXK, PACKED>(a, L, st, s_qoff, x0, y0, (int)threadIdx.x % a.TW,
+                                          (int)threadIdx.x / a.TW);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);
     }
