@@ -761,6 +761,14 @@ def run_ours(args):
         extra["trace_tuning"] = {"best": tt["best"],
                                  "ms": {json.dumps(t["config"], sort_keys=True): t["ms"]
                                         for t in tt["timings"]}}
+        # the G-buffer layout (row-major or 8 x 8 tiles in Morton order), per frame
+        lay = {}
+        for pname, lpat in (("group4x2", occ.Pattern.group(4, 2)), ("disk8", pat)):
+            lt = autotune.tune_layout(ctx, gb, bvh, occ.OCC_EFFECT_AO, lpat, occ.OCC_EST_BIASED,
+                                      rec, out, radius=RADIUS, iters=20, use_cache=False)
+            lay[pname] = {"best": lt["best"]["gbuffer_layout"],
+                          "frame_ms": {t["config"]["gbuffer_layout"]: t["ms"] for t in lt["timings"]}}
+        extra["layout_tuning"] = lay
         extra["shadow"] = shadow_frame(occ, ctx, gb, bvh, pat, rec, out, flush, stream)
         extra["packed"] = packed_frame(occ, ctx, gb, bvh, pat, out, flush, stream)
         extra["fused"] = fused_frame(occ, ctx, gb, bvh, rec, out, flush, stream)
@@ -845,6 +853,7 @@ def run_ours(args):
                                    frac_hbm=P * GROUP_BYTES_PER_PX / extra["reuse_group4x2"]["s"] / 1e9 / hbm,
                                    neighbour_samples_per_s=P * 8 / extra["reuse_group4x2"]["s"]),
             "trace_tuning_ao": extra["trace_tuning"],
+            "layout_tuning_ao": extra["layout_tuning"],
             "shadow_frame": extra["shadow"],
             "packed_frame": dict(extra["packed"],
                                  group_frac_hbm=P * PACKED_GROUP_BYTES_PER_PX

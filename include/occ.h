@@ -109,15 +109,24 @@ typedef struct occ_bvh occ_bvh;   /* opaque: device-resident wide BVH */
 /* G-buffer of receivers.  pos4[q] = (x.xyz, valid): x is the receiver point
  * (the visible surface point already offset along its normal), valid is 1
  * for a receiver and 0 for background.  nrm4[q] = (n.xyz, unused): the unit
- * geometric normal facing the viewer.  Row-major float4 planes: pixel (x, y) sits at
- * q = y * pitch_px + x, pitch_px >= W (0 means W), so a G-buffer may be a window of a
- * wider render target.  Records and outputs stay dense (W per row) whatever the pitch. */
+ * geometric normal facing the viewer.  Two layouts of the float4 planes:
+ *   OCC_LAYOUT_LINEAR (0): row-major, pixel (x, y) at q = y * pitch_px + x, pitch_px >= W
+ *     (0 means W), so a G-buffer may be a window of a wider render target;
+ *   OCC_LAYOUT_TILED (1): 8 x 8-pixel tiles, tiles_x = ceil(W / 8) per tile row; tile
+ *     (x / 8, y / 8) holds the 64 entries from ((y / 8) * tiles_x + x / 8) * 64 on, the
+ *     pixel (u, v) = (x mod 8, y mod 8) at its Morton index u0 | v0 << 1 | u1 << 2 |
+ *     v1 << 3 | u2 << 4 | v2 << 5 (u_i, v_i the bits of u, v).  Each plane holds
+ *     ceil(W / 8) * ceil(H / 8) * 64 entries; entries of tile pixels outside the image are
+ *     never read.  pitch_px must be 0.  occ_tile_gbuffer writes this layout.
+ * Records and outputs stay dense row-major (W per row) whatever the G-buffer layout. */
+enum { OCC_LAYOUT_LINEAR = 0, OCC_LAYOUT_TILED = 1 };
 typedef struct {
     int32_t W, H;
     const float* pos4;         /* FP32: pos4 plane; PACKED: the packed plane */
     const float* nrm4;         /* FP32: nrm4 plane; PACKED: unused (NULL) */
     int32_t format;            /* OCC_GB_FP32 (0) or OCC_GB_PACKED */
-    int64_t pitch_px;          /* row pitch of the planes in pixels (0: W) */
+    int32_t layout;            /* OCC_LAYOUT_LINEAR (0) or OCC_LAYOUT_TILED */
+    int64_t pitch_px;          /* LINEAR: row pitch of the planes in pixels (0: W); TILED: 0 */
 } occ_gbuffer;
 
 /* Rectangle light c + a eu + b ev, a, b in [-1/2, 1/2], eu orthogonal to ev.
@@ -190,10 +199,21 @@ occ_status occ_gbuffer_pinhole(occ_ctx* ctx, const occ_bvh* bvh, const float* ca
                                float eps, int32_t W, int32_t H, float* pos4, float* nrm4,
                                void* stream);
 
-/* Packs an FP32 G-buffer into the PACKED format (16 bytes per pixel): receiver
- * point kept in FP32, normal octahedral-encoded; invalid pixels get the invalid
- * code.  packed_out: W*H float4, device, 16-byte aligned. */
+/* Packs an FP32 G-buffer (either layout) into the PACKED format (16 bytes per pixel):
+ * receiver point kept in FP32, normal octahedral-encoded; invalid pixels get the invalid
+ * code.  packed_out: W*H float4, row-major (OCC_LAYOUT_LINEAR, pitch W), device, 16-byte
+ * aligned. */
 occ_status occ_pack_gbuffer(occ_ctx* ctx, const occ_gbuffer* gb, float* packed_out, void* stream);
+
+/* Copies a G-buffer (either format, either layout) into OCC_LAYOUT_TILED (see
+ * occ_gbuffer), same format: pos_out (and nrm_out for FP32; NULL for PACKED) hold
+ * ceil(W/8) * ceil(H/8) * 64 float4 each, device, 16-byte aligned, owned by the caller;
+ * they must not overlap the input.  The G-buffer to pass on is {W, H, pos_out, nrm_out,
+ * format, OCC_LAYOUT_TILED, 0}.  Asynchronous on `stream`.  Every kernel takes either
+ * layout; the TMA window kernel needs row-major planes, so window patterns on a tiled
+ * G-buffer run the per-receiver kernel (the same estimates as reuse_window_path 2). */
+occ_status occ_tile_gbuffer(occ_ctx* ctx, const occ_gbuffer* gb, float* pos_out, float* nrm_out,
+                            void* stream);
 
 /* ---- hot path ------------------------------------------------------------- */
 

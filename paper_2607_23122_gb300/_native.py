@@ -26,12 +26,13 @@ OCC_EST_LIGHT_UNBIASED = 4
 OCC_PAT_GROUP, OCC_PAT_BOX, OCC_PAT_OFFSETS, OCC_PAT_RANDOM = 0, 1, 2, 3
 OCC_REC_FP32, OCC_REC_PACKED = 0, 1
 OCC_GB_FP32, OCC_GB_PACKED = 0, 1
+OCC_LAYOUT_LINEAR, OCC_LAYOUT_TILED = 0, 1
 MAX_MEMBERS = 64
 
 
 class occ_gbuffer(C.Structure):
     _fields_ = [("W", c_int32), ("H", c_int32), ("pos4", c_void_p), ("nrm4", c_void_p),
-                ("format", c_int32), ("pitch_px", c_int64)]
+                ("format", c_int32), ("layout", c_int32), ("pitch_px", c_int64)]
 
 
 class occ_rect_light(C.Structure):
@@ -122,6 +123,7 @@ SIGNATURES = {
     "occ_gbuffer_pinhole": (c_int32, [c_void_p, c_void_p, c_void_p, c_float, c_int32, c_int32,
                                       c_void_p, c_void_p, c_void_p]),
     "occ_pack_gbuffer": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p, c_void_p]),
+    "occ_tile_gbuffer": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p, c_void_p, c_void_p]),
     "occ_trace_ao": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p, c_float, c_uint64,
                                c_uint32, C.POINTER(occ_occluders), c_void_p]),
     "occ_trace_shadow": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p,

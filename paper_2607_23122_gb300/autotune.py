@@ -10,7 +10,9 @@ and stores it in a JSON cache so later runs apply it without measuring:
   * the step-1 trace: one CTA per 16 x 8 tile, or persistent CTAs taking rays from a
     counter with a refill threshold of 8, 16 or 24 idle lanes, all or half of the CTAs that
     fit, and the rays handed out by tiles row-major or by 8 x 8-tile blocks in Morton order;
-  * persistent batched kernels: CTAs per SM (1, 2, 4, 8 or all that fit).
+  * persistent batched kernels: CTAs per SM (1, 2, 4, 8 or all that fit);
+  * the G-buffer layout: row-major, or 8 x 8-pixel tiles in Morton order (a tiled copy made
+    once by occ_tile_gbuffer), timed over a whole frame (step-1 trace + reuse).
 
 Cache: $OCC_TUNE_CACHE, else ~/.cache/occreuse/tuning.json.
 """
@@ -71,6 +73,12 @@ def reuse_key(gb: O.GBuffer, rec: O.Occluders, pattern: O.Pattern, estimator: in
 def trace_key(gb: O.GBuffer, rec: O.Occluders, bvh: O.BVH, effect: int) -> str:
     return (f"trace/{gb.W}x{gb.H}/gb{int(gb.packed)}/rec{int(rec.packed)}/eff{effect}/"
             f"tris{bvh.stats['num_tris']}")
+
+
+def layout_key(gb: O.GBuffer, rec: O.Occluders, pattern: O.Pattern, estimator: int,
+               effect: int) -> str:
+    return (f"layout/{gb.W}x{gb.H}/pat{pattern.kind}:{pattern.gw}x{pattern.gh}/K{pattern.K}/"
+            f"gb{int(gb.packed)}/rec{int(rec.packed)}/eff{effect}/est{estimator}")
 
 
 def batch_key(views: list) -> str:
@@ -181,4 +189,47 @@ def tune_batch(ctx: O.Context, bvh: O.BVH, views: list, iters: int = 10,
         cache = load_cache()
         cache[key] = entry
         save_cache(cache)
+    return entry
+
+
+LAYOUT_CANDIDATES = ("linear", "tiled")
+
+
+def tune_layout(ctx: O.Context, gb: O.GBuffer, bvh: O.BVH, effect: int, pattern: O.Pattern,
+                estimator: int, rec: O.Occluders, out, radius: float = 0.0, light=None,
+                iters: int = 10, use_cache: bool = True) -> dict:
+    """Picks the G-buffer layout for this workload: the caller's row-major G-buffer or a
+    tiled copy of it (made once, outside the timing), each timed over a frame (step-1 trace
+    into `rec`, then reuse into `out`).  Returns the cache entry plus "gbuffer": the G-buffer
+    to use (the tiled copy when it won)."""
+    key = layout_key(gb, rec, pattern, estimator, effect)
+    with _LOCK:
+        cache = load_cache() if use_cache else {}
+    if key in cache:
+        entry = dict(cache[key])
+        entry["gbuffer"] = (O.occ_tile_gbuffer(ctx, gb)
+                            if entry["best"]["gbuffer_layout"] == "tiled" else gb)
+        return entry
+    tiled = O.occ_tile_gbuffer(ctx, gb)
+    reuse = O.occ_reuse_ao if effect == O.OCC_EFFECT_AO else O.occ_reuse_shadow
+    traces = estimator in (O.OCC_EST_UNBIASED, O.OCC_EST_LIGHT_UNBIASED)
+
+    def frame(g):
+        if effect == O.OCC_EFFECT_AO:
+            O.occ_trace_ao(ctx, g, bvh, radius, 1, 0, out=rec)
+        else:
+            O.occ_trace_shadow(ctx, g, bvh, light, 1, 0, out=rec)
+        reuse(ctx, g, rec, pattern, pattern.K, estimator, bvh=bvh if traces else None, out=out)
+
+    timings = []
+    for name, g in zip(LAYOUT_CANDIDATES, (gb, tiled)):
+        timings.append({"config": {"gbuffer_layout": name}, "ms": _time(lambda: frame(g), iters)})
+    best = min(timings, key=lambda t: t["ms"])
+    entry = {"best": best["config"], "timings": timings}
+    with _LOCK:
+        cache = load_cache()
+        cache[key] = entry
+        save_cache(cache)
+    entry = dict(entry)
+    entry["gbuffer"] = tiled if best["config"]["gbuffer_layout"] == "tiled" else gb
     return entry

@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include "occ_kernels.h"
+#include "occ_path.cuh"
 
 namespace occ {
 namespace {
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(128) k_stream_ceiling(GBufView gb, RecView rec
     const int x = (blockIdx.x * 4 + warp) * 16 + g * 4 + (m & 3);
     const int y = blockIdx.y * 2 + (m >> 2);
     if (x >= gb.W || y >= gb.H) return;
-    const int i = y * gb.W + x, gi = y * gb.pitch + x;
+    const int i = y * gb.W + x, gi = gb_index(gb, x, y);
     const float4 P = __ldg(gb.pos + gi), N = __ldg(gb.nrm + gi), R0 = __ldg(rec.r0 + i);
     float4 R1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (P.w != 0.0f && __float_as_int(R0.w) >= 0) R1 = __ldg(rec.r1 + i);

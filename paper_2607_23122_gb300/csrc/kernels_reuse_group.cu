@@ -88,13 +88,13 @@ __global__ void OCC_GROUP_BOUNDS k_reuse_group(ReuseArgs a) {
     const int y = blockIdx.y * GH + m / GW;
     const bool inside = x < a.gb.W && y < a.gb.H;
     const int i = inside ? y * a.gb.W + x : 0;
-    const int gi = inside ? y * a.gb.pitch + x : 0;   // G-buffer index
+    const int gi = inside ? gb_index(a.gb, x, y) : 0;   // G-buffer entry
     RectLight L;
     if (EFFECT == kShadow) L = make_light(a.lp);
     // Prefetch into L2 the rows of the CTA one wave of resident CTAs later (CTAs start in
     // launch order, so its loads then hit L2 instead of waiting for DRAM): one thread per
     // row and plane, one bulk prefetch each.
-    if (a.pf_planes > 0 && threadIdx.x < (unsigned)(GH * a.pf_planes)) {
+    if (a.pf_planes > 0 && !a.gb.tiled && threadIdx.x < (unsigned)(GH * a.pf_planes)) {
         constexpr int CW = OCC_GROUP_WARPS * BW;
         const unsigned t = blockIdx.y * gridDim.x + blockIdx.x + (unsigned)a.pf_ahead;
         if (t < gridDim.x * gridDim.y) {

@@ -773,8 +773,8 @@ cudaError_t launch_t(const CUtensorMap* maps, const TileArgs& a, size_t smem, in
 }  // namespace
 
 // Returns false (nothing launched) when the pattern or the staging does not fit this
-// kernel: not a box / offsets pattern, K > 16, a halo wider than the TMA box allows, or a
-// tile that does not fit in shared memory.
+// kernel: not a box / offsets pattern, a tiled G-buffer, K > 16, a halo wider than the TMA
+// box allows, or a tile that does not fit in shared memory.
 cudaError_t launch_debug_wait_timeout(uint32_t spins, unsigned* status, cudaStream_t s) {
     k_debug_wait_timeout<<<1, 32, 0, s>>>(spins, status);
     return cudaGetLastError();
@@ -786,6 +786,7 @@ bool launch_reuse_tile(int effect, const GBufView& gb, const RecView& rec, const
     *err = cudaSuccess;
     if (pat.kind != 1 && pat.kind != 2) return false;
     if ((gb.packed != 0) != (rec.packed != 0)) return false;
+    if (gb.tiled) return false;   // the bulk-tensor copies stage row-major boxes
     const bool packed = gb.packed != 0;
     const size_t planes = packed ? 2 : 4;
     if (pat.K > 16) return false;

@@ -309,6 +309,20 @@ __global__ void k_pack_gbuffer(GBufView gb, float4* out) {
     out[p] = make_float4(P.x, P.y, P.z, __uint_as_float(code));
 }
 
+// G-buffer -> the same format in the tiled layout: pixel p's entries move from gb_at to
+// their tiled index.
+__global__ void k_tile_gbuffer(GBufView gb, float4* pos_out, float4* nrm_out) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)gb.W * gb.H) return;
+    const int y = (int)(p / gb.W), x = (int)(p - (int64_t)y * gb.W);
+    const int g = gb_at(gb, (int)p);
+    GBufView t = gb;
+    t.tiled = 1;
+    const int d = gb_index(t, x, y);
+    pos_out[d] = __ldg(gb.pos + g);
+    if (nrm_out) nrm_out[d] = __ldg(gb.nrm + g);
+}
+
 dim3 tile_grid(int W, int H) {
     return dim3((unsigned)((W + kTileW - 1) / kTileW), (unsigned)((H + kTileH - 1) / kTileH));
 }
@@ -386,6 +400,14 @@ cudaError_t launch_gbuffer(const DevBVH& bvh, const float* cam, float eps, int W
     const float th = tanf(0.5f * cam[9] * 3.14159265358979f / 180.0f);
     k_gbuffer<<<tile_grid(W, H), 128, 0, s>>>(bvh, eye, f, rt, up, th, (float)W / (float)H, eps,
                                               W, H, pos, nrm, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_gbuffer(const GBufView& gb, float4* pos_out, float4* nrm_out,
+                                cudaStream_t s) {
+    const int64_t P = (int64_t)gb.W * gb.H;
+    if (P <= 0) return cudaSuccess;
+    k_tile_gbuffer<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(gb, pos_out, gb.packed ? nullptr : nrm_out);
     return cudaGetLastError();
 }
 

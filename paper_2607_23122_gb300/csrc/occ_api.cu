@@ -43,6 +43,11 @@ occ_status check_ctx(occ_ctx* ctx) {
     return OCC_OK;
 }
 
+// float4 entries of each plane of a tiled W x H G-buffer
+int64_t tiled_entries(int32_t W, int32_t H) {
+    return (int64_t)((W + 7) / 8) * ((H + 7) / 8) * 64;
+}
+
 occ_status check_gbuffer(occ_ctx* ctx, const occ_gbuffer* gb) {
     if (!gb) return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer is NULL");
     if (gb->W <= 0 || gb->H <= 0 || (int64_t)gb->W * gb->H > (int64_t)1 << 31)
@@ -53,6 +58,16 @@ occ_status check_gbuffer(occ_ctx* ctx, const occ_gbuffer* gb) {
         return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pointers are NULL");
     if (!aligned16(gb->pos4) || (gb->format == OCC_GB_FP32 && !aligned16(gb->nrm4)))
         return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pointers must be 16-byte aligned");
+    if (gb->layout != OCC_LAYOUT_LINEAR && gb->layout != OCC_LAYOUT_TILED)
+        return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer layout %d invalid", gb->layout);
+    if (gb->layout == OCC_LAYOUT_TILED) {
+        if (gb->pitch_px != 0)
+            return fail(ctx, OCC_ERR_INVALID_ARG, "a tiled gbuffer takes pitch_px 0, not %lld",
+                        (long long)gb->pitch_px);
+        if (tiled_entries(gb->W, gb->H) > ((int64_t)1 << 31))
+            return fail(ctx, OCC_ERR_INVALID_ARG, "tiled gbuffer %dx%d too large", gb->W, gb->H);
+        return OCC_OK;
+    }
     if (gb->pitch_px != 0 &&
         (gb->pitch_px < gb->W || (int64_t)(gb->H - 1) * gb->pitch_px + gb->W > ((int64_t)1 << 31)))
         return fail(ctx, OCC_ERR_INVALID_ARG, "gbuffer pitch %lld invalid for width %d",
@@ -170,7 +185,8 @@ using occ::to_params;
 occ::GBufView view(const occ_gbuffer* gb) {
     return occ::GBufView{gb->W, gb->H, reinterpret_cast<const float4*>(gb->pos4),
                          reinterpret_cast<const float4*>(gb->nrm4), gb->format == OCC_GB_PACKED,
-                         gb->pitch_px ? (int32_t)gb->pitch_px : gb->W};
+                         gb->pitch_px ? (int32_t)gb->pitch_px : gb->W,
+                         gb->layout == OCC_LAYOUT_TILED ? 1 : 0};
 }
 
 occ::RecView rec_view(const occ_occluders* o) {
@@ -526,6 +542,37 @@ OCC_EXPORT occ_status occ_pack_gbuffer(occ_ctx* ctx, const occ_gbuffer* gb, floa
                     occ::launch_pack_gbuffer(view(gb), reinterpret_cast<float4*>(packed_out),
                                              (cudaStream_t)stream),
                     "pack launch");
+}
+
+OCC_EXPORT occ_status occ_tile_gbuffer(occ_ctx* ctx, const occ_gbuffer* gb, float* pos_out,
+                                       float* nrm_out, void* stream) {
+    occ_status st = check_ctx(ctx);
+    if (st != OCC_OK) return st;
+    if ((st = check_gbuffer(ctx, gb)) != OCC_OK) return st;
+    const bool fp32 = gb->format == OCC_GB_FP32;
+    if (!pos_out || !aligned16(pos_out) || (fp32 && (!nrm_out || !aligned16(nrm_out))) ||
+        (!fp32 && nrm_out))
+        return fail(ctx, OCC_ERR_INVALID_ARG,
+                    "occ_tile_gbuffer needs 16-byte aligned pos_out (and nrm_out for FP32 only)");
+    if (tiled_entries(gb->W, gb->H) > ((int64_t)1 << 31))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "tiled gbuffer %dx%d too large", gb->W, gb->H);
+    // byte ranges: the input planes and the outputs must not overlap
+    const int64_t out_bytes = tiled_entries(gb->W, gb->H) * 16;
+    const int64_t in_bytes = 16 * (gb->layout == OCC_LAYOUT_TILED
+                                       ? tiled_entries(gb->W, gb->H)
+                                       : (int64_t)(gb->H - 1) * (gb->pitch_px ? gb->pitch_px : gb->W) + gb->W);
+    auto overlap = [](const void* a, int64_t an, const void* b, int64_t bn) {
+        const char *pa = static_cast<const char*>(a), *pb = static_cast<const char*>(b);
+        return a && b && pa < pb + bn && pb < pa + an;
+    };
+    if (overlap(pos_out, out_bytes, gb->pos4, in_bytes) || overlap(pos_out, out_bytes, gb->nrm4, in_bytes) ||
+        overlap(nrm_out, out_bytes, gb->pos4, in_bytes) || overlap(nrm_out, out_bytes, gb->nrm4, in_bytes) ||
+        overlap(pos_out, out_bytes, nrm_out, out_bytes))
+        return fail(ctx, OCC_ERR_INVALID_ARG, "occ_tile_gbuffer outputs overlap its input or each other");
+    return launched(ctx,
+                    occ::launch_tile_gbuffer(view(gb), reinterpret_cast<float4*>(pos_out),
+                                             reinterpret_cast<float4*>(nrm_out), (cudaStream_t)stream),
+                    "tile launch");
 }
 
 OCC_EXPORT occ_status occ_trace_ao(occ_ctx* ctx, const occ_gbuffer* gb, const occ_bvh* bvh,

@@ -15,6 +15,7 @@ struct GBufView {
     int32_t packed;
     int32_t pitch;       // row pitch of the planes in pixels (>= W); pixel p = y W + x sits at
                          // y pitch + x
+    int32_t tiled;       // 8 x 8 tiles, Morton order inside a tile (pitch unused; see gb_index)
 };
 
 // Occluder records.  FP32: plane 0 (z.xyz, tri id bits), plane 1 (n_z.xyz, t).
@@ -95,6 +96,9 @@ cudaError_t launch_debug_rays(int effect, const GBufView& gb, float radius,
                               const LightParams& light, uint64_t seed, uint32_t sample,
                               float4* out, cudaStream_t s);
 // Streaming ceiling of the group reuse kernel's memory pattern (kernels_probe.cu).
+// G-buffer (either format, either layout) -> the same format in the tiled layout
+cudaError_t launch_tile_gbuffer(const GBufView& gb, float4* pos_out, float4* nrm_out,
+                                cudaStream_t s);
 cudaError_t launch_stream_ceiling(const GBufView& gb, const RecView& rec, float* out,
                                   cudaStream_t s);
 // FP32 throughput probe (kernels_probe.cu): *flop = FLOPs of the launch.

@@ -12,10 +12,24 @@ namespace occ {
 constexpr float kSupportSlack = 1.0f + 1.0f / 65536.0f;
 
 // G-buffer index of pixel p = y W + x (records and outputs use p itself): y pitch + x.
+// Entry of pixel (x, y) in a G-buffer plane: row-major with the view's pitch, or the tiled
+// layout (8 x 8 tiles in row-major tile order, the tile's pixels in Morton order).
+__device__ __forceinline__ int gb_index(const GBufView& gb, int x, int y) {
+    if (gb.tiled) {
+        const int tiles_x = (gb.W + 7) >> 3;
+        const int u = x & 7, v = y & 7;
+        const int m = (u & 1) | ((v & 1) << 1) | ((u & 2) << 1) | ((v & 2) << 2) | ((u & 4) << 2) |
+                      ((v & 4) << 3);
+        return ((y >> 3) * tiles_x + (x >> 3)) * 64 + m;
+    }
+    return y * gb.pitch + x;
+}
+
+// Entry of pixel p = y W + x.
 __device__ __forceinline__ int gb_at(const GBufView& gb, int p) {
-    if (gb.pitch == gb.W) return p;
+    if (!gb.tiled && gb.pitch == gb.W) return p;
     const int y = p / gb.W;
-    return y * gb.pitch + (p - y * gb.W);
+    return gb_index(gb, p - y * gb.W, y);
 }
 
 // G-buffer entry of pixel p: receiver point, normal, validity.

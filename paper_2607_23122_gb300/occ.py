@@ -14,7 +14,8 @@ import torch
 from . import _native as N
 from ._native import (  # noqa: F401
     OCC_EFFECT_AO, OCC_EFFECT_SHADOW, OCC_EST_BIASED, OCC_EST_BOXMEAN, OCC_EST_LIGHT_UNBIASED,
-    OCC_EST_NOREUSE, OCC_EST_UNBIASED, OCC_GB_FP32, OCC_GB_PACKED, OCC_PAT_BOX, OCC_PAT_GROUP, OCC_PAT_OFFSETS,
+    OCC_EST_NOREUSE, OCC_EST_UNBIASED, OCC_GB_FP32, OCC_GB_PACKED, OCC_LAYOUT_LINEAR,
+    OCC_LAYOUT_TILED, OCC_PAT_BOX, OCC_PAT_GROUP, OCC_PAT_OFFSETS,
     OCC_PAT_RANDOM,
     OCC_REC_FP32, OCC_REC_PACKED, MAX_MEMBERS)
 
@@ -111,17 +112,25 @@ def occ_bvh_build(ctx: Context, tris: np.ndarray) -> BVH:
 @dataclass
 class GBuffer:
     """pos4 / nrm4: float32 CUDA tensors [H, W, 4] (see occ_gbuffer).  A packed G-buffer
-    has only pos4 (the packed plane) and nrm4 = None."""
+    has only pos4 (the packed plane) and nrm4 = None.  A tiled G-buffer (OCC_LAYOUT_TILED,
+    made by occ_tile_gbuffer) holds [ceil(H/8) * ceil(W/8), 64, 4] tensors and its size in
+    `size` = (W, H)."""
     pos4: torch.Tensor
     nrm4: torch.Tensor | None = None
+    layout: int = N.OCC_LAYOUT_LINEAR
+    size: tuple | None = None
+
+    @property
+    def tiled(self) -> bool:
+        return self.layout == N.OCC_LAYOUT_TILED
 
     @property
     def W(self) -> int:
-        return int(self.pos4.shape[1])
+        return int(self.size[0]) if self.tiled else int(self.pos4.shape[1])
 
     @property
     def H(self) -> int:
-        return int(self.pos4.shape[0])
+        return int(self.size[1]) if self.tiled else int(self.pos4.shape[0])
 
     @property
     def packed(self) -> bool:
@@ -129,19 +138,27 @@ class GBuffer:
 
     @property
     def pitch(self) -> int:
-        """Row pitch of the planes in pixels (the tensors may be windows of wider ones)."""
-        return int(self.pos4.stride(0)) // 4
+        """Row pitch of the planes in pixels (the tensors may be windows of wider ones); 0 for
+        a tiled G-buffer."""
+        return 0 if self.tiled else int(self.pos4.stride(0)) // 4
 
     def c(self) -> N.occ_gbuffer:
         for t in (self.pos4,) if self.packed else (self.pos4, self.nrm4):
-            if not (t.is_cuda and t.dtype == torch.float32 and tuple(t.shape) == (self.H, self.W, 4)
-                    and t.stride(2) == 1 and t.stride(1) == 4 and t.stride(0) % 4 == 0
-                    and t.stride(0) // 4 == self.pitch and self.pitch >= self.W):
+            if self.tiled:
+                n = ((self.W + 7) // 8) * ((self.H + 7) // 8)
+                if not (t.is_cuda and t.dtype == torch.float32 and tuple(t.shape) == (n, 64, 4)
+                        and t.is_contiguous()):
+                    raise ValueError("tiled G-buffer tensors must be contiguous float32 CUDA "
+                                     "[ceil(H/8) * ceil(W/8), 64, 4]")
+            elif not (t.is_cuda and t.dtype == torch.float32 and tuple(t.shape) == (self.H, self.W, 4)
+                      and t.stride(2) == 1 and t.stride(1) == 4 and t.stride(0) % 4 == 0
+                      and t.stride(0) // 4 == self.pitch and self.pitch >= self.W):
                 raise ValueError("G-buffer tensors must be float32 CUDA [H, W, 4] with contiguous "
                                  "rows and the same row pitch")
-        return N.occ_gbuffer(self.W, self.H, self.pos4.data_ptr(),
-                             None if self.packed else self.nrm4.data_ptr(),
-                             N.OCC_GB_PACKED if self.packed else N.OCC_GB_FP32, self.pitch)
+        return N.occ_gbuffer(W=self.W, H=self.H, pos4=self.pos4.data_ptr(),
+                             nrm4=None if self.packed else self.nrm4.data_ptr(),
+                             format=N.OCC_GB_PACKED if self.packed else N.OCC_GB_FP32,
+                             layout=self.layout, pitch_px=self.pitch)
 
     @staticmethod
     def from_numpy(pos4: np.ndarray, nrm4: np.ndarray, device="cuda") -> "GBuffer":
@@ -287,6 +304,19 @@ def occ_pack_gbuffer(ctx: Context, gb: GBuffer, stream=None) -> GBuffer:
     ctx.check(ctx.lib.occ_pack_gbuffer(ctx.handle, C.byref(g), out.data_ptr(),
                                        _stream_handle(stream)))
     return GBuffer(out, None)
+
+
+def occ_tile_gbuffer(ctx: Context, gb: GBuffer, stream=None) -> GBuffer:
+    """The same G-buffer in the tiled layout (8 x 8 tiles, Morton order inside a tile)."""
+    n = ((gb.W + 7) // 8) * ((gb.H + 7) // 8)
+    dev = gb.pos4.device
+    pos = torch.empty((n, 64, 4), dtype=torch.float32, device=dev)
+    nrm = None if gb.packed else torch.empty((n, 64, 4), dtype=torch.float32, device=dev)
+    g = gb.c()
+    ctx.check(ctx.lib.occ_tile_gbuffer(ctx.handle, C.byref(g), pos.data_ptr(),
+                                       None if nrm is None else nrm.data_ptr(),
+                                       _stream_handle(stream)))
+    return GBuffer(pos, nrm, layout=N.OCC_LAYOUT_TILED, size=(gb.W, gb.H))
 
 
 def occ_trace_ao(ctx: Context, gb: GBuffer, bvh: BVH, radius: float, seed: int, sample: int,

@@ -322,4 +322,15 @@ def test_autotuner_picks_caches_and_reapplies(occ, ctx, c1, tmp_path, monkeypatc
                             use_cache=False)
     assert g["best"] in autotune.GROUP_CANDIDATES
     occ.occ_set_tuning(ctx)
+    # G-buffer layout: row-major or a tiled copy, timed over a frame; the cached choice comes
+    # back with the G-buffer to use
+    lay = autotune.tune_layout(ctx, gb, c1["bvh"], AO, occ.Pattern.group(4, 2), BIASED, rec, out,
+                               radius=R_C1, iters=2)
+    assert [t["config"]["gbuffer_layout"] for t in lay["timings"]] == list(autotune.LAYOUT_CANDIDATES)
+    assert lay["gbuffer"].tiled == (lay["best"]["gbuffer_layout"] == "tiled")
+    monkeypatch.setattr(autotune, "_time", lambda *a, **k: pytest.fail("re-measured"))
+    lay2 = autotune.tune_layout(ctx, gb, c1["bvh"], AO, occ.Pattern.group(4, 2), BIASED, rec, out,
+                                radius=R_C1)
+    assert lay2["best"] == lay["best"] and lay2["gbuffer"].tiled == lay["gbuffer"].tiled
+    monkeypatch.setattr(autotune, "_time", timer)
     ctx.sync()

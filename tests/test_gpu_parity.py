@@ -357,6 +357,86 @@ def test_pitched_gbuffer_matches_its_dense_copy(occ, ctx, c1):
         occ.GBuffer(big_pos[:, :W].transpose(0, 1), big_nrm[:, :W].transpose(0, 1)).c()
 
 
+def _morton8(u, v):
+    """Position of pixel (u, v) of an 8 x 8 tile in the tiled layout (include/occ.h)."""
+    m = 0
+    for b in range(3):
+        m |= ((u >> b) & 1) << (2 * b) | ((v >> b) & 1) << (2 * b + 1)
+    return m
+
+
+def test_tiled_gbuffer_matches_linear(occ, ctx, c1):
+    """A G-buffer copied into the tiled layout (8 x 8 tiles, Morton order inside a tile) holds
+    each pixel where include/occ.h puts it (checked against a host-side copy), and gives the
+    same records and estimates, bit for bit, as the row-major one it came from (a pitched
+    window of odd size, so tiles are cut by the image border): both traces, the fused trace +
+    group reuse, group / box / offsets / random patterns with every estimator (window
+    patterns on the per-receiver kernel on both sides, as a tiled G-buffer has no bulk-tensor
+    path), in both formats; packing a tiled FP32 G-buffer gives the same packed plane."""
+    import torch
+    W, H, x0, y0 = 45, 29, 7, 13
+    big_pos = torch.from_numpy(c1["pos"]).cuda()
+    big_nrm = torch.from_numpy(c1["nrm"]).cuda()
+    lin = occ.GBuffer(big_pos[y0:y0 + H, x0:x0 + W], big_nrm[y0:y0 + H, x0:x0 + W])
+    til = occ.occ_tile_gbuffer(ctx, lin)
+    plin = occ.occ_pack_gbuffer(ctx, lin)
+    ptil = occ.occ_tile_gbuffer(ctx, plin)
+    ctx.sync()
+    assert til.tiled and til.W == W and til.H == H and til.pitch == 0
+    tx = (W + 7) // 8
+    pos_t, nrm_t = til.pos4.cpu().numpy(), til.nrm4.cpu().numpy()
+    pos_l, nrm_l = lin.pos4.cpu().numpy(), lin.nrm4.cpu().numpy()
+    ptil_t, plin_l = ptil.pos4.cpu().numpy(), plin.pos4.cpu().numpy()
+    for y in range(H):
+        for x in range(W):
+            t, m = (y // 8) * tx + x // 8, _morton8(x % 8, y % 8)
+            assert np.array_equal(pos_t[t, m], pos_l[y, x]) and np.array_equal(nrm_t[t, m], nrm_l[y, x])
+            assert np.array_equal(ptil_t[t, m].view(np.int32), plin_l[y, x].view(np.int32))
+    assert torch.equal(occ.occ_pack_gbuffer(ctx, til).pos4.view(torch.int32), plin.pos4.view(torch.int32))
+    pats = _patterns(occ)
+    occ.occ_set_tuning(ctx, reuse_window_path=2)
+    try:
+        for packed, (gl, gt) in ((False, (lin, til)), (True, (plin, ptil))):
+            for effect in (AO, SH):
+                def trace(gb):
+                    if effect == AO:
+                        return occ.occ_trace_ao(ctx, gb, c1["bvh"], R_C1, 4, 2, packed=packed)
+                    return occ.occ_trace_shadow(ctx, gb, c1["bvh"], LIGHT_C1, 4, 2, packed=packed)
+                ol, ot = trace(gl), trace(gt)
+                ctx.sync()
+                assert torch.equal(ol.data.view(torch.int32), ot.data.view(torch.int32)), (packed, effect)
+                fn = occ.occ_reuse_ao if effect == AO else occ.occ_reuse_shadow
+                for pname in ("group4x2", "group3x2", "box3x3", "disk8", "random8"):
+                    pat = pats[pname]
+                    for est in (NOREUSE, BIASED, UNBIASED, BOXMEAN):
+                        bv = c1["bvh"] if est == UNBIASED else None
+                        a = fn(ctx, gl, ol, pat, pat.K, est, bvh=bv)
+                        b = fn(ctx, gt, ot, pat, pat.K, est, bvh=bv)
+                        ctx.sync()
+                        assert torch.equal(a, b), (packed, effect, pname, est)
+                if not packed:
+                    fused = occ.occ_trace_reuse_ao if effect == AO else occ.occ_trace_reuse_shadow
+                    arg = R_C1 if effect == AO else LIGHT_C1
+                    a = fused(ctx, gl, c1["bvh"], arg, 4, 2, pats["group4x2"], 8, BIASED)
+                    b = fused(ctx, gt, c1["bvh"], arg, 4, 2, pats["group4x2"], 8, BIASED)
+                    ctx.sync()
+                    assert torch.equal(a, b), ("fused", effect)
+    finally:
+        occ.occ_set_tuning(ctx)
+    # a tiled G-buffer takes no pitch, and the layout code is checked
+    import ctypes
+    g = til.c()
+    g.pitch_px = 64
+    assert ctx.lib.occ_pack_gbuffer(ctx.handle, ctypes.byref(g), plin.pos4.data_ptr(), None) != 0
+    g = lin.c()
+    g.layout = 2
+    assert ctx.lib.occ_pack_gbuffer(ctx.handle, ctypes.byref(g), plin.pos4.data_ptr(), None) != 0
+    # the copy refuses outputs that overlap its input
+    g = lin.c()
+    assert ctx.lib.occ_tile_gbuffer(ctx.handle, ctypes.byref(g), lin.pos4.data_ptr(),
+                                    til.nrm4.data_ptr(), None) != 0
+
+
 def test_all_invalid_gbuffer_and_max_k(orc, occ, ctx, c1):
     pos = np.zeros((20, 30, 4), dtype=np.float32)
     gb = occ.GBuffer.from_numpy(pos, pos)
