@@ -286,6 +286,23 @@ def test_trace_and_group_tuning_choices_are_bit_identical(occ, ctx, c1, cfg, eff
     assert occ.torch.equal(rec0.view(i32), rec1.view(i32)) and occ.torch.equal(out0, out1)
 
 
+def test_batch_of_tiled_views_matches_row_major(occ, ctx, c1):
+    """Every view of a batch given as a tiled G-buffer (occ_tile_gbuffer) gives the same
+    records and estimates, bit for bit, as the same batch with row-major G-buffers (views of
+    every size, both formats, every estimator)."""
+    views, _ = _make_views(occ, c1)
+    tviews, _ = _make_views(occ, c1)
+    for v in tviews:
+        v.gb = occ.occ_tile_gbuffer(ctx, v.gb)
+    occ.occ_frame_batch(ctx, c1["bvh"], views)
+    occ.occ_frame_batch(ctx, c1["bvh"], tviews)
+    ctx.sync()
+    for i, (a, b) in enumerate(zip(views, tviews)):
+        assert b.gb.tiled
+        assert np.array_equal(_bits(a.rec), _bits(b.rec)), f"view {i} records"
+        assert np.array_equal(a.out.cpu().numpy(), b.out.cpu().numpy()), f"view {i} estimate"
+
+
 def test_autotuner_picks_caches_and_reapplies(occ, ctx, c1, tmp_path, monkeypatch):
     from paper_2607_23122_gb300 import autotune
     monkeypatch.setenv("OCC_TUNE_CACHE", str(tmp_path / "tune.json"))

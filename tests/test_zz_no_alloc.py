@@ -49,14 +49,17 @@ def _noalloc(occ, gb, bvh, effect, radius, light, seed, sample, pat, est, out):
     return st, flags.value, msg.value.decode()
 
 
-@pytest.mark.parametrize("effect,est,pname,packed", [(0, 1, "disk", False), (0, 2, "box", False),
-                                                     (1, 1, "group", False), (1, 3, "box", False),
-                                                     (0, 1, "group", True)])
-def test_noalloc_matches_allocating_path_twice(setup, effect, est, pname, packed):
+@pytest.mark.parametrize("effect,est,pname,fmt", [(0, 1, "disk", "fp32"), (0, 2, "box", "fp32"),
+                                                  (1, 1, "group", "fp32"), (1, 3, "box", "fp32"),
+                                                  (0, 1, "group", "packed"), (1, 1, "disk", "tiled")])
+def test_noalloc_matches_allocating_path_twice(setup, effect, est, pname, fmt):
     import torch
     occ, ctx, bvh, gb = setup
-    if packed:                 # packed G-buffer; the scratch records stay FP32
+    if fmt == "packed":        # packed G-buffer; the scratch records stay FP32
         gb = occ.occ_pack_gbuffer(ctx, gb)
+        ctx.sync()
+    elif fmt == "tiled":       # tiled G-buffer layout (the window runs the per-receiver kernel)
+        gb = occ.occ_tile_gbuffer(ctx, gb)
         ctx.sync()
     pat = {"disk": occ.Pattern.offsets_of(synth.disk_offsets(8, 6.0, seed=3)),
            "box": occ.Pattern.box(3, 3), "group": occ.Pattern.group(4, 2)}[pname]
