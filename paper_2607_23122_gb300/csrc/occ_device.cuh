@@ -380,6 +380,27 @@ __device__ __forceinline__ uint32_t entry_ref(StackEntry e) { return e; }
 __device__ __forceinline__ bool entry_live(StackEntry, float) { return true; }
 #endif
 
+// Push of a hit child (a full stack drops it and records the overflow).  Storing every
+// slot's entry and advancing the top by the hit flag, without branches, measured slower
+// (1080p AO trace 0.359 against 0.341 ms).
+__device__ __forceinline__ void push_entry(StackEntry* stack, int& sp, bool& overflow, bool hit,
+                                           StackEntry e) {
+    if (hit) {
+        if (sp < kStackSize) stack[sp++] = e;
+        else overflow = true;
+    }
+}
+
+// A visit pushes at most kWidth - 1 entries: with that much room left (OCC_PUSH_ROOM=1) the
+// pushes skip the per-entry bound test; 0 tests every push (1080p: AO equal, shadow trace
+// 0.253 against 0.256 ms).
+#ifndef OCC_PUSH_ROOM
+#define OCC_PUSH_ROOM 1
+#endif
+__device__ __forceinline__ bool push_room(int sp) {
+    return OCC_PUSH_ROOM && sp <= kStackSize - (kWidth - 1);
+}
+
 // Child reference of slot s (0..3) of a node's reference quad.
 __device__ __forceinline__ uint32_t child_of(uint4 ch, uint32_t s) {
     const uint32_t lo = (s & 1u) ? ch.y : ch.x, hi = (s & 1u) ? ch.w : ch.z;
@@ -437,15 +458,30 @@ __device__ __forceinline__ void visit_node4(const DevBVH& bvh, uint32_t cur, con
     }
     OCC_USWAP(0, 1) OCC_USWAP(2, 3) OCC_USWAP(0, 2) OCC_USWAP(1, 3) OCC_USWAP(1, 2)
 #undef OCC_USWAP
+    if (push_room(sp)) {
 #pragma unroll
-    for (int c = 3; c >= 1; --c) {
-        if (k[c] < kMissKey) {
-            if (sp < kStackSize) stack[sp++] = stack_entry(child_of(ch, k[c] & 3u), __uint_as_float(k[c] & ~3u));
-            else overflow = true;
-        }
+        for (int c = 3; c >= 1; --c)
+            if (k[c] < kMissKey) stack[sp++] = stack_entry(child_of(ch, k[c] & 3u), __uint_as_float(k[c] & ~3u));
+    } else {
+#pragma unroll
+        for (int c = 3; c >= 1; --c)
+            push_entry(stack, sp, overflow, k[c] < kMissKey,
+                       stack_entry(child_of(ch, k[c] & 3u), __uint_as_float(k[c] & ~3u)));
     }
     *next = k[0] < kMissKey ? child_of(ch, k[0] & 3u) : kEmptyRef;
 }
+
+// Scalar visit: entry / exit distances by three-input max / min (1) or pairwise (0)
+#ifndef OCC_VISIT_MAX3
+#define OCC_VISIT_MAX3 1
+#endif
+// Child slots: 1 also tests the reference of a slot against kEmptyRef; 0 relies on the
+// empty slots' inverted boxes alone (1080p AO trace 0.342-0.344 against 0.352-0.353 ms with
+// the test and the pairwise max / min)
+#ifndef OCC_VISIT_EMPTY_TEST
+#define OCC_VISIT_EMPTY_TEST 0
+#endif
+
 
 // Four-wide nodes: 1 sorts the hit children fully; 0 stops after the three comparators
 // that find the nearest (the others are pushed in partial order).
@@ -485,11 +521,20 @@ __device__ __forceinline__ void visit_node(const DevBVH& bvh, uint32_t cur, cons
         const uint32_t cref[4] = {ch.x, ch.y, ch.z, ch.w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
+#if OCC_VISIT_MAX3
+            const float tn = max3f(fmaf(nxs[c], r.idir.x, -r.oidir.x), fmaf(nys[c], r.idir.y, -r.oidir.y),
+                                   fmaxf(fmaf(nzs[c], r.idir.z, -r.oidir.z), 0.0f));
+            const float tf = min3f(fmaf(fxs[c], r.idir.x, -r.oidir.x), fmaf(fys[c], r.idir.y, -r.oidir.y),
+                                   fminf(fmaf(fzs[c], r.idir.z, -r.oidir.z), tbest));
+#else
             const float tn = fmaxf(fmaxf(fmaf(nxs[c], r.idir.x, -r.oidir.x), fmaf(nys[c], r.idir.y, -r.oidir.y)),
                                    fmaxf(fmaf(nzs[c], r.idir.z, -r.oidir.z), 0.0f));
             const float tf = fminf(fminf(fmaf(fxs[c], r.idir.x, -r.oidir.x), fmaf(fys[c], r.idir.y, -r.oidir.y)),
                                    fminf(fmaf(fzs[c], r.idir.z, -r.oidir.z), tbest));
-            const bool hit = cref[c] != kEmptyRef && tn <= tf;
+#endif
+            // an empty slot has the box (+inf, -inf): its near distance is +inf and its far
+            // distance -inf for every direction, so it never passes (as in visit_node4)
+            const bool hit = OCC_VISIT_EMPTY_TEST ? (cref[c] != kEmptyRef && tn <= tf) : tn <= tf;
             key[4 * h + c] = hit ? tn : inf;
             ref[4 * h + c] = cref[c];
         }
@@ -509,12 +554,14 @@ __device__ __forceinline__ void visit_node(const DevBVH& bvh, uint32_t cur, cons
         OCC_CSWAP(2, 4) OCC_CSWAP(3, 5) OCC_CSWAP(1, 4) OCC_CSWAP(3, 6)
         OCC_CSWAP(1, 2) OCC_CSWAP(3, 4) OCC_CSWAP(5, 6)
     }
+    if (push_room(sp)) {
 #pragma unroll
-    for (int c = kWidth - 1; c >= 1; --c) {
-        if (key[c] != inf) {
-            if (sp < kStackSize) stack[sp++] = stack_entry(ref[c], key[c]);
-            else overflow = true;
-        }
+        for (int c = kWidth - 1; c >= 1; --c)
+            if (key[c] != inf) stack[sp++] = stack_entry(ref[c], key[c]);
+    } else {
+#pragma unroll
+        for (int c = kWidth - 1; c >= 1; --c)
+            push_entry(stack, sp, overflow, key[c] != inf, stack_entry(ref[c], key[c]));
     }
     *next = key[0] != inf ? ref[0] : kEmptyRef;
 }
