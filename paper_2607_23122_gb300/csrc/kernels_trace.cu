@@ -88,6 +88,11 @@ __global__ void __launch_bounds__(128, OCC_TRACE_MIN_BLOCKS) k_trace(GBufView gb
 #ifndef OCC_TRACE_DYN_MIN_IDLE
 #define OCC_TRACE_DYN_MIN_IDLE 16
 #endif
+// AO rays in the persistent kernel visit nodes with the scalar slab test (0) or the paired
+// one (1, as the shadow rays)
+#ifndef OCC_TRACE_AO_PAIRED
+#define OCC_TRACE_AO_PAIRED 0
+#endif
 // 7 resident CTAs per SM (70 registers, no spill) measured 0.371 against 0.374 ms with 8
 // (64 registers); 6: 0.373 ms.
 #ifndef OCC_TRACE_DYN_MIN_BLOCKS
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(128, OCC_TRACE_DYN_MIN_BLOCKS)
         }
         if (!__any_sync(0xFFFFFFFFu, have)) break;
         if (have) {
-            trav_round<false, EFFECT != kAO>(t, bvh, stack);
+            trav_round<false, EFFECT != kAO || OCC_TRACE_AO_PAIRED>(t, bvh, stack);
             if (trav_done(t)) {
                 overflow |= t.overflow;
                 bad |= t.bad;

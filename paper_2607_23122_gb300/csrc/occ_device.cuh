@@ -484,9 +484,10 @@ __device__ __forceinline__ void visit_node4(const DevBVH& bvh, uint32_t cur, con
 
 
 // Four-wide nodes: 1 sorts the hit children fully; 0 stops after the three comparators
-// that find the nearest (the others are pushed in partial order).
+// that find the nearest (the others are pushed in partial order; 1080p AO trace 0.333
+// against 0.340 ms with the full sort, shadows keep the paired visit's full sort).
 #ifndef OCC_VISIT_FULL_SORT
-#define OCC_VISIT_FULL_SORT 1
+#define OCC_VISIT_FULL_SORT 0
 #endif
 
 // Children of node `cur` hit by the ray before tbest, nearest first: the nearest goes to
@@ -629,7 +630,8 @@ __device__ __forceinline__ bool trav_done(const Traversal& t) {
 // the closest-hit one, so the answer is the same).
 template <bool ANY = false, bool PAIRED = kVisitPaired>
 __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, StackEntry* stack) {
-    while (t.cur != kEmptyRef && !is_leaf_ref(t.cur)) {
+    // internal references are below kEmptyRef, leaf references above it
+    while (t.cur < kEmptyRef) {
 #if OCC_CHECKS
         if (t.cur >= bvh.n_nodes) {
             t.bad = true;
@@ -644,7 +646,7 @@ __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, Stac
         else
             visit_node(bvh, t.cur, t.r, t.tbest, stack, t.sp, t.overflow, &next);
         t.cur = next != kEmptyRef ? next : pop_next(stack, t.sp, t.tbest);
-        if (t.cur != kEmptyRef && is_leaf_ref(t.cur) && t.leaf == kEmptyRef) {
+        if (is_leaf_ref(t.cur) && t.leaf == kEmptyRef) {
             t.leaf = t.cur;   // postpone the leaf and keep walking internal nodes
             t.cur = pop_next(stack, t.sp, t.tbest);
         }
@@ -669,7 +671,7 @@ __device__ __forceinline__ void trav_round(Traversal& t, const DevBVH& bvh, Stac
         }
         if (ANY && t.best_id != kNoHit) {
             t.cur = t.leaf = kEmptyRef;
-        } else if (t.cur != kEmptyRef && is_leaf_ref(t.cur)) {
+        } else if (is_leaf_ref(t.cur)) {
             t.leaf = t.cur;
             t.cur = pop_next(stack, t.sp, t.tbest);
         } else {

@@ -67,6 +67,8 @@ using BvhNode = BvhNode4;
 
 constexpr uint32_t kEmptyRef = 0x7FFFFFFFu;
 constexpr uint32_t kLeafBit = 0x80000000u;
+static_assert((kEmptyRef & kLeafBit) == 0 && kEmptyRef == kLeafBit - 1u,
+              "internal references lie below kEmptyRef and leaf references above it");
 constexpr int kLeafCountShift = 26;
 constexpr uint32_t kLeafFirstMask = (1u << kLeafCountShift) - 1u;
 constexpr int kMaxLeafTris = 32;
