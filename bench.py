@@ -271,15 +271,15 @@ def cpu_baseline(scene, cam, offs, budget_s: float = 12.0) -> dict:
 GROUP_BYTES_PER_PX = 52   # x 12, n 12, z 12, n_z 12, out 4
 # DRAM bytes (read + write) per launch from one `ncu --set full` capture of
 # `bench.py --profile-step` (cold L2); None once a kernel changes
-NCU_TRAFFIC = {"k_trace_dyn<AO>": 71.326464e6 + 28.522752e6,
+NCU_TRAFFIC = {"k_trace_dyn<AO>": 72.004352e6 + 28.321792e6,
                "k_reuse_tile<AO,8>": 132.7616e6 + 7.310336e6,
                "k_reuse_group<AO,biased,4,2>": 114.169088e6 + 5.264384e6}
-NCU_TRACE_ISSUE_ACTIVE = 0.6904   # smsp__issue_active of k_trace_dyn<AO> in its capture
-NCU_TRACE_WARP_INSTR = 284.584687e6   # smsp__inst_executed.sum of k_trace_dyn<AO>, same capture
+NCU_TRACE_ISSUE_ACTIVE = 0.6522   # smsp__issue_active of k_trace_dyn<AO> in its capture
+NCU_TRACE_WARP_INSTR = 255.203861e6   # smsp__inst_executed.sum of k_trace_dyn<AO>, same capture
 # What the 1080p AO trace (seed 1, sample 0) traverses, from the instrumented library:
 # OCC_LIB_VARIANT=counters python bench.py --count-touch
-TRACE_TOUCH = {"rays": 1409214, "node_visits": 21596236, "triangle_tests": 5786195,
-               "distinct_nodes": 42707, "distinct_triangles": 118376, "distinct_bytes": 11148544}
+TRACE_TOUCH = {"rays": 1409214, "node_visits": 21643959, "triangle_tests": 5850259,
+               "distinct_nodes": 44564, "distinct_triangles": 122825, "distinct_bytes": 11599792}
 
 
 def fp32_peak(occ, ctx, dev, stream) -> dict:
