@@ -445,6 +445,21 @@ occ_status occ_debug_stream_ceiling(occ_ctx* ctx, const occ_gbuffer* gb, const o
 occ_status occ_debug_bvh_counters(occ_ctx* ctx, const occ_bvh* bvh, int32_t reset,
                                   uint64_t* out_host);
 
+/* The builder alone, on the host (no context, no device): builds the BVH of tris_host
+ * ([T][3][3] floats) as occ_bvh_build does and copies the tree out.  nodes_out receives
+ * n_nodes nodes of 32 floats (128 bytes: planes lo_x, hi_x, lo_y, hi_y, lo_z, hi_z of the
+ * four children as 6 x 4 floats, then the four child references as uint32 bits, then 4
+ * floats of padding); tris_out receives T triangles of 12 floats (v0.xyz, input id bits,
+ * v1.xyz, 0, v2.xyz, 0) in leaf order.  A child reference is an internal node index, the
+ * empty marker 0x7FFFFFFF, or a leaf: bit 31 set, bits 26..30 = count - 1, bits 0..25 = the
+ * first triangle.  With nodes_out NULL only n_nodes and depth are written; otherwise
+ * nodes_cap (nodes) and tris_cap (triangles) must hold the tree.  OCC_ERR_INVALID_ARG on
+ * invalid input, a tree too deep for the traversal stack, or capacities too small.
+ * The builder test (tests/test_bvh_host.py) checks the tree on the CPU. */
+occ_status occ_debug_bvh_host(const float* tris_host, int64_t T, float* nodes_out,
+                              int64_t nodes_cap, float* tris_out, int64_t tris_cap,
+                              int64_t* n_nodes, int32_t* depth);
+
 /* The traversal on arbitrary rays: rays_dev holds 8 floats per ray (o.xyz, tmax,
  * d.xyz, unused), t in units of |d| on (0, tmax].  any = 0: tri_dev[i] = the closest
  * hit's input triangle id (-1 none) and t_dev[i] its t (-1 none); any = 1: tri_dev[i] = 1

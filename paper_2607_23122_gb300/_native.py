@@ -124,6 +124,8 @@ SIGNATURES = {
                                       c_void_p, c_void_p, c_void_p]),
     "occ_pack_gbuffer": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p, c_void_p]),
     "occ_tile_gbuffer": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p, c_void_p, c_void_p]),
+    "occ_debug_bvh_host": (c_int32, [c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
+                                     C.POINTER(c_int64), C.POINTER(c_int32)]),
     "occ_trace_ao": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p, c_float, c_uint64,
                                c_uint32, C.POINTER(occ_occluders), c_void_p]),
     "occ_trace_shadow": (c_int32, [c_void_p, C.POINTER(occ_gbuffer), c_void_p,

@@ -438,6 +438,24 @@ OCC_EXPORT occ_status occ_trace_reuse_shadow(occ_ctx* ctx, const occ_gbuffer* gb
                               K, estimator, occ_or_null, out, stream);
 }
 
+OCC_EXPORT occ_status occ_debug_bvh_host(const float* tris_host, int64_t T, float* nodes_out,
+                                         int64_t nodes_cap, float* tris_out, int64_t tris_cap,
+                                         int64_t* n_nodes, int32_t* depth) {
+    if (!tris_host || T <= 0 || !n_nodes || !depth) return OCC_ERR_INVALID_ARG;
+    occ::HostBVH hb;
+    std::string err;
+    if (!occ::build_bvh4(tris_host, T, &hb, &err)) return OCC_ERR_INVALID_ARG;
+    *n_nodes = (int64_t)hb.nodes.size();
+    *depth = hb.depth;
+    if (!nodes_out) return OCC_OK;
+    if (nodes_cap < (int64_t)hb.nodes.size() || !tris_out || tris_cap < T ||
+        sizeof(occ::BvhNode) != 128)
+        return OCC_ERR_INVALID_ARG;
+    std::memcpy(nodes_out, hb.nodes.data(), hb.nodes.size() * sizeof(occ::BvhNode));
+    std::memcpy(tris_out, hb.tris.data(), hb.tris.size() * sizeof(float4));
+    return OCC_OK;
+}
+
 OCC_EXPORT occ_status occ_bvh_build(occ_ctx* ctx, const float* tris_host, int64_t T, occ_bvh** out) {
     occ_status st = check_ctx(ctx);
     if (st != OCC_OK) return st;

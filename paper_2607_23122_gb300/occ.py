@@ -109,6 +109,25 @@ def occ_bvh_build(ctx: Context, tris: np.ndarray) -> BVH:
     return BVH(ctx, tris)
 
 
+def occ_debug_bvh_host(tris: np.ndarray):
+    """The BVH builder alone on the host (no device): (nodes [N, 32] float32, triangles
+    [T, 12] float32 in leaf order, depth); layouts as in include/occ.h."""
+    lib = N.load()
+    t = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 9)
+    T = t.shape[0]
+    n, d = C.c_int64(0), C.c_int32(0)
+    st = lib.occ_debug_bvh_host(t.ctypes.data, T, None, 0, None, 0, C.byref(n), C.byref(d))
+    if st != 0:
+        raise OccError(st, "host BVH build failed")
+    nodes = np.empty((n.value, 32), dtype=np.float32)
+    out = np.empty((T, 12), dtype=np.float32)
+    st = lib.occ_debug_bvh_host(t.ctypes.data, T, nodes.ctypes.data, n.value, out.ctypes.data, T,
+                                C.byref(n), C.byref(d))
+    if st != 0:
+        raise OccError(st, "host BVH build failed")
+    return nodes, out, d.value
+
+
 @dataclass
 class GBuffer:
     """pos4 / nrm4: float32 CUDA tensors [H, W, 4] (see occ_gbuffer).  A packed G-buffer
