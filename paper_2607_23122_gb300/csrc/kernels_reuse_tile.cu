@@ -4,16 +4,17 @@
 // format: FP32 (G-buffer and record planes, four float4 planes) or packed (two 16-byte
 // planes, decoded from shared memory).
 //
-// Persistent CTAs walk the image in TW x TH receiver tiles.  For each tile one thread
-// issues four (FP32) or two (packed) 2D bulk-tensor copies (cp.async.bulk.tensor) of the G-buffer and record
-// planes -- (TW + halo) x (TH + halo) float4 each, zero-filled outside the image --
-// completing on an mbarrier; every thread then evaluates its receiver's K x K pair
-// densities from shared memory (K receivers held in registers, K candidate records
-// read once each), normalises by P_j = sum_k p(z_j|x_k) and writes 1 - B_i.  Missing
-// members carry zero receiver terms, whose densities are 0, so the pair loop has no
-// per-member test.
-// Waits on the mbarrier are bounded: on expiry the CTA records kStatusWaitTimeoutBit,
-// drains its copies (again bounded) and returns.
+// Persistent CTAs walk the image in TW x TH receiver tiles.  For each tile a producer warp
+// (one thread of the CTA's last warp; OCC_TILE_WS) issues four (FP32) or two (packed) 2D
+// bulk-tensor copies (cp.async.bulk.tensor) of the G-buffer and record planes -- (TW +
+// halo) x (TH + halo) float4 each, zero-filled outside the image -- into one of two
+// buffers, completing on an mbarrier; every receiver thread then evaluates its receiver's
+// pair densities from shared memory (K receivers held in registers, each candidate record
+// that holds an occluder read once), normalises by P_j = sum_k p(z_j|x_k) and writes
+// 1 - B_i, and its warp releases the buffer on a second mbarrier.  Missing members carry
+// zero receiver terms, whose densities are 0, so the pair loop has no per-member test.
+// Waits on the mbarriers are bounded: on expiry the waiter records kStatusWaitTimeoutBit and
+// returns, and the producer waits (again bounded) for its own copies before it exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
