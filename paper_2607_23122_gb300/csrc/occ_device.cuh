@@ -223,11 +223,12 @@ __device__ __forceinline__ float3 light_direction(const RectLight& L, float3 x, 
 // 4-wide node visits evaluate the slab distances of two children per instruction (paired
 // FP32), take 3-input min / max, and sort packed (distance, slot) keys (OCC_VISIT_PAIRED=1);
 // 0 selects the scalar visit (also used by 8-wide trees).  The paired visit issues ~10 %
-// fewer instructions; measured at 1080p it is faster for the shadow trace (0.268 against
-// 0.275 ms) and slower for the persistent AO trace (0.378 against 0.371 ms), which keeps
-// the scalar visit (trav_round's PAIRED argument).
+// fewer instructions; measured at 1080p it was faster for the shadow trace (0.268 against
+// 0.275 ms) and slower for the persistent AO trace (0.378 against 0.371 ms).  Once the scalar
+// visit dropped its empty-slot test and full sort, it is the faster one for shadows too
+// (0.249 against 0.253 ms), so the paired form is off by default.
 #ifndef OCC_VISIT_PAIRED
-#define OCC_VISIT_PAIRED 1
+#define OCC_VISIT_PAIRED 0
 #endif
 constexpr bool kVisitPaired = OCC_VISIT_PAIRED && kWidth == 4;
 
