@@ -28,3 +28,18 @@ def test_candidates_are_valid_tuning_values():
         assert c["trace_path"] in (1, 2)
         assert 0 <= c.get("trace_refill", 0) <= 32 and 0 <= c.get("trace_ctas_per_sm", 0) <= 16
         assert c.get("trace_order", 0) in (0, 1, 2)
+
+
+def test_layout_candidates_and_key():
+    assert autotune.LAYOUT_CANDIDATES == ("linear", "tiled")
+
+    class _Pat:
+        kind, gw, gh, K = 2, 0, 0, 8
+
+    class _Buf:
+        W, H, packed = 1920, 1080, False
+
+    key = autotune.layout_key(_Buf(), _Buf(), _Pat(), 1, 0)
+    assert key.startswith("layout/1920x1080/") and "K8" in key and "est1" in key
+    # a different pattern or estimator is a different workload
+    assert key != autotune.layout_key(_Buf(), _Buf(), _Pat(), 2, 0)
